@@ -1,0 +1,262 @@
+"""Benchmark: input Mfaces/s simplified to the target face count.
+
+Workload: the bumped level-8 icosphere (1,310,720 faces, 32 seeded Gaussian
+bumps) simplified to 1 % (13,107 faces) -- a synthetic stand-in with the
+paper's scale for its Thingi10K meshes.  One step = one full simplification
+(Algorithm 1 from the input mesh to the target) through the C ABI.
+
+  value   device-resident input, CUDA events per step on the launching
+          stream, L2 flushed (256 MiB write) between steps outside the timing
+  e2e     the same call with host buffers (pamo_simplify_host): host->device
+          copy of the input and device->host copy of the output inside timing
+  roofline  dominant kernel class, algorithmic bytes / event-timed duration
+  cpu_baseline  the CPU oracle (test infrastructure) on a bounded sample
+
+Multi-GPU: a single mesh does not shard (every round needs global 2-hop
+minima and a global intersection check), so N ranks run N independent
+replicas (weak scaling, no collective on the data path).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "input Mfaces/s simplified to target, plain vs batched/learned; % HBM roofline"
+WORKLOAD = "bumped_icosphere_l8"
+CLASS_NAMES = ("adjacency", "cost", "select", "collapse", "bvh", "query", "commit", "other")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) > 8 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 8 and r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for r in self.rows if len(r) > 8
+                          for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(sm)}
+
+
+def make_workload():
+    import meshgen
+    cache = os.environ.get("PAMO_BENCH_CACHE", "/tmp/pamo_bench_l8.npz")
+    if os.path.exists(cache):
+        d = np.load(cache)
+        return d["V"], d["F"], int(d["target"])
+    V, F, target = meshgen.mesh_config(WORKLOAD)
+    try:
+        np.savez(cache, V=V, F=F, target=target)
+    except OSError:
+        pass
+    return V, F, target
+
+
+def cpu_oracle_sample(seconds_hint=True):
+    """The oracle (as it stands) on a bounded sample of the workload: the same
+    generator at level 7 (327,680 faces) to 1 %, single-threaded."""
+    import meshgen
+    import oracle
+    V, F = meshgen.bumped_icosphere(7, 0)
+    target = len(F) // 100
+    t = time.perf_counter()
+    r = oracle.simplify(V, F, target, keep_pairs=False)
+    dt = time.perf_counter() - t
+    return {"value": len(F) / dt / 1e6, "unit": "Mfaces/s", "cores": 1, "kind": "oracle",
+            "sample": f"bumped icosphere level 7 ({len(F)} faces) -> {target} faces, "
+                      f"{len(r.rounds)} rounds in {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle  # noqa: F401  (build happens on import)
+    vals = []
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        cpu_oracle_sample()
+    for _ in range(args.steps):
+        vals.append(cpu_oracle_sample())
+    v = statistics.median(x["value"] for x in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mfaces/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 327680 / (v * 1e6) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (oracle runs the level-7 sample)",
+                       "target": "1%", "parallelism": "replicas"},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": vals[0]["sample"],
+                             "value": v},
+            "e2e": {"value": v, "unit": "Mfaces/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    import paper_2509_05595_gb300 as pamo
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    V, F, target = make_workload()
+    Vd = torch.from_numpy(V).cuda()
+    Fd = torch.from_numpy(F).cuda()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # which class dominates: one profiled warm-up run with every class timed
+    opts = pamo.Options(validate_input=0, profile=0xFF)
+    _, _, st_prof, _ = pamo.pamo_simplify(Vd, Fd, target, options=opts)
+    dom = int(np.argmax(st_prof["class_ms"]))
+    timed_opts = pamo.Options(validate_input=0, profile=1 << dom)
+    for _ in range(args.warmup):
+        pamo.pamo_simplify(Vd, Fd, target, options=timed_opts)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    times, dom_ms, dom_launch, dom_bytes, launches = [], 0.0, 0, 0.0, 0
+    out = None
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        Vo, Fo, st, status = pamo.pamo_simplify(Vd, Fd, target, options=timed_opts)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        dom_ms += st["class_ms"][dom]
+        dom_launch += st["class_launches"][dom]
+        dom_bytes += st["class_bytes"][dom]
+        launches += st["launches"]
+        out = (Vo, Fo, st, status)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * len(F) / (ms_per_step * 1e-3) / 1e6
+
+    # end to end through the host-buffer entry point
+    hV = torch.from_numpy(V).pin_memory().numpy()
+    hF = torch.from_numpy(F).pin_memory().numpy()
+    e2e_t = []
+    for i in range(2 + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Vh, Fh, sth, _ = pamo.pamo_simplify_host(hV, hF, target, validate_input=0)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = statistics.median(e2e_t[2:])
+    e2e = {"value": len(F) / e2e_s / 1e6, "unit": "Mfaces/s",
+           "h2d_bytes_per_step": int(V.nbytes + F.nbytes),
+           "d2h_bytes_per_step": int(Vh.nbytes + Fh.nbytes)}
+
+    peak, peak_kind = peaks()
+    avg_launch_ms = dom_ms / max(dom_launch, 1)
+    bytes_per_launch = dom_bytes / max(dom_launch, 1)
+    achieved = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9 if avg_launch_ms > 0 else 0.0
+    roof = {"bound": "hbm", "kernel_class": CLASS_NAMES[dom], "achieved": achieved,
+            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+            "peak_source": peak_kind,
+            "class_share": {CLASS_NAMES[i]: round(st_prof["class_ms"][i] /
+                                                  max(sum(st_prof["class_ms"]), 1e-9), 4)
+                            for i in range(7)}}
+    Vo, Fo, st, status = out
+    line = {"metric": METRIC, "value": value, "unit": "Mfaces/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "faces_in": int(len(F)), "target": int(target),
+                       "faces_out": int(len(Fo)), "rounds": st["rounds"], "status": status,
+                       "undo_iters_hist": st["undo_iters_hist"][:4],
+                       "l2": "flushed between steps (256 MiB write, outside the timed span)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof, "clocks": clk, "e2e": e2e,
+            "gpu_launches": int(launches // args.steps)}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_sample()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

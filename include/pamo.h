@@ -1,0 +1,223 @@
+/*
+ * pamo.h -- C ABI of the GB300 (sm_103a) parallel intersection-free
+ * edge-collapse simplifier.
+ *
+ * The operation is the simplification stage of PaMO (arXiv 2509.05595),
+ * Algorithm 1 ("ParallelSimplification") with the edge cost of Eq. 1, the
+ * independent-region selection and link condition of Section 5.1, the
+ * self-intersection check of Section 5.2 / Algorithm 3 / supplementary
+ * Section 3, and the undo loop and invalid-edge flags of Section 5.3.
+ *
+ * Conventions shared by every entry point
+ *   - Array arguments named d_* are DEVICE pointers (CUDA global memory on the
+ *     current device); h_* are HOST pointers.  The caller owns every array it
+ *     passes; the library never frees or retains caller memory beyond a call,
+ *     except the input mesh a context copies at creation.
+ *   - Vertices: float32 [nV][3], row-major, x y z.  Faces: int32 [nF][3],
+ *     corner indices into the vertex array, counter-clockwise seen from
+ *     outside.  The input mesh must be closed, oriented, edge- and
+ *     vertex-manifold and free of self-intersections (the problem statement of
+ *     Section 3 and Algorithm 1's input); validation of the topology is done
+ *     when pamo_options.validate_input is set.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls enqueue work on it; calls that return counts to host
+ *     memory synchronise that stream before returning.
+ *   - Internal scratch is allocated with cudaMallocAsync on `stream` and freed
+ *     before the call returns (or by pamo_ctx_destroy for a context).
+ *   - Errors are reported by return code; nothing aborts.  pamo_last_error()
+ *     returns a thread-local message for the last failing call.
+ *   - Indices are int32: nF < 2^31 and the edge count (3 nF / 2) < 2^31.
+ */
+#ifndef PAMO_H
+#define PAMO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PAMO_OK = 0,
+  PAMO_EINVAL = 1,       /* bad argument or input mesh (message says which) */
+  PAMO_ENOMEM = 2,       /* device allocation failed */
+  PAMO_ECUDA = 3,        /* a CUDA runtime call failed */
+  PAMO_ESTALL = 4,       /* stopped before the target; output is valid */
+  PAMO_ETIMEOUT = 5,     /* a device-side bounded wait ran out */
+  PAMO_ENOTMANIFOLD = 6, /* input is not a closed oriented manifold */
+  PAMO_EINTERNAL = 7     /* an internal capacity or consistency check failed */
+} pamo_status;
+
+/* Options.  pamo_default_options() fills the paper's defaults. */
+typedef struct {
+  double w_e;              /* Eq. 1 length weight, default 0.001 (Sec. 5.1) */
+  double w_s;              /* Eq. 1 skinny weight, default 0.005 (Sec. 5.1) */
+  int32_t tolerance;       /* flag tolerance in rounds, default 4 (Sec. 5.3) */
+  int32_t max_rounds;      /* default 100000; reaching it returns PAMO_ESTALL */
+  int32_t stall_limit;     /* consecutive rounds without a committed collapse
+                              before PAMO_ESTALL, default 12 */
+  int32_t validate_input;  /* 1 = check closed/oriented/manifold/finite, default 1 */
+  int32_t check_mode;      /* 0 = check faces changed this round against all
+                              faces (default; equivalent to Algorithm 3 on
+                              every face because the previous mesh is
+                              intersection-free), 1 = every face against every
+                              face through the BVH, 3 = no check (debug only:
+                              output may self-intersect) */
+  int32_t record_rounds;   /* 1 = keep per-round counters and collapse sets for
+                              pamo_ctx_round_info / pamo_ctx_round_pairs */
+  int32_t profile;         /* bit mask of PAMO_KC_* kernel classes to time with
+                              CUDA events (0 = none; timing adds event records) */
+} pamo_options;
+
+/* Kernel classes reported in pamo_stats (index = bit of pamo_options.profile). */
+enum {
+  PAMO_KC_ADJACENCY = 0, /* vertex->face lists and the canonical edge list */
+  PAMO_KC_COST = 1,      /* edge costs, link condition, keys (Eq. 1) */
+  PAMO_KC_SELECT = 2,    /* propagation and independent regions (Sec. 5.1) */
+  PAMO_KC_COLLAPSE = 3,  /* M_s copy, collapses and undos */
+  PAMO_KC_BVH = 4,       /* Morton keys, radix sort, hierarchy, refit */
+  PAMO_KC_QUERY = 5,     /* BVH traversal + exact narrow phase (Alg. 3) */
+  PAMO_KC_COMMIT = 6,    /* stable compaction and flag list */
+  PAMO_KC_COUNT = 8
+};
+
+/* Statistics of one simplification (Section 7 reports time, rounds and the
+ * undo-iteration histogram of Table 'worst'). */
+typedef struct {
+  int32_t rounds;
+  int32_t undo_iters_hist[8];  /* rounds with 0,1,..,7+ undo iterations */
+  int64_t committed, undone, link_rejects, winners;
+  int64_t nV_out, nF_out;
+  double ms_total;             /* wall time on the stream, CUDA events */
+  double bytes_model;          /* algorithmic bytes moved (sum over rounds) */
+  int64_t launches;            /* kernels launched by the call */
+  /* per kernel class (PAMO_KC_*): event-timed milliseconds (only classes in
+   * options.profile), launches, and algorithmic bytes (compulsory reads and
+   * writes of each launch's inputs and outputs, summed) */
+  double class_ms[8];
+  int64_t class_launches[8];
+  double class_bytes[8];
+} pamo_stats;
+
+typedef struct pamo_ctx pamo_ctx;
+
+/* Fill *o with the defaults listed above. */
+void pamo_default_options(pamo_options* o);
+
+/* Simplify until the face count is <= target_faces (Algorithm 1, P: while
+ * |F(M_1)| > N_t).  Every round collapses all winners, so the result can end
+ * below the target.
+ *   d_V [nV][3] float32, d_F [nF][3] int32: input mesh (device, read only).
+ *   d_Vout >= nV*3 floats, d_Fout >= nF*3 ints: output capacity (device).
+ *   *nV_out, *nF_out: output sizes (host).  stats may be NULL.
+ * Returns PAMO_OK, or PAMO_ESTALL with a valid (manifold, intersection-free)
+ * output larger than the target, or an error with outputs untouched. */
+pamo_status pamo_simplify(const float* d_V, int64_t nV, const int32_t* d_F,
+                          int64_t nF, int64_t target_faces,
+                          const pamo_options* opt, void* stream, float* d_Vout,
+                          int64_t* nV_out, int32_t* d_Fout, int64_t* nF_out,
+                          pamo_stats* stats);
+
+/* pamo_simplify with HOST arrays: copies the mesh to the device, simplifies,
+ * copies the result back (h_Vout >= nV*3, h_Fout >= nF*3).  Synchronous. */
+pamo_status pamo_simplify_host(const float* h_V, int64_t nV, const int32_t* h_F,
+                               int64_t nF, int64_t target_faces,
+                               const pamo_options* opt, void* stream,
+                               float* h_Vout, int64_t* nV_out, int32_t* h_Fout,
+                               int64_t* nF_out, pamo_stats* stats);
+
+/* ---- per-round entry points (one round = one iteration of Algorithm 1's
+ * while loop) over a context that owns the evolving mesh ---- */
+
+/* Copy the input mesh (device) into a new context; computes vertex quadrics.
+ * Returns PAMO_EINVAL / PAMO_ENOTMANIFOLD for bad input. */
+pamo_status pamo_ctx_create(const float* d_V, int64_t nV, const int32_t* d_F,
+                            int64_t nF, const pamo_options* opt, void* stream,
+                            pamo_ctx** out);
+
+/* Edge costs and keys of the current mesh (Eq. 1; Alg. 1 first loop). */
+pamo_status pamo_round_cost(pamo_ctx* ctx);
+
+/* Cost propagation and independent-region selection (Sec. 5.1; Alg. 1
+ * second loop and the collapse condition).  *n_winners (host) receives the
+ * number of selected collapses. */
+pamo_status pamo_round_select(pamo_ctx* ctx, int64_t* n_winners);
+
+/* Collapse every selected edge into the tentative mesh M_s (Alg. 1
+ * CollapseEdge). */
+pamo_status pamo_round_collapse(pamo_ctx* ctx);
+
+/* repeat { IntersectionCheck(M_s); UndoCollapse } until clean (Alg. 1,
+ * Sec. 5.2-5.3).  *undo_iters (host, may be NULL) receives the number of undo
+ * iterations performed. */
+pamo_status pamo_round_check_undo(pamo_ctx* ctx, int32_t* undo_iters);
+
+/* Commit M_s as the next M_1: stable compaction of live vertices and faces,
+ * invalid-edge flags for the next round (Sec. 5.3).  *nF_now (host, may be
+ * NULL) receives the new face count. */
+pamo_status pamo_round_commit(pamo_ctx* ctx, int64_t* nF_now);
+
+/* Current mesh sizes (host). */
+pamo_status pamo_ctx_sizes(const pamo_ctx* ctx, int64_t* nV, int64_t* nF,
+                           int64_t* nE);
+
+/* Copy the current mesh out (device arrays of capacity >= current sizes).
+ * d_keys (nullable, nE uint64) receives the last computed edge keys
+ * (cost bits << 32 | edge id, ~0 = ineligible); d_edges (nullable, nE x 2
+ * int32) the edge endpoints (sorted unique (min,max) pairs). */
+pamo_status pamo_ctx_export(pamo_ctx* ctx, float* d_V, int32_t* d_F,
+                            uint64_t* d_keys, int32_t* d_edges);
+
+/* Per-round record (requires options.record_rounds).  out[11] receives
+ * nV nF nE link_rejects flagged eligible winners committed undone undo_iters
+ * pairs_found of round r. */
+pamo_status pamo_ctx_round_info(const pamo_ctx* ctx, int64_t r, int64_t* out);
+
+/* Vertex pairs (in round r's input numbering) of kind 0 = winners,
+ * 1 = committed, 2 = undone.  h_out (host, nullable) receives up to cap pairs;
+ * *n receives the total. */
+pamo_status pamo_ctx_round_pairs(const pamo_ctx* ctx, int64_t r, int32_t kind,
+                                 int32_t* h_out, int64_t cap, int64_t* n);
+
+/* Number of recorded rounds and the run status so far (PAMO_OK / ESTALL). */
+pamo_status pamo_ctx_rounds(const pamo_ctx* ctx, int64_t* rounds);
+
+/* Run rounds until |F| <= target (the loop of pamo_simplify on a context). */
+pamo_status pamo_ctx_run(pamo_ctx* ctx, int64_t target_faces, pamo_stats* stats);
+
+void pamo_ctx_destroy(pamo_ctx* ctx);
+
+/* ---- the intersection check on its own (Algorithm 3) ---- */
+
+/* All intersecting face pairs of a mesh (LBVH broad phase, exact narrow
+ * phase with the shared-vertex cases of supplementary Section 3).
+ * *n_pairs (host) receives the count; d_pairs (nullable, device int32
+ * [cap][2]) receives up to cap pairs (f < g), in no particular order. */
+pamo_status pamo_check_self_intersections(const float* d_V, int64_t nV,
+                                          const int32_t* d_F, int64_t nF,
+                                          void* stream, int64_t* n_pairs,
+                                          int32_t* d_pairs, int64_t cap);
+
+/* The triangle-pair predicate on a batch (device arrays):
+ * d_P [n][18] float32 (T's corners then C's), d_idx [n][6] int32 vertex
+ * indices (equal indices = shared vertices), d_out [n] uint8 (1 = intersect).
+ * Stream-ordered; does not synchronise. */
+pamo_status pamo_tri_intersect_batch(const float* d_P, const int32_t* d_idx,
+                                     int64_t n, uint8_t* d_out, void* stream);
+
+/* Exact orientation signs on a batch (device arrays, stream-ordered):
+ * orient3d: d_P [n][12] -> d_out [n] in {-1,0,1}, the sign of
+ * det[a-d; b-d; c-d]; orient2d: d_P [n][6] -> sign of (b-a) x (c-a). */
+pamo_status pamo_orient3d_batch(const float* d_P, int64_t n, int8_t* d_out,
+                                void* stream);
+pamo_status pamo_orient2d_batch(const float* d_P, int64_t n, int8_t* d_out,
+                                void* stream);
+
+/* Thread-local message of the last failing call ("" if none). */
+const char* pamo_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PAMO_H */

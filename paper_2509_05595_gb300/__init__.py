@@ -1,0 +1,329 @@
+"""Python binding of libpamo.so: the GB300 (sm_103a) parallel intersection-free
+edge-collapse simplifier (the simplification stage of PaMO, arXiv 2509.05595:
+Algorithm 1, Eq. 1, Sections 5.1-5.3, Algorithm 3).
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels.  Device arrays are torch CUDA tensors; the current torch stream is
+passed to the library.  There is no CPU fallback: if the shared library is
+missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, fields
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpamo.so")
+_lib = None
+
+STATUS = {0: "PAMO_OK", 1: "PAMO_EINVAL", 2: "PAMO_ENOMEM", 3: "PAMO_ECUDA",
+          4: "PAMO_ESTALL", 5: "PAMO_ETIMEOUT", 6: "PAMO_ENOTMANIFOLD",
+          7: "PAMO_EINTERNAL"}
+PAMO_OK, PAMO_ESTALL = 0, 4
+
+KERNEL_CLASSES = ("adjacency", "cost", "select", "collapse", "bvh", "query", "commit", "other")
+
+ROUND_FIELDS = ("nV", "nF", "nE", "link_rejects", "flagged", "eligible",
+                "winners", "committed", "undone", "undo_iters", "pairs_found")
+
+
+class PamoError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = lib().pamo_last_error().decode()
+        super().__init__(f"{where}: {STATUS.get(code, code)}: {msg}")
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("w_e", ctypes.c_double), ("w_s", ctypes.c_double),
+                ("tolerance", ctypes.c_int32), ("max_rounds", ctypes.c_int32),
+                ("stall_limit", ctypes.c_int32), ("validate_input", ctypes.c_int32),
+                ("check_mode", ctypes.c_int32), ("record_rounds", ctypes.c_int32),
+                ("profile", ctypes.c_int32)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int32), ("undo_iters_hist", ctypes.c_int32 * 8),
+                ("committed", ctypes.c_int64), ("undone", ctypes.c_int64),
+                ("link_rejects", ctypes.c_int64), ("winners", ctypes.c_int64),
+                ("nV_out", ctypes.c_int64), ("nF_out", ctypes.c_int64),
+                ("ms_total", ctypes.c_double), ("bytes_model", ctypes.c_double),
+                ("launches", ctypes.c_int64), ("class_ms", ctypes.c_double * 8),
+                ("class_launches", ctypes.c_int64 * 8), ("class_bytes", ctypes.c_double * 8)]
+
+
+@dataclass
+class Options:
+    """pamo_options (defaults = the paper's: Eq. 1 weights, tolerance 4)."""
+    w_e: float = 0.001
+    w_s: float = 0.005
+    tolerance: int = 4
+    max_rounds: int = 100000
+    stall_limit: int = 12
+    validate_input: int = 1
+    check_mode: int = 0
+    record_rounds: int = 0
+    profile: int = 0
+
+    def c(self):
+        return _Options(**{f.name: getattr(self, f.name) for f in fields(self)})
+
+
+def lib():
+    """Load libpamo.so (built by paper_2509_05595_gb300/build.py)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build it with "
+                "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        P, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        pi64 = ctypes.POINTER(ctypes.c_int64)
+        sig = {
+            "pamo_default_options": (None, [P]),
+            "pamo_simplify": (ctypes.c_int, [P, i64, P, i64, i64, P, P, P, pi64, P, pi64, P]),
+            "pamo_simplify_host": (ctypes.c_int, [P, i64, P, i64, i64, P, P, P, pi64, P, pi64, P]),
+            "pamo_ctx_create": (ctypes.c_int, [P, i64, P, i64, P, P, ctypes.POINTER(P)]),
+            "pamo_round_cost": (ctypes.c_int, [P]),
+            "pamo_round_select": (ctypes.c_int, [P, pi64]),
+            "pamo_round_collapse": (ctypes.c_int, [P]),
+            "pamo_round_check_undo": (ctypes.c_int, [P, ctypes.POINTER(i32)]),
+            "pamo_round_commit": (ctypes.c_int, [P, pi64]),
+            "pamo_ctx_sizes": (ctypes.c_int, [P, pi64, pi64, pi64]),
+            "pamo_ctx_export": (ctypes.c_int, [P, P, P, P, P]),
+            "pamo_ctx_round_info": (ctypes.c_int, [P, i64, P]),
+            "pamo_ctx_round_pairs": (ctypes.c_int, [P, i64, i32, P, i64, pi64]),
+            "pamo_ctx_rounds": (ctypes.c_int, [P, pi64]),
+            "pamo_ctx_run": (ctypes.c_int, [P, i64, P]),
+            "pamo_ctx_destroy": (None, [P]),
+            "pamo_check_self_intersections": (ctypes.c_int, [P, i64, P, i64, P, pi64, P, i64]),
+            "pamo_tri_intersect_batch": (ctypes.c_int, [P, P, i64, P, P]),
+            "pamo_orient3d_batch": (ctypes.c_int, [P, i64, P, P]),
+            "pamo_orient2d_batch": (ctypes.c_int, [P, i64, P, P]),
+            "pamo_last_error": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev(t, dtype, cols=None):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        t = torch.as_tensor(np.asarray(t))
+    t = t.to(device="cuda", dtype=dtype).contiguous()
+    if cols is not None and (t.dim() != 2 or t.shape[1] != cols):
+        raise ValueError(f"expected [n, {cols}] array, got {tuple(t.shape)}")
+    return t
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check(code, where, ok=(PAMO_OK,)):
+    if code not in ok:
+        raise PamoError(code, where)
+    return code
+
+
+def _stats_dict(s: _Stats):
+    return dict(rounds=s.rounds, undo_iters_hist=list(s.undo_iters_hist),
+                committed=s.committed, undone=s.undone, link_rejects=s.link_rejects,
+                winners=s.winners, nV_out=s.nV_out, nF_out=s.nF_out,
+                ms_total=s.ms_total, bytes_model=s.bytes_model, launches=s.launches,
+                class_ms=list(s.class_ms), class_launches=list(s.class_launches),
+                class_bytes=list(s.class_bytes))
+
+
+def pamo_simplify(V, F, target_faces, options: Options | None = None, **kw):
+    """Simplify a closed manifold mesh on the GPU until |F| <= target_faces.
+
+    V: [nV,3] float32, F: [nF,3] int32 (torch CUDA tensors or array-likes).
+    Returns (V', F', stats, status) with V', F' CUDA tensors; status is
+    "PAMO_OK" or "PAMO_ESTALL" (valid output above the target)."""
+    import torch
+    o = options or Options(**kw)
+    V = _dev(V, torch.float32, 3)
+    F = _dev(F, torch.int32, 3)
+    Vo = torch.empty_like(V)
+    Fo = torch.empty_like(F)
+    nv, nf = ctypes.c_int64(), ctypes.c_int64()
+    st = _Stats()
+    opt = o.c()
+    code = lib().pamo_simplify(_ptr(V), V.shape[0], _ptr(F), F.shape[0], int(target_faces),
+                               ctypes.byref(opt), _stream(), _ptr(Vo), ctypes.byref(nv),
+                               _ptr(Fo), ctypes.byref(nf), ctypes.byref(st))
+    _check(code, "pamo_simplify", ok=(PAMO_OK, PAMO_ESTALL))
+    return Vo[: nv.value], Fo[: nf.value], _stats_dict(st), STATUS[code]
+
+
+def pamo_simplify_host(V, F, target_faces, options: Options | None = None, **kw):
+    """pamo_simplify on host (numpy) arrays; copies in and out inside the call."""
+    o = options or Options(**kw)
+    V = np.ascontiguousarray(V, dtype=np.float32)
+    F = np.ascontiguousarray(F, dtype=np.int32)
+    Vo = np.empty_like(V)
+    Fo = np.empty_like(F)
+    nv, nf = ctypes.c_int64(), ctypes.c_int64()
+    st = _Stats()
+    opt = o.c()
+    code = lib().pamo_simplify_host(V.ctypes.data_as(ctypes.c_void_p), V.shape[0],
+                                    F.ctypes.data_as(ctypes.c_void_p), F.shape[0],
+                                    int(target_faces), ctypes.byref(opt), _stream(),
+                                    Vo.ctypes.data_as(ctypes.c_void_p), ctypes.byref(nv),
+                                    Fo.ctypes.data_as(ctypes.c_void_p), ctypes.byref(nf),
+                                    ctypes.byref(st))
+    _check(code, "pamo_simplify_host", ok=(PAMO_OK, PAMO_ESTALL))
+    return Vo[: nv.value], Fo[: nf.value], _stats_dict(st), STATUS[code]
+
+
+class Ctx:
+    """A simplification context (pamo_ctx) for round-by-round control."""
+
+    def __init__(self, V, F, options: Options | None = None, **kw):
+        import torch
+        o = options or Options(**kw)
+        self._V = _dev(V, torch.float32, 3)
+        self._F = _dev(F, torch.int32, 3)
+        self._h = ctypes.c_void_p()
+        opt = o.c()
+        _check(lib().pamo_ctx_create(_ptr(self._V), self._V.shape[0], _ptr(self._F),
+                                     self._F.shape[0], ctypes.byref(opt), _stream(),
+                                     ctypes.byref(self._h)), "pamo_ctx_create")
+
+    def round_cost(self):
+        _check(lib().pamo_round_cost(self._h), "pamo_round_cost")
+
+    def round_select(self):
+        n = ctypes.c_int64()
+        _check(lib().pamo_round_select(self._h, ctypes.byref(n)), "pamo_round_select")
+        return n.value
+
+    def round_collapse(self):
+        _check(lib().pamo_round_collapse(self._h), "pamo_round_collapse")
+
+    def round_check_undo(self):
+        n = ctypes.c_int32()
+        _check(lib().pamo_round_check_undo(self._h, ctypes.byref(n)), "pamo_round_check_undo")
+        return n.value
+
+    def round_commit(self):
+        n = ctypes.c_int64()
+        _check(lib().pamo_round_commit(self._h, ctypes.byref(n)), "pamo_round_commit")
+        return n.value
+
+    def sizes(self):
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().pamo_ctx_sizes(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+               "pamo_ctx_sizes")
+        return a.value, b.value, c.value
+
+    def export(self, keys=False):
+        """Current mesh (and, with keys=True, edge keys and endpoints)."""
+        import torch
+        nv, nf, ne = self.sizes()
+        V = torch.empty((nv, 3), dtype=torch.float32, device="cuda")
+        F = torch.empty((nf, 3), dtype=torch.int32, device="cuda")
+        K = E = None
+        if keys:
+            K = torch.empty(ne, dtype=torch.int64, device="cuda")
+            E = torch.empty((ne, 2), dtype=torch.int32, device="cuda")
+        _check(lib().pamo_ctx_export(self._h, _ptr(V), _ptr(F), _ptr(K) if keys else None,
+                                     _ptr(E) if keys else None), "pamo_ctx_export")
+        return (V, F, K, E) if keys else (V, F)
+
+    def rounds(self):
+        n = ctypes.c_int64()
+        code = lib().pamo_ctx_rounds(self._h, ctypes.byref(n))
+        return n.value, STATUS[code]
+
+    def round_info(self, r):
+        out = np.zeros(11, np.int64)
+        _check(lib().pamo_ctx_round_info(self._h, r, out.ctypes.data_as(ctypes.c_void_p)),
+               "pamo_ctx_round_info")
+        return dict(zip(ROUND_FIELDS, (int(x) for x in out)))
+
+    def round_pairs(self, r, kind):
+        n = ctypes.c_int64()
+        _check(lib().pamo_ctx_round_pairs(self._h, r, kind, None, 0, ctypes.byref(n)),
+               "pamo_ctx_round_pairs")
+        out = np.zeros((max(n.value, 1), 2), np.int32)
+        _check(lib().pamo_ctx_round_pairs(self._h, r, kind, out.ctypes.data_as(ctypes.c_void_p),
+                                          n.value, ctypes.byref(n)), "pamo_ctx_round_pairs")
+        return out[: n.value]
+
+    def run(self, target_faces):
+        st = _Stats()
+        code = lib().pamo_ctx_run(self._h, int(target_faces), ctypes.byref(st))
+        _check(code, "pamo_ctx_run", ok=(PAMO_OK, PAMO_ESTALL))
+        return _stats_dict(st), STATUS[code]
+
+    def close(self):
+        if self._h:
+            lib().pamo_ctx_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pamo_check_self_intersections(V, F, cap=1 << 20):
+    """All intersecting face pairs (Algorithm 3 over every face)."""
+    import torch
+    V = _dev(V, torch.float32, 3)
+    F = _dev(F, torch.int32, 3)
+    out = torch.empty((max(cap, 1), 2), dtype=torch.int32, device="cuda")
+    n = ctypes.c_int64()
+    _check(lib().pamo_check_self_intersections(_ptr(V), V.shape[0], _ptr(F), F.shape[0],
+                                               _stream(), ctypes.byref(n), _ptr(out), cap),
+           "pamo_check_self_intersections")
+    return n.value, out[: min(n.value, cap)]
+
+
+def pamo_tri_intersect_batch(P, idx):
+    """The triangle-pair predicate: P [n,18] float32, idx [n,6] int32 -> bool [n]."""
+    import torch
+    P = _dev(P, torch.float32, 18)
+    idx = _dev(idx, torch.int32, 6)
+    out = torch.empty(P.shape[0], dtype=torch.uint8, device="cuda")
+    _check(lib().pamo_tri_intersect_batch(_ptr(P), _ptr(idx), P.shape[0], _ptr(out), _stream()),
+           "pamo_tri_intersect_batch")
+    return out.bool()
+
+
+def pamo_orient3d_batch(P):
+    import torch
+    P = _dev(P, torch.float32, 12)
+    out = torch.empty(P.shape[0], dtype=torch.int8, device="cuda")
+    _check(lib().pamo_orient3d_batch(_ptr(P), P.shape[0], _ptr(out), _stream()),
+           "pamo_orient3d_batch")
+    return out
+
+
+def pamo_orient2d_batch(P):
+    import torch
+    P = _dev(P, torch.float32, 6)
+    out = torch.empty(P.shape[0], dtype=torch.int8, device="cuda")
+    _check(lib().pamo_orient2d_batch(_ptr(P), P.shape[0], _ptr(out), _stream()),
+           "pamo_orient2d_batch")
+    return out
+
+
+def pamo_last_error():
+    return lib().pamo_last_error().decode()

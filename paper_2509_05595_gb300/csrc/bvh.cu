@@ -1,0 +1,484 @@
+// Intersection check of Section 5.2 / Algorithm 3: a linear BVH over the
+// faces (Karras 2012: Morton codes of the face-box centres, a radix sort, the
+// binary radix tree built in parallel, boxes refitted bottom-up), queried
+// with the faces that changed this round; every candidate pair whose closed
+// boxes overlap goes straight to the exact narrow phase (exact.cuh), fused
+// into the traversal so no candidate list is stored.
+//
+// Face boxes are the min/max of float32 corner coordinates, which is exact,
+// and overlap is tested on closed intervals, so the broad phase never drops a
+// touching pair.
+#include "common.cuh"
+#include "exact.cuh"
+
+namespace pamo {
+
+namespace {
+
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kBlock * kSortItems;  // 4096 keys per block
+constexpr int kStack = 64;
+
+__device__ __forceinline__ unsigned spread10(unsigned x) {
+  x &= 0x3ffu;
+  x = (x | (x << 16)) & 0x030000ffu;
+  x = (x | (x << 8)) & 0x0300f00fu;
+  x = (x | (x << 4)) & 0x030c30c3u;
+  x = (x | (x << 2)) & 0x09249249u;
+  return x;
+}
+
+__device__ __forceinline__ unsigned quant(float c, float lo, float inv) {
+  float t = (c - lo) * inv;
+  t = fminf(fmaxf(t, 0.0f), 1.0f);
+  return (unsigned)(t * 1023.0f);
+}
+
+__device__ __forceinline__ uint8_t pack_info(exact::FaceInfo fi) {
+  return (uint8_t)(fi.axis * 3 + (fi.o + 1));
+}
+__device__ __forceinline__ exact::FaceInfo unpack_info(uint8_t b) {
+  exact::FaceInfo fi;
+  fi.axis = b / 3;
+  fi.o = (int)(b % 3) - 1;
+  return fi;
+}
+
+// leaf boxes (into the leaf half of the node array is done after sorting;
+// here: Morton keys, face ids and per-face predicate info)
+__global__ void k_leaf_keys(const float4* __restrict__ pos, const int4* __restrict__ F,
+                            const uint8_t* __restrict__ fdead, int n, float lx, float ly, float lz,
+                            float ix, float iy, float iz, unsigned* __restrict__ keys,
+                            int32_t* __restrict__ vals, uint8_t* __restrict__ info) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= n) return;
+  vals[f] = f;
+  if (fdead && fdead[f]) {
+    keys[f] = 1u << 30;
+    info[f] = pack_info(exact::FaceInfo{0, 0});
+    return;
+  }
+  const int4 t = F[f];
+  const float4 a = pos[t.x], b = pos[t.y], c = pos[t.z];
+  const float cx = 0.5f * (fminf(fminf(a.x, b.x), c.x) + fmaxf(fmaxf(a.x, b.x), c.x));
+  const float cy = 0.5f * (fminf(fminf(a.y, b.y), c.y) + fmaxf(fmaxf(a.y, b.y), c.y));
+  const float cz = 0.5f * (fminf(fminf(a.z, b.z), c.z) + fmaxf(fmaxf(a.z, b.z), c.z));
+  keys[f] = (spread10(quant(cx, lx, ix)) << 2) | (spread10(quant(cy, ly, iy)) << 1) |
+            spread10(quant(cz, lz, iz));
+  info[f] = pack_info(exact::face_info(make_float3(a.x, a.y, a.z), make_float3(b.x, b.y, b.z),
+                                       make_float3(c.x, c.y, c.z)));
+}
+
+__global__ void k_face_info(const float4* __restrict__ pos, const int4* __restrict__ F,
+                            const uint8_t* __restrict__ fdead, int n, uint8_t* __restrict__ info) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= n) return;
+  if (fdead && fdead[f]) {
+    info[f] = pack_info(exact::FaceInfo{0, 0});
+    return;
+  }
+  const int4 t = F[f];
+  const float4 a = pos[t.x], b = pos[t.y], c = pos[t.z];
+  info[f] = pack_info(exact::face_info(make_float3(a.x, a.y, a.z), make_float3(b.x, b.y, b.z),
+                                       make_float3(c.x, c.y, c.z)));
+}
+
+// ---- LSD radix sort of (key, value), 8 bits per pass, stable -------------
+__global__ void k_digit_hist(const unsigned* __restrict__ keys, int n, int shift, int tiles,
+                             int32_t* __restrict__ hist) {
+  __shared__ int h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int base = blockIdx.x * kSortTile;
+#pragma unroll 4
+  for (int i = 0; i < kSortItems; i++) {
+    const int j = base + i * kBlock + threadIdx.x;
+    if (j < n) atomicAdd(&h[(keys[j] >> shift) & 0xffu], 1);
+  }
+  __syncthreads();
+  hist[threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kBlock) k_digit_scatter(
+    const unsigned* __restrict__ keys, const int32_t* __restrict__ vals, int n, int shift,
+    int tiles, const int32_t* __restrict__ offs, unsigned* __restrict__ okeys,
+    int32_t* __restrict__ ovals) {
+  __shared__ int wcount[kBlock / 32][256];
+  __shared__ int goff[256];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < (kBlock / 32) * 256; i += kBlock) (&wcount[0][0])[i] = 0;
+  goff[threadIdx.x] = offs[threadIdx.x * tiles + blockIdx.x];
+  __syncthreads();
+  const int base = blockIdx.x * kSortTile + wid * (kSortItems * 32);
+  unsigned k[kSortItems];
+  int v[kSortItems], r[kSortItems];
+  const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int i = 0; i < kSortItems; i++) {
+    const int j = base + i * 32 + lane;
+    const bool ok = j < n;
+    k[i] = ok ? keys[j] : 0u;
+    v[i] = ok ? vals[j] : 0;
+    const unsigned d = ok ? ((k[i] >> shift) & 0xffu) : (0x100u | lane);
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    int before = 0;
+    if (ok) before = wcount[wid][d];
+    r[i] = before + __popc(peers & lt);
+    __syncwarp();
+    if (ok && (peers & lt) == 0) wcount[wid][d] = before + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  {  // exclusive prefix over warps for each digit
+    int run = 0;
+    for (int w = 0; w < kBlock / 32; w++) {
+      int t = wcount[w][threadIdx.x];
+      wcount[w][threadIdx.x] = run;
+      run += t;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < kSortItems; i++) {
+    const int j = base + i * 32 + lane;
+    if (j < n) {
+      const unsigned d = (k[i] >> shift) & 0xffu;
+      const int p = goff[d] + wcount[wid][d] + r[i];
+      okeys[p] = k[i];
+      ovals[p] = v[i];
+    }
+  }
+}
+
+// ---- Karras binary radix tree ---------------------------------------------
+__device__ __forceinline__ int delta(const unsigned* __restrict__ k, int n, int i, int j) {
+  if (j < 0 || j >= n) return -1;
+  const unsigned a = k[i], b = k[j];
+  if (a == b) return 32 + __clz(i ^ j);
+  return __clz(a ^ b);
+}
+
+__global__ void k_karras(const unsigned* __restrict__ k, int n, float4* __restrict__ nodes,
+                         int32_t* __restrict__ parent) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n - 1) return;
+  const int d = (delta(k, n, i, i + 1) - delta(k, n, i, i - 1)) >= 0 ? 1 : -1;
+  const int dmin = delta(k, n, i, i - d);
+  int lmax = 2;
+  while (delta(k, n, i, i + lmax * d) > dmin) lmax <<= 1;
+  int l = 0;
+  for (int t = lmax >> 1; t >= 1; t >>= 1)
+    if (delta(k, n, i, i + (l + t) * d) > dmin) l += t;
+  const int j = i + l * d;
+  const int dnode = delta(k, n, i, j);
+  int s = 0;
+  for (int div = 2;; div <<= 1) {
+    const int t = (l + div - 1) / div;
+    if (delta(k, n, i, i + (s + t) * d) > dnode) s += t;
+    if (t <= 1) break;
+  }
+  const int g = i + s * d + (d < 0 ? -1 : 0);
+  const int left = (min(i, j) == g) ? (n - 1 + g) : g;
+  const int right = (max(i, j) == g + 1) ? (n - 1 + g + 1) : g + 1;
+  nodes[2 * i] = make_float4(0.f, 0.f, 0.f, __int_as_float(left));
+  nodes[2 * i + 1] = make_float4(0.f, 0.f, 0.f, __int_as_float(right));
+  parent[left] = i;
+  parent[right] = i;
+  if (i == 0) parent[0] = -1;
+}
+
+__device__ __forceinline__ void face_box(const float4* __restrict__ pos, const int4& t, float3& lo,
+                                         float3& hi) {
+  const float4 a = pos[t.x], b = pos[t.y], c = pos[t.z];
+  lo = make_float3(fminf(fminf(a.x, b.x), c.x), fminf(fminf(a.y, b.y), c.y),
+                   fminf(fminf(a.z, b.z), c.z));
+  hi = make_float3(fmaxf(fmaxf(a.x, b.x), c.x), fmaxf(fmaxf(a.y, b.y), c.y),
+                   fmaxf(fmaxf(a.z, b.z), c.z));
+}
+
+// leaf boxes, then bottom-up union: the second child to arrive at a parent
+// computes it (no waiting; every thread stops at a first arrival or the root)
+__global__ void k_refit(const float4* __restrict__ pos, const int4* __restrict__ F,
+                        const uint8_t* __restrict__ fdead, const int32_t* __restrict__ vals, int n,
+                        float4* __restrict__ nodes, const int32_t* __restrict__ parent,
+                        int32_t* __restrict__ flags, int* __restrict__ overflow) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int f = vals[j];
+  float3 lo, hi;
+  if (fdead && fdead[f]) {
+    lo = make_float3(INFINITY, INFINITY, INFINITY);
+    hi = make_float3(-INFINITY, -INFINITY, -INFINITY);
+  } else {
+    face_box(pos, F[f], lo, hi);
+  }
+  int node = n - 1 + j;
+  nodes[2 * node] = make_float4(lo.x, lo.y, lo.z, __int_as_float(f));
+  nodes[2 * node + 1] = make_float4(hi.x, hi.y, hi.z, __int_as_float(-1));
+  if (n == 1) return;
+  __threadfence();
+  int p = parent[node];
+  // a radix tree over n leaves is at most n - 1 levels deep; the cap only
+  // guards against a malformed tree
+  for (int steps = 0; p >= 0; steps++) {
+    if (steps >= n) {
+      atomicOr(overflow, 2);
+      return;
+    }
+    if (atomicAdd(&flags[p], 1) == 0) return;  // sibling not ready: it finishes
+    __threadfence();
+    const float4 pl = nodes[2 * p], ph = nodes[2 * p + 1];
+    const int L = __float_as_int(pl.w), R = __float_as_int(ph.w);
+    const float4 al = __ldcg(&nodes[2 * L]), ah = __ldcg(&nodes[2 * L + 1]);
+    const float4 bl = __ldcg(&nodes[2 * R]), bh = __ldcg(&nodes[2 * R + 1]);
+    nodes[2 * p] = make_float4(fminf(al.x, bl.x), fminf(al.y, bl.y), fminf(al.z, bl.z), pl.w);
+    nodes[2 * p + 1] = make_float4(fmaxf(ah.x, bh.x), fmaxf(ah.y, bh.y), fmaxf(ah.z, bh.z), ph.w);
+    __threadfence();
+    p = parent[p];
+  }
+}
+
+__global__ void k_fold_overflow(const int32_t* __restrict__ src, int* __restrict__ dst) {
+  if (*src) atomicOr(dst, *src);
+}
+
+__device__ __forceinline__ bool overlap(const float3& alo, const float3& ahi, const float4& blo,
+                                        const float4& bhi) {
+  return !(alo.x > bhi.x || blo.x > ahi.x || alo.y > bhi.y || blo.y > ahi.y || alo.z > bhi.z ||
+           blo.z > ahi.z);
+}
+
+// One thread per query face.  Query faces: every live face when query_all,
+// else the faces with ftag[f] >= 0 (changed this round).  A pair of two query
+// faces is evaluated once, from its lower face id.  Intersecting pairs mark
+// the collapses that tagged either face.
+__global__ void __launch_bounds__(kBlock) k_query(
+    const float4* __restrict__ nodes, int n, const float4* __restrict__ pos,
+    const int4* __restrict__ F, const uint8_t* __restrict__ fdead,
+    const uint8_t* __restrict__ info, const int32_t* __restrict__ ftag, int query_all,
+    uint8_t* __restrict__ undo, RoundCounters* __restrict__ dc, int32_t* __restrict__ pairs_out,
+    int64_t cap) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= n) return;
+  if (fdead && fdead[f]) return;
+  const int tf = ftag ? ftag[f] : -1;
+  if (!query_all && tf < 0) return;
+  const int4 tv = F[f];
+  const int ti[3] = {tv.x, tv.y, tv.z};
+  float3 T[3];
+  {
+    const float4 a = pos[tv.x], b = pos[tv.y], c = pos[tv.z];
+    T[0] = make_float3(a.x, a.y, a.z);
+    T[1] = make_float3(b.x, b.y, b.z);
+    T[2] = make_float3(c.x, c.y, c.z);
+  }
+  const float3 lo = make_float3(fminf(fminf(T[0].x, T[1].x), T[2].x),
+                                fminf(fminf(T[0].y, T[1].y), T[2].y),
+                                fminf(fminf(T[0].z, T[1].z), T[2].z));
+  const float3 hi = make_float3(fmaxf(fmaxf(T[0].x, T[1].x), T[2].x),
+                                fmaxf(fmaxf(T[0].y, T[1].y), T[2].y),
+                                fmaxf(fmaxf(T[0].z, T[1].z), T[2].z));
+  const exact::FaceInfo fiT = unpack_info(info[f]);
+  int stack[kStack];
+  int sp = 0;
+  int node = 0;
+  if (n == 1) return;
+  // a tree has 2n - 1 nodes; the visit cap only guards against a malformed one
+  for (int visits = 0;; visits++) {
+    if (visits >= 2 * n) {
+      atomicOr(&dc->overflow, 4);
+      return;
+    }
+    const float4 nl = nodes[2 * node], nh = nodes[2 * node + 1];
+    const int L = __float_as_int(nl.w), R = __float_as_int(nh.w);
+    // children of an internal node
+    int next = -1;
+    const int ch[2] = {L, R};
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+      const int cn = ch[c];
+      const float4 cl = nodes[2 * cn], chh = nodes[2 * cn + 1];
+      if (!overlap(lo, hi, cl, chh)) continue;
+      if (cn >= n - 1) {  // leaf
+        const int g = __float_as_int(cl.w);
+        if (g == f) continue;
+        const int tg = ftag ? ftag[g] : -1;
+        if (query_all ? (g < f) : (tg >= 0 && g < f)) continue;
+        const int4 cv = F[g];
+        const int ci[3] = {cv.x, cv.y, cv.z};
+        const float4 a = pos[cv.x], b = pos[cv.y], cc = pos[cv.z];
+        const float3 C[3] = {make_float3(a.x, a.y, a.z), make_float3(b.x, b.y, b.z),
+                             make_float3(cc.x, cc.y, cc.z)};
+        if (exact::faces_intersect(T, ti, fiT, C, ci, unpack_info(info[g]))) {
+          if (undo) {
+            if (tf >= 0) undo[tf] = 1;
+            if (tg >= 0) undo[tg] = 1;
+          }
+          const int slot = atomicAdd(&dc->n_pairs, 1);
+          if (pairs_out && slot < cap) {
+            pairs_out[2 * slot] = min(f, g);
+            pairs_out[2 * slot + 1] = max(f, g);
+          }
+        }
+      } else if (next < 0) {
+        next = cn;
+      } else {
+        if (sp >= kStack) {
+          atomicOr(&dc->overflow, 1);
+          return;
+        }
+        stack[sp++] = cn;
+      }
+    }
+    if (next >= 0) {
+      node = next;
+    } else {
+      if (sp == 0) break;
+      node = stack[--sp];
+    }
+  }
+}
+
+__global__ void k_tri_batch(const float* __restrict__ P, const int32_t* __restrict__ idx,
+                            int64_t n, uint8_t* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float* p = P + 18 * i;
+  float3 T[3], C[3];
+  for (int k = 0; k < 3; k++) {
+    T[k] = make_float3(p[3 * k], p[3 * k + 1], p[3 * k + 2]);
+    C[k] = make_float3(p[9 + 3 * k], p[9 + 3 * k + 1], p[9 + 3 * k + 2]);
+  }
+  const int ti[3] = {idx[6 * i], idx[6 * i + 1], idx[6 * i + 2]};
+  const int ci[3] = {idx[6 * i + 3], idx[6 * i + 4], idx[6 * i + 5]};
+  out[i] = exact::faces_intersect(T, ti, exact::face_info(T[0], T[1], T[2]), C, ci,
+                                  exact::face_info(C[0], C[1], C[2]))
+               ? 1
+               : 0;
+}
+
+__global__ void k_orient3d_batch(const float* __restrict__ P, int64_t n, int8_t* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float* p = P + 12 * i;
+  out[i] = (int8_t)exact::orient3d(make_float3(p[0], p[1], p[2]), make_float3(p[3], p[4], p[5]),
+                                   make_float3(p[6], p[7], p[8]), make_float3(p[9], p[10], p[11]));
+}
+
+__global__ void k_orient2d_batch(const float* __restrict__ P, int64_t n, int8_t* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float* p = P + 6 * i;
+  out[i] = (int8_t)exact::orient2d(p[0], p[1], p[2], p[3], p[4], p[5]);
+}
+
+}  // namespace
+
+pamo_status bvh_build(Bvh& b, const float4* pos, const int4* F, const uint8_t* fdead, int nF,
+                      const float lo[3], const float hi[3], cudaStream_t st) {
+  const int n = nF;
+  b.n = n;
+  const int tiles = (n + kSortTile - 1) / kSortTile;
+  PAMO_TRY(buf_reserve(b.nodes, sizeof(float4) * 2 * (size_t)(2 * n), st));
+  PAMO_TRY(buf_reserve(b.parent, sizeof(int32_t) * (size_t)(2 * n), st));
+  PAMO_TRY(buf_reserve(b.flags, sizeof(int32_t) * (size_t)(n + 2), st));
+  PAMO_TRY(buf_reserve(b.keys, sizeof(unsigned) * (size_t)n, st));
+  PAMO_TRY(buf_reserve(b.vals, sizeof(int32_t) * (size_t)n, st));
+  PAMO_TRY(buf_reserve(b.keys2, sizeof(unsigned) * (size_t)n, st));
+  PAMO_TRY(buf_reserve(b.vals2, sizeof(int32_t) * (size_t)n, st));
+  PAMO_TRY(buf_reserve(b.hist, sizeof(int32_t) * (size_t)(2 * 256 * tiles + 2), st));
+  PAMO_TRY(buf_reserve(b.face_aux, (size_t)n + 16, st));
+  float inv[3];
+  for (int k = 0; k < 3; k++) {
+    float e = hi[k] - lo[k];
+    inv[k] = e > 0.f ? 1.0f / e : 0.0f;
+  }
+  unsigned* keys = (unsigned*)b.keys.p;
+  int32_t* vals = (int32_t*)b.vals.p;
+  unsigned* keys2 = (unsigned*)b.keys2.p;
+  int32_t* vals2 = (int32_t*)b.vals2.p;
+  k_leaf_keys<<<grid_for(n), kBlock, 0, st>>>(pos, F, fdead, n, lo[0], lo[1], lo[2], inv[0],
+                                              inv[1], inv[2], keys, vals, (uint8_t*)b.face_aux.p); note_launch();
+  PAMO_CUDA(cudaGetLastError());
+  int32_t* hist = (int32_t*)b.hist.p;
+  int32_t* offs = hist + 256 * tiles + 1;
+  Buf scan_tmp;
+  for (int pass = 0; pass < 4; pass++) {
+    const int shift = 8 * pass;
+    k_digit_hist<<<tiles, kBlock, 0, st>>>(keys, n, shift, tiles, hist); note_launch();
+    PAMO_TRY(exclusive_scan_i32(hist, offs, 256 * (int64_t)tiles, scan_tmp, st));
+    k_digit_scatter<<<tiles, kBlock, 0, st>>>(keys, vals, n, shift, tiles, offs, keys2, vals2); note_launch();
+    PAMO_CUDA(cudaGetLastError());
+    unsigned* tk = keys; keys = keys2; keys2 = tk;
+    int32_t* tv = vals; vals = vals2; vals2 = tv;
+  }
+  buf_free(scan_tmp, st);
+  // four passes: sorted data is back in b.keys / b.vals
+  if (n >= 2) {
+    k_karras<<<grid_for(n - 1), kBlock, 0, st>>>(keys, n, (float4*)b.nodes.p, (int32_t*)b.parent.p); note_launch();
+    PAMO_CUDA(cudaGetLastError());
+  }
+  return bvh_refit(b, pos, F, fdead, st);
+}
+
+pamo_status bvh_refit(Bvh& b, const float4* pos, const int4* F, const uint8_t* fdead,
+                      cudaStream_t st) {
+  const int n = b.n;
+  PAMO_CUDA(cudaMemsetAsync(b.flags.p, 0, sizeof(int32_t) * (size_t)(n + 2), st));
+  int32_t* fl = (int32_t*)b.flags.p;
+  k_refit<<<grid_for(n), kBlock, 0, st>>>(pos, F, fdead, (const int32_t*)b.vals.p, n,
+                                          (float4*)b.nodes.p, (const int32_t*)b.parent.p, fl,
+                                          fl + n + 1); note_launch();
+  k_face_info<<<grid_for(n), kBlock, 0, st>>>(pos, F, fdead, n, (uint8_t*)b.face_aux.p); note_launch();
+  PAMO_CUDA(cudaGetLastError());
+  return PAMO_OK;
+}
+
+pamo_status bvh_check(Bvh& b, const float4* pos, const int4* F, const uint8_t* fdead,
+                      const int32_t* ftag, int query_all, uint8_t* undo, RoundCounters* dc,
+                      int32_t* pairs_out, int64_t cap, cudaStream_t st) {
+  const int n = b.n;
+  // fold a refit overflow (flags[n+1]) into the round's overflow word
+  k_fold_overflow<<<1, 1, 0, st>>>((const int32_t*)b.flags.p + n + 1, &dc->overflow); note_launch();
+  k_query<<<grid_for(n), kBlock, 0, st>>>((const float4*)b.nodes.p, n, pos, F, fdead,
+                                          (const uint8_t*)b.face_aux.p, ftag, query_all, undo, dc,
+                                          pairs_out, cap); note_launch();
+  PAMO_CUDA(cudaGetLastError());
+  return PAMO_OK;
+}
+
+void bvh_free(Bvh& b, cudaStream_t st) {
+  buf_free(b.nodes, st);
+  buf_free(b.parent, st);
+  buf_free(b.flags, st);
+  buf_free(b.keys, st);
+  buf_free(b.vals, st);
+  buf_free(b.keys2, st);
+  buf_free(b.vals2, st);
+  buf_free(b.hist, st);
+  buf_free(b.face_aux, st);
+}
+
+pamo_status tri_batch(const float* P, const int32_t* idx, int64_t n, uint8_t* out,
+                      cudaStream_t st) {
+  if (n <= 0) return PAMO_OK;
+  k_tri_batch<<<grid_for(n), kBlock, 0, st>>>(P, idx, n, out); note_launch();
+  PAMO_CUDA(cudaGetLastError());
+  return PAMO_OK;
+}
+
+pamo_status orient3d_batch(const float* P, int64_t n, int8_t* out, cudaStream_t st) {
+  if (n <= 0) return PAMO_OK;
+  k_orient3d_batch<<<grid_for(n), kBlock, 0, st>>>(P, n, out); note_launch();
+  PAMO_CUDA(cudaGetLastError());
+  return PAMO_OK;
+}
+
+pamo_status orient2d_batch(const float* P, int64_t n, int8_t* out, cudaStream_t st) {
+  if (n <= 0) return PAMO_OK;
+  k_orient2d_batch<<<grid_for(n), kBlock, 0, st>>>(P, n, out); note_launch();
+  PAMO_CUDA(cudaGetLastError());
+  return PAMO_OK;
+}
+
+}  // namespace pamo

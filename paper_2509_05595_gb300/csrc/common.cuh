@@ -1,0 +1,199 @@
+// Internal declarations of the sm_103a simplifier (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pamo.h"
+
+namespace pamo {
+
+constexpr int kBlock = 256;
+
+// ----------------------------------------------------------------------------
+// error plumbing: every host helper returns pamo_status; the message is kept
+// per thread and surfaced by pamo_last_error().
+// ----------------------------------------------------------------------------
+void set_error(const std::string& msg);
+// process-wide count of kernels launched by this library
+void note_launch();
+long long launch_count();
+pamo_status cuda_fail(cudaError_t e, const char* what);
+
+#define PAMO_CUDA(call)                                     \
+  do {                                                      \
+    cudaError_t e__ = (call);                               \
+    if (e__ != cudaSuccess) return ::pamo::cuda_fail(e__, #call); \
+  } while (0)
+
+#define PAMO_TRY(call)                           \
+  do {                                           \
+    pamo_status s__ = (call);                    \
+    if (s__ != PAMO_OK) return s__;              \
+  } while (0)
+
+inline unsigned grid_for(int64_t n, int block = kBlock) {
+  int64_t g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+// device-side counters of one round, mirrored to pinned host memory
+struct RoundCounters {
+  unsigned long long link_rejects, flagged, eligible;
+  int n_win, n_pairs, n_undo, n_undone_total, overflow, bad;
+  int pad[6];
+};
+
+// Scratch buffer owned by a context, grown on demand (stream-ordered).
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+pamo_status buf_reserve(Buf& b, size_t bytes, cudaStream_t st);
+void buf_free(Buf& b, cudaStream_t st);
+
+// Linear BVH over the faces of a mesh (Karras 2012): nodes [0, n-1) are
+// internal, [n-1, 2n-1) are leaves in Morton order.  Each node is two float4:
+// (lo.xyz, left) and (hi.xyz, right); a leaf stores its face id in `left`.
+struct Bvh {
+  int n = 0;
+  Buf nodes, parent, flags, keys, vals, keys2, vals2, hist, face_aux;
+};
+
+struct RoundRecord {
+  int64_t info[11];
+  std::vector<int32_t> win, com, und;
+};
+
+}  // namespace pamo
+
+// The context (opaque to C callers).
+struct pamo_ctx {
+  cudaStream_t st = nullptr;
+  pamo_options opt{};
+  int64_t nV0 = 0, nF0 = 0, Emax = 0;
+  int64_t nV = 0, nF = 0, nE = 0;     // current M_1 sizes
+  int64_t nW = 0;                      // winners this round
+  int undo_iters = 0;
+  int64_t last_pairs = 0;              // intersecting pairs found this round
+  bool stalled = false;
+  double scale = 1.0;                  // 1 / max bbox extent of the input
+  float bb_lo[3], bb_hi[3];            // input bounding box (Morton frame)
+  int stage = 0;                       // 0 idle, 1 costed, 2 selected, 3 collapsed, 4 checked
+  int status = PAMO_OK;                // PAMO_ESTALL once stalled
+  // --- M_1 (current mesh) and M_s (tentative mesh of this round)
+  float4* pos = nullptr;   float4* pos_s = nullptr;   // [nV0]
+  double* K = nullptr;     double* K_s = nullptr;     // [nV0][10]
+  int4* F = nullptr;       int4* F_s = nullptr;       // [nF0]
+  // --- adjacency of M_1: faces around each vertex, ascending face id
+  int32_t* vf_off = nullptr;  // [nV0+1]
+  int32_t* vf_idx = nullptr;  // [3 nF0]
+  int32_t* vcount = nullptr;  // [nV0+1] scratch counts / cursors
+  // --- edges of M_1 (sorted unique (a<b) pairs) and their keys
+  int2* E = nullptr;          // [Emax]
+  int32_t* e_off = nullptr;   // [nV0+1]
+  unsigned long long* key = nullptr;   // [Emax]
+  float4* vbar = nullptr;     // [Emax]
+  unsigned long long* vkey = nullptr;  // [nV0]
+  uint8_t* win = nullptr;     // [Emax] winner flag -> scan input
+  int32_t* wscan = nullptr;   // [Emax+1]
+  int32_t* wlist = nullptr;   // [Emax] winner edge ids (ascending)
+  uint8_t* standing = nullptr;  // [Emax] per winner slot
+  uint8_t* undo = nullptr;      // [Emax] per winner slot
+  int32_t* ftag = nullptr;      // [nF0] winner slot that rewrote the face
+  uint8_t* fdead = nullptr;     // [nF0]
+  uint8_t* vdead = nullptr;     // [nV0]
+  int32_t* vmap = nullptr;      // [nV0+1]
+  int32_t* dbuf = nullptr;      // [max(nV0,nF0)+1] dead-before scan
+  uint8_t* alive_tmp = nullptr; // [max(nV0,nF0)]
+  // --- invalid-edge flags (sorted vertex pairs a<<32|b)
+  unsigned long long* flags = nullptr;       // [Emax]
+  unsigned long long* flags_next = nullptr;  // [Emax]
+  int64_t nflags = 0;
+  int hold = 0, zero_streak = 0;
+  std::vector<unsigned long long> h_flags;
+  // --- per-round counters
+  pamo::RoundCounters* dc = nullptr;    // device
+  pamo::RoundCounters* hc = nullptr;    // pinned host mirror
+  // --- scratch
+  pamo::Buf scan_tmp, quad_tmp;
+  pamo::Bvh bvh;
+  // --- per-kernel-class accounting (pamo_stats.class_*)
+  long long kc_launch0[8] = {0};
+  cudaEvent_t kc_open[8] = {nullptr};
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> kc_pending;
+  std::vector<cudaEvent_t> ev_pool;
+  double class_ms[8] = {0};
+  long long class_launches[8] = {0};
+  double class_bytes[8] = {0};
+  // --- records
+  std::vector<pamo::RoundRecord> rec;
+  int64_t rounds = 0;
+  int64_t committed_total = 0, undone_total = 0, link_total = 0, win_total = 0;
+  int32_t undo_hist[8] = {0};
+  double bytes_model = 0.0;
+};
+
+namespace pamo {
+
+// kernel-class accounting (api.cu): launches between begin/end are charged to
+// the class with the given algorithmic bytes; CUDA events time the span when
+// the class is in options.profile.
+void kc_begin(pamo_ctx* c, int cls);
+void kc_end(pamo_ctx* c, int cls, double bytes);
+void kc_resolve(pamo_ctx* c);
+
+// scan.cu -------------------------------------------------------------------
+// Exclusive prefix sum of n int32 (or uint8 flags) into out[0..n]; out[n] is
+// the total.  Deterministic.  tmp is grown as needed.
+pamo_status exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, Buf& tmp,
+                               cudaStream_t st);
+pamo_status exclusive_scan_u8(const uint8_t* in, int32_t* out, int64_t n, Buf& tmp,
+                              cudaStream_t st);
+
+// mesh.cu -------------------------------------------------------------------
+pamo_status mesh_bbox(const float4* pos, int64_t nV, float lo[3], float hi[3],
+                      Buf& tmp, cudaStream_t st);
+pamo_status validate_mesh(pamo_ctx* c);
+pamo_status build_vertex_faces(pamo_ctx* c);
+pamo_status build_edges(pamo_ctx* c);
+pamo_status init_quadrics(pamo_ctx* c);
+pamo_status commit_compact(pamo_ctx* c, int64_t* n_undone);
+pamo_status load_mesh(const float* d_V, int64_t nV, const int32_t* d_F, int64_t nF,
+                      float4* pos, int4* F, cudaStream_t st);
+pamo_status store_mesh(const float4* pos, int64_t nV, const int4* F, int64_t nF,
+                       float* d_V, int32_t* d_F, cudaStream_t st);
+
+// cost.cu -------------------------------------------------------------------
+pamo_status edge_costs(pamo_ctx* c);
+
+// select.cu -----------------------------------------------------------------
+pamo_status select_winners(pamo_ctx* c);
+pamo_status collapse_winners(pamo_ctx* c);
+pamo_status undo_marked(pamo_ctx* c);
+
+// bvh.cu --------------------------------------------------------------------
+// Build the LBVH over faces F[0..nF) of positions pos (dead faces, if fdead
+// is non-null, get empty boxes).  Morton frame = [lo, hi].
+pamo_status bvh_build(Bvh& b, const float4* pos, const int4* F, const uint8_t* fdead,
+                      int nF, const float lo[3], const float hi[3], cudaStream_t st);
+pamo_status bvh_refit(Bvh& b, const float4* pos, const int4* F, const uint8_t* fdead,
+                      cudaStream_t st);
+// Query live faces (all of them when query_all, else those with ftag >= 0)
+// against the tree; for every intersecting pair mark undo[ftag[f]] and
+// undo[ftag[g]] (when tagged and undo is non-null), count pairs in
+// dc->n_pairs, and when pairs_out is non-null write pairs (f<g) up to cap.
+pamo_status bvh_check(Bvh& b, const float4* pos, const int4* F, const uint8_t* fdead,
+                      const int32_t* ftag, int query_all, uint8_t* undo, RoundCounters* dc,
+                      int32_t* pairs_out, int64_t cap, cudaStream_t st);
+void bvh_free(Bvh& b, cudaStream_t st);
+pamo_status tri_batch(const float* P, const int32_t* idx, int64_t n, uint8_t* out,
+                      cudaStream_t st);
+pamo_status orient3d_batch(const float* P, int64_t n, int8_t* out, cudaStream_t st);
+pamo_status orient2d_batch(const float* P, int64_t n, int8_t* out, cudaStream_t st);
+
+}  // namespace pamo

@@ -1,0 +1,226 @@
+// Edge costs of one round (Algorithm 1, first parallel loop; Eq. 1):
+//   C_ab = s^2 Q_ab + w_e s l_ab + w_s sum(1 - C_ijk)
+// with the Garland-Heckbert quadric error Q_ab at the optimal placement, the
+// edge length, and the skinny term over the triangles the collapse produces;
+// s = 1 / (largest extent of the input box) puts the costs in the [0,1]^3 frame
+// the paper normalises to (start of Section 4).  The same kernel evaluates the
+// link condition (Dey et al., cited in Section 5.1) and the invalid-edge flags
+// (Section 5.3) and packs the 64-bit key (float cost bits << 32 | edge id).
+//
+// All float64 arithmetic is IEEE round-to-nearest with no contraction (the
+// library is compiled with --fmad=false), in a fixed evaluation order, so the
+// keys are reproducible bit for bit.
+#include "common.cuh"
+
+namespace pamo {
+
+namespace {
+
+constexpr double kFourSqrt3 = 4.0 * 1.7320508075688772;
+
+__device__ __forceinline__ double det3(double a00, double a01, double a02, double a10, double a11,
+                                       double a12, double a20, double a21, double a22) {
+  return (a00 * (a11 * a22 - a12 * a21) - a01 * (a10 * a22 - a12 * a20)) +
+         a02 * (a10 * a21 - a11 * a20);
+}
+
+// v^T A v + 2 b^T v + c of the summed quadric
+__device__ __forceinline__ double qeval(const double* K, double x, double y, double z) {
+  double ax = (K[0] * x + K[1] * y) + K[2] * z;
+  double ay = (K[1] * x + K[4] * y) + K[5] * z;
+  double az = (K[2] * x + K[5] * y) + K[7] * z;
+  double bv = (K[3] * x + K[6] * y) + K[8] * z;
+  return (((x * ax + y * ay) + z * az) + 2.0 * bv) + K[9];
+}
+
+// C_ijk = 4 sqrt(3) A / (l_ij^2 + l_jk^2 + l_ki^2)
+__device__ __forceinline__ double quality(double x0, double y0, double z0, double x1, double y1,
+                                          double z1, double x2, double y2, double z2) {
+  double ux = x1 - x0, uy = y1 - y0, uz = z1 - z0;
+  double wx = x2 - x0, wy = y2 - y0, wz = z2 - z0;
+  double tx = x2 - x1, ty = y2 - y1, tz = z2 - z1;
+  double cx = uy * wz - uz * wy;
+  double cy = uz * wx - ux * wz;
+  double cz = ux * wy - uy * wx;
+  double area = 0.5 * sqrt((cx * cx + cy * cy) + cz * cz);
+  double den = (((ux * ux + uy * uy) + uz * uz) + ((tx * tx + ty * ty) + tz * tz)) +
+               ((wx * wx + wy * wy) + wz * wz);
+  return den > 0.0 ? (kFourSqrt3 * area) / den : 0.0;
+}
+
+__device__ __forceinline__ int next_of(const int4& f, int v) {
+  return f.x == v ? f.y : (f.y == v ? f.z : f.x);
+}
+__device__ __forceinline__ bool has(const int4& f, int v) {
+  return f.x == v || f.y == v || f.z == v;
+}
+
+__device__ __forceinline__ bool is_flagged(const unsigned long long* flags, int64_t n,
+                                           unsigned long long k) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    int64_t m = (lo + hi) >> 1;
+    unsigned long long x = flags[m];
+    if (x == k) return true;
+    if (x < k) lo = m + 1;
+    else hi = m;
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(kBlock) k_edge_cost(
+    const int2* __restrict__ E, int64_t nE, const float4* __restrict__ pos,
+    const double* __restrict__ Kv, const int4* __restrict__ F, const int32_t* __restrict__ off,
+    const int32_t* __restrict__ idx, const unsigned long long* __restrict__ flags, int64_t nflags,
+    double s2, double wes, double ws, unsigned long long* __restrict__ key,
+    float4* __restrict__ vbar, RoundCounters* __restrict__ dc) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int link_bad = 0, flagged = 0, eligible = 0;
+  if (e < nE) {
+    const int2 ab = E[e];
+    const int a = ab.x, b = ab.y;
+    const int a0 = off[a], a1 = off[a + 1], b0 = off[b], b1 = off[b + 1];
+    // ---- link condition: exactly two common neighbours (the apexes of the
+    // two faces on ab) and not both faces (a,c,d), (b,c,d) present
+    int common = 0;
+    int apex[2] = {-1, -1}, na = 0;
+    for (int i = a0; i < a1; i++) {
+      const int4 fa = F[idx[i]];
+      const int x = next_of(fa, a);
+      if (has(fa, b)) {
+        const int t = fa.x != a && fa.x != b ? fa.x : (fa.y != a && fa.y != b ? fa.y : fa.z);
+        if (na < 2) apex[na] = t;
+        na++;
+      }
+      for (int j = b0; j < b1; j++) common += next_of(F[idx[j]], b) == x;
+    }
+    bool link_ok = (common == 2) && (na == 2);
+    if (link_ok) {
+      const int c = apex[0], d = apex[1];
+      bool acd = false, bcd = false;
+      for (int i = off[c]; i < off[c + 1]; i++) {
+        const int4 f = F[idx[i]];
+        if (has(f, d)) {
+          acd |= has(f, a);
+          bcd |= has(f, b);
+        }
+      }
+      link_ok = !(acd && bcd);
+    }
+    const bool flag =
+        nflags > 0 &&
+        is_flagged(flags, nflags, ((unsigned long long)(unsigned)a << 32) | (unsigned)b);
+    // ---- Q_ab at the optimal placement (Cramer solve of A v = -b)
+    double K[10];
+    {
+      const double2* ka = reinterpret_cast<const double2*>(Kv + 10 * (int64_t)a);
+      const double2* kb = reinterpret_cast<const double2*>(Kv + 10 * (int64_t)b);
+#pragma unroll
+      for (int i = 0; i < 5; i++) {
+        double2 x = ka[i], y = kb[i];
+        K[2 * i] = x.x + y.x;
+        K[2 * i + 1] = x.y + y.y;
+      }
+    }
+    const float4 pa = pos[a], pb = pos[b];
+    const double r0 = -K[3], r1 = -K[6], r2 = -K[8];
+    const double mx = fmax(fmax(fmax(fabs(K[0]), fabs(K[1])), fmax(fabs(K[2]), fabs(K[4]))),
+                           fmax(fabs(K[5]), fabs(K[7])));
+    const double det = det3(K[0], K[1], K[2], K[1], K[4], K[5], K[2], K[5], K[7]);
+    float vx = 0.f, vy = 0.f, vz = 0.f;
+    bool solved = false;
+    if (mx != 0.0 && !(fabs(det) <= 1e-12 * ((mx * mx) * mx))) {
+      const double x = det3(r0, K[1], K[2], r1, K[4], K[5], r2, K[5], K[7]) / det;
+      const double y = det3(K[0], r0, K[2], K[1], r1, K[5], K[2], r2, K[7]) / det;
+      const double z = det3(K[0], K[1], r0, K[1], K[4], r1, K[2], K[5], r2) / det;
+      vx = __double2float_rn(x);
+      vy = __double2float_rn(y);
+      vz = __double2float_rn(z);
+      solved = isfinite(vx) && isfinite(vy) && isfinite(vz);
+    }
+    double Q;
+    if (solved) {
+      Q = qeval(K, vx, vy, vz);
+    } else {
+      // best of a, b, midpoint by Q; ties keep the earlier candidate
+      const float mxp = __double2float_rn(((double)pa.x + (double)pb.x) * 0.5);
+      const float myp = __double2float_rn(((double)pa.y + (double)pb.y) * 0.5);
+      const float mzp = __double2float_rn(((double)pa.z + (double)pb.z) * 0.5);
+      Q = qeval(K, pa.x, pa.y, pa.z);
+      vx = pa.x; vy = pa.y; vz = pa.z;
+      const double qb = qeval(K, pb.x, pb.y, pb.z);
+      if (qb < Q) { Q = qb; vx = pb.x; vy = pb.y; vz = pb.z; }
+      const double qm = qeval(K, mxp, myp, mzp);
+      if (qm < Q) { Q = qm; vx = mxp; vy = myp; vz = mzp; }
+    }
+    // ---- l_ab
+    const double dx = (double)pb.x - (double)pa.x, dy = (double)pb.y - (double)pa.y,
+                 dz = (double)pb.z - (double)pa.z;
+    const double l = sqrt((dx * dx + dy * dy) + dz * dz);
+    // ---- skinny term: faces around a or b, except the two on ab, ascending
+    // face id (merge of the two sorted incidence lists)
+    double Cs = 0.0;
+    {
+      int i = a0, j = b0;
+      while (i < a1 || j < b1) {
+        int f;
+        const int fi = i < a1 ? idx[i] : 0x7fffffff;
+        const int fj = j < b1 ? idx[j] : 0x7fffffff;
+        if (fi == fj) {  // a face on edge ab: deleted by the collapse
+          i++;
+          j++;
+          continue;
+        }
+        if (fi < fj) { f = fi; i++; }
+        else { f = fj; j++; }
+        const int4 t = F[f];
+        double q[9];
+        const int cs[3] = {t.x, t.y, t.z};
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+          if (cs[k] == a || cs[k] == b) {
+            q[3 * k] = vx; q[3 * k + 1] = vy; q[3 * k + 2] = vz;
+          } else {
+            const float4 p = pos[cs[k]];
+            q[3 * k] = p.x; q[3 * k + 1] = p.y; q[3 * k + 2] = p.z;
+          }
+        }
+        Cs = Cs + (1.0 - quality(q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7], q[8]));
+      }
+    }
+    const double cost = ((s2 * Q) + (wes * l)) + (ws * Cs);
+    float cf = __double2float_rn(cost);
+    unsigned long long k = ~0ull;
+    if (!isnan(cost) && !isinf(cf) && link_ok && !flag) {
+      if (!(cf > 0.0f)) cf = 0.0f;
+      k = ((unsigned long long)__float_as_uint(cf) << 32) | (unsigned long long)(uint32_t)e;
+      eligible = 1;
+    }
+    key[e] = k;
+    vbar[e] = make_float4(vx, vy, vz, 0.0f);
+    link_bad = !link_ok;
+    flagged = flag;
+  }
+  // block totals of the round counters
+  link_bad = __reduce_add_sync(0xffffffffu, link_bad);
+  flagged = __reduce_add_sync(0xffffffffu, flagged);
+  eligible = __reduce_add_sync(0xffffffffu, eligible);
+  if ((threadIdx.x & 31) == 0) {
+    if (link_bad) atomicAdd(&dc->link_rejects, (unsigned long long)link_bad);
+    if (flagged) atomicAdd(&dc->flagged, (unsigned long long)flagged);
+    if (eligible) atomicAdd(&dc->eligible, (unsigned long long)eligible);
+  }
+}
+
+}  // namespace
+
+pamo_status edge_costs(pamo_ctx* c) {
+  const double s2 = c->scale * c->scale, wes = c->opt.w_e * c->scale;
+  k_edge_cost<<<grid_for(c->nE), kBlock, 0, c->st>>>(c->E, c->nE, c->pos, c->K, c->F, c->vf_off,
+                                                     c->vf_idx, c->flags, c->nflags, s2, wes,
+                                                     c->opt.w_s, c->key, c->vbar, c->dc); note_launch();
+  PAMO_CUDA(cudaGetLastError());
+  return PAMO_OK;
+}
+
+}  // namespace pamo
