@@ -89,13 +89,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def make_workload():
+def make_workload(level=8):
     import meshgen
-    cache = os.environ.get("PAMO_BENCH_CACHE", "/tmp/pamo_bench_l8.npz")
+    cache = os.environ.get("PAMO_BENCH_CACHE", f"/tmp/pamo_bench_l{level}.npz")
     if os.path.exists(cache):
         d = np.load(cache)
         return d["V"], d["F"], int(d["target"])
-    V, F, target = meshgen.mesh_config(WORKLOAD)
+    if level == 8:
+        V, F, target = meshgen.mesh_config(WORKLOAD)
+    else:
+        V, F = meshgen.bumped_icosphere(level, 0)
+        target = len(F) // 100
     try:
         np.savez(cache, V=V, F=F, target=target)
     except OSError:
@@ -141,6 +145,22 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def host_leg(pamo, torch, V, F, target, steps):
+    """pamo_simplify_host from pinned host arrays: copies inside the timing."""
+    hV = torch.from_numpy(V).pin_memory().numpy()
+    hF = torch.from_numpy(F).pin_memory().numpy()
+    ts = []
+    for _ in range(2 + steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Vh, Fh, _, _ = pamo.pamo_simplify_host(hV, hF, target, validate_input=0)
+        ts.append(time.perf_counter() - t0)
+    dt = statistics.median(ts[2:])
+    return {"value": len(F) / dt / 1e6, "unit": "Mfaces/s",
+            "h2d_bytes_per_step": int(V.nbytes + F.nbytes),
+            "d2h_bytes_per_step": int(Vh.nbytes + Fh.nbytes)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -148,6 +168,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
+    ap.add_argument("--level", type=int, default=8,
+                    help="icosphere level of the workload (8 = the benchmark; smaller "
+                         "levels only for profiling captures)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -164,7 +188,8 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    V, F, target = make_workload()
+    V, F, target = make_workload(args.level)
+    workload = WORKLOAD if args.level == 8 else f"bumped_icosphere_l{args.level}"
     Vd = torch.from_numpy(V).cuda()
     Fd = torch.from_numpy(F).cuda()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -215,19 +240,9 @@ def main():
     value = world * len(F) / (ms_per_step * 1e-3) / 1e6
 
     # end to end through the host-buffer entry point
-    hV = torch.from_numpy(V).pin_memory().numpy()
-    hF = torch.from_numpy(F).pin_memory().numpy()
-    e2e_t = []
-    for i in range(2 + args.steps):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        Vh, Fh, sth, _ = pamo.pamo_simplify_host(hV, hF, target, validate_input=0)
-        e2e_t.append(time.perf_counter() - t0)
-    e2e_s = statistics.median(e2e_t[2:])
-    e2e = {"value": len(F) / e2e_s / 1e6, "unit": "Mfaces/s",
-           "h2d_bytes_per_step": int(V.nbytes + F.nbytes),
-           "d2h_bytes_per_step": int(Vh.nbytes + Fh.nbytes)}
-
+    e2e = None
+    if not args.no_e2e:
+        e2e = host_leg(pamo, torch, V, F, target, args.steps)
     peak, peak_kind = peaks()
     avg_launch_ms = dom_ms / max(dom_launch, 1)
     bytes_per_launch = dom_bytes / max(dom_launch, 1)
@@ -243,7 +258,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "faces_in": int(len(F)), "target": int(target),
+            "config": {"workload": workload, "faces_in": int(len(F)), "target": int(target),
                        "faces_out": int(len(Fo)), "rounds": st["rounds"], "status": status,
                        "undo_iters_hist": st["undo_iters_hist"][:4],
                        "l2": "flushed between steps (256 MiB write, outside the timed span)",

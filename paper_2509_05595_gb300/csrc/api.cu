@@ -121,10 +121,14 @@ void free_ctx_buffers(pamo_ctx* c) {
   release(c->vf_off, st); release(c->vf_idx, st); release(c->vcount, st);
   release(c->E, st); release(c->e_off, st); release(c->key, st); release(c->vbar, st);
   release(c->vkey, st); release(c->win, st); release(c->wscan, st); release(c->wlist, st);
-  release(c->standing, st); release(c->undo, st); release(c->ftag, st);
+  release(c->standing, st); release(c->undo, st); release(c->ftag, st); release(c->qlist, st);
   release(c->fdead, st); release(c->vdead, st); release(c->vmap, st); release(c->dbuf, st);
   release(c->alive_tmp, st); release(c->flags, st); release(c->flags_next, st);
   release(c->dc, st);
+  release(c->E_prev, st); release(c->e_off_prev, st); release(c->cbits, st);
+  release(c->cbits_prev, st); release(c->vbar_prev, st); release(c->link, st);
+  release(c->link_prev, st); release(c->ivmap, st); release(c->vsurv, st); release(c->vdirty, st);
+  release(c->dlist, st);
   buf_free(c->scan_tmp, st);
   buf_free(c->quad_tmp, st);
   bvh_free(c->bvh, st);
@@ -183,8 +187,11 @@ pamo_status create(const float* d_V, int64_t nV, const int32_t* d_F, int64_t nF,
   A(vf_off, nV + 1); A(vf_idx, 3 * nF); A(vcount, nV + 1);
   A(E, c->Emax); A(e_off, nV + 1); A(key, c->Emax); A(vbar, c->Emax); A(vkey, nV);
   A(win, c->Emax); A(wscan, c->Emax + 1); A(wlist, c->Emax); A(standing, c->Emax);
-  A(undo, c->Emax); A(ftag, nF); A(fdead, nF); A(vdead, nV); A(vmap, nV + 1);
+  A(undo, c->Emax); A(ftag, nF); A(qlist, nF); A(fdead, nF); A(vdead, nV); A(vmap, nV + 1);
   A(dbuf, mx + 1); A(alive_tmp, mx); A(flags, c->Emax); A(flags_next, c->Emax); A(dc, 1);
+  A(E_prev, c->Emax); A(e_off_prev, nV + 1); A(cbits, c->Emax); A(cbits_prev, c->Emax);
+  A(vbar_prev, c->Emax); A(link, c->Emax); A(link_prev, c->Emax); A(ivmap, nV);
+  A(vsurv, nV); A(vdirty, nV); A(dlist, c->Emax);
 #undef A
   if (s == PAMO_OK) {
     cudaError_t e = cudaMallocHost((void**)&c->hc, sizeof(RoundCounters));
@@ -229,6 +236,12 @@ pamo_status round_cost(pamo_ctx* c) {
   cudaStream_t st = c->st;
   const double nV = (double)c->nV, nF = (double)c->nF, nE = 1.5 * nF;
   kc_begin(c, PAMO_KC_ADJACENCY);
+  // last round's edges and their costs become the reuse source
+  std::swap(c->E, c->E_prev);
+  std::swap(c->e_off, c->e_off_prev);
+  std::swap(c->cbits, c->cbits_prev);
+  std::swap(c->vbar, c->vbar_prev);
+  std::swap(c->link, c->link_prev);
   if (c->rounds > 0) PAMO_TRY(build_vertex_faces(c));
   PAMO_TRY(build_edges(c));
   // F read; CSR written and read back; edges and offsets written
@@ -302,8 +315,8 @@ pamo_status round_check_undo(pamo_ctx* c) {
     for (int64_t it = 0; it <= c->nW; it++) {
       PAMO_CUDA(cudaMemsetAsync(&c->dc->n_pairs, 0, 2 * sizeof(int), st));  // n_pairs, n_undo
       kc_begin(c, PAMO_KC_QUERY);
-      PAMO_TRY(bvh_check(c->bvh, c->pos_s, c->F_s, c->fdead, c->ftag, all, c->undo, c->dc,
-                         nullptr, 0, st));
+      PAMO_TRY(bvh_check(c->bvh, c->pos_s, c->F_s, c->fdead, c->ftag, all, c->qlist,
+                         &c->dc->n_query, c->nF, c->undo, c->dc, nullptr, 0, st));
       kc_end(c, PAMO_KC_QUERY, b_query);
       kc_begin(c, PAMO_KC_COLLAPSE);
       PAMO_TRY(undo_marked(c));
@@ -403,6 +416,7 @@ pamo_status round_commit(pamo_ctx* c) {
   c->win_total += nW;
   c->undo_hist[std::min(c->undo_iters, 7)]++;
   c->rounds++;
+  c->have_prev = true;
   c->stage = 0;
   const bool stall_empty = (eligible == 0 && nflags_in == 0);
   if (stall_empty || c->zero_streak >= c->opt.stall_limit) c->stalled = true;
@@ -702,7 +716,8 @@ pamo_status pamo_check_self_intersections(const float* d_V, int64_t nV, const in
     if (e != cudaSuccess) s = cuda_fail(e, "cudaMemsetAsync");
   }
   if (s == PAMO_OK) s = bvh_build(b, pos, F, nullptr, (int)nF, lo, hi, st);
-  if (s == PAMO_OK) s = bvh_check(b, pos, F, nullptr, nullptr, 1, nullptr, dc, d_pairs, cap, st);
+  if (s == PAMO_OK)
+    s = bvh_check(b, pos, F, nullptr, nullptr, 1, nullptr, nullptr, 0, nullptr, dc, d_pairs, cap, st);
   RoundCounters h{};
   if (s == PAMO_OK) {
     cudaError_t e = cudaMemcpyAsync(&h, dc, sizeof(h), cudaMemcpyDeviceToHost, st);

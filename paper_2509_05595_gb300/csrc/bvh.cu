@@ -256,10 +256,18 @@ __global__ void __launch_bounds__(kBlock) k_query(
     const float4* __restrict__ nodes, int n, const float4* __restrict__ pos,
     const int4* __restrict__ F, const uint8_t* __restrict__ fdead,
     const uint8_t* __restrict__ info, const int32_t* __restrict__ ftag, int query_all,
+    const int32_t* __restrict__ qlist, const int* __restrict__ qcount,
     uint8_t* __restrict__ undo, RoundCounters* __restrict__ dc, int32_t* __restrict__ pairs_out,
     int64_t cap) {
-  const int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= n) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int f;
+  if (query_all) {
+    if (i >= n) return;
+    f = i;
+  } else {
+    if (i >= *qcount) return;
+    f = qlist[i];
+  }
   if (fdead && fdead[f]) return;
   const int tf = ftag ? ftag[f] : -1;
   if (!query_all && tf < 0) return;
@@ -435,14 +443,16 @@ pamo_status bvh_refit(Bvh& b, const float4* pos, const int4* F, const uint8_t* f
 }
 
 pamo_status bvh_check(Bvh& b, const float4* pos, const int4* F, const uint8_t* fdead,
-                      const int32_t* ftag, int query_all, uint8_t* undo, RoundCounters* dc,
+                      const int32_t* ftag, int query_all, const int32_t* qlist,
+                      const int* qcount, int64_t nq_max, uint8_t* undo, RoundCounters* dc,
                       int32_t* pairs_out, int64_t cap, cudaStream_t st) {
   const int n = b.n;
   // fold a refit overflow (flags[n+1]) into the round's overflow word
   k_fold_overflow<<<1, 1, 0, st>>>((const int32_t*)b.flags.p + n + 1, &dc->overflow); note_launch();
-  k_query<<<grid_for(n), kBlock, 0, st>>>((const float4*)b.nodes.p, n, pos, F, fdead,
-                                          (const uint8_t*)b.face_aux.p, ftag, query_all, undo, dc,
-                                          pairs_out, cap); note_launch();
+  const int64_t threads = query_all ? n : nq_max;
+  k_query<<<grid_for(threads), kBlock, 0, st>>>((const float4*)b.nodes.p, n, pos, F, fdead,
+                                                (const uint8_t*)b.face_aux.p, ftag, query_all,
+                                                qlist, qcount, undo, dc, pairs_out, cap); note_launch();
   PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;
 }

@@ -44,8 +44,8 @@ inline unsigned grid_for(int64_t n, int block = kBlock) {
 // device-side counters of one round, mirrored to pinned host memory
 struct RoundCounters {
   unsigned long long link_rejects, flagged, eligible;
-  int n_win, n_pairs, n_undo, n_undone_total, overflow, bad;
-  int pad[6];
+  int n_win, n_pairs, n_undo, n_undone_total, overflow, bad, n_query, n_dirty;
+  int pad[4];
 };
 
 // Scratch buffer owned by a context, grown on demand (stream-ordered).
@@ -96,6 +96,20 @@ struct pamo_ctx {
   // --- edges of M_1 (sorted unique (a<b) pairs) and their keys
   int2* E = nullptr;          // [Emax]
   int32_t* e_off = nullptr;   // [nV0+1]
+  // --- previous round's edge data, reused for edges whose inputs did not
+  // change (cost is a pure function of the edge's two vertex rings)
+  int2* E_prev = nullptr;              // [Emax]
+  int32_t* e_off_prev = nullptr;       // [nV0+1]
+  uint32_t* cbits = nullptr;           // [Emax] float bits of the cost (~0 = non-finite)
+  uint32_t* cbits_prev = nullptr;      // [Emax]
+  float4* vbar_prev = nullptr;         // [Emax]
+  uint8_t* link = nullptr;             // [Emax] link condition holds
+  uint8_t* link_prev = nullptr;        // [Emax]
+  int32_t* ivmap = nullptr;            // [nV0] new vertex id -> previous id
+  uint8_t* vsurv = nullptr;            // [nV0] survivor of a committed collapse
+  uint8_t* vdirty = nullptr;           // [nV0] survivor or neighbour of one
+  int32_t* dlist = nullptr;            // [Emax] edges whose cost is recomputed
+  bool have_prev = false;
   unsigned long long* key = nullptr;   // [Emax]
   float4* vbar = nullptr;     // [Emax]
   unsigned long long* vkey = nullptr;  // [nV0]
@@ -105,6 +119,7 @@ struct pamo_ctx {
   uint8_t* standing = nullptr;  // [Emax] per winner slot
   uint8_t* undo = nullptr;      // [Emax] per winner slot
   int32_t* ftag = nullptr;      // [nF0] winner slot that rewrote the face
+  int32_t* qlist = nullptr;     // [nF0] faces changed this round (query list)
   uint8_t* fdead = nullptr;     // [nF0]
   uint8_t* vdead = nullptr;     // [nV0]
   int32_t* vmap = nullptr;      // [nV0+1]
@@ -187,8 +202,10 @@ pamo_status bvh_refit(Bvh& b, const float4* pos, const int4* F, const uint8_t* f
 // against the tree; for every intersecting pair mark undo[ftag[f]] and
 // undo[ftag[g]] (when tagged and undo is non-null), count pairs in
 // dc->n_pairs, and when pairs_out is non-null write pairs (f<g) up to cap.
+// qlist/qcount (device): the query faces when not query_all.
 pamo_status bvh_check(Bvh& b, const float4* pos, const int4* F, const uint8_t* fdead,
-                      const int32_t* ftag, int query_all, uint8_t* undo, RoundCounters* dc,
+                      const int32_t* ftag, int query_all, const int32_t* qlist,
+                      const int* qcount, int64_t nq_max, uint8_t* undo, RoundCounters* dc,
                       int32_t* pairs_out, int64_t cap, cudaStream_t st);
 void bvh_free(Bvh& b, cudaStream_t st);
 pamo_status tri_batch(const float* P, const int32_t* idx, int64_t n, uint8_t* out,

@@ -319,6 +319,13 @@ __device__ __forceinline__ bool faces_intersect(const float3* t, const int* ti, 
     const float3& C = t[(st0 + 2) % 3];
     const float3& D = c[(sc0 + 1) % 3];
     const float3& E = c[(sc0 + 2) % 3];
+    // Early outs: if D and E lie strictly on one side of T's plane, the other
+    // face meets that plane only at A, so the faces share nothing but A (and
+    // symmetrically for B, C against the other face's plane).
+    const int sD = orient3d(A, B, C, D), sE = orient3d(A, B, C, E);
+    if (sD * sE > 0) return false;
+    const int sB = orient3d(A, D, E, B), sC = orient3d(A, D, E, C);
+    if (sB * sC > 0) return false;
     if (segtri(B, C, A, D, E, fc)) return true;
     if (segtri(D, E, A, B, C, ft)) return true;
     if (ray_in_angle(A, B, D, E, fc)) return true;
@@ -326,6 +333,18 @@ __device__ __forceinline__ bool faces_intersect(const float3* t, const int* ti, 
     if (ray_in_angle(A, D, B, C, ft)) return true;
     if (ray_in_angle(A, E, B, C, ft)) return true;
     return false;
+  }
+  // s = 0.  Early outs: a face whose corners all lie strictly on one side of
+  // the other face's plane cannot meet it.
+  {
+    const int a0 = orient3d(t[0], t[1], t[2], c[0]);
+    const int a1 = orient3d(t[0], t[1], t[2], c[1]);
+    const int a2 = orient3d(t[0], t[1], t[2], c[2]);
+    if ((a0 > 0 && a1 > 0 && a2 > 0) || (a0 < 0 && a1 < 0 && a2 < 0)) return false;
+    const int b0 = orient3d(c[0], c[1], c[2], t[0]);
+    const int b1 = orient3d(c[0], c[1], c[2], t[1]);
+    const int b2 = orient3d(c[0], c[1], c[2], t[2]);
+    if ((b0 > 0 && b1 > 0 && b2 > 0) || (b0 < 0 && b1 < 0 && b2 < 0)) return false;
   }
   for (int i = 0; i < 3; i++)
     if (segtri(t[i], t[(i + 1) % 3], c[0], c[1], c[2], fc)) return true;

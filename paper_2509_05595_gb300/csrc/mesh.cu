@@ -290,7 +290,7 @@ __global__ void k_compact_vertices(const float4* __restrict__ pos_s, const doubl
                                    const uint8_t* __restrict__ vdead,
                                    const int32_t* __restrict__ dead_before, int64_t nV,
                                    float4* __restrict__ pos, double* __restrict__ K,
-                                   int32_t* __restrict__ vmap) {
+                                   int32_t* __restrict__ vmap, int32_t* __restrict__ ivmap) {
   int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= nV) return;
   if (vdead[v]) {
@@ -299,6 +299,7 @@ __global__ void k_compact_vertices(const float4* __restrict__ pos_s, const doubl
   }
   int64_t n = v - dead_before[v];
   vmap[v] = (int32_t)n;
+  ivmap[n] = (int32_t)v;
   pos[n] = pos_s[v];
   const double2* src = reinterpret_cast<const double2*>(K_s + 10 * v);
   double2* dst = reinterpret_cast<double2*>(K + 10 * n);
@@ -325,6 +326,28 @@ __global__ void k_undone_pairs(const int32_t* __restrict__ wlist, const int2* __
   if (w >= nW || standing[w]) return;
   int2 e = E[wlist[w]];
   out[uscan[w]] = ((unsigned long long)(unsigned)vmap[e.x] << 32) | (unsigned)vmap[e.y];
+}
+
+// survivors of committed collapses (new numbering)
+__global__ void k_mark_survivors(const int32_t* __restrict__ wlist, const int2* __restrict__ E,
+                                 const uint8_t* __restrict__ standing, int64_t nW,
+                                 const int32_t* __restrict__ vmap, uint8_t* __restrict__ vsurv) {
+  int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= nW || !standing[w]) return;
+  vsurv[vmap[E[wlist[w]].x]] = 1;
+}
+
+// a vertex is dirty when it is a survivor or shares a face with one
+__global__ void k_mark_dirty(const int4* __restrict__ F, int64_t nF, const uint8_t* __restrict__ vsurv,
+                             uint8_t* __restrict__ vdirty) {
+  int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nF) return;
+  const int4 t = F[f];
+  if (vsurv[t.x] | vsurv[t.y] | vsurv[t.z]) {
+    vdirty[t.x] = 1;
+    vdirty[t.y] = 1;
+    vdirty[t.z] = 1;
+  }
 }
 
 __global__ void k_not(const uint8_t* __restrict__ in, int64_t n, uint8_t* __restrict__ out) {
@@ -442,15 +465,15 @@ pamo_status commit_compact(pamo_ctx* c, int64_t* n_undone) {
   // vertices: new id = old id - (dead vertices before it)
   PAMO_TRY(exclusive_scan_u8(c->vdead, c->dbuf, c->nV, c->scan_tmp, st));
   k_compact_vertices<<<grid_for(c->nV), kBlock, 0, st>>>(c->pos_s, c->K_s, c->vdead, c->dbuf,
-                                                         c->nV, c->pos, c->K, c->vmap); note_launch();
+                                                         c->nV, c->pos, c->K, c->vmap, c->ivmap); note_launch();
   PAMO_CUDA(cudaGetLastError());
   // faces, corners remapped
   PAMO_TRY(exclusive_scan_u8(c->fdead, c->dbuf, c->nF, c->scan_tmp, st));
   k_compact_faces<<<grid_for(c->nF), kBlock, 0, st>>>(c->F_s, c->fdead, c->dbuf, c->nF, c->vmap,
                                                       c->F); note_launch();
   PAMO_CUDA(cudaGetLastError());
-  // undone winners -> next round's flag candidates (sorted vertex pairs)
   int64_t nW = c->nW;
+  // undone winners -> next round's flag candidates (sorted vertex pairs)
   *n_undone = 0;
   if (nW > 0) {
     k_not<<<grid_for(nW), kBlock, 0, st>>>(c->standing, nW, c->alive_tmp); note_launch();
@@ -462,6 +485,18 @@ pamo_status commit_compact(pamo_ctx* c, int64_t* n_undone) {
     PAMO_CUDA(cudaMemcpyAsync(&hn, c->wscan + nW, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     PAMO_CUDA(cudaStreamSynchronize(st));
     *n_undone = hn;
+  }
+  // dirty vertices of the next round (survivors and their neighbours), in the
+  // new numbering over the new faces
+  const int64_t committed = nW - *n_undone;
+  const int64_t nV_new = c->nV - committed, nF_new = c->nF - 2 * committed;
+  PAMO_CUDA(cudaMemsetAsync(c->vsurv, 0, nV_new, st));
+  PAMO_CUDA(cudaMemsetAsync(c->vdirty, 0, nV_new, st));
+  if (committed > 0) {
+    k_mark_survivors<<<grid_for(nW), kBlock, 0, st>>>(c->wlist, c->E, c->standing, nW, c->vmap,
+                                                      c->vsurv); note_launch();
+    k_mark_dirty<<<grid_for(nF_new), kBlock, 0, st>>>(c->F, nF_new, c->vsurv, c->vdirty); note_launch();
+    PAMO_CUDA(cudaGetLastError());
   }
   return PAMO_OK;
 }

@@ -68,7 +68,8 @@ __global__ void k_collapse(const int32_t* __restrict__ wlist, int64_t nW, const 
                            const int4* __restrict__ F, float4* __restrict__ pos_s,
                            double* __restrict__ K_s, int4* __restrict__ F_s,
                            uint8_t* __restrict__ fdead, uint8_t* __restrict__ vdead,
-                           int32_t* __restrict__ ftag, uint8_t* __restrict__ standing) {
+                           int32_t* __restrict__ ftag, uint8_t* __restrict__ standing,
+                           int32_t* __restrict__ qlist, int* __restrict__ qcount) {
   const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= nW) return;
   const int e = wlist[w];
@@ -86,10 +87,15 @@ __global__ void k_collapse(const int32_t* __restrict__ wlist, int64_t nW, const 
   }
   vdead[b] = 1;
   standing[w] = 1;
+  // the faces this collapse changes (alive ones) go to the query list as one
+  // contiguous, spatially coherent run
+  const int na = off[a + 1] - off[a], nb = off[b + 1] - off[b];
+  int q = atomicAdd(qcount, na + nb - 4);
   for (int s = off[a]; s < off[a + 1]; s++) {
     const int f = idx[s];
     const int4 t = F[f];
     if (t.x == b || t.y == b || t.z == b) fdead[f] = 1;
+    else qlist[q++] = f;
     ftag[f] = (int32_t)w;
   }
   for (int s = off[b]; s < off[b + 1]; s++) {
@@ -101,6 +107,7 @@ __global__ void k_collapse(const int32_t* __restrict__ wlist, int64_t nW, const 
     if (t.z == b) t.z = a;
     F_s[f] = t;
     ftag[f] = (int32_t)w;
+    qlist[q++] = f;
   }
 }
 
@@ -172,10 +179,12 @@ pamo_status collapse_winners(pamo_ctx* c) {
   PAMO_CUDA(cudaMemsetAsync(c->vdead, 0, c->nV, st));
   PAMO_CUDA(cudaMemsetAsync(c->ftag, 0xff, sizeof(int32_t) * c->nF, st));
   PAMO_CUDA(cudaMemsetAsync(c->undo, 0, c->nW > 0 ? c->nW : 1, st));
+  PAMO_CUDA(cudaMemsetAsync(&c->dc->n_query, 0, sizeof(int), st));
   if (c->nW > 0) {
     k_collapse<<<grid_for(c->nW), kBlock, 0, st>>>(c->wlist, c->nW, c->E, c->vbar, c->K, c->vf_off,
                                                    c->vf_idx, c->F, c->pos_s, c->K_s, c->F_s,
-                                                   c->fdead, c->vdead, c->ftag, c->standing); note_launch();
+                                                   c->fdead, c->vdead, c->ftag, c->standing,
+                                                   c->qlist, &c->dc->n_query); note_launch();
     PAMO_CUDA(cudaGetLastError());
   }
   return PAMO_OK;
