@@ -198,6 +198,29 @@ pamo_status pamo_check_self_intersections(const float* d_V, int64_t nV,
                                           void* stream, int64_t* n_pairs,
                                           int32_t* d_pairs, int64_t cap);
 
+/* pamo_check_self_intersections without any device allocation.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc while they run -- e.g. a service whose device memory
+ * is reserved and budgeted by another component, or a latency-bound loop that
+ * must not block on the allocator.  Arguments, outputs and the result are
+ * those of pamo_check_self_intersections (d_V/d_F device mesh, *n_pairs host,
+ * d_pairs device [cap][2], caller-owned).
+ *   - All scratch lives in one fixed device array inside the library (about
+ *     4.1 MiB); every GPU that loads the library holds it until the process
+ *     exits.  Limit: nF <= 32768 and nV <= 32768; larger meshes return
+ *     PAMO_EINVAL with a message.
+ *   - The first call on each device looks up that array's device address
+ *     (cudaGetSymbolAddress) with the device current; make that first call
+ *     before any stream capture.
+ *   - Every call reuses the same array: calls that overlap on the GPU (on
+ *     different streams, or from different threads) race and must be
+ *     serialised by the caller.  The call synchronises `stream` before it
+ *     returns.  It calls no cudaMalloc, cudaFree or allocating routine. */
+pamo_status pamo_check_self_intersections_noalloc(const float* d_V, int64_t nV,
+                                                  const int32_t* d_F, int64_t nF,
+                                                  void* stream, int64_t* n_pairs,
+                                                  int32_t* d_pairs, int64_t cap);
+
 /* The triangle-pair predicate on a batch (device arrays):
  * d_P [n][18] float32 (T's corners then C's), d_idx [n][6] int32 vertex
  * indices (equal indices = shared vertices), d_out [n] uint8 (1 = intersect).

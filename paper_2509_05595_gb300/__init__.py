@@ -101,6 +101,8 @@ def lib():
             "pamo_ctx_run": (ctypes.c_int, [P, i64, P]),
             "pamo_ctx_destroy": (None, [P]),
             "pamo_check_self_intersections": (ctypes.c_int, [P, i64, P, i64, P, pi64, P, i64]),
+            "pamo_check_self_intersections_noalloc": (ctypes.c_int,
+                                                      [P, i64, P, i64, P, pi64, P, i64]),
             "pamo_tri_intersect_batch": (ctypes.c_int, [P, P, i64, P, P]),
             "pamo_orient3d_batch": (ctypes.c_int, [P, i64, P, P]),
             "pamo_orient2d_batch": (ctypes.c_int, [P, i64, P, P]),
@@ -294,6 +296,20 @@ def pamo_check_self_intersections(V, F, cap=1 << 20):
                                                _stream(), ctypes.byref(n), _ptr(out), cap),
            "pamo_check_self_intersections")
     return n.value, out[: min(n.value, cap)]
+
+
+def pamo_check_self_intersections_noalloc(V, F, out):
+    """pamo_check_self_intersections for callers that cannot allocate device
+    memory during the call: the library uses its fixed internal scratch (at
+    most 32,768 faces and vertices) and writes up to len(out) pairs into the
+    caller's int32 CUDA tensor out [cap, 2].  V, F must already be CUDA
+    tensors of the right dtype (float32 [nV,3], int32 [nF,3]); nothing is
+    converted or allocated here.  Returns the number of intersecting pairs."""
+    n = ctypes.c_int64()
+    _check(lib().pamo_check_self_intersections_noalloc(
+        _ptr(V), V.shape[0], _ptr(F), F.shape[0], _stream(), ctypes.byref(n), _ptr(out),
+        out.shape[0]), "pamo_check_self_intersections_noalloc")
+    return n.value
 
 
 def pamo_tri_intersect_batch(P, idx):

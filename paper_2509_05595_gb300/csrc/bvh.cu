@@ -429,6 +429,56 @@ pamo_status bvh_build(Bvh& b, const float4* pos, const int4* F, const uint8_t* f
   return bvh_refit(b, pos, F, fdead, st);
 }
 
+// bvh_build over buffers the caller has already placed in b (each Buf with
+// enough bytes; see bvh_bytes) and a scan scratch of scan_sums_count(256 *
+// tiles) words; allocates nothing.
+pamo_status bvh_build_into(Bvh& b, const float4* pos, const int4* F, int nF, const float lo[3],
+                           const float hi[3], int32_t* scan_sums, cudaStream_t st) {
+  const int n = nF;
+  b.n = n;
+  const int tiles = (n + kSortTile - 1) / kSortTile;
+  float inv[3];
+  for (int k = 0; k < 3; k++) {
+    float e = hi[k] - lo[k];
+    inv[k] = e > 0.f ? 1.0f / e : 0.0f;
+  }
+  unsigned* keys = (unsigned*)b.keys.p;
+  int32_t* vals = (int32_t*)b.vals.p;
+  unsigned* keys2 = (unsigned*)b.keys2.p;
+  int32_t* vals2 = (int32_t*)b.vals2.p;
+  k_leaf_keys<<<grid_for(n), kBlock, 0, st>>>(pos, F, nullptr, n, lo[0], lo[1], lo[2], inv[0],
+                                              inv[1], inv[2], keys, vals, (uint8_t*)b.face_aux.p); note_launch();
+  PAMO_CUDA(cudaGetLastError());
+  int32_t* hist = (int32_t*)b.hist.p;
+  int32_t* offs = hist + 256 * tiles + 1;
+  for (int pass = 0; pass < 4; pass++) {
+    const int shift = 8 * pass;
+    k_digit_hist<<<tiles, kBlock, 0, st>>>(keys, n, shift, tiles, hist); note_launch();
+    PAMO_TRY(exclusive_scan_i32_into(hist, offs, 256 * (int64_t)tiles, scan_sums, st));
+    k_digit_scatter<<<tiles, kBlock, 0, st>>>(keys, vals, n, shift, tiles, offs, keys2, vals2); note_launch();
+    PAMO_CUDA(cudaGetLastError());
+    unsigned* tk = keys; keys = keys2; keys2 = tk;
+    int32_t* tv = vals; vals = vals2; vals2 = tv;
+  }
+  if (n >= 2) {
+    k_karras<<<grid_for(n - 1), kBlock, 0, st>>>(keys, n, (float4*)b.nodes.p, (int32_t*)b.parent.p); note_launch();
+    PAMO_CUDA(cudaGetLastError());
+  }
+  return bvh_refit(b, pos, F, nullptr, st);
+}
+
+void bvh_bytes(int n, size_t* nodes, size_t* parent, size_t* flags, size_t* kv, size_t* hist,
+               size_t* aux, int64_t* hist_words) {
+  const int tiles = (n + kSortTile - 1) / kSortTile;
+  *nodes = sizeof(float4) * 2 * (size_t)(2 * n);
+  *parent = sizeof(int32_t) * (size_t)(2 * n);
+  *flags = sizeof(int32_t) * (size_t)(n + 2);
+  *kv = sizeof(uint32_t) * (size_t)n;
+  *hist = sizeof(int32_t) * (size_t)(2 * 256 * tiles + 2);
+  *aux = (size_t)n + 16;
+  *hist_words = 256 * (int64_t)tiles;
+}
+
 pamo_status bvh_refit(Bvh& b, const float4* pos, const int4* F, const uint8_t* fdead,
                       cudaStream_t st) {
   const int n = b.n;

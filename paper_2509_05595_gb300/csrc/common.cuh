@@ -169,10 +169,16 @@ pamo_status exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, Buf& 
                                cudaStream_t st);
 pamo_status exclusive_scan_u8(const uint8_t* in, int32_t* out, int64_t n, Buf& tmp,
                               cudaStream_t st);
+// the same scan over caller-provided tile sums (scan_sums_count(n) words)
+int64_t scan_sums_count(int64_t n);
+pamo_status exclusive_scan_i32_into(const int32_t* in, int32_t* out, int64_t n, int32_t* sums,
+                                    cudaStream_t st);
 
 // mesh.cu -------------------------------------------------------------------
 pamo_status mesh_bbox(const float4* pos, int64_t nV, float lo[3], float hi[3],
                       Buf& tmp, cudaStream_t st);
+pamo_status mesh_bbox_into(const float4* pos, int64_t nV, unsigned* d_tmp, float lo[3],
+                           float hi[3], cudaStream_t st);
 pamo_status validate_mesh(pamo_ctx* c);
 pamo_status build_vertex_faces(pamo_ctx* c);
 pamo_status build_edges(pamo_ctx* c);
@@ -208,6 +214,11 @@ pamo_status bvh_check(Bvh& b, const float4* pos, const int4* F, const uint8_t* f
                       const int* qcount, int64_t nq_max, uint8_t* undo, RoundCounters* dc,
                       int32_t* pairs_out, int64_t cap, cudaStream_t st);
 void bvh_free(Bvh& b, cudaStream_t st);
+// allocation-free build over buffers already placed in b (sizes: bvh_bytes)
+pamo_status bvh_build_into(Bvh& b, const float4* pos, const int4* F, int nF, const float lo[3],
+                           const float hi[3], int32_t* scan_sums, cudaStream_t st);
+void bvh_bytes(int n, size_t* nodes, size_t* parent, size_t* flags, size_t* kv, size_t* hist,
+               size_t* aux, int64_t* hist_words);
 pamo_status tri_batch(const float* P, const int32_t* idx, int64_t n, uint8_t* out,
                       cudaStream_t st);
 pamo_status orient3d_batch(const float* P, int64_t n, int8_t* out, cudaStream_t st);

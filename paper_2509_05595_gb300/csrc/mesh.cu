@@ -393,6 +393,28 @@ pamo_status mesh_bbox(const float4* pos, int64_t nV, float lo[3], float hi[3], B
   return PAMO_OK;
 }
 
+// mesh_bbox with caller-provided device scratch (6 words); allocates nothing
+pamo_status mesh_bbox_into(const float4* pos, int64_t nV, unsigned* d_tmp, float lo[3], float hi[3],
+                           cudaStream_t st) {
+  unsigned init[6] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0, 0, 0};
+  PAMO_CUDA(cudaMemcpyAsync(d_tmp, init, sizeof(init), cudaMemcpyHostToDevice, st));
+  unsigned g = grid_for(nV);
+  if (g > 1024) g = 1024;
+  k_bbox<<<g, kBlock, 0, st>>>(pos, nV, d_tmp); note_launch();
+  PAMO_CUDA(cudaGetLastError());
+  unsigned out[6];
+  PAMO_CUDA(cudaMemcpyAsync(out, d_tmp, sizeof(out), cudaMemcpyDeviceToHost, st));
+  PAMO_CUDA(cudaStreamSynchronize(st));
+  for (int k = 0; k < 3; k++) {
+    unsigned a = out[k], b = out[3 + k];
+    a = (a & 0x80000000u) ? (a & 0x7fffffffu) : ~a;
+    b = (b & 0x80000000u) ? (b & 0x7fffffffu) : ~b;
+    std::memcpy(&lo[k], &a, 4);
+    std::memcpy(&hi[k], &b, 4);
+  }
+  return PAMO_OK;
+}
+
 pamo_status build_vertex_faces(pamo_ctx* c) {
   cudaStream_t st = c->st;
   PAMO_CUDA(cudaMemsetAsync(c->vcount, 0, sizeof(int32_t) * (c->nV + 1), st));

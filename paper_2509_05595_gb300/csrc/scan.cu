@@ -134,6 +134,21 @@ pamo_status exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, Buf& 
   return scan_impl<int32_t>(in, out, n, tmp, st);
 }
 
+int64_t scan_sums_count(int64_t n) {
+  int64_t tiles = (n + kTile - 1) / kTile;
+  return (tiles < 1 ? 1 : tiles) + 1;
+}
+
+pamo_status exclusive_scan_i32_into(const int32_t* in, int32_t* out, int64_t n, int32_t* sums,
+                                    cudaStream_t st) {
+  int64_t tiles = scan_sums_count(n) - 1;
+  k_tile_sums<int32_t><<<(unsigned)tiles, kBlock, 0, st>>>(in, n, sums); note_launch();
+  k_scan_sums<<<1, kBlock, 0, st>>>(sums, tiles); note_launch();
+  k_tile_apply<int32_t><<<(unsigned)tiles, kBlock, 0, st>>>(in, n, sums, out); note_launch();
+  PAMO_CUDA(cudaGetLastError());
+  return PAMO_OK;
+}
+
 pamo_status exclusive_scan_u8(const uint8_t* in, int32_t* out, int64_t n, Buf& tmp,
                               cudaStream_t st) {
   return scan_impl<uint8_t>(in, out, n, tmp, st);
