@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -129,6 +130,7 @@ void free_ctx_buffers(pamo_ctx* c) {
   release(c->cbits_prev, st); release(c->vbar_prev, st); release(c->link, st);
   release(c->link_prev, st); release(c->ivmap, st); release(c->vsurv, st); release(c->vdirty, st);
   release(c->dlist, st);
+  for (int r = 0; r < 3; r++) release(c->cand[r], st);
   buf_free(c->scan_tmp, st);
   buf_free(c->quad_tmp, st);
   bvh_free(c->bvh, st);
@@ -180,6 +182,11 @@ pamo_status create(const float* d_V, int64_t nV, const int32_t* d_F, int64_t nF,
   c->nV0 = c->nV = nV;
   c->nF0 = c->nF = nF;
   c->Emax = (3 * nF) / 2 + 2;
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+      cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  }
   const int64_t mx = std::max(nV, nF);
   pamo_status s = PAMO_OK;
 #define A(ptr, n) if (s == PAMO_OK) s = alloc(&c->ptr, (size_t)(n), st)
@@ -192,6 +199,16 @@ pamo_status create(const float* d_V, int64_t nV, const int32_t* d_F, int64_t nF,
   A(E_prev, c->Emax); A(e_off_prev, nV + 1); A(cbits, c->Emax); A(cbits_prev, c->Emax);
   A(vbar_prev, c->Emax); A(link, c->Emax); A(link_prev, c->Emax); A(ivmap, nV);
   A(vsurv, nV); A(vdirty, nV); A(dlist, c->Emax);
+  // candidate pairs of the split check: a changed face has at most 3
+  // edge-neighbours; vertex-neighbours and other overlaps are bounded
+  // generously, and an overflow falls back to the fused check
+  c->cand_cap[0] = 4 * nF; c->cand_cap[1] = 12 * nF; c->cand_cap[2] = 3 * nF;
+  if (const char* e = std::getenv("PAMO_CAND_CAP_DIVISOR")) {  // test hook for the fallback
+    const long d = std::atol(e);
+    if (d > 1)
+      for (int r = 0; r < 3; r++) c->cand_cap[r] = std::max<int64_t>(1, c->cand_cap[r] / d);
+  }
+  A(cand[0], c->cand_cap[0]); A(cand[1], c->cand_cap[1]); A(cand[2], c->cand_cap[2]);
 #undef A
   if (s == PAMO_OK) {
     cudaError_t e = cudaMallocHost((void**)&c->hc, sizeof(RoundCounters));
@@ -315,13 +332,24 @@ pamo_status round_check_undo(pamo_ctx* c) {
     for (int64_t it = 0; it <= c->nW; it++) {
       PAMO_CUDA(cudaMemsetAsync(&c->dc->n_pairs, 0, 2 * sizeof(int), st));  // n_pairs, n_undo
       kc_begin(c, PAMO_KC_QUERY);
-      PAMO_TRY(bvh_check(c->bvh, c->pos_s, c->F_s, c->fdead, c->ftag, all, c->qlist,
-                         &c->dc->n_query, c->nF, c->undo, c->dc, nullptr, 0, st));
+      PAMO_TRY(bvh_check_split(c->bvh, c->pos_s, c->F_s, c->fdead, c->ftag, all, c->qlist,
+                               &c->dc->n_query, c->undo, c->dc, c->cand, c->cand_cap,
+                               c->dc->ncand, c->sm_count * 8, st));
       kc_end(c, PAMO_KC_QUERY, b_query);
       kc_begin(c, PAMO_KC_COLLAPSE);
-      PAMO_TRY(undo_marked(c));
+      PAMO_TRY(undo_marked(c));  // skipped on the device if a bucket overflowed
       kc_end(c, PAMO_KC_COLLAPSE, (double)c->nW * 2);
       PAMO_TRY(sync_counters(c));
+      if (c->hc->cand_overflow) {
+        // candidate buffers too small this time: the fused check finds every
+        // pair of the same mesh state, then the undo runs
+        PAMO_CUDA(cudaMemsetAsync(&c->dc->n_pairs, 0, 2 * sizeof(int), st));
+        PAMO_CUDA(cudaMemsetAsync(&c->dc->cand_overflow, 0, sizeof(int), st));
+        PAMO_TRY(bvh_check(c->bvh, c->pos_s, c->F_s, c->fdead, c->ftag, all, c->qlist,
+                           &c->dc->n_query, c->nF, c->undo, c->dc, nullptr, 0, st));
+        PAMO_TRY(undo_marked(c));
+        PAMO_TRY(sync_counters(c));
+      }
       if (c->hc->overflow) {
         set_error("BVH traversal stack overflow");
         return PAMO_EINTERNAL;
@@ -370,6 +398,13 @@ pamo_status round_commit(pamo_ctx* c) {
   kc_begin(c, PAMO_KC_COMMIT);
   PAMO_TRY(commit_compact(c, &nund));
   // M_s read (positions, quadrics, faces, liveness), M_1 written, vertex map
+  // keep the BVH leaf order for the compacted faces (only valid if this
+  // round's check built the tree over these nF_in faces)
+  if (c->bvh.order_ok && c->bvh.n == nF_in)
+    PAMO_TRY(bvh_compact_order(c->bvh, c->fdead, c->dbuf, (int)(nF_in - 2 * (nW - nund)),
+                               c->scan_tmp, st));
+  else
+    c->bvh.order_ok = false;
   kc_end(c, PAMO_KC_COMMIT, (double)nV_in * (16 + 80 + 1 + 4) * 2 + (double)nF_in * (16 + 1 + 4) * 2);
   PAMO_TRY(sync_counters(c));
   kc_resolve(c);

@@ -8,6 +8,8 @@
 // Face boxes are the min/max of float32 corner coordinates, which is exact,
 // and overlap is tested on closed intervals, so the broad phase never drops a
 // touching pair.
+#include <utility>
+
 #include "common.cuh"
 #include "exact.cuh"
 
@@ -187,6 +189,24 @@ __global__ void k_karras(const unsigned* __restrict__ k, int n, float4* __restri
   if (i == 0) parent[0] = -1;
 }
 
+__global__ void k_order_alive(const int32_t* __restrict__ vals, int n, const uint8_t* __restrict__ fdead,
+                              uint8_t* __restrict__ alive) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) alive[i] = fdead[vals[i]] ? 0 : 1;
+}
+
+__global__ void k_order_write(const int32_t* __restrict__ vals, const unsigned* __restrict__ keys,
+                              int n, const uint8_t* __restrict__ alive,
+                              const int32_t* __restrict__ pos, const int32_t* __restrict__ dead_before,
+                              int32_t* __restrict__ out, unsigned* __restrict__ okeys) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && alive[i]) {
+    const int f = vals[i];
+    out[pos[i]] = f - dead_before[f];
+    okeys[pos[i]] = keys[i];
+  }
+}
+
 __device__ __forceinline__ void face_box(const float4* __restrict__ pos, const int4& t, float3& lo,
                                          float3& hi) {
   const float4 a = pos[t.x], b = pos[t.y], c = pos[t.z];
@@ -347,6 +367,132 @@ __global__ void __launch_bounds__(kBlock) k_query(
   }
 }
 
+// ---- split check: traversal -> candidate pairs -> exact pair test --------
+// Candidates are bucketed by the number of shared vertex indices (0, 1, >=2)
+// so that warps of the pair kernel follow one branch of the predicate.
+struct CandBufs {
+  int2* c[3];
+  int64_t cap[3];
+};
+
+__global__ void __launch_bounds__(kBlock) k_traverse(
+    const float4* __restrict__ nodes, int n, const float4* __restrict__ pos,
+    const int4* __restrict__ F, const uint8_t* __restrict__ fdead,
+    const int32_t* __restrict__ ftag, int query_all, const int32_t* __restrict__ qlist,
+    const int* __restrict__ qcount, CandBufs cb, int* __restrict__ ncand,
+    RoundCounters* __restrict__ dc) {
+  const int total = query_all ? n : *qcount;
+  if (n < 2) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int f = query_all ? i : qlist[i];
+    if (fdead && fdead[f]) continue;
+    const int tf = ftag ? ftag[f] : -1;
+    if (!query_all && tf < 0) continue;
+    const int4 tv = F[f];
+    const float4 a = pos[tv.x], b = pos[tv.y], c = pos[tv.z];
+    const float3 lo = make_float3(fminf(fminf(a.x, b.x), c.x), fminf(fminf(a.y, b.y), c.y),
+                                  fminf(fminf(a.z, b.z), c.z));
+    const float3 hi = make_float3(fmaxf(fmaxf(a.x, b.x), c.x), fmaxf(fmaxf(a.y, b.y), c.y),
+                                  fmaxf(fmaxf(a.z, b.z), c.z));
+    int stack[kStack];
+    int sp = 0, node = 0;
+    for (int visits = 0;; visits++) {
+      if (visits >= 2 * n) {
+        atomicOr(&dc->overflow, 4);
+        break;
+      }
+      const int L = __float_as_int(nodes[2 * node].w), R = __float_as_int(nodes[2 * node + 1].w);
+      int next = -1;
+#pragma unroll
+      for (int k = 0; k < 2; k++) {
+        const int cn = k ? R : L;
+        const float4 cl = nodes[2 * cn], ch = nodes[2 * cn + 1];
+        if (!overlap(lo, hi, cl, ch)) continue;
+        if (cn >= n - 1) {
+          const int g = __float_as_int(cl.w);
+          if (g == f) continue;
+          const int tg = ftag ? ftag[g] : -1;
+          if (query_all ? (g < f) : (tg >= 0 && g < f)) continue;
+          const int4 gv = F[g];
+          int s = 0;
+          s += (gv.x == tv.x) | (gv.x == tv.y) | (gv.x == tv.z);
+          s += (gv.y == tv.x) | (gv.y == tv.y) | (gv.y == tv.z);
+          s += (gv.z == tv.x) | (gv.z == tv.y) | (gv.z == tv.z);
+          const int r = s >= 2 ? 2 : s;
+          // warp-aggregated append into bucket r
+          const unsigned act = __activemask();
+          const unsigned peers = __match_any_sync(act, r);
+          const int leader = __ffs(peers) - 1;
+          const int lane = threadIdx.x & 31;
+          int base = 0;
+          if (lane == leader) base = atomicAdd(&ncand[r], __popc(peers));
+          base = __shfl_sync(peers, base, leader);
+          const int slot = base + __popc(peers & ((1u << lane) - 1u));
+          if (slot < cb.cap[r]) cb.c[r][slot] = make_int2(f, g);
+        } else if (next < 0) {
+          next = cn;
+        } else {
+          if (sp >= kStack) {
+            atomicOr(&dc->overflow, 1);
+            next = -2;
+            break;
+          }
+          stack[sp++] = cn;
+        }
+      }
+      if (next == -2) break;
+      if (next >= 0) {
+        node = next;
+      } else {
+        if (sp == 0) break;
+        node = stack[--sp];
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_pairs(
+    CandBufs cb, const int* __restrict__ ncand, const float4* __restrict__ pos,
+    const int4* __restrict__ F, const uint8_t* __restrict__ info,
+    const int32_t* __restrict__ ftag, uint8_t* __restrict__ undo, RoundCounters* __restrict__ dc) {
+  const int n2 = min((int64_t)ncand[2], cb.cap[2]);
+  const int n1 = min((int64_t)ncand[1], cb.cap[1]);
+  const int n0 = min((int64_t)ncand[0], cb.cap[0]);
+  const int total = n2 + n1 + n0;
+  if (blockIdx.x == 0 && threadIdx.x == 0 &&
+      (ncand[0] > cb.cap[0] || ncand[1] > cb.cap[1] || ncand[2] > cb.cap[2]))
+    dc->cand_overflow = 1;
+  int found = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int2 p = i < n2 ? cb.c[2][i] : (i < n2 + n1 ? cb.c[1][i - n2] : cb.c[0][i - n2 - n1]);
+    const int f = p.x, g = p.y;
+    const int4 tv = F[f], cv = F[g];
+    const int ti[3] = {tv.x, tv.y, tv.z};
+    const int ci[3] = {cv.x, cv.y, cv.z};
+    float3 T[3], C[3];
+    {
+      const float4 a = pos[tv.x], b = pos[tv.y], c = pos[tv.z];
+      T[0] = make_float3(a.x, a.y, a.z);
+      T[1] = make_float3(b.x, b.y, b.z);
+      T[2] = make_float3(c.x, c.y, c.z);
+      const float4 d = pos[cv.x], e = pos[cv.y], h = pos[cv.z];
+      C[0] = make_float3(d.x, d.y, d.z);
+      C[1] = make_float3(e.x, e.y, e.z);
+      C[2] = make_float3(h.x, h.y, h.z);
+    }
+    if (exact::faces_intersect(T, ti, unpack_info(info[f]), C, ci, unpack_info(info[g]))) {
+      found++;
+      if (undo) {
+        const int tf = ftag[f], tg = ftag[g];
+        if (tf >= 0) undo[tf] = 1;
+        if (tg >= 0) undo[tg] = 1;
+      }
+    }
+  }
+  found = __reduce_add_sync(0xffffffffu, found);
+  if ((threadIdx.x & 31) == 0 && found) atomicAdd(&dc->n_pairs, found);
+}
+
 __global__ void k_tri_batch(const float* __restrict__ P, const int32_t* __restrict__ idx,
                             int64_t n, uint8_t* __restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -384,8 +530,18 @@ __global__ void k_orient2d_batch(const float* __restrict__ P, int64_t n, int8_t*
 
 pamo_status bvh_build(Bvh& b, const float4* pos, const int4* F, const uint8_t* fdead, int nF,
                       const float lo[3], const float hi[3], cudaStream_t st) {
+  if (b.order_ok && b.n == nF && 2 * (int64_t)nF > b.n_sorted && nF >= 2) {
+    // carried-over order with the Morton keys of the last sort (still sorted):
+    // hierarchy at the same prefix splits, then boxes of the current faces
+    k_karras<<<grid_for(nF - 1), kBlock, 0, st>>>((const unsigned*)b.keys.p, nF, (float4*)b.nodes.p,
+                                                  (int32_t*)b.parent.p); note_launch();
+    PAMO_CUDA(cudaGetLastError());
+    return bvh_refit(b, pos, F, fdead, st);
+  }
   const int n = nF;
   b.n = n;
+  b.n_sorted = n;
+  b.order_ok = true;
   const int tiles = (n + kSortTile - 1) / kSortTile;
   PAMO_TRY(buf_reserve(b.nodes, sizeof(float4) * 2 * (size_t)(2 * n), st));
   PAMO_TRY(buf_reserve(b.parent, sizeof(int32_t) * (size_t)(2 * n), st));
@@ -503,6 +659,44 @@ pamo_status bvh_check(Bvh& b, const float4* pos, const int4* F, const uint8_t* f
   k_query<<<grid_for(threads), kBlock, 0, st>>>((const float4*)b.nodes.p, n, pos, F, fdead,
                                                 (const uint8_t*)b.face_aux.p, ftag, query_all,
                                                 qlist, qcount, undo, dc, pairs_out, cap); note_launch();
+  PAMO_CUDA(cudaGetLastError());
+  return PAMO_OK;
+}
+
+pamo_status bvh_compact_order(Bvh& b, const uint8_t* fdead, const int32_t* dead_before,
+                              int nF_new, Buf& tmp, cudaStream_t st) {
+  if (!b.order_ok) return PAMO_OK;
+  const int n = b.n;
+  uint8_t* alive = (uint8_t*)b.face_aux.p;     // face info is rebuilt at the next refit
+  int32_t* pos = (int32_t*)b.parent.p;         // parents are rebuilt with the tree
+  k_order_alive<<<grid_for(n), kBlock, 0, st>>>((const int32_t*)b.vals.p, n, fdead, alive); note_launch();
+  PAMO_TRY(exclusive_scan_u8(alive, pos, n, tmp, st));
+  k_order_write<<<grid_for(n), kBlock, 0, st>>>((const int32_t*)b.vals.p, (const unsigned*)b.keys.p,
+                                                n, alive, pos, dead_before, (int32_t*)b.vals2.p,
+                                                (unsigned*)b.keys2.p); note_launch();
+  PAMO_CUDA(cudaGetLastError());
+  std::swap(b.vals, b.vals2);
+  std::swap(b.keys, b.keys2);
+  b.n = nF_new;
+  return PAMO_OK;
+}
+
+pamo_status bvh_check_split(Bvh& b, const float4* pos, const int4* F, const uint8_t* fdead,
+                            const int32_t* ftag, int query_all, const int32_t* qlist,
+                            const int* qcount, uint8_t* undo, RoundCounters* dc, int2* const cand[3],
+                            const int64_t cap[3], int* ncand, int grid, cudaStream_t st) {
+  const int n = b.n;
+  k_fold_overflow<<<1, 1, 0, st>>>((const int32_t*)b.flags.p + n + 1, &dc->overflow); note_launch();
+  PAMO_CUDA(cudaMemsetAsync(ncand, 0, 4 * sizeof(int), st));  // ncand[3], cand_overflow
+  CandBufs cb;
+  for (int r = 0; r < 3; r++) {
+    cb.c[r] = cand[r];
+    cb.cap[r] = cap[r];
+  }
+  k_traverse<<<grid, kBlock, 0, st>>>((const float4*)b.nodes.p, n, pos, F, fdead, ftag, query_all,
+                                      qlist, qcount, cb, ncand, dc); note_launch();
+  k_pairs<<<grid, kBlock, 0, st>>>(cb, ncand, pos, F, (const uint8_t*)b.face_aux.p, ftag, undo,
+                                   dc); note_launch();
   PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;
 }

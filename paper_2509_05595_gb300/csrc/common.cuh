@@ -45,7 +45,8 @@ inline unsigned grid_for(int64_t n, int block = kBlock) {
 struct RoundCounters {
   unsigned long long link_rejects, flagged, eligible;
   int n_win, n_pairs, n_undo, n_undone_total, overflow, bad, n_query, n_dirty;
-  int pad[4];
+  int ncand[3];
+  int cand_overflow;  // a candidate bucket overflowed: undo waits for the fused check
 };
 
 // Scratch buffer owned by a context, grown on demand (stream-ordered).
@@ -62,6 +63,11 @@ void buf_free(Buf& b, cudaStream_t st);
 struct Bvh {
   int n = 0;
   Buf nodes, parent, flags, keys, vals, keys2, vals2, hist, face_aux;
+  // leaf order carried over rounds: vals holds a spatially coherent face
+  // order for the current mesh (valid when order_ok); re-sorted by Morton
+  // code when the face count has halved since the last sort
+  bool order_ok = false;
+  int n_sorted = 0;
 };
 
 struct RoundRecord {
@@ -120,6 +126,9 @@ struct pamo_ctx {
   uint8_t* undo = nullptr;      // [Emax] per winner slot
   int32_t* ftag = nullptr;      // [nF0] winner slot that rewrote the face
   int32_t* qlist = nullptr;     // [nF0] faces changed this round (query list)
+  int2* cand[3] = {nullptr, nullptr, nullptr};  // candidate pairs by shared-vertex count
+  int64_t cand_cap[3] = {0, 0, 0};
+  int sm_count = 152;
   uint8_t* fdead = nullptr;     // [nF0]
   uint8_t* vdead = nullptr;     // [nV0]
   int32_t* vmap = nullptr;      // [nV0+1]
@@ -214,6 +223,18 @@ pamo_status bvh_check(Bvh& b, const float4* pos, const int4* F, const uint8_t* f
                       const int* qcount, int64_t nq_max, uint8_t* undo, RoundCounters* dc,
                       int32_t* pairs_out, int64_t cap, cudaStream_t st);
 void bvh_free(Bvh& b, cudaStream_t st);
+// The same check in two passes: traversal appends candidate pairs into three
+// buckets (by shared-vertex count, capacities cap[]), then one thread per pair
+// runs the exact test.  ncand[3] (device) receives the bucket counts; a count
+// above its capacity means the caller must redo the check with bvh_check.
+pamo_status bvh_check_split(Bvh& b, const float4* pos, const int4* F, const uint8_t* fdead,
+                            const int32_t* ftag, int query_all, const int32_t* qlist,
+                            const int* qcount, uint8_t* undo, RoundCounters* dc, int2* const cand[3],
+                            const int64_t cap[3], int* ncand, int grid, cudaStream_t st);
+// After a commit: keep the leaf order for the compacted faces (stable filter
+// of the current order through fdead / dead_before), nF_new faces.
+pamo_status bvh_compact_order(Bvh& b, const uint8_t* fdead, const int32_t* dead_before,
+                              int nF_new, Buf& tmp, cudaStream_t st);
 // allocation-free build over buffers already placed in b (sizes: bvh_bytes)
 pamo_status bvh_build_into(Bvh& b, const float4* pos, const int4* F, int nF, const float lo[3],
                            const float hi[3], int32_t* scan_sums, cudaStream_t st);

@@ -121,6 +121,7 @@ __global__ void k_undo(const int32_t* __restrict__ wlist, int64_t nW, const int2
                        int32_t* __restrict__ ftag, uint8_t* __restrict__ standing,
                        uint8_t* __restrict__ undo, RoundCounters* __restrict__ dc) {
   const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (dc->cand_overflow) return;  // marks incomplete: the host reruns the fused check
   int n = 0;
   if (w < nW && undo[w]) {
     undo[w] = 0;

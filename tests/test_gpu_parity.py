@@ -142,6 +142,14 @@ def test_nested_shells_with_undos_bit_exact(level, div):
     assert stats["undone"] == sum(d["undone"] for d in ref.rounds)
 
 
+def test_candidate_overflow_fallback_bit_exact(monkeypatch):
+    """Tiny candidate buffers force the fused-check fallback in every check
+    iteration; the run must not change."""
+    monkeypatch.setenv("PAMO_CAND_CAP_DIVISOR", "1000000")
+    V, F = meshgen.nested_shells(4, check=False)
+    _assert_same_run(V, F, len(F) // 50)
+
+
 def test_planar_box_exercises_exact_predicates():
     V, F = meshgen.box_grid(8)
     _assert_same_run(V, F, 40)
