@@ -39,8 +39,9 @@
 //      committed collapse the flags accumulate, cleared after `tolerance`
 //      such rounds.
 //
-// Floating point: compiled with -ffp-contract=off, IEEE double throughout
-// the cost, float only for stored positions.
+// Floating point: compiled with -ffp-contract=off (no implicit contraction),
+// IEEE double throughout the cost with explicit std::fma where the order says
+// so, float only for stored positions.
 
 #include <algorithm>
 #include <cmath>
@@ -442,32 +443,43 @@ static Quadric face_quadric(const float* p0, const float* p1, const float* p2) {
   return q;
 }
 
+// Evaluation order (reading R2/R3): products are accumulated with fused
+// multiply-adds (std::fma: one rounding), written out explicitly so that the
+// order is fixed.  Cramer's rule expanded along the first row.
 static double det3(double a00, double a01, double a02, double a10, double a11,
                    double a12, double a20, double a21, double a22) {
-  return (a00 * (a11 * a22 - a12 * a21) - a01 * (a10 * a22 - a12 * a20)) +
-         a02 * (a10 * a21 - a11 * a20);
+  double m0 = std::fma(a11, a22, -(a12 * a21));
+  double m1 = std::fma(a10, a22, -(a12 * a20));
+  double m2 = std::fma(a10, a21, -(a11 * a20));
+  return std::fma(a02, m2, std::fma(-a01, m1, a00 * m0));
 }
 
 // Q(v) = v^T A v + 2 b^T v + c for the summed quadric K
 static double quadric_eval(const double* K, double x, double y, double z) {
-  double ax = (K[0] * x + K[1] * y) + K[2] * z;
-  double ay = (K[1] * x + K[4] * y) + K[5] * z;
-  double az = (K[2] * x + K[5] * y) + K[7] * z;
-  double bv = (K[3] * x + K[6] * y) + K[8] * z;
-  return (((x * ax + y * ay) + z * az) + 2.0 * bv) + K[9];
+  double ax = std::fma(K[2], z, std::fma(K[1], y, K[0] * x));
+  double ay = std::fma(K[5], z, std::fma(K[4], y, K[1] * x));
+  double az = std::fma(K[7], z, std::fma(K[5], y, K[2] * x));
+  double bv = std::fma(K[8], z, std::fma(K[6], y, K[3] * x));
+  return std::fma(2.0, bv, std::fma(z, az, std::fma(y, ay, x * ax))) + K[9];
 }
 
+static double dot3(double ax, double ay, double az, double bx, double by, double bz) {
+  return std::fma(az, bz, std::fma(ay, by, ax * bx));
+}
+
+// C_ijk = 4 sqrt(3) A / (l_ij^2 + l_jk^2 + l_ki^2) with u = q1 - q0, w = q2 - q0:
+// (2A)^2 = |u x w|^2 = |u|^2 |w|^2 - (u.w)^2 (Lagrange's identity) and
+// l_ij^2 + l_jk^2 + l_ki^2 = |u|^2 + |w|^2 + |w - u|^2 = 2 (|u|^2 + |w|^2 - u.w).
 static double tri_quality(const double* q0, const double* q1, const double* q2) {
   double ux = q1[0] - q0[0], uy = q1[1] - q0[1], uz = q1[2] - q0[2];
   double wx = q2[0] - q0[0], wy = q2[1] - q0[1], wz = q2[2] - q0[2];
-  double tx = q2[0] - q1[0], ty = q2[1] - q1[1], tz = q2[2] - q1[2];
-  double cx = uy * wz - uz * wy;
-  double cy = uz * wx - ux * wz;
-  double cz = ux * wy - uy * wx;
-  double area = 0.5 * std::sqrt((cx * cx + cy * cy) + cz * cz);
-  double den = (((ux * ux + uy * uy) + uz * uz) + ((tx * tx + ty * ty) + tz * tz)) +
-               ((wx * wx + wy * wy) + wz * wz);
-  if (den > 0.0) return ((4.0 * kSqrt3) * area) / den;
+  double a = dot3(ux, uy, uz, ux, uy, uz);
+  double b = dot3(wx, wy, wz, wx, wy, wz);
+  double c = dot3(ux, uy, uz, wx, wy, wz);
+  double cr2 = std::fma(a, b, -(c * c));
+  if (!(cr2 > 0.0)) cr2 = 0.0;
+  double den = 2.0 * ((a + b) - c);
+  if (den > 0.0) return ((2.0 * kSqrt3) * std::sqrt(cr2)) / den;
   return 0.0;
 }
 
@@ -659,7 +671,7 @@ static void edge_cost(const Mesh& m, const std::vector<int64_t>& off,
   }
   double dx = (double)pb[0] - (double)pa[0], dy = (double)pb[1] - (double)pa[1],
          dz = (double)pb[2] - (double)pa[2];
-  double l = std::sqrt((dx * dx + dy * dy) + dz * dz);
+  double l = std::sqrt(dot3(dx, dy, dz, dx, dy, dz));
   // skinny term over the triangles the collapse produces, R3
   double Cs = 0.0;
   std::vector<int32_t> ring = edge_ring(off, idx, a, b);
@@ -678,7 +690,7 @@ static void edge_cost(const Mesh& m, const std::vector<int64_t>& off,
     Cs = Cs + (1.0 - tri_quality(q[0], q[1], q[2]));
   }
   double s2 = scale * scale, wes = o.w_e * scale;
-  double cost = ((s2 * Q) + (wes * l)) + (o.w_s * Cs);
+  double cost = std::fma(o.w_s, Cs, std::fma(wes, l, s2 * Q));
   e.Q = Q;
   e.l = l;
   e.Cs = Cs;

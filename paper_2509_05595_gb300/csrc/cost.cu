@@ -7,45 +7,67 @@
 // link condition (Dey et al., cited in Section 5.1) and the invalid-edge flags
 // (Section 5.3) and packs the 64-bit key (float cost bits << 32 | edge id).
 //
-// All float64 arithmetic is IEEE round-to-nearest with no contraction (the
-// library is compiled with --fmad=false), in a fixed evaluation order, so the
-// keys are reproducible bit for bit.
+// All float64 arithmetic is IEEE round-to-nearest in a fixed evaluation order
+// (the library is compiled with --fmad=false, so only the explicit __fma_rn
+// calls fuse), so the keys are reproducible bit for bit.
 #include "common.cuh"
 
 namespace pamo {
 
 namespace {
 
-constexpr double kFourSqrt3 = 4.0 * 1.7320508075688772;
+constexpr double kTwoSqrt3 = 2.0 * 1.7320508075688772;
 
+// float -> double on the integer pipe (exact for normal floats; zero,
+// subnormals, inf and NaN take the hardware conversion).  The float64 unit is
+// the scarce resource of this kernel.
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return (double)f;
+  const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
+                               ((unsigned long long)(e + 896u) << 52) |
+                               ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)d);
+}
+
+// Fixed evaluation order with explicit fused multiply-adds (one rounding each).
 __device__ __forceinline__ double det3(double a00, double a01, double a02, double a10, double a11,
                                        double a12, double a20, double a21, double a22) {
-  return (a00 * (a11 * a22 - a12 * a21) - a01 * (a10 * a22 - a12 * a20)) +
-         a02 * (a10 * a21 - a11 * a20);
+  const double m0 = __fma_rn(a11, a22, -(a12 * a21));
+  const double m1 = __fma_rn(a10, a22, -(a12 * a20));
+  const double m2 = __fma_rn(a10, a21, -(a11 * a20));
+  return __fma_rn(a02, m2, __fma_rn(-a01, m1, a00 * m0));
 }
 
 // v^T A v + 2 b^T v + c of the summed quadric
 __device__ __forceinline__ double qeval(const double* K, double x, double y, double z) {
-  double ax = (K[0] * x + K[1] * y) + K[2] * z;
-  double ay = (K[1] * x + K[4] * y) + K[5] * z;
-  double az = (K[2] * x + K[5] * y) + K[7] * z;
-  double bv = (K[3] * x + K[6] * y) + K[8] * z;
-  return (((x * ax + y * ay) + z * az) + 2.0 * bv) + K[9];
+  const double ax = __fma_rn(K[2], z, __fma_rn(K[1], y, K[0] * x));
+  const double ay = __fma_rn(K[5], z, __fma_rn(K[4], y, K[1] * x));
+  const double az = __fma_rn(K[7], z, __fma_rn(K[5], y, K[2] * x));
+  const double bv = __fma_rn(K[8], z, __fma_rn(K[6], y, K[3] * x));
+  return __fma_rn(2.0, bv, __fma_rn(z, az, __fma_rn(y, ay, x * ax))) + K[9];
 }
 
-// C_ijk = 4 sqrt(3) A / (l_ij^2 + l_jk^2 + l_ki^2)
+__device__ __forceinline__ double dot3(double ax, double ay, double az, double bx, double by,
+                                       double bz) {
+  return __fma_rn(az, bz, __fma_rn(ay, by, ax * bx));
+}
+
+// C_ijk = 4 sqrt(3) A / (l_ij^2 + l_jk^2 + l_ki^2), with u = q1 - q0, w = q2 - q0:
+// |u x w|^2 = |u|^2 |w|^2 - (u.w)^2 and the three squared lengths sum to
+// 2 (|u|^2 + |w|^2 - u.w)
 __device__ __forceinline__ double quality(double x0, double y0, double z0, double x1, double y1,
                                           double z1, double x2, double y2, double z2) {
-  double ux = x1 - x0, uy = y1 - y0, uz = z1 - z0;
-  double wx = x2 - x0, wy = y2 - y0, wz = z2 - z0;
-  double tx = x2 - x1, ty = y2 - y1, tz = z2 - z1;
-  double cx = uy * wz - uz * wy;
-  double cy = uz * wx - ux * wz;
-  double cz = ux * wy - uy * wx;
-  double area = 0.5 * sqrt((cx * cx + cy * cy) + cz * cz);
-  double den = (((ux * ux + uy * uy) + uz * uz) + ((tx * tx + ty * ty) + tz * tz)) +
-               ((wx * wx + wy * wy) + wz * wz);
-  return den > 0.0 ? (kFourSqrt3 * area) / den : 0.0;
+  const double ux = x1 - x0, uy = y1 - y0, uz = z1 - z0;
+  const double wx = x2 - x0, wy = y2 - y0, wz = z2 - z0;
+  const double a = dot3(ux, uy, uz, ux, uy, uz);
+  const double b = dot3(wx, wy, wz, wx, wy, wz);
+  const double c = dot3(ux, uy, uz, wx, wy, wz);
+  double cr2 = __fma_rn(a, b, -(c * c));
+  if (!(cr2 > 0.0)) cr2 = 0.0;
+  const double den = 2.0 * ((a + b) - c);
+  return den > 0.0 ? (kTwoSqrt3 * sqrt(cr2)) / den : 0.0;
 }
 
 __device__ __forceinline__ int next_of(const int4& f, int v) {
@@ -207,26 +229,27 @@ __global__ void __launch_bounds__(kBlock) k_edge_cost(
     }
     double Q;
     if (solved) {
-      Q = qeval(K, vx, vy, vz);
+      Q = qeval(K, f2d(vx), f2d(vy), f2d(vz));
     } else {
       // best of a, b, midpoint by Q; ties keep the earlier candidate
       const float mxp = __double2float_rn(((double)pa.x + (double)pb.x) * 0.5);
       const float myp = __double2float_rn(((double)pa.y + (double)pb.y) * 0.5);
       const float mzp = __double2float_rn(((double)pa.z + (double)pb.z) * 0.5);
-      Q = qeval(K, pa.x, pa.y, pa.z);
+      Q = qeval(K, f2d(pa.x), f2d(pa.y), f2d(pa.z));
       vx = pa.x; vy = pa.y; vz = pa.z;
-      const double qb = qeval(K, pb.x, pb.y, pb.z);
+      const double qb = qeval(K, f2d(pb.x), f2d(pb.y), f2d(pb.z));
       if (qb < Q) { Q = qb; vx = pb.x; vy = pb.y; vz = pb.z; }
-      const double qm = qeval(K, mxp, myp, mzp);
+      const double qm = qeval(K, f2d(mxp), f2d(myp), f2d(mzp));
       if (qm < Q) { Q = qm; vx = mxp; vy = myp; vz = mzp; }
     }
     // ---- l_ab
-    const double dx = (double)pb.x - (double)pa.x, dy = (double)pb.y - (double)pa.y,
-                 dz = (double)pb.z - (double)pa.z;
-    const double l = sqrt((dx * dx + dy * dy) + dz * dz);
+    const double dx = f2d(pb.x) - f2d(pa.x), dy = f2d(pb.y) - f2d(pa.y),
+                 dz = f2d(pb.z) - f2d(pa.z);
+    const double l = sqrt(dot3(dx, dy, dz, dx, dy, dz));
     // ---- skinny term: faces around a or b, except the two on ab, ascending
     // face id (merge of the two sorted incidence lists)
     double Cs = 0.0;
+    const double vxd = f2d(vx), vyd = f2d(vy), vzd = f2d(vz);
     {
       int i = a0, j = b0;
       while (i < a1 || j < b1) {
@@ -246,16 +269,16 @@ __global__ void __launch_bounds__(kBlock) k_edge_cost(
 #pragma unroll
         for (int k = 0; k < 3; k++) {
           if (cs[k] == a || cs[k] == b) {
-            q[3 * k] = vx; q[3 * k + 1] = vy; q[3 * k + 2] = vz;
+            q[3 * k] = vxd; q[3 * k + 1] = vyd; q[3 * k + 2] = vzd;
           } else {
             const float4 p = pos[cs[k]];
-            q[3 * k] = p.x; q[3 * k + 1] = p.y; q[3 * k + 2] = p.z;
+            q[3 * k] = f2d(p.x); q[3 * k + 1] = f2d(p.y); q[3 * k + 2] = f2d(p.z);
           }
         }
         Cs = Cs + (1.0 - quality(q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7], q[8]));
       }
     }
-    const double cost = ((s2 * Q) + (wes * l)) + (ws * Cs);
+    const double cost = __fma_rn(ws, Cs, __fma_rn(wes, l, s2 * Q));
     float cf = __double2float_rn(cost);
     uint32_t cb = 0xffffffffu;  // non-finite: never eligible
     if (!isnan(cost) && !isinf(cf)) {
