@@ -160,8 +160,15 @@ __device__ __forceinline__ int delta(const unsigned* __restrict__ k, int n, int 
   return __clz(a ^ b);
 }
 
-__global__ void k_karras(const unsigned* __restrict__ k, int n, float4* __restrict__ nodes,
-                         int32_t* __restrict__ parent) {
+// Node layout (64 bytes, internal nodes only): the boxes of both children and
+// the child links, so that one 64-byte load serves a whole traversal level.
+//   floats 0-5:  left child box  (lo.xyz, hi.xyz)
+//   floats 6-11: right child box (lo.xyz, hi.xyz)
+//   ints 12, 13: left, right child (internal index >= 0, or ~face for a leaf)
+// parent[x] = (parent node << 1) | side for internal x in [0, n-1) and leaf
+// positions x = n-1+j; the root has -1.
+__global__ void k_karras(const unsigned* __restrict__ k, const int32_t* __restrict__ vals, int n,
+                         float* __restrict__ nodes, int32_t* __restrict__ parent) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n - 1) return;
   const int d = (delta(k, n, i, i + 1) - delta(k, n, i, i - 1)) >= 0 ? 1 : -1;
@@ -180,12 +187,14 @@ __global__ void k_karras(const unsigned* __restrict__ k, int n, float4* __restri
     if (t <= 1) break;
   }
   const int g = i + s * d + (d < 0 ? -1 : 0);
-  const int left = (min(i, j) == g) ? (n - 1 + g) : g;
-  const int right = (max(i, j) == g + 1) ? (n - 1 + g + 1) : g + 1;
-  nodes[2 * i] = make_float4(0.f, 0.f, 0.f, __int_as_float(left));
-  nodes[2 * i + 1] = make_float4(0.f, 0.f, 0.f, __int_as_float(right));
-  parent[left] = i;
-  parent[right] = i;
+  const bool lleaf = min(i, j) == g, rleaf = max(i, j) == g + 1;
+  const int left = lleaf ? ~vals[g] : g;
+  const int right = rleaf ? ~vals[g + 1] : g + 1;
+  int* links = reinterpret_cast<int*>(nodes + 16 * (size_t)i + 12);
+  links[0] = left;
+  links[1] = right;
+  parent[lleaf ? n - 1 + g : g] = (i << 1) | 0;
+  parent[rleaf ? n - 1 + g + 1 : g + 1] = (i << 1) | 1;
   if (i == 0) parent[0] = -1;
 }
 
@@ -216,14 +225,23 @@ __device__ __forceinline__ void face_box(const float4* __restrict__ pos, const i
                    fmaxf(fmaxf(a.z, b.z), c.z));
 }
 
-// leaf boxes, then bottom-up union: the second child to arrive at a parent
-// computes it (no waiting; every thread stops at a first arrival or the root)
+__device__ __forceinline__ void store_box(float* __restrict__ nodes, int p, int side,
+                                          const float3& lo, const float3& hi) {
+  float2* dst = reinterpret_cast<float2*>(nodes + 16 * (size_t)p + 6 * side);
+  dst[0] = make_float2(lo.x, lo.y);
+  dst[1] = make_float2(lo.z, hi.x);
+  dst[2] = make_float2(hi.y, hi.z);
+}
+
+// leaf boxes go into their parent's slot; then bottom-up unions: the second
+// child to arrive at a parent computes the parent's box and stores it in the
+// grandparent (no waiting; every thread stops at a first arrival or the root)
 __global__ void k_refit(const float4* __restrict__ pos, const int4* __restrict__ F,
                         const uint8_t* __restrict__ fdead, const int32_t* __restrict__ vals, int n,
-                        float4* __restrict__ nodes, const int32_t* __restrict__ parent,
+                        float* __restrict__ nodes, const int32_t* __restrict__ parent,
                         int32_t* __restrict__ flags, int* __restrict__ overflow) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
+  if (j >= n || n < 2) return;
   const int f = vals[j];
   float3 lo, hi;
   if (fdead && fdead[f]) {
@@ -232,29 +250,27 @@ __global__ void k_refit(const float4* __restrict__ pos, const int4* __restrict__
   } else {
     face_box(pos, F[f], lo, hi);
   }
-  int node = n - 1 + j;
-  nodes[2 * node] = make_float4(lo.x, lo.y, lo.z, __int_as_float(f));
-  nodes[2 * node + 1] = make_float4(hi.x, hi.y, hi.z, __int_as_float(-1));
-  if (n == 1) return;
+  int ps = parent[n - 1 + j];
+  store_box(nodes, ps >> 1, ps & 1, lo, hi);
   __threadfence();
-  int p = parent[node];
   // a radix tree over n leaves is at most n - 1 levels deep; the cap only
   // guards against a malformed tree
-  for (int steps = 0; p >= 0; steps++) {
+  for (int steps = 0;; steps++) {
+    const int p = ps >> 1;
     if (steps >= n) {
       atomicOr(overflow, 2);
       return;
     }
     if (atomicAdd(&flags[p], 1) == 0) return;  // sibling not ready: it finishes
     __threadfence();
-    const float4 pl = nodes[2 * p], ph = nodes[2 * p + 1];
-    const int L = __float_as_int(pl.w), R = __float_as_int(ph.w);
-    const float4 al = __ldcg(&nodes[2 * L]), ah = __ldcg(&nodes[2 * L + 1]);
-    const float4 bl = __ldcg(&nodes[2 * R]), bh = __ldcg(&nodes[2 * R + 1]);
-    nodes[2 * p] = make_float4(fminf(al.x, bl.x), fminf(al.y, bl.y), fminf(al.z, bl.z), pl.w);
-    nodes[2 * p + 1] = make_float4(fmaxf(ah.x, bh.x), fmaxf(ah.y, bh.y), fmaxf(ah.z, bh.z), ph.w);
+    const float4* q = reinterpret_cast<const float4*>(nodes + 16 * (size_t)p);
+    const float4 a = __ldcg(q), b = __ldcg(q + 1), c = __ldcg(q + 2);
+    ps = parent[p];
+    if (ps < 0) return;  // root: its box is never needed
+    lo = make_float3(fminf(a.x, b.z), fminf(a.y, b.w), fminf(a.z, c.x));
+    hi = make_float3(fmaxf(a.w, c.y), fmaxf(b.x, c.z), fmaxf(b.y, c.w));
+    store_box(nodes, ps >> 1, ps & 1, lo, hi);
     __threadfence();
-    p = parent[p];
   }
 }
 
@@ -262,10 +278,27 @@ __global__ void k_fold_overflow(const int32_t* __restrict__ src, int* __restrict
   if (*src) atomicOr(dst, *src);
 }
 
-__device__ __forceinline__ bool overlap(const float3& alo, const float3& ahi, const float4& blo,
-                                        const float4& bhi) {
-  return !(alo.x > bhi.x || blo.x > ahi.x || alo.y > bhi.y || blo.y > ahi.y || alo.z > bhi.z ||
-           blo.z > ahi.z);
+__device__ __forceinline__ bool overlap(const float3& alo, const float3& ahi, float blx, float bly,
+                                        float blz, float bhx, float bhy, float bhz) {
+  return !(alo.x > bhx || blx > ahi.x || alo.y > bhy || bly > ahi.y || alo.z > bhz || blz > ahi.z);
+}
+
+// one 64-byte node: which children overlap the query box, and their links
+struct NodeHits {
+  bool l, r;
+  int L, R;
+};
+
+__device__ __forceinline__ NodeHits visit(const float* __restrict__ nodes, int node,
+                                          const float3& lo, const float3& hi) {
+  const float4* q = reinterpret_cast<const float4*>(nodes + 16 * (size_t)node);
+  const float4 a = q[0], b = q[1], c = q[2], d = q[3];
+  NodeHits h;
+  h.l = overlap(lo, hi, a.x, a.y, a.z, a.w, b.x, b.y);
+  h.r = overlap(lo, hi, b.z, b.w, c.x, c.y, c.z, c.w);
+  h.L = __float_as_int(d.x);
+  h.R = __float_as_int(d.y);
+  return h;
 }
 
 // One thread per query face.  Query faces: every live face when query_all,
@@ -273,7 +306,7 @@ __device__ __forceinline__ bool overlap(const float3& alo, const float3& ahi, co
 // faces is evaluated once, from its lower face id.  Intersecting pairs mark
 // the collapses that tagged either face.
 __global__ void __launch_bounds__(kBlock) k_query(
-    const float4* __restrict__ nodes, int n, const float4* __restrict__ pos,
+    const float* __restrict__ nodes, int n, const float4* __restrict__ pos,
     const int4* __restrict__ F, const uint8_t* __restrict__ fdead,
     const uint8_t* __restrict__ info, const int32_t* __restrict__ ftag, int query_all,
     const int32_t* __restrict__ qlist, const int* __restrict__ qcount,
@@ -317,18 +350,14 @@ __global__ void __launch_bounds__(kBlock) k_query(
       atomicOr(&dc->overflow, 4);
       return;
     }
-    const float4 nl = nodes[2 * node], nh = nodes[2 * node + 1];
-    const int L = __float_as_int(nl.w), R = __float_as_int(nh.w);
-    // children of an internal node
+    const NodeHits h = visit(nodes, node, lo, hi);
     int next = -1;
-    const int ch[2] = {L, R};
 #pragma unroll
     for (int c = 0; c < 2; c++) {
-      const int cn = ch[c];
-      const float4 cl = nodes[2 * cn], chh = nodes[2 * cn + 1];
-      if (!overlap(lo, hi, cl, chh)) continue;
-      if (cn >= n - 1) {  // leaf
-        const int g = __float_as_int(cl.w);
+      if (!(c ? h.r : h.l)) continue;
+      const int cn = c ? h.R : h.L;
+      if (cn < 0) {  // leaf
+        const int g = ~cn;
         if (g == f) continue;
         const int tg = ftag ? ftag[g] : -1;
         if (query_all ? (g < f) : (tg >= 0 && g < f)) continue;
@@ -376,7 +405,7 @@ struct CandBufs {
 };
 
 __global__ void __launch_bounds__(kBlock) k_traverse(
-    const float4* __restrict__ nodes, int n, const float4* __restrict__ pos,
+    const float* __restrict__ nodes, int n, const float4* __restrict__ pos,
     const int4* __restrict__ F, const uint8_t* __restrict__ fdead,
     const int32_t* __restrict__ ftag, int query_all, const int32_t* __restrict__ qlist,
     const int* __restrict__ qcount, CandBufs cb, int* __restrict__ ncand,
@@ -401,15 +430,14 @@ __global__ void __launch_bounds__(kBlock) k_traverse(
         atomicOr(&dc->overflow, 4);
         break;
       }
-      const int L = __float_as_int(nodes[2 * node].w), R = __float_as_int(nodes[2 * node + 1].w);
+      const NodeHits h = visit(nodes, node, lo, hi);
       int next = -1;
 #pragma unroll
       for (int k = 0; k < 2; k++) {
-        const int cn = k ? R : L;
-        const float4 cl = nodes[2 * cn], ch = nodes[2 * cn + 1];
-        if (!overlap(lo, hi, cl, ch)) continue;
-        if (cn >= n - 1) {
-          const int g = __float_as_int(cl.w);
+        if (!(k ? h.r : h.l)) continue;
+        const int cn = k ? h.R : h.L;
+        if (cn < 0) {
+          const int g = ~cn;
           if (g == f) continue;
           const int tg = ftag ? ftag[g] : -1;
           if (query_all ? (g < f) : (tg >= 0 && g < f)) continue;
@@ -533,8 +561,8 @@ pamo_status bvh_build(Bvh& b, const float4* pos, const int4* F, const uint8_t* f
   if (b.order_ok && b.n == nF && 2 * (int64_t)nF > b.n_sorted && nF >= 2) {
     // carried-over order with the Morton keys of the last sort (still sorted):
     // hierarchy at the same prefix splits, then boxes of the current faces
-    k_karras<<<grid_for(nF - 1), kBlock, 0, st>>>((const unsigned*)b.keys.p, nF, (float4*)b.nodes.p,
-                                                  (int32_t*)b.parent.p); note_launch();
+    k_karras<<<grid_for(nF - 1), kBlock, 0, st>>>((const unsigned*)b.keys.p, (const int32_t*)b.vals.p,
+                                                  nF, (float*)b.nodes.p, (int32_t*)b.parent.p); note_launch();
     PAMO_CUDA(cudaGetLastError());
     return bvh_refit(b, pos, F, fdead, st);
   }
@@ -579,7 +607,7 @@ pamo_status bvh_build(Bvh& b, const float4* pos, const int4* F, const uint8_t* f
   buf_free(scan_tmp, st);
   // four passes: sorted data is back in b.keys / b.vals
   if (n >= 2) {
-    k_karras<<<grid_for(n - 1), kBlock, 0, st>>>(keys, n, (float4*)b.nodes.p, (int32_t*)b.parent.p); note_launch();
+    k_karras<<<grid_for(n - 1), kBlock, 0, st>>>(keys, vals, n, (float*)b.nodes.p, (int32_t*)b.parent.p); note_launch();
     PAMO_CUDA(cudaGetLastError());
   }
   return bvh_refit(b, pos, F, fdead, st);
@@ -617,7 +645,7 @@ pamo_status bvh_build_into(Bvh& b, const float4* pos, const int4* F, int nF, con
     int32_t* tv = vals; vals = vals2; vals2 = tv;
   }
   if (n >= 2) {
-    k_karras<<<grid_for(n - 1), kBlock, 0, st>>>(keys, n, (float4*)b.nodes.p, (int32_t*)b.parent.p); note_launch();
+    k_karras<<<grid_for(n - 1), kBlock, 0, st>>>(keys, vals, n, (float*)b.nodes.p, (int32_t*)b.parent.p); note_launch();
     PAMO_CUDA(cudaGetLastError());
   }
   return bvh_refit(b, pos, F, nullptr, st);
@@ -641,7 +669,7 @@ pamo_status bvh_refit(Bvh& b, const float4* pos, const int4* F, const uint8_t* f
   PAMO_CUDA(cudaMemsetAsync(b.flags.p, 0, sizeof(int32_t) * (size_t)(n + 2), st));
   int32_t* fl = (int32_t*)b.flags.p;
   k_refit<<<grid_for(n), kBlock, 0, st>>>(pos, F, fdead, (const int32_t*)b.vals.p, n,
-                                          (float4*)b.nodes.p, (const int32_t*)b.parent.p, fl,
+                                          (float*)b.nodes.p, (const int32_t*)b.parent.p, fl,
                                           fl + n + 1); note_launch();
   k_face_info<<<grid_for(n), kBlock, 0, st>>>(pos, F, fdead, n, (uint8_t*)b.face_aux.p); note_launch();
   PAMO_CUDA(cudaGetLastError());
@@ -656,7 +684,7 @@ pamo_status bvh_check(Bvh& b, const float4* pos, const int4* F, const uint8_t* f
   // fold a refit overflow (flags[n+1]) into the round's overflow word
   k_fold_overflow<<<1, 1, 0, st>>>((const int32_t*)b.flags.p + n + 1, &dc->overflow); note_launch();
   const int64_t threads = query_all ? n : nq_max;
-  k_query<<<grid_for(threads), kBlock, 0, st>>>((const float4*)b.nodes.p, n, pos, F, fdead,
+  k_query<<<grid_for(threads), kBlock, 0, st>>>((const float*)b.nodes.p, n, pos, F, fdead,
                                                 (const uint8_t*)b.face_aux.p, ftag, query_all,
                                                 qlist, qcount, undo, dc, pairs_out, cap); note_launch();
   PAMO_CUDA(cudaGetLastError());
@@ -693,7 +721,7 @@ pamo_status bvh_check_split(Bvh& b, const float4* pos, const int4* F, const uint
     cb.c[r] = cand[r];
     cb.cap[r] = cap[r];
   }
-  k_traverse<<<grid, kBlock, 0, st>>>((const float4*)b.nodes.p, n, pos, F, fdead, ftag, query_all,
+  k_traverse<<<grid, kBlock, 0, st>>>((const float*)b.nodes.p, n, pos, F, fdead, ftag, query_all,
                                       qlist, qcount, cb, ncand, dc); note_launch();
   k_pairs<<<grid, kBlock, 0, st>>>(cb, ncand, pos, F, (const uint8_t*)b.face_aux.p, ftag, undo,
                                    dc); note_launch();
