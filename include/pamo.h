@@ -97,6 +97,10 @@ typedef struct {
   double class_ms[8];
   int64_t class_launches[8];
   double class_bytes[8];
+  /* algorithmic float64 operations per class (edge cost only: per evaluated
+   * edge 114 + 32 per produced triangle, counting +,-,*,/,sqrt as 1 and a
+   * fused multiply-add as 2) */
+  double class_flops[8];
 } pamo_stats;
 
 typedef struct pamo_ctx pamo_ctx;

@@ -52,7 +52,8 @@ class _Stats(ctypes.Structure):
                 ("nV_out", ctypes.c_int64), ("nF_out", ctypes.c_int64),
                 ("ms_total", ctypes.c_double), ("bytes_model", ctypes.c_double),
                 ("launches", ctypes.c_int64), ("class_ms", ctypes.c_double * 8),
-                ("class_launches", ctypes.c_int64 * 8), ("class_bytes", ctypes.c_double * 8)]
+                ("class_launches", ctypes.c_int64 * 8), ("class_bytes", ctypes.c_double * 8),
+                ("class_flops", ctypes.c_double * 8)]
 
 
 @dataclass
@@ -147,7 +148,7 @@ def _stats_dict(s: _Stats):
                 winners=s.winners, nV_out=s.nV_out, nF_out=s.nF_out,
                 ms_total=s.ms_total, bytes_model=s.bytes_model, launches=s.launches,
                 class_ms=list(s.class_ms), class_launches=list(s.class_launches),
-                class_bytes=list(s.class_bytes))
+                class_bytes=list(s.class_bytes), class_flops=list(s.class_flops))
 
 
 def pamo_simplify(V, F, target_faces, options: Options | None = None, **kw):

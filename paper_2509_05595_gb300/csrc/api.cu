@@ -408,6 +408,8 @@ pamo_status round_commit(pamo_ctx* c) {
   kc_end(c, PAMO_KC_COMMIT, (double)nV_in * (16 + 80 + 1 + 4) * 2 + (double)nF_in * (16 + 1 + 4) * 2);
   PAMO_TRY(sync_counters(c));
   kc_resolve(c);
+  // float64 operations of the edge costs evaluated this round
+  c->class_flops[PAMO_KC_COST] += 114.0 * c->hc->n_dirty + 32.0 * (double)c->hc->cost_tris;
   const int64_t committed = nW - nund;
   c->nV = nV_in - committed;
   c->nF = nF_in - 2 * committed;
@@ -494,6 +496,7 @@ void fill_stats(const pamo_ctx* c, pamo_stats* s, double ms) {
     s->class_ms[i] = c->class_ms[i];
     s->class_launches[i] = c->class_launches[i];
     s->class_bytes[i] = c->class_bytes[i];
+    s->class_flops[i] = c->class_flops[i];
   }
 }
 

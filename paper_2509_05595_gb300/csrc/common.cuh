@@ -44,6 +44,7 @@ inline unsigned grid_for(int64_t n, int block = kBlock) {
 // device-side counters of one round, mirrored to pinned host memory
 struct RoundCounters {
   unsigned long long link_rejects, flagged, eligible;
+  unsigned long long cost_tris;  // triangles produced, summed over evaluated edges
   int n_win, n_pairs, n_undo, n_undone_total, overflow, bad, n_query, n_dirty;
   int ncand[3];
   int cand_overflow;  // a candidate bucket overflowed: undo waits for the fused check
@@ -154,6 +155,7 @@ struct pamo_ctx {
   double class_ms[8] = {0};
   long long class_launches[8] = {0};
   double class_bytes[8] = {0};
+  double class_flops[8] = {0};
   // --- records
   std::vector<pamo::RoundRecord> rec;
   int64_t rounds = 0;

@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kBlock) k_edge_cost(
     float4* __restrict__ vbar, uint32_t* __restrict__ cbits, uint8_t* __restrict__ link,
     RoundCounters* __restrict__ dc) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int link_bad = 0, flagged = 0, eligible = 0;
+  int link_bad = 0, flagged = 0, eligible = 0, ntri = 0;
   if (i < *ndirty) {
     const int64_t e = dlist[i];
     const int2 ab = E[e];
@@ -276,6 +276,7 @@ __global__ void __launch_bounds__(kBlock) k_edge_cost(
           }
         }
         Cs = Cs + (1.0 - quality(q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7], q[8]));
+        ntri++;
       }
     }
     const double cost = __fma_rn(ws, Cs, __fma_rn(wes, l, s2 * Q));
@@ -301,7 +302,9 @@ __global__ void __launch_bounds__(kBlock) k_edge_cost(
   link_bad = __reduce_add_sync(0xffffffffu, link_bad);
   flagged = __reduce_add_sync(0xffffffffu, flagged);
   eligible = __reduce_add_sync(0xffffffffu, eligible);
+  ntri = __reduce_add_sync(0xffffffffu, ntri);
   if ((threadIdx.x & 31) == 0) {
+    if (ntri) atomicAdd(&dc->cost_tris, (unsigned long long)ntri);
     if (link_bad) atomicAdd(&dc->link_rejects, (unsigned long long)link_bad);
     if (flagged) atomicAdd(&dc->flagged, (unsigned long long)flagged);
     if (eligible) atomicAdd(&dc->eligible, (unsigned long long)eligible);

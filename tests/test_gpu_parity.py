@@ -250,3 +250,44 @@ def test_full_size_run_properties(sphere_l8):
     assert gn == 0
     _, n = oracle.self_intersections(Vo, Fo)
     assert n == 0
+
+
+def test_nested_shells_l6_full_parity():
+    """163,840 faces of near-contact shells (many undos): the full run is
+    bit-identical to the oracle."""
+    V, F = meshgen.nested_shells(6, check=False)
+    ref, _ = _assert_same_run(V, F, len(F) // 100)
+    assert sum(d["undone"] for d in ref.rounds) > 100
+
+
+@pytest.fixture(scope="module")
+def shells_l8():
+    return meshgen.mesh_config("nested_shells_l8")
+
+
+def test_nested_shells_full_size_round0_keys(shells_l8):
+    V, F, _ = shells_l8
+    K, E = _ctx_round0(V, F)
+    T = oracle.edge_table(V, F)
+    assert (E == T["ab"]).all()
+    assert (K == T["key"]).all()
+
+
+def test_nested_shells_full_size_run_properties(shells_l8):
+    """2,621,440 faces -> 0.1 %: two closed manifold shells that nearly touch;
+    the output must stay manifold, keep both components and be free of
+    self-intersections, checked by the GPU and by the oracle's exact scan."""
+    V, F, target = shells_l8
+    Vo, Fo, stats, status = pamo.pamo_simplify(torch.from_numpy(V), torch.from_numpy(F),
+                                               target, validate_input=0)
+    Vo, Fo = Vo.cpu().numpy(), Fo.cpu().numpy()
+    assert status in ("PAMO_OK", "PAMO_ESTALL")
+    if status == "PAMO_OK":
+        assert len(Fo) <= target
+    assert stats["undone"] > 0
+    assert is_closed_manifold(Fo, len(Vo))
+    assert euler(Fo, len(Vo)) == 4 and components(Fo, len(Vo)) == 2
+    gn, _ = pamo.pamo_check_self_intersections(torch.from_numpy(Vo), torch.from_numpy(Fo))
+    assert gn == 0
+    _, n = oracle.self_intersections(Vo, Fo)
+    assert n == 0
