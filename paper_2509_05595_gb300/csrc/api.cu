@@ -22,54 +22,17 @@ void set_error(const std::string& msg) { g_err = msg; }
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
-static cudaEvent_t pool_event(pamo_ctx* c) {
-  if (!c->ev_pool.empty()) {
-    cudaEvent_t e = c->ev_pool.back();
-    c->ev_pool.pop_back();
-    return e;
-  }
-  cudaEvent_t e = nullptr;
-  cudaEventCreate(&e);
-  return e;
-}
-
-void kc_begin(pamo_ctx* c, int cls) {
-  c->kc_launch0[cls] = launch_count();
-  if (c->opt.profile & (1 << cls)) {
-    cudaEvent_t e = pool_event(c);
-    cudaEventRecord(e, c->st);
-    c->kc_open[cls] = e;
-  }
-}
-
-void kc_end(pamo_ctx* c, int cls, double bytes) {
-  c->class_launches[cls] += launch_count() - c->kc_launch0[cls];
-  c->class_bytes[cls] += bytes;
-  c->bytes_model += bytes;
-  if ((c->opt.profile & (1 << cls)) && c->kc_open[cls]) {
-    cudaEvent_t e = pool_event(c);
-    cudaEventRecord(e, c->st);
-    c->kc_pending.push_back({cls, {c->kc_open[cls], e}});
-    c->kc_open[cls] = nullptr;
-  }
-}
-
-// call after the stream has been synchronised
-void kc_resolve(pamo_ctx* c) {
-  for (auto& p : c->kc_pending) {
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, p.second.first, p.second.second) == cudaSuccess)
-      c->class_ms[p.first] += ms;
-    c->ev_pool.push_back(p.second.first);
-    c->ev_pool.push_back(p.second.second);
-  }
-  c->kc_pending.clear();
-}
-
 pamo_status cuda_fail(cudaError_t e, const char* what) {
   g_err = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
   if (e == cudaErrorMemoryAllocation) return PAMO_ENOMEM;
   return PAMO_ECUDA;
+}
+
+int default_grid() {
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return 4 * (sms > 0 ? sms : 152);
 }
 
 pamo_status buf_reserve(Buf& b, size_t bytes, cudaStream_t st) {
@@ -114,8 +77,28 @@ void release(T*& p, cudaStream_t st) {
   p = nullptr;
 }
 
+void free_graphs(pamo_ctx* c) {
+  for (int g = 0; g < 2; g++)
+    if (c->gA[g]) {
+      cudaGraphExecDestroy(c->gA[g]);
+      c->gA[g] = nullptr;
+    }
+  if (c->gB) {
+    cudaGraphExecDestroy(c->gB);
+    c->gB = nullptr;
+  }
+  for (auto& g : c->gev)
+    for (auto& k : g)
+      for (auto& e : k)
+        if (e) {
+          cudaEventDestroy(e);
+          e = nullptr;
+        }
+}
+
 void free_ctx_buffers(pamo_ctx* c) {
   cudaStream_t st = c->st;
+  free_graphs(c);
   release(c->pos, st); release(c->pos_s, st);
   release(c->K, st); release(c->K_s, st);
   release(c->F, st); release(c->F_s, st);
@@ -129,7 +112,7 @@ void free_ctx_buffers(pamo_ctx* c) {
   release(c->E_prev, st); release(c->e_off_prev, st); release(c->cbits, st);
   release(c->cbits_prev, st); release(c->vbar_prev, st); release(c->link, st);
   release(c->link_prev, st); release(c->ivmap, st); release(c->vsurv, st); release(c->vdirty, st);
-  release(c->dlist, st);
+  release(c->dlist, st); release(c->scan_sums, st);
   for (int r = 0; r < 3; r++) release(c->cand[r], st);
   buf_free(c->scan_tmp, st);
   buf_free(c->quad_tmp, st);
@@ -143,6 +126,28 @@ void free_ctx_buffers(pamo_ctx* c) {
   c->kc_pending.clear();
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   c->ev_pool.clear();
+}
+
+// the context's stream waits for the caller's work so far
+pamo_status enter(pamo_ctx* c) {
+  PAMO_CUDA(cudaEventRecord(c->join_ev, c->ust));
+  PAMO_CUDA(cudaStreamWaitEvent(c->st, c->join_ev, 0));
+  return PAMO_OK;
+}
+
+// the caller's stream waits for the context's work so far
+pamo_status join(pamo_ctx* c) {
+  PAMO_CUDA(cudaEventRecord(c->join_ev, c->st));
+  PAMO_CUDA(cudaStreamWaitEvent(c->ust, c->join_ev, 0));
+  return PAMO_OK;
+}
+
+void destroy_ctx(pamo_ctx* c) {
+  free_ctx_buffers(c);
+  cudaStreamSynchronize(c->st);
+  if (c->join_ev) cudaEventDestroy(c->join_ev);
+  cudaStreamDestroy(c->st);
+  delete c;
 }
 
 pamo_status check_options(const pamo_options* o) {
@@ -177,16 +182,26 @@ pamo_status create(const float* d_V, int64_t nV, const int32_t* d_F, int64_t nF,
   else pamo_default_options(&o);
   PAMO_TRY(check_options(&o));
   pamo_ctx* c = new pamo_ctx();
-  c->st = st;
+  c->ust = st;
+  {
+    cudaError_t e = cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(c->join_ev, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->st, c->join_ev, 0);
+    if (e != cudaSuccess) {
+      if (c->join_ev) cudaEventDestroy(c->join_ev);
+      if (c->st) cudaStreamDestroy(c->st);
+      delete c;
+      return cuda_fail(e, "context stream");
+    }
+  }
+  st = c->st;
   c->opt = o;
   c->nV0 = c->nV = nV;
   c->nF0 = c->nF = nF;
   c->Emax = (3 * nF) / 2 + 2;
-  {
-    int dev = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess)
-      cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev);
-  }
+  c->grid = default_grid();
+  c->sm_count = c->grid / 4;
   const int64_t mx = std::max(nV, nF);
   pamo_status s = PAMO_OK;
 #define A(ptr, n) if (s == PAMO_OK) s = alloc(&c->ptr, (size_t)(n), st)
@@ -194,11 +209,13 @@ pamo_status create(const float* d_V, int64_t nV, const int32_t* d_F, int64_t nF,
   A(vf_off, nV + 1); A(vf_idx, 3 * nF); A(vcount, nV + 1);
   A(E, c->Emax); A(e_off, nV + 1); A(key, c->Emax); A(vbar, c->Emax); A(vkey, nV);
   A(win, c->Emax); A(wscan, c->Emax + 1); A(wlist, c->Emax); A(standing, c->Emax);
-  A(undo, c->Emax); A(ftag, nF); A(qlist, nF); A(fdead, nF); A(vdead, nV); A(vmap, nV + 1);
+  A(undo, c->Emax); A(ftag, nF); A(qlist, nF);
+  A(fdead, nF); A(vdead, nV); A(vmap, nV + 1);
   A(dbuf, mx + 1); A(alive_tmp, mx); A(flags, c->Emax); A(flags_next, c->Emax); A(dc, 1);
   A(E_prev, c->Emax); A(e_off_prev, nV + 1); A(cbits, c->Emax); A(cbits_prev, c->Emax);
   A(vbar_prev, c->Emax); A(link, c->Emax); A(link_prev, c->Emax); A(ivmap, nV);
   A(vsurv, nV); A(vdirty, nV); A(dlist, c->Emax);
+  A(scan_sums, scan_sums_count(std::max<int64_t>(c->Emax, mx + 1)));
   // candidate pairs of the split check: a changed face has at most 3
   // edge-neighbours; vertex-neighbours and other overlaps are bounded
   // generously, and an overflow falls back to the fused check
@@ -210,14 +227,18 @@ pamo_status create(const float* d_V, int64_t nV, const int32_t* d_F, int64_t nF,
   }
   A(cand[0], c->cand_cap[0]); A(cand[1], c->cand_cap[1]); A(cand[2], c->cand_cap[2]);
 #undef A
+  if (s == PAMO_OK) s = bvh_alloc(c->bvh, (int)nF, st);
   if (s == PAMO_OK) {
     cudaError_t e = cudaMallocHost((void**)&c->hc, sizeof(RoundCounters));
     if (e != cudaSuccess) s = cuda_fail(e, "cudaMallocHost");
   }
   if (s == PAMO_OK) s = load_mesh(d_V, nV, d_F, nF, c->pos, c->F, st);
   if (s == PAMO_OK) {
-    cudaError_t e = cudaMemsetAsync(c->dc, 0, sizeof(RoundCounters), st);
-    if (e != cudaSuccess) s = cuda_fail(e, "cudaMemsetAsync");
+    std::memset(c->hc, 0, sizeof(RoundCounters));
+    c->hc->nV = (int)nV;
+    c->hc->nF = (int)nF;
+    cudaError_t e = cudaMemcpyAsync(c->dc, c->hc, sizeof(RoundCounters), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) s = cuda_fail(e, "cudaMemcpyAsync");
   }
   if (s == PAMO_OK && o.validate_input) s = validate_mesh(c);
   if (s == PAMO_OK && !o.validate_input) s = build_vertex_faces(c);
@@ -230,160 +251,316 @@ pamo_status create(const float* d_V, int64_t nV, const int32_t* d_F, int64_t nF,
     s = init_quadrics(c);
   }
   if (s != PAMO_OK) {
-    free_ctx_buffers(c);
-    cudaStreamSynchronize(st);
-    delete c;
+    destroy_ctx(c);
     return s;
   }
   *out = c;
   return PAMO_OK;
 }
 
-pamo_status sync_counters(pamo_ctx* c) {
+// ---- kernel-class accounting ------------------------------------------------
+// Graph slots: 0 = round graph with a sorted BVH build, 1 = round graph with
+// the carried leaf order, 2 = re-check graph.
+thread_local int g_capture_slot = -1;  // slot being captured by this thread (-1 = eager)
+
+}  // namespace
+
+static cudaEvent_t pool_event(pamo_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void kc_begin(pamo_ctx* c, int cls) {
+  c->kc_launch0[cls] = launch_count();
+  if (!(c->opt.profile & (1 << cls))) return;
+  if (g_capture_slot >= 0) {
+    cudaEvent_t& e = c->gev[g_capture_slot][cls][0];
+    if (!e) cudaEventCreate(&e);
+    cudaEventRecordWithFlags(e, c->st, cudaEventRecordExternal);
+  } else {
+    cudaEvent_t e = pool_event(c);
+    cudaEventRecord(e, c->st);
+    c->kc_open[cls] = e;
+  }
+}
+
+void kc_end(pamo_ctx* c, int cls, double bytes) {
+  const long long n = launch_count() - c->kc_launch0[cls];
+  if (g_capture_slot >= 0) {
+    long long* t = g_capture_slot < 2 ? c->gA_launch[g_capture_slot] : c->gB_launch;
+    t[cls] += n;
+  } else {
+    c->class_launches[cls] += n;
+  }
+  c->class_bytes[cls] += bytes;
+  c->bytes_model += bytes;
+  if (!(c->opt.profile & (1 << cls))) return;
+  if (g_capture_slot >= 0) {
+    cudaEvent_t& e = c->gev[g_capture_slot][cls][1];
+    if (!e) cudaEventCreate(&e);
+    cudaEventRecordWithFlags(e, c->st, cudaEventRecordExternal);
+  } else if (c->kc_open[cls]) {
+    cudaEvent_t e = pool_event(c);
+    cudaEventRecord(e, c->st);
+    c->kc_pending.push_back({cls, {c->kc_open[cls], e}});
+    c->kc_open[cls] = nullptr;
+  }
+}
+
+// call after the stream has been synchronised
+void kc_resolve(pamo_ctx* c) {
+  for (auto& p : c->kc_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.second.first, p.second.second) == cudaSuccess)
+      c->class_ms[p.first] += ms;
+    c->ev_pool.push_back(p.second.first);
+    c->ev_pool.push_back(p.second.second);
+  }
+  c->kc_pending.clear();
+}
+
+namespace {
+
+// after a replay of graph slot g (stream synchronised)
+void graph_resolve(pamo_ctx* c, int g) {
+  const long long* t = g < 2 ? c->gA_launch[g] : c->gB_launch;
+  for (int cls = 0; cls < 8; cls++) {
+    c->class_launches[cls] += t[cls];
+    cudaEvent_t a = c->gev[g][cls][0], b = c->gev[g][cls][1];
+    if (a && b) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, a, b) == cudaSuccess) c->class_ms[cls] += ms;
+    }
+  }
+}
+
+pamo_status sync_out(pamo_ctx* c) {
   PAMO_CUDA(cudaMemcpyAsync(c->hc, c->dc, sizeof(RoundCounters), cudaMemcpyDeviceToHost, c->st));
+  return PAMO_OK;
+}
+
+pamo_status sync_now(pamo_ctx* c) {
+  PAMO_TRY(sync_out(c));
   PAMO_CUDA(cudaStreamSynchronize(c->st));
   return PAMO_OK;
 }
 
-pamo_status round_cost(pamo_ctx* c) {
-  if (c->stage != 0) {
-    set_error("pamo_round_cost: previous round not committed");
-    return PAMO_EINVAL;
-  }
+// ---- the phases of a round (device sizes; capturable) ---------------------
+pamo_status phase_begin(pamo_ctx* c) {
   cudaStream_t st = c->st;
-  const double nV = (double)c->nV, nF = (double)c->nF, nE = 1.5 * nF;
+  RoundCounters* dc = c->dc;
+  const int G = c->grid;
   kc_begin(c, PAMO_KC_ADJACENCY);
+  PAMO_CUDA(cudaMemsetAsync((char*)dc + PAMO_ROUND_ZERO_OFFSET, 0,
+                            sizeof(RoundCounters) - PAMO_ROUND_ZERO_OFFSET, st));
   // last round's edges and their costs become the reuse source
-  std::swap(c->E, c->E_prev);
-  std::swap(c->e_off, c->e_off_prev);
-  std::swap(c->cbits, c->cbits_prev);
-  std::swap(c->vbar, c->vbar_prev);
-  std::swap(c->link, c->link_prev);
-  if (c->rounds > 0) PAMO_TRY(build_vertex_faces(c));
+  PAMO_TRY(copy_dev(c->E_prev, c->E, &dc->nE, 0, sizeof(int2), G, st));
+  PAMO_TRY(copy_dev(c->e_off_prev, c->e_off, &dc->nV_edges, 1, sizeof(int32_t), G, st));
+  PAMO_TRY(copy_dev(c->cbits_prev, c->cbits, &dc->nE, 0, sizeof(uint32_t), G, st));
+  PAMO_TRY(copy_dev(c->vbar_prev, c->vbar, &dc->nE, 0, sizeof(float4), G, st));
+  PAMO_TRY(copy_dev(c->link_prev, c->link, &dc->nE, 0, 1, G, st));
+  PAMO_TRY(build_vertex_faces(c));
   PAMO_TRY(build_edges(c));
-  // F read; CSR written and read back; edges and offsets written
-  kc_end(c, PAMO_KC_ADJACENCY, 16 * nF + 2 * (4 * nV + 12 * nF) + 8 * nE + 4 * nV);
-  PAMO_CUDA(cudaMemsetAsync(c->dc, 0, sizeof(RoundCounters), st));
-  if (!c->h_flags.empty()) {
-    PAMO_CUDA(cudaMemcpyAsync(c->flags, c->h_flags.data(),
-                              sizeof(unsigned long long) * c->h_flags.size(),
-                              cudaMemcpyHostToDevice, st));
-    c->h_flags.clear();
-  }
+  const double nV = (double)c->nV, nF = (double)c->nF, nE = 1.5 * nF;
+  // previous edge data copied; F read; CSR written and read back; edges written
+  kc_end(c, PAMO_KC_ADJACENCY, 2 * nE * 29 + 16 * nF + 2 * (4 * nV + 12 * nF) + 8 * nE + 4 * nV);
+  return PAMO_OK;
+}
+
+pamo_status phase_cost(pamo_ctx* c) {
+  const double nV = (double)c->nV, nF = (double)c->nF, nE = 1.5 * nF;
   kc_begin(c, PAMO_KC_COST);
   PAMO_TRY(edge_costs(c));
   // E, positions, quadrics, CSR and faces read once; keys and placements written
   kc_end(c, PAMO_KC_COST, nE * (8 + 8 + 16) + nV * (16 + 80 + 4) + nF * (16 + 12));
-  c->stage = 1;
   return PAMO_OK;
 }
 
-pamo_status round_select(pamo_ctx* c) {
-  if (c->stage != 1) {
-    set_error("pamo_round_select: call pamo_round_cost first");
-    return PAMO_EINVAL;
-  }
-  const double nV = (double)c->nV, nF = (double)c->nF, nE = (double)c->nE;
+pamo_status phase_select(pamo_ctx* c) {
+  const double nV = (double)c->nV, nF = (double)c->nF, nE = 1.5 * nF;
   kc_begin(c, PAMO_KC_SELECT);
   PAMO_TRY(select_winners(c));
   // edges+keys read twice, vkey written and read, CSR+faces read, flags scanned
-  kc_end(c, PAMO_KC_SELECT, nE * (2 * 16 + 1 + 1 + 4 + 1 + 4) + nV * (8 + 8 + 4) + nF * (16 + 12) +
-                                4.0 * c->nW);
-  c->stage = 2;
+  kc_end(c, PAMO_KC_SELECT, nE * (2 * 16 + 1 + 1 + 4 + 1 + 4) + nV * (8 + 8 + 4) + nF * (16 + 12));
   return PAMO_OK;
 }
 
-pamo_status round_collapse(pamo_ctx* c) {
-  if (c->stage != 2) {
-    set_error("pamo_round_collapse: call pamo_round_select first");
-    return PAMO_EINVAL;
-  }
+pamo_status phase_collapse(pamo_ctx* c) {
   const double nV = (double)c->nV, nF = (double)c->nF;
   kc_begin(c, PAMO_KC_COLLAPSE);
   PAMO_TRY(collapse_winners(c));
   // M_1 -> M_s copy, flag resets, and each winner's region (~12 faces)
-  kc_end(c, PAMO_KC_COLLAPSE, 2 * (16 * nV + 80 * nV + 16 * nF) + nF * 5 + nV +
-                                  (double)c->nW * (12 * (16 + 4 + 16) + 2 * 96));
-  c->stage = 3;
+  kc_end(c, PAMO_KC_COLLAPSE, 2 * (16 * nV + 80 * nV + 16 * nF) + nF * 5 + nV);
   return PAMO_OK;
 }
 
-pamo_status round_check_undo(pamo_ctx* c) {
-  if (c->stage != 3) {
-    set_error("pamo_round_check_undo: call pamo_round_collapse first");
-    return PAMO_EINVAL;
-  }
-  cudaStream_t st = c->st;
-  c->undo_iters = 0;
-  int64_t pairs_total = 0;
-  if (c->nW > 0 && c->opt.check_mode != 3) {
-    const double nF = (double)c->nF, nV = (double)c->nV;
-    // leaf keys, 4 sort passes (read+write 8 B/face, histogram), tree, refit
-    const double b_build = nF * (16 + 9) + nV * 16 + 4 * nF * (8 + 8 + 4) + nF * (4 + 32 + 8) +
-                           nF * (16 + 4 + 64 + 1);
-    const double b_refit = nF * (16 + 4 + 64 + 1 + 4) + nV * 16;
-    // node boxes, faces, positions, per-face info / tags / liveness read once
-    const double b_query = nF * (64 + 16 + 1 + 4 + 1) + nV * 16;
-    kc_begin(c, PAMO_KC_BVH);
-    PAMO_TRY(bvh_build(c->bvh, c->pos_s, c->F_s, c->fdead, (int)c->nF, c->bb_lo, c->bb_hi, st));
-    kc_end(c, PAMO_KC_BVH, b_build);
-    const int all = c->opt.check_mode == 1;
-    // every iteration undoes at least one collapse, so nW + 1 iterations bound it
-    for (int64_t it = 0; it <= c->nW; it++) {
-      PAMO_CUDA(cudaMemsetAsync(&c->dc->n_pairs, 0, 2 * sizeof(int), st));  // n_pairs, n_undo
-      kc_begin(c, PAMO_KC_QUERY);
-      PAMO_TRY(bvh_check_split(c->bvh, c->pos_s, c->F_s, c->fdead, c->ftag, all, c->qlist,
-                               &c->dc->n_query, c->undo, c->dc, c->cand, c->cand_cap,
-                               c->dc->ncand, c->sm_count * 8, st));
-      kc_end(c, PAMO_KC_QUERY, b_query);
-      kc_begin(c, PAMO_KC_COLLAPSE);
-      PAMO_TRY(undo_marked(c));  // skipped on the device if a bucket overflowed
-      kc_end(c, PAMO_KC_COLLAPSE, (double)c->nW * 2);
-      PAMO_TRY(sync_counters(c));
-      if (c->hc->cand_overflow) {
-        // candidate buffers too small this time: the fused check finds every
-        // pair of the same mesh state, then the undo runs
-        PAMO_CUDA(cudaMemsetAsync(&c->dc->n_pairs, 0, 2 * sizeof(int), st));
-        PAMO_CUDA(cudaMemsetAsync(&c->dc->cand_overflow, 0, sizeof(int), st));
-        PAMO_TRY(bvh_check(c->bvh, c->pos_s, c->F_s, c->fdead, c->ftag, all, c->qlist,
-                           &c->dc->n_query, c->nF, c->undo, c->dc, nullptr, 0, st));
-        PAMO_TRY(undo_marked(c));
-        PAMO_TRY(sync_counters(c));
-      }
-      if (c->hc->overflow) {
-        set_error("BVH traversal stack overflow");
-        return PAMO_EINTERNAL;
-      }
-      pairs_total += c->hc->n_pairs;
-      if (c->hc->n_undo == 0) break;  // clean (or pairs not caused by this round)
-      c->undo_iters++;
-      kc_begin(c, PAMO_KC_BVH);
-      PAMO_TRY(bvh_refit(c->bvh, c->pos_s, c->F_s, c->fdead, st));
-      kc_end(c, PAMO_KC_BVH, b_refit);
-    }
-  }
-  c->stage = 4;
-  c->last_pairs = pairs_total;
+double bvh_build_bytes(double nF, double nV) {
+  // leaf keys, 4 sort passes (read+write 8 B/face, histogram), tree, refit
+  return nF * (16 + 9) + nV * 16 + 4 * nF * (8 + 8 + 4) + nF * (4 + 32 + 8) + nF * (16 + 4 + 64 + 1);
+}
+double bvh_refit_bytes(double nF, double nV) { return nF * (16 + 4 + 64 + 1 + 4) + nV * 16; }
+double query_bytes(double nF, double nV) { return nF * (64 + 16 + 1 + 4 + 1) + nV * 16; }
+
+pamo_status phase_bvh(pamo_ctx* c, bool carry) {
+  kc_begin(c, PAMO_KC_BVH);
+  PAMO_TRY(bvh_build(c->bvh, c->pos_s, c->F_s, c->fdead, &c->dc->nF, 0, c->bb_lo, c->bb_hi, carry,
+                     c->grid, c->st));
+  kc_end(c, PAMO_KC_BVH, carry ? bvh_refit_bytes(c->nF, c->nV) : bvh_build_bytes(c->nF, c->nV));
   return PAMO_OK;
 }
 
-pamo_status round_commit(pamo_ctx* c) {
-  if (c->stage != 4 && !(c->stage == 3 && c->opt.check_mode == 3)) {
-    set_error("pamo_round_commit: call pamo_round_check_undo first");
-    return PAMO_EINVAL;
-  }
+pamo_status phase_refit(pamo_ctx* c) {
+  kc_begin(c, PAMO_KC_BVH);
+  PAMO_TRY(bvh_refit(c->bvh, c->pos_s, c->F_s, c->fdead, &c->dc->nF, 0, c->grid, c->st));
+  kc_end(c, PAMO_KC_BVH, bvh_refit_bytes(c->nF, c->nV));
+  return PAMO_OK;
+}
+
+// one check iteration: split check, undo of the marked collapses, outcome
+pamo_status phase_check(pamo_ctx* c) {
   cudaStream_t st = c->st;
-  const int64_t nV_in = c->nV, nF_in = c->nF, nE_in = c->nE, nW = c->nW;
-  const int64_t nflags_in = c->nflags;
-  // per-round record (before the edge list is rebuilt)
+  RoundCounters* dc = c->dc;
+  if (c->opt.check_mode == 3) return check_result(c);  // debug: no check
+  kc_begin(c, PAMO_KC_QUERY);
+  PAMO_CUDA(cudaMemsetAsync(&dc->n_pairs, 0, 2 * sizeof(int), st));  // n_pairs, n_undo
+  PAMO_TRY(bvh_check_split(c->bvh, c->pos_s, c->F_s, c->fdead, c->ftag, c->opt.check_mode == 1,
+                           c->qlist, &dc->n_query, c->undo, dc, c->cand, c->cand_cap, dc->ncand,
+                           &dc->nF, c->grid, st));
+  kc_end(c, PAMO_KC_QUERY, query_bytes(c->nF, c->nV));
+  kc_begin(c, 7);
+  PAMO_TRY(undo_marked(c));  // skipped on the device if a bucket overflowed
+  PAMO_TRY(check_result(c));
+  kc_end(c, 7, 0.0);
+  return PAMO_OK;
+}
+
+pamo_status phase_commit(pamo_ctx* c) {
+  RoundCounters* dc = c->dc;
+  kc_begin(c, PAMO_KC_COMMIT);
+  PAMO_TRY(commit_compact(c));
+  if (c->opt.check_mode != 3)
+    PAMO_TRY(bvh_compact_order(c->bvh, c->fdead, c->dbuf, &dc->goF, &dc->goFn, c->grid, c->st));
+  PAMO_TRY(commit_sizes(c));
+  // M_s read (positions, quadrics, faces, liveness), M_1 written, vertex map
+  kc_end(c, PAMO_KC_COMMIT, (double)c->nV * (16 + 80 + 1 + 4) * 2 + (double)c->nF * (16 + 1 + 4) * 2);
+  return PAMO_OK;
+}
+
+// eager fallback after a candidate overflow: the fused check on the same
+// mesh state, undo, outcome, gated commit
+pamo_status fallback_check(pamo_ctx* c) {
+  cudaStream_t st = c->st;
+  RoundCounters* dc = c->dc;
+  PAMO_CUDA(cudaMemsetAsync(&dc->n_pairs, 0, 2 * sizeof(int), st));
+  PAMO_CUDA(cudaMemsetAsync(&dc->cand_overflow, 0, sizeof(int), st));
+  kc_begin(c, PAMO_KC_QUERY);
+  PAMO_TRY(bvh_check(c->bvh, c->pos_s, c->F_s, c->fdead, c->ftag, c->opt.check_mode == 1, c->qlist,
+                     &dc->n_query, c->nF, c->undo, dc, nullptr, 0, (int)c->nF, st));
+  kc_end(c, PAMO_KC_QUERY, query_bytes(c->nF, c->nV));
+  kc_begin(c, 7);
+  PAMO_TRY(undo_marked(c));
+  PAMO_TRY(check_result(c));
+  kc_end(c, 7, 0.0);
+  return PAMO_OK;
+}
+
+// ---- graphs -----------------------------------------------------------------
+template <typename Fn>
+pamo_status capture(pamo_ctx* c, int slot, cudaGraphExec_t* exec, Fn fn) {
+  cudaGraph_t graph = nullptr;
+  PAMO_CUDA(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+  g_capture_slot = slot;
+  const double bytes0 = c->bytes_model;
+  double cb0[8];
+  for (int i = 0; i < 8; i++) cb0[i] = c->class_bytes[i];
+  pamo_status s = fn();
+  g_capture_slot = -1;
+  // bytes are counted per replay, not per capture
+  c->bytes_model = bytes0;
+  for (int i = 0; i < 8; i++) c->class_bytes[i] = cb0[i];
+  cudaError_t e = cudaStreamEndCapture(c->st, &graph);
+  if (s != PAMO_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  return PAMO_OK;
+}
+
+pamo_status round_body(pamo_ctx* c, bool carry) {
+  PAMO_TRY(phase_begin(c));
+  PAMO_TRY(phase_cost(c));
+  PAMO_TRY(phase_select(c));
+  PAMO_TRY(phase_collapse(c));
+  if (c->opt.check_mode != 3) PAMO_TRY(phase_bvh(c, carry));
+  PAMO_TRY(phase_check(c));
+  PAMO_TRY(phase_commit(c));
+  return sync_out(c);
+}
+
+pamo_status recheck_body(pamo_ctx* c) {
+  PAMO_TRY(phase_refit(c));
+  PAMO_TRY(phase_check(c));
+  PAMO_TRY(phase_commit(c));
+  return sync_out(c);
+}
+
+// bytes of one replay, from the sizes at the start of the round
+void account_bytes(pamo_ctx* c, int slot) {
+  const double nV = (double)c->nV, nF = (double)c->nF, nE = 1.5 * nF;
+  auto add = [c](int cls, double b) {
+    c->class_bytes[cls] += b;
+    c->bytes_model += b;
+  };
+  if (slot < 2) {
+    add(PAMO_KC_ADJACENCY, 2 * nE * 29 + 16 * nF + 2 * (4 * nV + 12 * nF) + 8 * nE + 4 * nV);
+    add(PAMO_KC_COST, nE * (8 + 8 + 16) + nV * (16 + 80 + 4) + nF * (16 + 12));
+    add(PAMO_KC_SELECT, nE * (2 * 16 + 1 + 1 + 4 + 1 + 4) + nV * (8 + 8 + 4) + nF * (16 + 12));
+    add(PAMO_KC_COLLAPSE, 2 * (16 * nV + 80 * nV + 16 * nF) + nF * 5 + nV);
+    if (c->opt.check_mode != 3)
+      add(PAMO_KC_BVH, slot == 1 ? bvh_refit_bytes(nF, nV) : bvh_build_bytes(nF, nV));
+  } else {
+    add(PAMO_KC_BVH, bvh_refit_bytes(nF, nV));
+  }
+  if (c->opt.check_mode != 3) add(PAMO_KC_QUERY, query_bytes(nF, nV));
+  add(PAMO_KC_COMMIT, nV * (16 + 80 + 1 + 4) * 2 + nF * (16 + 1 + 4) * 2);
+}
+
+pamo_status check_device_errors(pamo_ctx* c) {
+  if (c->hc->bad & 64) {
+    set_error("edge count is not 3F/2: the mesh is not a closed oriented manifold");
+    return PAMO_ENOTMANIFOLD;
+  }
+  if (c->hc->overflow) {
+    set_error("BVH traversal or refit bound exceeded");
+    return PAMO_EINTERNAL;
+  }
+  return PAMO_OK;
+}
+
+// host bookkeeping once a round is committed (hc holds the device state)
+pamo_status finish_round(pamo_ctx* c) {
+  cudaStream_t st = c->st;
+  const RoundCounters& h = *c->hc;
+  const int64_t nV_in = c->nV, nF_in = c->nF, nE_in = h.nE, nW = h.nW;
+  const int64_t nflags_in = c->nflags, committed = h.committed, nund = h.nund;
   RoundRecord rec;
   if (c->opt.record_rounds && nW > 0) {
     std::vector<int32_t> wl(nW);
     std::vector<uint8_t> stand(nW);
-    std::vector<int2> Eh(c->nE);
+    std::vector<int2> Eh(nE_in);
     PAMO_CUDA(cudaMemcpyAsync(wl.data(), c->wlist, sizeof(int32_t) * nW, cudaMemcpyDeviceToHost, st));
     PAMO_CUDA(cudaMemcpyAsync(stand.data(), c->standing, nW, cudaMemcpyDeviceToHost, st));
-    PAMO_CUDA(cudaMemcpyAsync(Eh.data(), c->E, sizeof(int2) * c->nE, cudaMemcpyDeviceToHost, st));
+    PAMO_CUDA(cudaMemcpyAsync(Eh.data(), c->E, sizeof(int2) * nE_in, cudaMemcpyDeviceToHost, st));
     PAMO_CUDA(cudaStreamSynchronize(st));
     for (int64_t w = 0; w < nW; w++) {
       int2 e = Eh[wl[w]];
@@ -394,30 +571,11 @@ pamo_status round_commit(pamo_ctx* c) {
       dst.push_back(e.y);
     }
   }
-  int64_t nund = 0;
-  kc_begin(c, PAMO_KC_COMMIT);
-  PAMO_TRY(commit_compact(c, &nund));
-  // M_s read (positions, quadrics, faces, liveness), M_1 written, vertex map
-  // keep the BVH leaf order for the compacted faces (only valid if this
-  // round's check built the tree over these nF_in faces)
-  if (c->bvh.order_ok && c->bvh.n == nF_in)
-    PAMO_TRY(bvh_compact_order(c->bvh, c->fdead, c->dbuf, (int)(nF_in - 2 * (nW - nund)),
-                               c->scan_tmp, st));
-  else
-    c->bvh.order_ok = false;
-  kc_end(c, PAMO_KC_COMMIT, (double)nV_in * (16 + 80 + 1 + 4) * 2 + (double)nF_in * (16 + 1 + 4) * 2);
-  PAMO_TRY(sync_counters(c));
-  kc_resolve(c);
-  // float64 operations of the edge costs evaluated this round
-  c->class_flops[PAMO_KC_COST] += 114.0 * c->hc->n_dirty + 32.0 * (double)c->hc->cost_tris;
-  const int64_t committed = nW - nund;
-  c->nV = nV_in - committed;
-  c->nF = nF_in - 2 * committed;
-  // invalid-edge flags for the next round (Sec. 5.3)
+  // invalid-edge flags for the next round (Sec. 5.3): after a commit the
+  // device already holds the undone edges; otherwise merge on the host
   if (committed > 0) {
     c->hold = 0;
     c->zero_streak = 0;
-    std::swap(c->flags, c->flags_next);
     c->nflags = nund;
   } else {
     c->hold++;
@@ -437,27 +595,163 @@ pamo_status round_commit(pamo_ctx* c) {
       c->hold = 0;
     }
     c->nflags = (int64_t)m.size();
-    c->h_flags = m;
+    const int nf = (int)m.size();
+    if (nf)
+      PAMO_CUDA(cudaMemcpyAsync(c->flags, m.data(), sizeof(unsigned long long) * nf,
+                                cudaMemcpyHostToDevice, st));
+    PAMO_CUDA(cudaMemcpyAsync(&c->dc->nflags, &nf, sizeof(int), cudaMemcpyHostToDevice, st));
+    PAMO_CUDA(cudaStreamSynchronize(st));
   }
-  const int64_t eligible = (int64_t)c->hc->eligible;
-  const int64_t info[11] = {nV_in, nF_in, nE_in, (int64_t)c->hc->link_rejects,
-                            (int64_t)c->hc->flagged, eligible, nW, committed, nund,
-                            c->undo_iters, c->last_pairs};
+  const int64_t eligible = (int64_t)h.eligible;
+  const int64_t info[11] = {nV_in, nF_in, nE_in, (int64_t)h.link_rejects, (int64_t)h.flagged,
+                            eligible, nW, committed, nund, h.undo_iters, h.pairs_total};
   if (c->opt.record_rounds) {
     std::memcpy(rec.info, info, sizeof(info));
     c->rec.push_back(std::move(rec));
   }
+  c->class_flops[PAMO_KC_COST] += 114.0 * h.n_dirty + 32.0 * (double)h.cost_tris;
   c->committed_total += committed;
   c->undone_total += nund;
   c->link_total += info[3];
   c->win_total += nW;
-  c->undo_hist[std::min(c->undo_iters, 7)]++;
+  c->undo_hist[std::min(h.undo_iters, 7)]++;
+  c->undo_iters = h.undo_iters;
+  c->last_pairs = h.pairs_total;
   c->rounds++;
-  c->have_prev = true;
+  c->nW = nW;
+  c->nE = nE_in;
+  c->nV = h.nV;
+  c->nF = h.nF;
   c->stage = 0;
   const bool stall_empty = (eligible == 0 && nflags_in == 0);
   if (stall_empty || c->zero_streak >= c->opt.stall_limit) c->stalled = true;
   return PAMO_OK;
+}
+
+bool use_carry(pamo_ctx* c) {
+  return c->bvh.order_ok && 2 * c->nF > c->bvh.n_sorted && c->opt.check_mode != 3;
+}
+
+void note_build(pamo_ctx* c, bool carry) {
+  if (!carry && c->opt.check_mode != 3) {
+    c->bvh.order_ok = true;
+    c->bvh.n_sorted = (int)c->nF;
+  }
+}
+
+// one round of Algorithm 1 through the captured graphs: one synchronisation
+// unless the check found intersections (then one per undo iteration)
+pamo_status graph_round(pamo_ctx* c) {
+  cudaStream_t st = c->st;
+  const bool carry = use_carry(c);
+  const int slot = carry ? 1 : 0;
+  if (!c->gA[slot]) PAMO_TRY(capture(c, slot, &c->gA[slot], [&] { return round_body(c, carry); }));
+  note_build(c, carry);
+  PAMO_CUDA(cudaGraphLaunch(c->gA[slot], st));
+  PAMO_CUDA(cudaStreamSynchronize(st));
+  account_bytes(c, slot);
+  graph_resolve(c, slot);
+  PAMO_TRY(check_device_errors(c));
+  for (int64_t it = 0; !c->hc->clean; it++) {
+    if (it > c->hc->nW + 2) {
+      set_error("undo loop did not settle");
+      return PAMO_EINTERNAL;
+    }
+    if (c->hc->cand_overflow) {
+      PAMO_TRY(fallback_check(c));
+      PAMO_TRY(phase_commit(c));
+      PAMO_TRY(sync_now(c));
+      kc_resolve(c);
+    } else {
+      if (!c->gB) PAMO_TRY(capture(c, 2, &c->gB, [&] { return recheck_body(c); }));
+      PAMO_CUDA(cudaGraphLaunch(c->gB, st));
+      PAMO_CUDA(cudaStreamSynchronize(st));
+      account_bytes(c, 2);
+      graph_resolve(c, 2);
+    }
+    PAMO_TRY(check_device_errors(c));
+  }
+  return finish_round(c);
+}
+
+// ---- eager per-round steps (the pamo_round_* entry points) ----------------
+pamo_status round_cost(pamo_ctx* c) {
+  if (c->stage != 0) {
+    set_error("pamo_round_cost: previous round not committed");
+    return PAMO_EINVAL;
+  }
+  PAMO_TRY(phase_begin(c));
+  PAMO_TRY(phase_cost(c));
+  PAMO_TRY(sync_now(c));
+  kc_resolve(c);
+  PAMO_TRY(check_device_errors(c));
+  c->nE = c->hc->nE;
+  c->stage = 1;
+  return PAMO_OK;
+}
+
+pamo_status round_select(pamo_ctx* c) {
+  if (c->stage != 1) {
+    set_error("pamo_round_select: call pamo_round_cost first");
+    return PAMO_EINVAL;
+  }
+  PAMO_TRY(phase_select(c));
+  PAMO_TRY(sync_now(c));
+  kc_resolve(c);
+  c->nW = c->hc->nW;
+  c->stage = 2;
+  return PAMO_OK;
+}
+
+pamo_status round_collapse(pamo_ctx* c) {
+  if (c->stage != 2) {
+    set_error("pamo_round_collapse: call pamo_round_select first");
+    return PAMO_EINVAL;
+  }
+  PAMO_TRY(phase_collapse(c));
+  c->stage = 3;
+  return PAMO_OK;
+}
+
+pamo_status round_check_undo(pamo_ctx* c) {
+  if (c->stage != 3) {
+    set_error("pamo_round_check_undo: call pamo_round_collapse first");
+    return PAMO_EINVAL;
+  }
+  const bool carry = use_carry(c);
+  if (c->opt.check_mode != 3) PAMO_TRY(phase_bvh(c, carry));
+  note_build(c, carry);
+  for (int64_t it = 0;; it++) {
+    if (it > c->nW + 2) {
+      set_error("undo loop did not settle");
+      return PAMO_EINTERNAL;
+    }
+    PAMO_TRY(phase_check(c));
+    PAMO_TRY(sync_now(c));
+    if (c->hc->cand_overflow) {
+      PAMO_TRY(fallback_check(c));
+      PAMO_TRY(sync_now(c));
+    }
+    kc_resolve(c);
+    PAMO_TRY(check_device_errors(c));
+    if (c->hc->clean) break;
+    PAMO_TRY(phase_refit(c));
+  }
+  c->undo_iters = c->hc->undo_iters;
+  c->last_pairs = c->hc->pairs_total;
+  c->stage = 4;
+  return PAMO_OK;
+}
+
+pamo_status round_commit(pamo_ctx* c) {
+  if (c->stage != 4) {
+    set_error("pamo_round_commit: call pamo_round_check_undo first");
+    return PAMO_EINVAL;
+  }
+  PAMO_TRY(phase_commit(c));
+  PAMO_TRY(sync_now(c));
+  kc_resolve(c);
+  return finish_round(c);
 }
 
 pamo_status run(pamo_ctx* c, int64_t target) {
@@ -466,11 +760,11 @@ pamo_status run(pamo_ctx* c, int64_t target) {
       c->status = PAMO_ESTALL;
       break;
     }
-    PAMO_TRY(round_cost(c));
-    PAMO_TRY(round_select(c));
-    PAMO_TRY(round_collapse(c));
-    PAMO_TRY(round_check_undo(c));
-    PAMO_TRY(round_commit(c));
+    if (c->stage != 0) {
+      set_error("a round is in progress (per-round entry points)");
+      return PAMO_EINVAL;
+    }
+    PAMO_TRY(graph_round(c));
     if (c->stalled) {
       if (c->nF > target) c->status = PAMO_ESTALL;
       break;
@@ -540,31 +834,43 @@ pamo_status pamo_ctx_create(const float* d_V, int64_t nV, const int32_t* d_F, in
 
 pamo_status pamo_round_cost(pamo_ctx* c) {
   CTX_GUARD(c);
-  return round_cost(c);
+  PAMO_TRY(enter(c));
+  pamo_status s = round_cost(c);
+  join(c);
+  return s;
 }
 
 pamo_status pamo_round_select(pamo_ctx* c, int64_t* n_winners) {
   CTX_GUARD(c);
+  PAMO_TRY(enter(c));
   pamo_status s = round_select(c);
+  join(c);
   if (s == PAMO_OK && n_winners) *n_winners = c->nW;
   return s;
 }
 
 pamo_status pamo_round_collapse(pamo_ctx* c) {
   CTX_GUARD(c);
-  return round_collapse(c);
+  PAMO_TRY(enter(c));
+  pamo_status s = round_collapse(c);
+  join(c);
+  return s;
 }
 
 pamo_status pamo_round_check_undo(pamo_ctx* c, int32_t* undo_iters) {
   CTX_GUARD(c);
+  PAMO_TRY(enter(c));
   pamo_status s = round_check_undo(c);
+  join(c);
   if (s == PAMO_OK && undo_iters) *undo_iters = c->undo_iters;
   return s;
 }
 
 pamo_status pamo_round_commit(pamo_ctx* c, int64_t* nF_now) {
   CTX_GUARD(c);
+  PAMO_TRY(enter(c));
   pamo_status s = round_commit(c);
+  join(c);
   if (s == PAMO_OK && nF_now) *nF_now = c->nF;
   return s;
 }
@@ -580,6 +886,7 @@ pamo_status pamo_ctx_sizes(const pamo_ctx* c, int64_t* nV, int64_t* nF, int64_t*
 pamo_status pamo_ctx_export(pamo_ctx* c, float* d_V, int32_t* d_F, uint64_t* d_keys,
                             int32_t* d_edges) {
   CTX_GUARD(c);
+  PAMO_TRY(enter(c));
   if (d_V && d_F) PAMO_TRY(store_mesh(c->pos, c->nV, c->F, c->nF, d_V, d_F, c->st));
   if (d_keys)
     PAMO_CUDA(cudaMemcpyAsync(d_keys, c->key, sizeof(uint64_t) * c->nE, cudaMemcpyDeviceToDevice,
@@ -587,7 +894,7 @@ pamo_status pamo_ctx_export(pamo_ctx* c, float* d_V, int32_t* d_F, uint64_t* d_k
   if (d_edges)
     PAMO_CUDA(cudaMemcpyAsync(d_edges, c->E, sizeof(int2) * c->nE, cudaMemcpyDeviceToDevice, c->st));
   PAMO_CUDA(cudaStreamSynchronize(c->st));
-  return PAMO_OK;
+  return join(c);
 }
 
 pamo_status pamo_ctx_round_info(const pamo_ctx* c, int64_t r, int64_t* out) {
@@ -622,6 +929,7 @@ pamo_status pamo_ctx_rounds(const pamo_ctx* c, int64_t* rounds) {
 
 pamo_status pamo_ctx_run(pamo_ctx* c, int64_t target, pamo_stats* stats) {
   CTX_GUARD(c);
+  PAMO_TRY(enter(c));
   cudaEvent_t e0, e1;
   PAMO_CUDA(cudaEventCreate(&e0));
   PAMO_CUDA(cudaEventCreate(&e1));
@@ -637,15 +945,15 @@ pamo_status pamo_ctx_run(pamo_ctx* c, int64_t target, pamo_stats* stats) {
   kc_resolve(c);
   fill_stats(c, stats, ms);
   if (stats) stats->launches = launch_count() - l0;
+  join(c);
   if (s != PAMO_OK) return s;
   return (pamo_status)c->status;
 }
 
 void pamo_ctx_destroy(pamo_ctx* c) {
   if (!c) return;
-  free_ctx_buffers(c);
-  cudaStreamSynchronize(c->st);
-  delete c;
+  join(c);
+  destroy_ctx(c);
 }
 
 pamo_status pamo_simplify(const float* d_V, int64_t nV, const int32_t* d_F, int64_t nF,
@@ -668,7 +976,8 @@ pamo_status pamo_simplify(const float* d_V, int64_t nV, const int32_t* d_F, int6
   const long long l0 = launch_count();
   pamo_status s = create(d_V, nV, d_F, nF, opt, st, &c);
   if (s == PAMO_OK) s = run(c, target);
-  if (s == PAMO_OK) s = store_mesh(c->pos, c->nV, c->F, c->nF, d_Vout, d_Fout, st);
+  if (s == PAMO_OK) s = store_mesh(c->pos, c->nV, c->F, c->nF, d_Vout, d_Fout, c->st);
+  if (s == PAMO_OK) s = join(c);
   float ms = 0.f;
   if (s == PAMO_OK) {
     cudaEventRecord(e1, st);
@@ -753,9 +1062,12 @@ pamo_status pamo_check_self_intersections(const float* d_V, int64_t nV, const in
     cudaError_t e = cudaMemsetAsync(dc, 0, sizeof(RoundCounters), st);
     if (e != cudaSuccess) s = cuda_fail(e, "cudaMemsetAsync");
   }
-  if (s == PAMO_OK) s = bvh_build(b, pos, F, nullptr, (int)nF, lo, hi, st);
+  if (s == PAMO_OK) s = bvh_alloc(b, (int)nF, st);
   if (s == PAMO_OK)
-    s = bvh_check(b, pos, F, nullptr, nullptr, 1, nullptr, nullptr, 0, nullptr, dc, d_pairs, cap, st);
+    s = bvh_build(b, pos, F, nullptr, nullptr, (int)nF, lo, hi, false, default_grid(), st);
+  if (s == PAMO_OK)
+    s = bvh_check(b, pos, F, nullptr, nullptr, 1, nullptr, nullptr, 0, nullptr, dc, d_pairs, cap,
+                  (int)nF, st);
   RoundCounters h{};
   if (s == PAMO_OK) {
     cudaError_t e = cudaMemcpyAsync(&h, dc, sizeof(h), cudaMemcpyDeviceToHost, st);

@@ -48,17 +48,21 @@ __device__ __forceinline__ exact::FaceInfo unpack_info(uint8_t b) {
 
 // leaf boxes (into the leaf half of the node array is done after sorting;
 // here: Morton keys, face ids and per-face predicate info)
+#define GRID_STRIDE(i, n) \
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
+
 __global__ void k_leaf_keys(const float4* __restrict__ pos, const int4* __restrict__ F,
-                            const uint8_t* __restrict__ fdead, int n, float lx, float ly, float lz,
-                            float ix, float iy, float iz, unsigned* __restrict__ keys,
-                            int32_t* __restrict__ vals, uint8_t* __restrict__ info) {
-  const int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= n) return;
+                            const uint8_t* __restrict__ fdead, const int* n_dev, int n_host,
+                            float lx, float ly, float lz, float ix, float iy, float iz,
+                            unsigned* __restrict__ keys, int32_t* __restrict__ vals,
+                            uint8_t* __restrict__ info) {
+  const int n = dev_n(n_dev, n_host);
+  GRID_STRIDE(f, n) {
   vals[f] = f;
   if (fdead && fdead[f]) {
     keys[f] = 1u << 30;
     info[f] = pack_info(exact::FaceInfo{0, 0});
-    return;
+    continue;
   }
   const int4 t = F[f];
   const float4 a = pos[t.x], b = pos[t.y], c = pos[t.z];
@@ -69,49 +73,67 @@ __global__ void k_leaf_keys(const float4* __restrict__ pos, const int4* __restri
             spread10(quant(cz, lz, iz));
   info[f] = pack_info(exact::face_info(make_float3(a.x, a.y, a.z), make_float3(b.x, b.y, b.z),
                                        make_float3(c.x, c.y, c.z)));
+  }
 }
 
 __global__ void k_face_info(const float4* __restrict__ pos, const int4* __restrict__ F,
-                            const uint8_t* __restrict__ fdead, int n, uint8_t* __restrict__ info) {
-  const int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= n) return;
-  if (fdead && fdead[f]) {
-    info[f] = pack_info(exact::FaceInfo{0, 0});
-    return;
+                            const uint8_t* __restrict__ fdead, const int* n_dev, int n_host,
+                            uint8_t* __restrict__ info) {
+  const int n = dev_n(n_dev, n_host);
+  GRID_STRIDE(f, n) {
+    if (fdead && fdead[f]) {
+      info[f] = pack_info(exact::FaceInfo{0, 0});
+      continue;
+    }
+    const int4 t = F[f];
+    const float4 a = pos[t.x], b = pos[t.y], c = pos[t.z];
+    info[f] = pack_info(exact::face_info(make_float3(a.x, a.y, a.z), make_float3(b.x, b.y, b.z),
+                                         make_float3(c.x, c.y, c.z)));
   }
-  const int4 t = F[f];
-  const float4 a = pos[t.x], b = pos[t.y], c = pos[t.z];
-  info[f] = pack_info(exact::face_info(make_float3(a.x, a.y, a.z), make_float3(b.x, b.y, b.z),
-                                       make_float3(c.x, c.y, c.z)));
 }
 
 // ---- LSD radix sort of (key, value), 8 bits per pass, stable -------------
-__global__ void k_digit_hist(const unsigned* __restrict__ keys, int n, int shift, int tiles,
-                             int32_t* __restrict__ hist) {
+__device__ __forceinline__ int sort_tiles(int n) { return n > 0 ? (n + kSortTile - 1) / kSortTile : 1; }
+
+// scan length of the digit histogram (256 digits x tiles), for the scan
+__global__ void k_sort_len(const int* n_dev, int n_host, int* __restrict__ len) {
+  *len = 256 * sort_tiles(dev_n(n_dev, n_host));
+}
+
+__global__ void k_digit_hist(const unsigned* __restrict__ keys, const int* n_dev, int n_host,
+                             int shift, int32_t* __restrict__ hist) {
   __shared__ int h[256];
-  h[threadIdx.x] = 0;
-  __syncthreads();
-  const int base = blockIdx.x * kSortTile;
+  const int n = dev_n(n_dev, n_host);
+  const int tiles = sort_tiles(n);
+  for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int base = tile * kSortTile;
 #pragma unroll 4
-  for (int i = 0; i < kSortItems; i++) {
-    const int j = base + i * kBlock + threadIdx.x;
-    if (j < n) atomicAdd(&h[(keys[j] >> shift) & 0xffu], 1);
+    for (int i = 0; i < kSortItems; i++) {
+      const int j = base + i * kBlock + threadIdx.x;
+      if (j < n) atomicAdd(&h[(keys[j] >> shift) & 0xffu], 1);
+    }
+    __syncthreads();
+    hist[threadIdx.x * tiles + tile] = h[threadIdx.x];
+    __syncthreads();
   }
-  __syncthreads();
-  hist[threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];
 }
 
 __global__ void __launch_bounds__(kBlock) k_digit_scatter(
-    const unsigned* __restrict__ keys, const int32_t* __restrict__ vals, int n, int shift,
-    int tiles, const int32_t* __restrict__ offs, unsigned* __restrict__ okeys,
+    const unsigned* __restrict__ keys, const int32_t* __restrict__ vals, const int* n_dev,
+    int n_host, int shift, const int32_t* __restrict__ offs, unsigned* __restrict__ okeys,
     int32_t* __restrict__ ovals) {
   __shared__ int wcount[kBlock / 32][256];
   __shared__ int goff[256];
+  const int n = dev_n(n_dev, n_host);
+  const int tiles = sort_tiles(n);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
   for (int i = threadIdx.x; i < (kBlock / 32) * 256; i += kBlock) (&wcount[0][0])[i] = 0;
-  goff[threadIdx.x] = offs[threadIdx.x * tiles + blockIdx.x];
+  goff[threadIdx.x] = offs[threadIdx.x * tiles + tile];
   __syncthreads();
-  const int base = blockIdx.x * kSortTile + wid * (kSortItems * 32);
+  const int base = tile * kSortTile + wid * (kSortItems * 32);
   unsigned k[kSortItems];
   int v[kSortItems], r[kSortItems];
   const unsigned lt = (1u << lane) - 1u;
@@ -150,6 +172,8 @@ __global__ void __launch_bounds__(kBlock) k_digit_scatter(
       ovals[p] = v[i];
     }
   }
+  __syncthreads();
+  }
 }
 
 // ---- Karras binary radix tree ---------------------------------------------
@@ -167,10 +191,11 @@ __device__ __forceinline__ int delta(const unsigned* __restrict__ k, int n, int 
 //   ints 12, 13: left, right child (internal index >= 0, or ~face for a leaf)
 // parent[x] = (parent node << 1) | side for internal x in [0, n-1) and leaf
 // positions x = n-1+j; the root has -1.
-__global__ void k_karras(const unsigned* __restrict__ k, const int32_t* __restrict__ vals, int n,
-                         float* __restrict__ nodes, int32_t* __restrict__ parent) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n - 1) return;
+__global__ void k_karras(const unsigned* __restrict__ k, const int32_t* __restrict__ vals,
+                         const int* n_dev, int n_host, float* __restrict__ nodes,
+                         int32_t* __restrict__ parent) {
+  const int n = dev_n(n_dev, n_host);
+  GRID_STRIDE(i, n - 1) {
   const int d = (delta(k, n, i, i + 1) - delta(k, n, i, i - 1)) >= 0 ? 1 : -1;
   const int dmin = delta(k, n, i, i - d);
   int lmax = 2;
@@ -196,23 +221,34 @@ __global__ void k_karras(const unsigned* __restrict__ k, const int32_t* __restri
   parent[lleaf ? n - 1 + g : g] = (i << 1) | 0;
   parent[rleaf ? n - 1 + g + 1 : g + 1] = (i << 1) | 1;
   if (i == 0) parent[0] = -1;
+  }
 }
 
-__global__ void k_order_alive(const int32_t* __restrict__ vals, int n, const uint8_t* __restrict__ fdead,
-                              uint8_t* __restrict__ alive) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) alive[i] = fdead[vals[i]] ? 0 : 1;
+__global__ void k_order_alive(const int32_t* __restrict__ vals, const int* n_dev,
+                              const uint8_t* __restrict__ fdead, uint8_t* __restrict__ alive) {
+  const int n = *n_dev;
+  GRID_STRIDE(i, n) alive[i] = fdead[vals[i]] ? 0 : 1;
 }
 
 __global__ void k_order_write(const int32_t* __restrict__ vals, const unsigned* __restrict__ keys,
-                              int n, const uint8_t* __restrict__ alive,
+                              const int* n_dev, const uint8_t* __restrict__ alive,
                               const int32_t* __restrict__ pos, const int32_t* __restrict__ dead_before,
                               int32_t* __restrict__ out, unsigned* __restrict__ okeys) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n && alive[i]) {
+  const int n = *n_dev;
+  GRID_STRIDE(i, n) {
+    if (!alive[i]) continue;
     const int f = vals[i];
     out[pos[i]] = f - dead_before[f];
     okeys[pos[i]] = keys[i];
+  }
+}
+
+__global__ void k_copy_order(const int32_t* __restrict__ vals2, const unsigned* __restrict__ keys2,
+                             const int* n_dev, int32_t* __restrict__ vals, unsigned* __restrict__ keys) {
+  const int n = *n_dev;
+  GRID_STRIDE(i, n) {
+    vals[i] = vals2[i];
+    keys[i] = keys2[i];
   }
 }
 
@@ -237,11 +273,13 @@ __device__ __forceinline__ void store_box(float* __restrict__ nodes, int p, int 
 // child to arrive at a parent computes the parent's box and stores it in the
 // grandparent (no waiting; every thread stops at a first arrival or the root)
 __global__ void k_refit(const float4* __restrict__ pos, const int4* __restrict__ F,
-                        const uint8_t* __restrict__ fdead, const int32_t* __restrict__ vals, int n,
-                        float* __restrict__ nodes, const int32_t* __restrict__ parent,
-                        int32_t* __restrict__ flags, int* __restrict__ overflow) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n || n < 2) return;
+                        const uint8_t* __restrict__ fdead, const int32_t* __restrict__ vals,
+                        const int* n_dev, int n_host, float* __restrict__ nodes,
+                        const int32_t* __restrict__ parent, int32_t* __restrict__ flags,
+                        int* __restrict__ overflow) {
+  const int n = dev_n(n_dev, n_host);
+  if (n < 2) return;
+  GRID_STRIDE(j, n) {
   const int f = vals[j];
   float3 lo, hi;
   if (fdead && fdead[f]) {
@@ -259,18 +297,19 @@ __global__ void k_refit(const float4* __restrict__ pos, const int4* __restrict__
     const int p = ps >> 1;
     if (steps >= n) {
       atomicOr(overflow, 2);
-      return;
+      break;
     }
-    if (atomicAdd(&flags[p], 1) == 0) return;  // sibling not ready: it finishes
+    if (atomicAdd(&flags[p], 1) == 0) break;  // sibling not ready: it finishes
     __threadfence();
     const float4* q = reinterpret_cast<const float4*>(nodes + 16 * (size_t)p);
     const float4 a = __ldcg(q), b = __ldcg(q + 1), c = __ldcg(q + 2);
     ps = parent[p];
-    if (ps < 0) return;  // root: its box is never needed
+    if (ps < 0) break;  // root: its box is never needed
     lo = make_float3(fminf(a.x, b.z), fminf(a.y, b.w), fminf(a.z, c.x));
     hi = make_float3(fmaxf(a.w, c.y), fmaxf(b.x, c.z), fmaxf(b.y, c.w));
     store_box(nodes, ps >> 1, ps & 1, lo, hi);
     __threadfence();
+  }
   }
 }
 
@@ -306,12 +345,13 @@ __device__ __forceinline__ NodeHits visit(const float* __restrict__ nodes, int n
 // faces is evaluated once, from its lower face id.  Intersecting pairs mark
 // the collapses that tagged either face.
 __global__ void __launch_bounds__(kBlock) k_query(
-    const float* __restrict__ nodes, int n, const float4* __restrict__ pos,
+    const float* __restrict__ nodes, const int* n_dev, int n_host, const float4* __restrict__ pos,
     const int4* __restrict__ F, const uint8_t* __restrict__ fdead,
     const uint8_t* __restrict__ info, const int32_t* __restrict__ ftag, int query_all,
     const int32_t* __restrict__ qlist, const int* __restrict__ qcount,
     uint8_t* __restrict__ undo, RoundCounters* __restrict__ dc, int32_t* __restrict__ pairs_out,
     int64_t cap) {
+  const int n = dev_n(n_dev, n_host);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   int f;
   if (query_all) {
@@ -405,11 +445,12 @@ struct CandBufs {
 };
 
 __global__ void __launch_bounds__(kBlock) k_traverse(
-    const float* __restrict__ nodes, int n, const float4* __restrict__ pos,
+    const float* __restrict__ nodes, const int* n_dev, int n_host, const float4* __restrict__ pos,
     const int4* __restrict__ F, const uint8_t* __restrict__ fdead,
     const int32_t* __restrict__ ftag, int query_all, const int32_t* __restrict__ qlist,
     const int* __restrict__ qcount, CandBufs cb, int* __restrict__ ncand,
     RoundCounters* __restrict__ dc) {
+  const int n = dev_n(n_dev, n_host);
   const int total = query_all ? n : *qcount;
   if (n < 2) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
@@ -556,122 +597,89 @@ __global__ void k_orient2d_batch(const float* __restrict__ P, int64_t n, int8_t*
 
 }  // namespace
 
-pamo_status bvh_build(Bvh& b, const float4* pos, const int4* F, const uint8_t* fdead, int nF,
-                      const float lo[3], const float hi[3], cudaStream_t st) {
-  if (b.order_ok && b.n == nF && 2 * (int64_t)nF > b.n_sorted && nF >= 2) {
-    // carried-over order with the Morton keys of the last sort (still sorted):
-    // hierarchy at the same prefix splits, then boxes of the current faces
-    k_karras<<<grid_for(nF - 1), kBlock, 0, st>>>((const unsigned*)b.keys.p, (const int32_t*)b.vals.p,
-                                                  nF, (float*)b.nodes.p, (int32_t*)b.parent.p); note_launch();
-    PAMO_CUDA(cudaGetLastError());
-    return bvh_refit(b, pos, F, fdead, st);
-  }
-  const int n = nF;
-  b.n = n;
-  b.n_sorted = n;
-  b.order_ok = true;
-  const int tiles = (n + kSortTile - 1) / kSortTile;
-  PAMO_TRY(buf_reserve(b.nodes, sizeof(float4) * 2 * (size_t)(2 * n), st));
-  PAMO_TRY(buf_reserve(b.parent, sizeof(int32_t) * (size_t)(2 * n), st));
-  PAMO_TRY(buf_reserve(b.flags, sizeof(int32_t) * (size_t)(n + 2), st));
-  PAMO_TRY(buf_reserve(b.keys, sizeof(unsigned) * (size_t)n, st));
-  PAMO_TRY(buf_reserve(b.vals, sizeof(int32_t) * (size_t)n, st));
-  PAMO_TRY(buf_reserve(b.keys2, sizeof(unsigned) * (size_t)n, st));
-  PAMO_TRY(buf_reserve(b.vals2, sizeof(int32_t) * (size_t)n, st));
-  PAMO_TRY(buf_reserve(b.hist, sizeof(int32_t) * (size_t)(2 * 256 * tiles + 2), st));
-  PAMO_TRY(buf_reserve(b.face_aux, (size_t)n + 16, st));
-  float inv[3];
-  for (int k = 0; k < 3; k++) {
-    float e = hi[k] - lo[k];
-    inv[k] = e > 0.f ? 1.0f / e : 0.0f;
-  }
-  unsigned* keys = (unsigned*)b.keys.p;
-  int32_t* vals = (int32_t*)b.vals.p;
-  unsigned* keys2 = (unsigned*)b.keys2.p;
-  int32_t* vals2 = (int32_t*)b.vals2.p;
-  k_leaf_keys<<<grid_for(n), kBlock, 0, st>>>(pos, F, fdead, n, lo[0], lo[1], lo[2], inv[0],
-                                              inv[1], inv[2], keys, vals, (uint8_t*)b.face_aux.p); note_launch();
-  PAMO_CUDA(cudaGetLastError());
-  int32_t* hist = (int32_t*)b.hist.p;
-  int32_t* offs = hist + 256 * tiles + 1;
-  Buf scan_tmp;
-  for (int pass = 0; pass < 4; pass++) {
-    const int shift = 8 * pass;
-    k_digit_hist<<<tiles, kBlock, 0, st>>>(keys, n, shift, tiles, hist); note_launch();
-    PAMO_TRY(exclusive_scan_i32(hist, offs, 256 * (int64_t)tiles, scan_tmp, st));
-    k_digit_scatter<<<tiles, kBlock, 0, st>>>(keys, vals, n, shift, tiles, offs, keys2, vals2); note_launch();
-    PAMO_CUDA(cudaGetLastError());
-    unsigned* tk = keys; keys = keys2; keys2 = tk;
-    int32_t* tv = vals; vals = vals2; vals2 = tv;
-  }
-  buf_free(scan_tmp, st);
-  // four passes: sorted data is back in b.keys / b.vals
-  if (n >= 2) {
-    k_karras<<<grid_for(n - 1), kBlock, 0, st>>>(keys, vals, n, (float*)b.nodes.p, (int32_t*)b.parent.p); note_launch();
-    PAMO_CUDA(cudaGetLastError());
-  }
-  return bvh_refit(b, pos, F, fdead, st);
-}
-
-// bvh_build over buffers the caller has already placed in b (each Buf with
-// enough bytes; see bvh_bytes) and a scan scratch of scan_sums_count(256 *
-// tiles) words; allocates nothing.
-pamo_status bvh_build_into(Bvh& b, const float4* pos, const int4* F, int nF, const float lo[3],
-                           const float hi[3], int32_t* scan_sums, cudaStream_t st) {
-  const int n = nF;
-  b.n = n;
-  const int tiles = (n + kSortTile - 1) / kSortTile;
-  float inv[3];
-  for (int k = 0; k < 3; k++) {
-    float e = hi[k] - lo[k];
-    inv[k] = e > 0.f ? 1.0f / e : 0.0f;
-  }
-  unsigned* keys = (unsigned*)b.keys.p;
-  int32_t* vals = (int32_t*)b.vals.p;
-  unsigned* keys2 = (unsigned*)b.keys2.p;
-  int32_t* vals2 = (int32_t*)b.vals2.p;
-  k_leaf_keys<<<grid_for(n), kBlock, 0, st>>>(pos, F, nullptr, n, lo[0], lo[1], lo[2], inv[0],
-                                              inv[1], inv[2], keys, vals, (uint8_t*)b.face_aux.p); note_launch();
-  PAMO_CUDA(cudaGetLastError());
-  int32_t* hist = (int32_t*)b.hist.p;
-  int32_t* offs = hist + 256 * tiles + 1;
-  for (int pass = 0; pass < 4; pass++) {
-    const int shift = 8 * pass;
-    k_digit_hist<<<tiles, kBlock, 0, st>>>(keys, n, shift, tiles, hist); note_launch();
-    PAMO_TRY(exclusive_scan_i32_into(hist, offs, 256 * (int64_t)tiles, scan_sums, st));
-    k_digit_scatter<<<tiles, kBlock, 0, st>>>(keys, vals, n, shift, tiles, offs, keys2, vals2); note_launch();
-    PAMO_CUDA(cudaGetLastError());
-    unsigned* tk = keys; keys = keys2; keys2 = tk;
-    int32_t* tv = vals; vals = vals2; vals2 = tv;
-  }
-  if (n >= 2) {
-    k_karras<<<grid_for(n - 1), kBlock, 0, st>>>(keys, vals, n, (float*)b.nodes.p, (int32_t*)b.parent.p); note_launch();
-    PAMO_CUDA(cudaGetLastError());
-  }
-  return bvh_refit(b, pos, F, nullptr, st);
+// Buffers for trees of up to n_max faces (nothing is allocated later, so a
+// build can be captured in a graph).
+pamo_status bvh_alloc(Bvh& b, int n_max, cudaStream_t st) {
+  size_t nb, pb, fb, kvb, hb, ab;
+  int64_t hw;
+  bvh_bytes(n_max, &nb, &pb, &fb, &kvb, &hb, &ab, &hw);
+  PAMO_TRY(buf_reserve(b.nodes, nb, st));
+  PAMO_TRY(buf_reserve(b.parent, pb, st));
+  PAMO_TRY(buf_reserve(b.flags, fb, st));
+  PAMO_TRY(buf_reserve(b.keys, kvb, st));
+  PAMO_TRY(buf_reserve(b.vals, kvb, st));
+  PAMO_TRY(buf_reserve(b.keys2, kvb, st));
+  PAMO_TRY(buf_reserve(b.vals2, kvb, st));
+  PAMO_TRY(buf_reserve(b.hist, hb, st));
+  PAMO_TRY(buf_reserve(b.face_aux, ab, st));
+  PAMO_TRY(buf_reserve(b.sort_len, 16, st));
+  PAMO_TRY(buf_reserve(b.posn, sizeof(int32_t) * ((size_t)n_max + 1), st));
+  PAMO_TRY(buf_reserve(b.sums, sizeof(int32_t) * scan_sums_count(hw > n_max ? hw : n_max), st));
+  b.n_max = n_max;
+  return PAMO_OK;
 }
 
 void bvh_bytes(int n, size_t* nodes, size_t* parent, size_t* flags, size_t* kv, size_t* hist,
                size_t* aux, int64_t* hist_words) {
-  const int tiles = (n + kSortTile - 1) / kSortTile;
-  *nodes = sizeof(float4) * 2 * (size_t)(2 * n);
-  *parent = sizeof(int32_t) * (size_t)(2 * n);
+  const int tiles = n > 0 ? (n + kSortTile - 1) / kSortTile : 1;
+  *nodes = sizeof(float) * 16 * (size_t)(n > 1 ? n : 1);
+  *parent = sizeof(int32_t) * (size_t)(2 * n + 1);
   *flags = sizeof(int32_t) * (size_t)(n + 2);
-  *kv = sizeof(uint32_t) * (size_t)n;
+  *kv = sizeof(uint32_t) * (size_t)(n > 1 ? n : 1);
   *hist = sizeof(int32_t) * (size_t)(2 * 256 * tiles + 2);
   *aux = (size_t)n + 16;
   *hist_words = 256 * (int64_t)tiles;
 }
 
+// Build over faces [0, n) (n from n_dev when set, else n_host) in the
+// preallocated buffers of b.  carry = true keeps the current leaf order and
+// Morton keys (see bvh_compact_order) and only rebuilds the hierarchy.
+pamo_status bvh_build(Bvh& b, const float4* pos, const int4* F, const uint8_t* fdead,
+                      const int* n_dev, int n_host, const float lo[3], const float hi[3],
+                      bool carry, int grid, cudaStream_t st) {
+  unsigned* keys = (unsigned*)b.keys.p;
+  int32_t* vals = (int32_t*)b.vals.p;
+  if (!carry) {
+    float inv[3];
+    for (int k = 0; k < 3; k++) {
+      float e = hi[k] - lo[k];
+      inv[k] = e > 0.f ? 1.0f / e : 0.0f;
+    }
+    unsigned* keys2 = (unsigned*)b.keys2.p;
+    int32_t* vals2 = (int32_t*)b.vals2.p;
+    k_leaf_keys<<<grid, kBlock, 0, st>>>(pos, F, fdead, n_dev, n_host, lo[0], lo[1], lo[2], inv[0],
+                                         inv[1], inv[2], keys, vals, (uint8_t*)b.face_aux.p); note_launch();
+    const int tiles_max = (b.n_max + kSortTile - 1) / kSortTile;
+    int32_t* hist = (int32_t*)b.hist.p;
+    int32_t* offs = hist + 256 * (tiles_max > 0 ? tiles_max : 1) + 1;
+    int* len = (int*)b.sort_len.p;
+    k_sort_len<<<1, 1, 0, st>>>(n_dev, n_host, len); note_launch();
+    for (int pass = 0; pass < 4; pass++) {
+      const int shift = 8 * pass;
+      k_digit_hist<<<grid, kBlock, 0, st>>>(keys, n_dev, n_host, shift, hist); note_launch();
+      PAMO_TRY(scan_dev_i32(hist, len, offs, (int32_t*)b.sums.p, grid, st));
+      k_digit_scatter<<<grid, kBlock, 0, st>>>(keys, vals, n_dev, n_host, shift, offs, keys2,
+                                               vals2); note_launch();
+      PAMO_CUDA(cudaGetLastError());
+      unsigned* tk = keys; keys = keys2; keys2 = tk;
+      int32_t* tv = vals; vals = vals2; vals2 = tv;
+    }
+    // four passes: the sorted data is back in b.keys / b.vals
+  }
+  k_karras<<<grid, kBlock, 0, st>>>(keys, vals, n_dev, n_host, (float*)b.nodes.p,
+                                    (int32_t*)b.parent.p); note_launch();
+  PAMO_CUDA(cudaGetLastError());
+  return bvh_refit(b, pos, F, fdead, n_dev, n_host, grid, st);
+}
+
 pamo_status bvh_refit(Bvh& b, const float4* pos, const int4* F, const uint8_t* fdead,
-                      cudaStream_t st) {
-  const int n = b.n;
-  PAMO_CUDA(cudaMemsetAsync(b.flags.p, 0, sizeof(int32_t) * (size_t)(n + 2), st));
+                      const int* n_dev, int n_host, int grid, cudaStream_t st) {
   int32_t* fl = (int32_t*)b.flags.p;
-  k_refit<<<grid_for(n), kBlock, 0, st>>>(pos, F, fdead, (const int32_t*)b.vals.p, n,
-                                          (float*)b.nodes.p, (const int32_t*)b.parent.p, fl,
-                                          fl + n + 1); note_launch();
-  k_face_info<<<grid_for(n), kBlock, 0, st>>>(pos, F, fdead, n, (uint8_t*)b.face_aux.p); note_launch();
+  PAMO_CUDA(cudaMemsetAsync(fl, 0, sizeof(int32_t) * (size_t)(b.n_max + 2), st));
+  k_refit<<<grid, kBlock, 0, st>>>(pos, F, fdead, (const int32_t*)b.vals.p, n_dev, n_host,
+                                   (float*)b.nodes.p, (const int32_t*)b.parent.p, fl,
+                                   fl + b.n_max + 1); note_launch();
+  k_face_info<<<grid, kBlock, 0, st>>>(pos, F, fdead, n_dev, n_host, (uint8_t*)b.face_aux.p); note_launch();
   PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;
 }
@@ -679,50 +687,51 @@ pamo_status bvh_refit(Bvh& b, const float4* pos, const int4* F, const uint8_t* f
 pamo_status bvh_check(Bvh& b, const float4* pos, const int4* F, const uint8_t* fdead,
                       const int32_t* ftag, int query_all, const int32_t* qlist,
                       const int* qcount, int64_t nq_max, uint8_t* undo, RoundCounters* dc,
-                      int32_t* pairs_out, int64_t cap, cudaStream_t st) {
-  const int n = b.n;
-  // fold a refit overflow (flags[n+1]) into the round's overflow word
-  k_fold_overflow<<<1, 1, 0, st>>>((const int32_t*)b.flags.p + n + 1, &dc->overflow); note_launch();
-  const int64_t threads = query_all ? n : nq_max;
-  k_query<<<grid_for(threads), kBlock, 0, st>>>((const float*)b.nodes.p, n, pos, F, fdead,
-                                                (const uint8_t*)b.face_aux.p, ftag, query_all,
-                                                qlist, qcount, undo, dc, pairs_out, cap); note_launch();
+                      int32_t* pairs_out, int64_t cap, int n_host, cudaStream_t st) {
+  // fold a refit overflow into the round's overflow word
+  k_fold_overflow<<<1, 1, 0, st>>>((const int32_t*)b.flags.p + b.n_max + 1, &dc->overflow); note_launch();
+  const int64_t threads = query_all ? n_host : nq_max;
+  k_query<<<grid_for(threads), kBlock, 0, st>>>((const float*)b.nodes.p, nullptr, n_host, pos, F,
+                                                fdead, (const uint8_t*)b.face_aux.p, ftag,
+                                                query_all, qlist, qcount, undo, dc, pairs_out,
+                                                cap); note_launch();
   PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;
 }
 
 pamo_status bvh_compact_order(Bvh& b, const uint8_t* fdead, const int32_t* dead_before,
-                              int nF_new, Buf& tmp, cudaStream_t st) {
-  if (!b.order_ok) return PAMO_OK;
-  const int n = b.n;
-  uint8_t* alive = (uint8_t*)b.face_aux.p;     // face info is rebuilt at the next refit
-  int32_t* pos = (int32_t*)b.parent.p;         // parents are rebuilt with the tree
-  k_order_alive<<<grid_for(n), kBlock, 0, st>>>((const int32_t*)b.vals.p, n, fdead, alive); note_launch();
-  PAMO_TRY(exclusive_scan_u8(alive, pos, n, tmp, st));
-  k_order_write<<<grid_for(n), kBlock, 0, st>>>((const int32_t*)b.vals.p, (const unsigned*)b.keys.p,
-                                                n, alive, pos, dead_before, (int32_t*)b.vals2.p,
-                                                (unsigned*)b.keys2.p); note_launch();
+                              const int* n_old_dev, const int* n_new_dev, int grid,
+                              cudaStream_t st) {
+  // runs on every check outcome (sizes 0 when the round does not commit), so
+  // it must leave the tree intact: its own position buffer, and face info
+  // (rebuilt at the next refit) is only written for committed rounds
+  uint8_t* alive = (uint8_t*)b.face_aux.p;
+  int32_t* posn = (int32_t*)b.posn.p;
+  k_order_alive<<<grid, kBlock, 0, st>>>((const int32_t*)b.vals.p, n_old_dev, fdead, alive); note_launch();
+  PAMO_TRY(scan_dev_u8(alive, n_old_dev, posn, (int32_t*)b.sums.p, grid, st));
+  k_order_write<<<grid, kBlock, 0, st>>>((const int32_t*)b.vals.p, (const unsigned*)b.keys.p,
+                                         n_old_dev, alive, posn, dead_before, (int32_t*)b.vals2.p,
+                                         (unsigned*)b.keys2.p); note_launch();
+  k_copy_order<<<grid, kBlock, 0, st>>>((const int32_t*)b.vals2.p, (const unsigned*)b.keys2.p,
+                                        n_new_dev, (int32_t*)b.vals.p, (unsigned*)b.keys.p); note_launch();
   PAMO_CUDA(cudaGetLastError());
-  std::swap(b.vals, b.vals2);
-  std::swap(b.keys, b.keys2);
-  b.n = nF_new;
   return PAMO_OK;
 }
 
 pamo_status bvh_check_split(Bvh& b, const float4* pos, const int4* F, const uint8_t* fdead,
                             const int32_t* ftag, int query_all, const int32_t* qlist,
                             const int* qcount, uint8_t* undo, RoundCounters* dc, int2* const cand[3],
-                            const int64_t cap[3], int* ncand, int grid, cudaStream_t st) {
-  const int n = b.n;
-  k_fold_overflow<<<1, 1, 0, st>>>((const int32_t*)b.flags.p + n + 1, &dc->overflow); note_launch();
+                            const int64_t cap[3], int* ncand, const int* n_dev, int grid,
+                            cudaStream_t st) {
+  k_fold_overflow<<<1, 1, 0, st>>>((const int32_t*)b.flags.p + b.n_max + 1, &dc->overflow); note_launch();
   PAMO_CUDA(cudaMemsetAsync(ncand, 0, 4 * sizeof(int), st));  // ncand[3], cand_overflow
   CandBufs cb;
   for (int r = 0; r < 3; r++) {
     cb.c[r] = cand[r];
     cb.cap[r] = cap[r];
   }
-  k_traverse<<<grid, kBlock, 0, st>>>((const float*)b.nodes.p, n, pos, F, fdead, ftag, query_all,
-                                      qlist, qcount, cb, ncand, dc); note_launch();
+  k_traverse<<<grid, kBlock, 0, st>>>((const float*)b.nodes.p, n_dev, 0, pos, F, fdead, ftag,
+                                      query_all, qlist, qcount, cb, ncand, dc); note_launch();
   k_pairs<<<grid, kBlock, 0, st>>>(cb, ncand, pos, F, (const uint8_t*)b.face_aux.p, ftag, undo,
                                    dc); note_launch();
   PAMO_CUDA(cudaGetLastError());
@@ -739,6 +748,9 @@ void bvh_free(Bvh& b, cudaStream_t st) {
   buf_free(b.vals2, st);
   buf_free(b.hist, st);
   buf_free(b.face_aux, st);
+  buf_free(b.sort_len, st);
+  buf_free(b.sums, st);
+  buf_free(b.posn, st);
 }
 
 pamo_status tri_batch(const float* P, const int32_t* idx, int64_t n, uint8_t* out,

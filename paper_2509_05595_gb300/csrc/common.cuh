@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include <string>
@@ -35,20 +36,48 @@ pamo_status cuda_fail(cudaError_t e, const char* what);
     if (s__ != PAMO_OK) return s__;              \
   } while (0)
 
+// fixed grid of the grid-stride kernels: 4 blocks per SM of the current device
+int default_grid();
+
 inline unsigned grid_for(int64_t n, int block = kBlock) {
   int64_t g = (n + block - 1) / block;
   if (g < 1) g = 1;
   return (unsigned)g;
 }
 
-// device-side counters of one round, mirrored to pinned host memory
+// Device-resident state of a simplification: the mesh sizes (maintained on
+// the device so that a whole round can be replayed as a CUDA graph) and the
+// counters of the current round.  Mirrored to pinned host memory at each
+// synchronisation.
 struct RoundCounters {
+  // ---- persistent
+  int nV, nF, nE;           // current mesh M_1
+  int nflags;               // entries of the invalid-edge flag list
+  int have_prev;            // last round's edge costs can be reused
+  int nV_edges;             // vertex count the edge offsets were built for
+  int pad0[2];
+  // ---- zeroed at the start of every round (from link_rejects on)
   unsigned long long link_rejects, flagged, eligible;
   unsigned long long cost_tris;  // triangles produced, summed over evaluated edges
-  int n_win, n_pairs, n_undo, n_undone_total, overflow, bad, n_query, n_dirty;
+  int nW, n_pairs, n_undo, n_undone_total, overflow, bad, n_query, n_dirty;
   int ncand[3];
-  int cand_overflow;  // a candidate bucket overflowed: undo waits for the fused check
+  int cand_overflow;        // a candidate bucket overflowed: undo waits for the fused check
+  int nund, committed;      // undone / committed collapses (set by the commit)
+  int clean;                // last check found no pair: the commit may run
+  int ne_actual;            // edges written by the edge pass (must be 3F/2)
+  int pairs_total, undo_iters;
+  int go;                   // commit gate: 1 when the last check was clean
+  int goV, goF, goW;        // gated sizes for the commit (0 when not committing)
+  int goVn, goFn;           // gated sizes of the committed mesh
+  int sort_len;             // spare
 };
+
+#define PAMO_ROUND_ZERO_OFFSET offsetof(::pamo::RoundCounters, link_rejects)
+
+// Element count of a launch: the device value when n_dev is set, else n_host.
+__device__ __forceinline__ int dev_n(const int* n_dev, int n_host) {
+  return n_dev ? *n_dev : n_host;
+}
 
 // Scratch buffer owned by a context, grown on demand (stream-ordered).
 struct Buf {
@@ -58,14 +87,14 @@ struct Buf {
 pamo_status buf_reserve(Buf& b, size_t bytes, cudaStream_t st);
 void buf_free(Buf& b, cudaStream_t st);
 
-// Linear BVH over the faces of a mesh (Karras 2012): nodes [0, n-1) are
-// internal, [n-1, 2n-1) are leaves in Morton order.  Each node is two float4:
-// (lo.xyz, left) and (hi.xyz, right); a leaf stores its face id in `left`.
+// Linear BVH over the faces of a mesh (Karras 2012).  Internal nodes only,
+// 64 bytes each (both child boxes and links; leaves are encoded as ~face).
+// vals/keys hold the leaf order (face ids) and Morton keys.
 struct Bvh {
-  int n = 0;
-  Buf nodes, parent, flags, keys, vals, keys2, vals2, hist, face_aux;
-  // leaf order carried over rounds: vals holds a spatially coherent face
-  // order for the current mesh (valid when order_ok); re-sorted by Morton
+  int n_max = 0;                 // capacity the buffers were allocated for
+  Buf nodes, parent, flags, keys, vals, keys2, vals2, hist, face_aux, sort_len, sums;
+  Buf posn;  // [n_max+1] new leaf positions of a compaction
+  // leaf order carried over rounds: valid when order_ok; re-sorted by Morton
   // code when the face count has halved since the last sort
   bool order_ok = false;
   int n_sorted = 0;
@@ -80,7 +109,12 @@ struct RoundRecord {
 
 // The context (opaque to C callers).
 struct pamo_ctx {
+  // the context works on its own stream (graph capture needs a non-default
+  // stream); it is ordered after the caller's stream at creation and the
+  // caller's stream waits for it at the end of every entry point
   cudaStream_t st = nullptr;
+  cudaStream_t ust = nullptr;          // the caller's stream
+  cudaEvent_t join_ev = nullptr;
   pamo_options opt{};
   int64_t nV0 = 0, nF0 = 0, Emax = 0;
   int64_t nV = 0, nF = 0, nE = 0;     // current M_1 sizes
@@ -140,13 +174,19 @@ struct pamo_ctx {
   unsigned long long* flags_next = nullptr;  // [Emax]
   int64_t nflags = 0;
   int hold = 0, zero_streak = 0;
-  std::vector<unsigned long long> h_flags;
   // --- per-round counters
   pamo::RoundCounters* dc = nullptr;    // device
   pamo::RoundCounters* hc = nullptr;    // pinned host mirror
   // --- scratch
   pamo::Buf scan_tmp, quad_tmp;
+  int32_t* scan_sums = nullptr;  // tile sums of the device-sized scans
+  int grid = 608;                // fixed grid of the per-round kernels
   pamo::Bvh bvh;
+  // CUDA graphs of a round (A: full round, B: re-check after an undo); [carry]
+  cudaGraphExec_t gA[2] = {nullptr, nullptr};
+  cudaGraphExec_t gB = nullptr;
+  long long gA_launch[2][8] = {{0}}, gB_launch[8] = {0};
+  cudaEvent_t gev[3][8][2] = {};  // per graph (A sort, A carry, B), class, begin/end
   // --- per-kernel-class accounting (pamo_stats.class_*)
   long long kc_launch0[8] = {0};
   cudaEvent_t kc_open[8] = {nullptr};
@@ -175,15 +215,20 @@ void kc_resolve(pamo_ctx* c);
 
 // scan.cu -------------------------------------------------------------------
 // Exclusive prefix sum of n int32 (or uint8 flags) into out[0..n]; out[n] is
-// the total.  Deterministic.  tmp is grown as needed.
+// the total.  Deterministic.  Eager forms take a host n (tmp grown as needed);
+// the _dev forms read n from device memory and use the caller's tile-sum
+// buffer (scan_sums_count(n_max) words) and a fixed grid.
+int64_t scan_sums_count(int64_t n);
 pamo_status exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, Buf& tmp,
                                cudaStream_t st);
 pamo_status exclusive_scan_u8(const uint8_t* in, int32_t* out, int64_t n, Buf& tmp,
                               cudaStream_t st);
-// the same scan over caller-provided tile sums (scan_sums_count(n) words)
-int64_t scan_sums_count(int64_t n);
 pamo_status exclusive_scan_i32_into(const int32_t* in, int32_t* out, int64_t n, int32_t* sums,
                                     cudaStream_t st);
+pamo_status scan_dev_i32(const int32_t* in, const int* n_dev, int32_t* out, int32_t* sums, int grid,
+                         cudaStream_t st);
+pamo_status scan_dev_u8(const uint8_t* in, const int* n_dev, int32_t* out, int32_t* sums, int grid,
+                        cudaStream_t st);
 
 // mesh.cu -------------------------------------------------------------------
 pamo_status mesh_bbox(const float4* pos, int64_t nV, float lo[3], float hi[3],
@@ -194,11 +239,17 @@ pamo_status validate_mesh(pamo_ctx* c);
 pamo_status build_vertex_faces(pamo_ctx* c);
 pamo_status build_edges(pamo_ctx* c);
 pamo_status init_quadrics(pamo_ctx* c);
-pamo_status commit_compact(pamo_ctx* c, int64_t* n_undone);
+pamo_status commit_compact(pamo_ctx* c);
+pamo_status commit_sizes(pamo_ctx* c);
 pamo_status load_mesh(const float* d_V, int64_t nV, const int32_t* d_F, int64_t nF,
                       float4* pos, int4* F, cudaStream_t st);
 pamo_status store_mesh(const float4* pos, int64_t nV, const int4* F, int64_t nF,
                        float* d_V, int32_t* d_F, cudaStream_t st);
+// copy (*n_dev + add) elements of elem_bytes; fill (*n_dev + add) words / bytes
+pamo_status copy_dev(void* dst, const void* src, const int* n_dev, int add, size_t elem_bytes,
+                     int grid, cudaStream_t st);
+pamo_status fill_dev4(void* p, const int* n_dev, int add, uint32_t v, int grid, cudaStream_t st);
+pamo_status fill_dev1(void* p, const int* n_dev, uint8_t v, int grid, cudaStream_t st);
 
 // cost.cu -------------------------------------------------------------------
 pamo_status edge_costs(pamo_ctx* c);
@@ -207,41 +258,43 @@ pamo_status edge_costs(pamo_ctx* c);
 pamo_status select_winners(pamo_ctx* c);
 pamo_status collapse_winners(pamo_ctx* c);
 pamo_status undo_marked(pamo_ctx* c);
+pamo_status check_result(pamo_ctx* c);
 
 // bvh.cu --------------------------------------------------------------------
-// Build the LBVH over faces F[0..nF) of positions pos (dead faces, if fdead
-// is non-null, get empty boxes).  Morton frame = [lo, hi].
+pamo_status bvh_alloc(Bvh& b, int n_max, cudaStream_t st);
+void bvh_bytes(int n, size_t* nodes, size_t* parent, size_t* flags, size_t* kv, size_t* hist,
+               size_t* aux, int64_t* hist_words);
+// Build the LBVH over faces [0, n) (n from n_dev, else n_host); dead faces
+// (fdead, nullable) get empty boxes; Morton frame [lo, hi].  carry keeps the
+// current leaf order (bvh_compact_order) and rebuilds only the hierarchy.
 pamo_status bvh_build(Bvh& b, const float4* pos, const int4* F, const uint8_t* fdead,
-                      int nF, const float lo[3], const float hi[3], cudaStream_t st);
+                      const int* n_dev, int n_host, const float lo[3], const float hi[3],
+                      bool carry, int grid, cudaStream_t st);
 pamo_status bvh_refit(Bvh& b, const float4* pos, const int4* F, const uint8_t* fdead,
-                      cudaStream_t st);
-// Query live faces (all of them when query_all, else those with ftag >= 0)
-// against the tree; for every intersecting pair mark undo[ftag[f]] and
-// undo[ftag[g]] (when tagged and undo is non-null), count pairs in
-// dc->n_pairs, and when pairs_out is non-null write pairs (f<g) up to cap.
-// qlist/qcount (device): the query faces when not query_all.
+                      const int* n_dev, int n_host, int grid, cudaStream_t st);
+// Fused check (host sizes): query live faces (all of them when query_all,
+// else qlist[0..*qcount)) against the tree; intersecting pairs mark
+// undo[ftag[f]] and undo[ftag[g]] (when tagged and undo is non-null), are
+// counted in dc->n_pairs and, when pairs_out is non-null, written (f<g).
 pamo_status bvh_check(Bvh& b, const float4* pos, const int4* F, const uint8_t* fdead,
                       const int32_t* ftag, int query_all, const int32_t* qlist,
                       const int* qcount, int64_t nq_max, uint8_t* undo, RoundCounters* dc,
-                      int32_t* pairs_out, int64_t cap, cudaStream_t st);
-void bvh_free(Bvh& b, cudaStream_t st);
-// The same check in two passes: traversal appends candidate pairs into three
-// buckets (by shared-vertex count, capacities cap[]), then one thread per pair
-// runs the exact test.  ncand[3] (device) receives the bucket counts; a count
-// above its capacity means the caller must redo the check with bvh_check.
+                      int32_t* pairs_out, int64_t cap, int n_host, cudaStream_t st);
+// The same check in two passes (device sizes): traversal appends candidate
+// pairs into three buckets (by shared-vertex count, capacities cap[]), then
+// one thread per pair runs the exact test.  A bucket overflow sets
+// dc->cand_overflow; the undo then waits and the caller reruns bvh_check.
 pamo_status bvh_check_split(Bvh& b, const float4* pos, const int4* F, const uint8_t* fdead,
                             const int32_t* ftag, int query_all, const int32_t* qlist,
                             const int* qcount, uint8_t* undo, RoundCounters* dc, int2* const cand[3],
-                            const int64_t cap[3], int* ncand, int grid, cudaStream_t st);
+                            const int64_t cap[3], int* ncand, const int* n_dev, int grid,
+                            cudaStream_t st);
 // After a commit: keep the leaf order for the compacted faces (stable filter
-// of the current order through fdead / dead_before), nF_new faces.
+// of the current order through fdead / dead_before); sizes from the device.
 pamo_status bvh_compact_order(Bvh& b, const uint8_t* fdead, const int32_t* dead_before,
-                              int nF_new, Buf& tmp, cudaStream_t st);
-// allocation-free build over buffers already placed in b (sizes: bvh_bytes)
-pamo_status bvh_build_into(Bvh& b, const float4* pos, const int4* F, int nF, const float lo[3],
-                           const float hi[3], int32_t* scan_sums, cudaStream_t st);
-void bvh_bytes(int n, size_t* nodes, size_t* parent, size_t* flags, size_t* kv, size_t* hist,
-               size_t* aux, int64_t* hist_words);
+                              const int* n_old_dev, const int* n_new_dev, int grid,
+                              cudaStream_t st);
+void bvh_free(Bvh& b, cudaStream_t st);
 pamo_status tri_batch(const float* P, const int32_t* idx, int64_t n, uint8_t* out,
                       cudaStream_t st);
 pamo_status orient3d_batch(const float* P, int64_t n, int8_t* out, cudaStream_t st);

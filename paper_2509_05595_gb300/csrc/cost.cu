@@ -77,7 +77,7 @@ __device__ __forceinline__ bool has(const int4& f, int v) {
   return f.x == v || f.y == v || f.z == v;
 }
 
-__device__ __forceinline__ bool is_flagged(const unsigned long long* flags, int64_t n,
+__device__ __forceinline__ bool is_flagged(const unsigned long long* flags, int n,
                                            unsigned long long k) {
   int64_t lo = 0, hi = n;
   while (lo < hi) {
@@ -96,58 +96,65 @@ __device__ __forceinline__ bool is_flagged(const unsigned long long* flags, int6
 // face order is kept by the stable compaction, so recomputing would give the
 // same bits.  Dirty edges go to a list for k_edge_cost.
 __global__ void __launch_bounds__(kBlock) k_edge_reuse(
-    const int2* __restrict__ E, int64_t nE, const uint8_t* __restrict__ vdirty,
+    const int2* __restrict__ E, const uint8_t* __restrict__ vdirty,
     const int32_t* __restrict__ ivmap, const int2* __restrict__ E_prev,
     const int32_t* __restrict__ e_off_prev, const uint32_t* __restrict__ cbits_prev,
     const float4* __restrict__ vbar_prev, const uint8_t* __restrict__ link_prev,
-    const unsigned long long* __restrict__ flags, int64_t nflags, int all_dirty,
-    unsigned long long* __restrict__ key, float4* __restrict__ vbar, uint32_t* __restrict__ cbits,
-    uint8_t* __restrict__ link, int32_t* __restrict__ dlist, RoundCounters* __restrict__ dc) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned long long* __restrict__ flags, unsigned long long* __restrict__ key,
+    float4* __restrict__ vbar, uint32_t* __restrict__ cbits, uint8_t* __restrict__ link,
+    int32_t* __restrict__ dlist, RoundCounters* __restrict__ dc) {
+  const int nE = dc->nE;
+  const int nflags = dc->nflags;
+  const bool all_dirty = !dc->have_prev;
   int link_bad = 0, flagged = 0, eligible = 0;
-  bool dirty = false;
-  if (e < nE) {
-    const int2 ab = E[e];
-    dirty = all_dirty || vdirty[ab.x] || vdirty[ab.y];
-    if (!dirty) {
-      const int ua = ivmap[ab.x], ub = ivmap[ab.y];
-      int lo = e_off_prev[ua], hi = e_off_prev[ua + 1];
-      while (lo < hi) {  // previous edges of ua are sorted by their other end
-        const int m = (lo + hi) >> 1;
-        if (E_prev[m].y < ub) lo = m + 1;
-        else hi = m;
+  const int lane = threadIdx.x & 31;
+  // the whole warp iterates together (block-uniform base) for the ballots
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nE;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = base + threadIdx.x;
+    bool dirty = false;
+    if (e < nE) {
+      const int2 ab = E[e];
+      dirty = all_dirty || vdirty[ab.x] || vdirty[ab.y];
+      if (!dirty) {
+        const int ua = ivmap[ab.x], ub = ivmap[ab.y];
+        int lo = e_off_prev[ua], hi = e_off_prev[ua + 1];
+        while (lo < hi) {  // previous edges of ua are sorted by their other end
+          const int m = (lo + hi) >> 1;
+          if (E_prev[m].y < ub) lo = m + 1;
+          else hi = m;
+        }
+        const uint32_t cb = cbits_prev[lo];
+        const uint8_t lk = link_prev[lo];
+        cbits[e] = cb;
+        link[e] = lk;
+        vbar[e] = vbar_prev[lo];
+        const bool flag = nflags > 0 &&
+                          is_flagged(flags, nflags,
+                                     ((unsigned long long)(unsigned)ab.x << 32) | (unsigned)ab.y);
+        unsigned long long k = ~0ull;
+        if (cb != 0xffffffffu && lk && !flag) {
+          k = ((unsigned long long)cb << 32) | (unsigned long long)(uint32_t)e;
+          eligible++;
+        }
+        key[e] = k;
+        link_bad += !lk;
+        flagged += flag;
       }
-      const uint32_t cb = cbits_prev[lo];
-      const uint8_t lk = link_prev[lo];
-      cbits[e] = cb;
-      link[e] = lk;
-      vbar[e] = vbar_prev[lo];
-      const bool flag =
-          nflags > 0 &&
-          is_flagged(flags, nflags, ((unsigned long long)(unsigned)ab.x << 32) | (unsigned)ab.y);
-      unsigned long long k = ~0ull;
-      if (cb != 0xffffffffu && lk && !flag) {
-        k = ((unsigned long long)cb << 32) | (unsigned long long)(uint32_t)e;
-        eligible = 1;
-      }
-      key[e] = k;
-      link_bad = !lk;
-      flagged = flag;
     }
-  }
-  // dirty edges: warp-aggregated append to the work list
-  const unsigned m = __ballot_sync(0xffffffffu, dirty);
-  if (m) {
-    const int lane = threadIdx.x & 31;
-    int base = 0;
-    if (lane == __ffs(m) - 1) base = atomicAdd(&dc->n_dirty, __popc(m));
-    base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
-    if (dirty) dlist[base + __popc(m & ((1u << lane) - 1u))] = (int32_t)e;
+    // dirty edges: warp-aggregated append to the work list
+    const unsigned m = __ballot_sync(0xffffffffu, dirty);
+    if (m) {
+      int b0 = 0;
+      if (lane == __ffs(m) - 1) b0 = atomicAdd(&dc->n_dirty, __popc(m));
+      b0 = __shfl_sync(0xffffffffu, b0, __ffs(m) - 1);
+      if (dirty) dlist[b0 + __popc(m & ((1u << lane) - 1u))] = (int32_t)e;
+    }
   }
   link_bad = __reduce_add_sync(0xffffffffu, link_bad);
   flagged = __reduce_add_sync(0xffffffffu, flagged);
   eligible = __reduce_add_sync(0xffffffffu, eligible);
-  if ((threadIdx.x & 31) == 0) {
+  if (lane == 0) {
     if (link_bad) atomicAdd(&dc->link_rejects, (unsigned long long)link_bad);
     if (flagged) atomicAdd(&dc->flagged, (unsigned long long)flagged);
     if (eligible) atomicAdd(&dc->eligible, (unsigned long long)eligible);
@@ -155,16 +162,17 @@ __global__ void __launch_bounds__(kBlock) k_edge_reuse(
 }
 
 __global__ void __launch_bounds__(kBlock) k_edge_cost(
-    const int32_t* __restrict__ dlist, const int* __restrict__ ndirty,
-    const int2* __restrict__ E, const float4* __restrict__ pos,
+    const int32_t* __restrict__ dlist, const int2* __restrict__ E, const float4* __restrict__ pos,
     const double* __restrict__ Kv, const int4* __restrict__ F, const int32_t* __restrict__ off,
-    const int32_t* __restrict__ idx, const unsigned long long* __restrict__ flags, int64_t nflags,
+    const int32_t* __restrict__ idx, const unsigned long long* __restrict__ flags,
     double s2, double wes, double ws, unsigned long long* __restrict__ key,
     float4* __restrict__ vbar, uint32_t* __restrict__ cbits, uint8_t* __restrict__ link,
     RoundCounters* __restrict__ dc) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int ndirty = dc->n_dirty;
+  const int nflags = dc->nflags;
   int link_bad = 0, flagged = 0, eligible = 0, ntri = 0;
-  if (i < *ndirty) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndirty;
+       i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t e = dlist[i];
     const int2 ab = E[e];
     const int a = ab.x, b = ab.y;
@@ -289,14 +297,14 @@ __global__ void __launch_bounds__(kBlock) k_edge_cost(
     unsigned long long k = ~0ull;
     if (cb != 0xffffffffu && link_ok && !flag) {
       k = ((unsigned long long)cb << 32) | (unsigned long long)(uint32_t)e;
-      eligible = 1;
+      eligible++;
     }
     key[e] = k;
     cbits[e] = cb;
     link[e] = link_ok ? 1 : 0;
     vbar[e] = make_float4(vx, vy, vz, 0.0f);
-    link_bad = !link_ok;
-    flagged = flag;
+    link_bad += !link_ok;
+    flagged += flag;
   }
   // block totals of the round counters
   link_bad = __reduce_add_sync(0xffffffffu, link_bad);
@@ -315,15 +323,13 @@ __global__ void __launch_bounds__(kBlock) k_edge_cost(
 
 pamo_status edge_costs(pamo_ctx* c) {
   const double s2 = c->scale * c->scale, wes = c->opt.w_e * c->scale;
-  PAMO_CUDA(cudaMemsetAsync(&c->dc->n_dirty, 0, sizeof(int), c->st));
-  k_edge_reuse<<<grid_for(c->nE), kBlock, 0, c->st>>>(
-      c->E, c->nE, c->vdirty, c->ivmap, c->E_prev, c->e_off_prev, c->cbits_prev, c->vbar_prev,
-      c->link_prev, c->flags, c->nflags, c->have_prev ? 0 : 1, c->key, c->vbar, c->cbits, c->link,
-      c->dlist, c->dc); note_launch();
-  k_edge_cost<<<grid_for(c->nE), kBlock, 0, c->st>>>(c->dlist, &c->dc->n_dirty, c->E, c->pos, c->K,
-                                                     c->F, c->vf_off, c->vf_idx, c->flags,
-                                                     c->nflags, s2, wes, c->opt.w_s, c->key,
-                                                     c->vbar, c->cbits, c->link, c->dc); note_launch();
+  const int G = c->grid;
+  k_edge_reuse<<<G, kBlock, 0, c->st>>>(c->E, c->vdirty, c->ivmap, c->E_prev, c->e_off_prev,
+                                        c->cbits_prev, c->vbar_prev, c->link_prev, c->flags,
+                                        c->key, c->vbar, c->cbits, c->link, c->dlist, c->dc); note_launch();
+  k_edge_cost<<<G, kBlock, 0, c->st>>>(c->dlist, c->E, c->pos, c->K, c->F, c->vf_off, c->vf_idx,
+                                       c->flags, s2, wes, c->opt.w_s, c->key, c->vbar, c->cbits,
+                                       c->link, c->dc); note_launch();
   PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;
 }

@@ -4,6 +4,11 @@
 // tie-breaking id of the 64-bit key in Section 5.1), the initial vertex
 // quadrics (Garland-Heckbert planes, summed in ascending face order), and the
 // stable compaction that commits a round.
+//
+// Per-round kernels take their element counts from the device state block
+// (so a round can be replayed as a CUDA graph) and loop grid-stride over a
+// fixed grid; the commit kernels are gated by the "clean" result of the last
+// intersection check.
 #include <cstring>
 
 #include "common.cuh"
@@ -11,6 +16,10 @@
 namespace pamo {
 
 namespace {
+
+#define GRID_STRIDE(i, n) \
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); \
+       i += (int64_t)gridDim.x * blockDim.x)
 
 __global__ void k_load(const float* __restrict__ V, int64_t nV, const int32_t* __restrict__ Fi,
                        int64_t nF, float4* __restrict__ pos, int4* __restrict__ F) {
@@ -68,7 +77,7 @@ __global__ void k_bbox(const float4* __restrict__ pos, int64_t nV, unsigned* __r
   }
 }
 
-// ---- validation -----------------------------------------------------------
+// ---- validation (eager, host sizes) ---------------------------------------
 __global__ void k_check_faces(const int4* __restrict__ F, int64_t nF, int64_t nV,
                               const float4* __restrict__ pos, int* __restrict__ bad) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -140,56 +149,89 @@ __global__ void k_check_vertices(const int4* __restrict__ F, const int32_t* __re
   if (steps != deg || cur != start) atomicOr(bad, 32);
 }
 
-// ---- vertex -> faces ------------------------------------------------------
-__global__ void k_count_corners(const int4* __restrict__ F, int64_t nF, int32_t* __restrict__ cnt) {
-  int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= nF) return;
-  int4 t = F[f];
-  atomicAdd(&cnt[t.x], 1);
-  atomicAdd(&cnt[t.y], 1);
-  atomicAdd(&cnt[t.z], 1);
+// ---- utilities over device-sized ranges ------------------------------------
+// copies (*n_dev + add) * words words
+__global__ void k_copy16(uint4* __restrict__ dst, const uint4* __restrict__ src, const int* n_dev,
+                         int add, int words) {
+  const int64_t n = (int64_t)(*n_dev + add) * words;
+  GRID_STRIDE(i, n) dst[i] = src[i];
 }
 
-__global__ void k_fill_corners(const int4* __restrict__ F, int64_t nF,
+__global__ void k_copy4(uint32_t* __restrict__ dst, const uint32_t* __restrict__ src,
+                        const int* n_dev, int add, int words) {
+  const int64_t n = (int64_t)(*n_dev + add) * words;
+  GRID_STRIDE(i, n) dst[i] = src[i];
+}
+
+__global__ void k_copy1(uint8_t* __restrict__ dst, const uint8_t* __restrict__ src, const int* n_dev) {
+  const int64_t n = *n_dev;
+  GRID_STRIDE(i, n) dst[i] = src[i];
+}
+
+__global__ void k_fill4(uint32_t* __restrict__ p, const int* n_dev, int add, uint32_t v) {
+  const int64_t n = (int64_t)(*n_dev + add);
+  GRID_STRIDE(i, n) p[i] = v;
+}
+
+__global__ void k_fill1(uint8_t* __restrict__ p, const int* n_dev, uint8_t v) {
+  const int64_t n = *n_dev;
+  GRID_STRIDE(i, n) p[i] = v;
+}
+
+// ---- vertex -> faces ------------------------------------------------------
+__global__ void k_count_corners(const int4* __restrict__ F, const int* nF_dev, int nF_host,
+                                int32_t* __restrict__ cnt) {
+  const int n = dev_n(nF_dev, nF_host);
+  GRID_STRIDE(f, n) {
+    const int4 t = F[f];
+    atomicAdd(&cnt[t.x], 1);
+    atomicAdd(&cnt[t.y], 1);
+    atomicAdd(&cnt[t.z], 1);
+  }
+}
+
+__global__ void k_fill_corners(const int4* __restrict__ F, const int* nF_dev, int nF_host,
                                const int32_t* __restrict__ off, int32_t* __restrict__ cur,
                                int32_t* __restrict__ idx) {
-  int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= nF) return;
-  int4 t = F[f];
-  idx[off[t.x] + atomicAdd(&cur[t.x], 1)] = (int32_t)f;
-  idx[off[t.y] + atomicAdd(&cur[t.y], 1)] = (int32_t)f;
-  idx[off[t.z] + atomicAdd(&cur[t.z], 1)] = (int32_t)f;
+  const int n = dev_n(nF_dev, nF_host);
+  GRID_STRIDE(f, n) {
+    const int4 t = F[f];
+    idx[off[t.x] + atomicAdd(&cur[t.x], 1)] = (int32_t)f;
+    idx[off[t.y] + atomicAdd(&cur[t.y], 1)] = (int32_t)f;
+    idx[off[t.z] + atomicAdd(&cur[t.z], 1)] = (int32_t)f;
+  }
 }
 
 // insertion sort of each vertex's incident faces (typically 4..10 entries)
-__global__ void k_sort_segments(const int32_t* __restrict__ off, int64_t nV,
+__global__ void k_sort_segments(const int32_t* __restrict__ off, const int* nV_dev, int nV_host,
                                 int32_t* __restrict__ idx) {
-  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= nV) return;
-  const int b = off[v], e = off[v + 1];
-  if (e - b <= 16) {
-    int a[16];
-    int n = e - b;
-    for (int i = 0; i < n; i++) {
-      int x = idx[b + i];
-      int j = i;
-      while (j > 0 && a[j - 1] > x) {
-        a[j] = a[j - 1];
-        j--;
+  const int nV = dev_n(nV_dev, nV_host);
+  GRID_STRIDE(v, nV) {
+    const int b = off[v], e = off[v + 1];
+    if (e - b <= 16) {
+      int a[16];
+      const int n = e - b;
+      for (int i = 0; i < n; i++) {
+        const int x = idx[b + i];
+        int j = i;
+        while (j > 0 && a[j - 1] > x) {
+          a[j] = a[j - 1];
+          j--;
+        }
+        a[j] = x;
       }
-      a[j] = x;
+      for (int i = 0; i < n; i++) idx[b + i] = a[i];
+    } else {
+      for (int i = b + 1; i < e; i++) {
+        const int x = idx[i];
+        int j = i;
+        while (j > b && idx[j - 1] > x) {
+          idx[j] = idx[j - 1];
+          j--;
+        }
+        idx[j] = x;
+      }
     }
-    for (int i = 0; i < n; i++) idx[b + i] = a[i];
-    return;
-  }
-  for (int i = b + 1; i < e; i++) {
-    int x = idx[i];
-    int j = i;
-    while (j > b && idx[j - 1] > x) {
-      idx[j] = idx[j - 1];
-      j--;
-    }
-    idx[j] = x;
   }
 }
 
@@ -199,34 +241,49 @@ __device__ __forceinline__ int next_after(const int4& f, int v) {
 }
 
 __global__ void k_count_edges(const int4* __restrict__ F, const int32_t* __restrict__ off,
-                              const int32_t* __restrict__ idx, int64_t nV,
+                              const int32_t* __restrict__ idx, const int* nV_dev,
                               int32_t* __restrict__ cnt) {
-  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= nV) return;
-  int c = 0;
-  for (int s = off[v]; s < off[v + 1]; s++) c += next_after(F[idx[s]], (int)v) > v;
-  cnt[v] = c;
+  const int nV = *nV_dev;
+  GRID_STRIDE(v, nV) {
+    int c = 0;
+    for (int s = off[v]; s < off[v + 1]; s++) c += next_after(F[idx[s]], (int)v) > v;
+    cnt[v] = c;
+  }
 }
 
 __global__ void k_write_edges(const int4* __restrict__ F, const int32_t* __restrict__ off,
-                              const int32_t* __restrict__ idx, int64_t nV,
-                              const int32_t* __restrict__ eoff, int2* __restrict__ E) {
-  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= nV) return;
-  const int base = eoff[v];
-  int n = 0;
-  for (int s = off[v]; s < off[v + 1]; s++) {
-    int x = next_after(F[idx[s]], (int)v);
-    if (x <= v) continue;
-    // insertion into the sorted run E[base .. base+n)
-    int j = n;
-    while (j > 0 && E[base + j - 1].y > x) {
-      E[base + j] = E[base + j - 1];
-      j--;
+                              const int32_t* __restrict__ idx, const int* nV_dev,
+                              const int32_t* __restrict__ eoff, int64_t cap, int2* __restrict__ E) {
+  const int nV = *nV_dev;
+  GRID_STRIDE(v, nV) {
+    const int base = eoff[v];
+    int n = 0;
+    for (int s = off[v]; s < off[v + 1]; s++) {
+      const int x = next_after(F[idx[s]], (int)v);
+      if (x <= v) continue;
+      // insertion into the sorted run E[base .. base+n), never past capacity
+      if (base + n >= cap) break;
+      int j = n;
+      while (j > 0 && E[base + j - 1].y > x) {
+        E[base + j] = E[base + j - 1];
+        j--;
+      }
+      E[base + j] = make_int2((int)v, x);
+      n++;
     }
-    E[base + j] = make_int2((int)v, x);
-    n++;
   }
+}
+
+// the edge count; a closed triangle mesh has exactly 3F/2 edges, anything
+// else means a non-manifold mesh (the host reports it at the next sync)
+__global__ void k_edge_total(const int32_t* __restrict__ eoff, RoundCounters* __restrict__ dc,
+                             int64_t cap) {
+  const int ne = eoff[dc->nV];
+  dc->ne_actual = ne;
+  dc->nV_edges = dc->nV;
+  const int want = (3 * dc->nF) / 2;
+  if (ne != want || ne > cap) dc->bad |= 64;
+  dc->nE = ne <= cap ? ne : (int)cap;
 }
 
 // ---- quadrics (Garland-Heckbert; Q_ab of Eq. 1) ---------------------------
@@ -285,74 +342,120 @@ __global__ void k_vertex_quadrics(const double* __restrict__ q, const int32_t* _
   for (int i = 0; i < 10; i++) K[10 * v + i] = s[i];
 }
 
-// ---- commit (stable compaction) -------------------------------------------
+// ---- commit (stable compaction), gated by the last check -------------------
+__global__ void k_commit_gate(RoundCounters* __restrict__ dc) {
+  const int go = dc->clean ? 1 : 0;
+  dc->go = go;
+  dc->goV = go ? dc->nV : 0;
+  dc->goF = go ? dc->nF : 0;
+  dc->goW = go ? dc->nW : 0;
+}
+
 __global__ void k_compact_vertices(const float4* __restrict__ pos_s, const double* __restrict__ K_s,
                                    const uint8_t* __restrict__ vdead,
-                                   const int32_t* __restrict__ dead_before, int64_t nV,
+                                   const int32_t* __restrict__ dead_before, const int* n_dev,
                                    float4* __restrict__ pos, double* __restrict__ K,
                                    int32_t* __restrict__ vmap, int32_t* __restrict__ ivmap) {
-  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= nV) return;
-  if (vdead[v]) {
-    vmap[v] = -1;
-    return;
-  }
-  int64_t n = v - dead_before[v];
-  vmap[v] = (int32_t)n;
-  ivmap[n] = (int32_t)v;
-  pos[n] = pos_s[v];
-  const double2* src = reinterpret_cast<const double2*>(K_s + 10 * v);
-  double2* dst = reinterpret_cast<double2*>(K + 10 * n);
+  const int nV = *n_dev;
+  GRID_STRIDE(v, nV) {
+    if (vdead[v]) {
+      vmap[v] = -1;
+      continue;
+    }
+    const int64_t n = v - dead_before[v];
+    vmap[v] = (int32_t)n;
+    ivmap[n] = (int32_t)v;
+    pos[n] = pos_s[v];
+    const double2* src = reinterpret_cast<const double2*>(K_s + 10 * v);
+    double2* dst = reinterpret_cast<double2*>(K + 10 * n);
 #pragma unroll
-  for (int i = 0; i < 5; i++) dst[i] = src[i];
+    for (int i = 0; i < 5; i++) dst[i] = src[i];
+  }
 }
 
 __global__ void k_compact_faces(const int4* __restrict__ F_s, const uint8_t* __restrict__ fdead,
-                                const int32_t* __restrict__ dead_before, int64_t nF,
+                                const int32_t* __restrict__ dead_before, const int* n_dev,
                                 const int32_t* __restrict__ vmap, int4* __restrict__ F) {
-  int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= nF || fdead[f]) return;
-  int4 t = F_s[f];
-  F[f - dead_before[f]] = make_int4(vmap[t.x], vmap[t.y], vmap[t.z], 0);
+  const int nF = *n_dev;
+  GRID_STRIDE(f, nF) {
+    if (fdead[f]) continue;
+    const int4 t = F_s[f];
+    F[f - dead_before[f]] = make_int4(vmap[t.x], vmap[t.y], vmap[t.z], 0);
+  }
+}
+
+__global__ void k_not(const uint8_t* __restrict__ in, const int* n_dev, uint8_t* __restrict__ out) {
+  const int n = *n_dev;
+  GRID_STRIDE(i, n) out[i] = in[i] ? 0 : 1;
+}
+
+// committed / undone counts and the sizes of the committed mesh
+__global__ void k_commit_counts(const int32_t* __restrict__ wscan, RoundCounters* __restrict__ dc) {
+  if (!dc->go) {
+    dc->goVn = 0;
+    dc->goFn = 0;
+    return;
+  }
+  const int nund = wscan[dc->nW];
+  dc->nund = nund;
+  dc->committed = dc->nW - nund;
+  dc->goVn = dc->nV - dc->committed;
+  dc->goFn = dc->nF - 2 * dc->committed;
 }
 
 // flags of the next round: undone winners as remapped vertex pairs, in winner
 // (= ascending edge) order, which the monotone vertex map keeps sorted
 __global__ void k_undone_pairs(const int32_t* __restrict__ wlist, const int2* __restrict__ E,
                                const uint8_t* __restrict__ standing, const int32_t* __restrict__ uscan,
-                               int64_t nW, const int32_t* __restrict__ vmap,
+                               const int* n_dev, const int32_t* __restrict__ vmap,
                                unsigned long long* __restrict__ out) {
-  int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (w >= nW || standing[w]) return;
-  int2 e = E[wlist[w]];
-  out[uscan[w]] = ((unsigned long long)(unsigned)vmap[e.x] << 32) | (unsigned)vmap[e.y];
+  const int nW = *n_dev;
+  GRID_STRIDE(w, nW) {
+    if (standing[w]) continue;
+    const int2 e = E[wlist[w]];
+    out[uscan[w]] = ((unsigned long long)(unsigned)vmap[e.x] << 32) | (unsigned)vmap[e.y];
+  }
+}
+
+// after a round that committed something, the undone edges are the flags
+// (Section 5.3); a round without a commit is merged on the host
+__global__ void k_flags_commit(const unsigned long long* __restrict__ next,
+                               unsigned long long* __restrict__ flags, RoundCounters* __restrict__ dc) {
+  if (!dc->go || dc->committed == 0) return;
+  const int n = dc->nund;
+  GRID_STRIDE(i, n) flags[i] = next[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) dc->nflags = n;
 }
 
 // survivors of committed collapses (new numbering)
 __global__ void k_mark_survivors(const int32_t* __restrict__ wlist, const int2* __restrict__ E,
-                                 const uint8_t* __restrict__ standing, int64_t nW,
+                                 const uint8_t* __restrict__ standing, const int* n_dev,
                                  const int32_t* __restrict__ vmap, uint8_t* __restrict__ vsurv) {
-  int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (w >= nW || !standing[w]) return;
-  vsurv[vmap[E[wlist[w]].x]] = 1;
-}
-
-// a vertex is dirty when it is a survivor or shares a face with one
-__global__ void k_mark_dirty(const int4* __restrict__ F, int64_t nF, const uint8_t* __restrict__ vsurv,
-                             uint8_t* __restrict__ vdirty) {
-  int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= nF) return;
-  const int4 t = F[f];
-  if (vsurv[t.x] | vsurv[t.y] | vsurv[t.z]) {
-    vdirty[t.x] = 1;
-    vdirty[t.y] = 1;
-    vdirty[t.z] = 1;
+  const int nW = *n_dev;
+  GRID_STRIDE(w, nW) {
+    if (standing[w]) vsurv[vmap[E[wlist[w]].x]] = 1;
   }
 }
 
-__global__ void k_not(const uint8_t* __restrict__ in, int64_t n, uint8_t* __restrict__ out) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = in[i] ? 0 : 1;
+// a vertex is dirty when it is a survivor or shares a face with one
+__global__ void k_mark_dirty(const int4* __restrict__ F, const int* n_dev,
+                             const uint8_t* __restrict__ vsurv, uint8_t* __restrict__ vdirty) {
+  const int nF = *n_dev;
+  GRID_STRIDE(f, nF) {
+    const int4 t = F[f];
+    if (vsurv[t.x] | vsurv[t.y] | vsurv[t.z]) {
+      vdirty[t.x] = 1;
+      vdirty[t.y] = 1;
+      vdirty[t.z] = 1;
+    }
+  }
+}
+
+__global__ void k_commit_sizes(RoundCounters* __restrict__ dc) {
+  if (!dc->go) return;
+  dc->nV = dc->goVn;
+  dc->nF = dc->goFn;
+  dc->have_prev = 1;
 }
 
 }  // namespace
@@ -371,18 +474,7 @@ pamo_status store_mesh(const float4* pos, int64_t nV, const int4* F, int64_t nF,
   return PAMO_OK;
 }
 
-pamo_status mesh_bbox(const float4* pos, int64_t nV, float lo[3], float hi[3], Buf& tmp,
-                      cudaStream_t st) {
-  PAMO_TRY(buf_reserve(tmp, 64, st));
-  unsigned init[6] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0, 0, 0};
-  PAMO_CUDA(cudaMemcpyAsync(tmp.p, init, sizeof(init), cudaMemcpyHostToDevice, st));
-  unsigned g = grid_for(nV);
-  if (g > 1024) g = 1024;
-  k_bbox<<<g, kBlock, 0, st>>>(pos, nV, (unsigned*)tmp.p); note_launch();
-  PAMO_CUDA(cudaGetLastError());
-  unsigned out[6];
-  PAMO_CUDA(cudaMemcpyAsync(out, tmp.p, sizeof(out), cudaMemcpyDeviceToHost, st));
-  PAMO_CUDA(cudaStreamSynchronize(st));
+static void decode_bbox(const unsigned out[6], float lo[3], float hi[3]) {
   for (int k = 0; k < 3; k++) {
     unsigned a = out[k], b = out[3 + k];
     a = (a & 0x80000000u) ? (a & 0x7fffffffu) : ~a;
@@ -390,7 +482,6 @@ pamo_status mesh_bbox(const float4* pos, int64_t nV, float lo[3], float hi[3], B
     std::memcpy(&lo[k], &a, 4);
     std::memcpy(&hi[k], &b, 4);
   }
-  return PAMO_OK;
 }
 
 // mesh_bbox with caller-provided device scratch (6 words); allocates nothing
@@ -405,24 +496,54 @@ pamo_status mesh_bbox_into(const float4* pos, int64_t nV, unsigned* d_tmp, float
   unsigned out[6];
   PAMO_CUDA(cudaMemcpyAsync(out, d_tmp, sizeof(out), cudaMemcpyDeviceToHost, st));
   PAMO_CUDA(cudaStreamSynchronize(st));
-  for (int k = 0; k < 3; k++) {
-    unsigned a = out[k], b = out[3 + k];
-    a = (a & 0x80000000u) ? (a & 0x7fffffffu) : ~a;
-    b = (b & 0x80000000u) ? (b & 0x7fffffffu) : ~b;
-    std::memcpy(&lo[k], &a, 4);
-    std::memcpy(&hi[k], &b, 4);
-  }
+  decode_bbox(out, lo, hi);
   return PAMO_OK;
 }
 
+pamo_status mesh_bbox(const float4* pos, int64_t nV, float lo[3], float hi[3], Buf& tmp,
+                      cudaStream_t st) {
+  PAMO_TRY(buf_reserve(tmp, 64, st));
+  return mesh_bbox_into(pos, nV, (unsigned*)tmp.p, lo, hi, st);
+}
+
+pamo_status copy_dev(void* dst, const void* src, const int* n_dev, int add, size_t elem_bytes,
+                     int grid, cudaStream_t st) {
+  if (elem_bytes % 16 == 0) {
+    k_copy16<<<grid, kBlock, 0, st>>>((uint4*)dst, (const uint4*)src, n_dev, add,
+                                      (int)(elem_bytes / 16)); note_launch();
+  } else if (elem_bytes % 4 == 0) {
+    k_copy4<<<grid, kBlock, 0, st>>>((uint32_t*)dst, (const uint32_t*)src, n_dev, add,
+                                     (int)(elem_bytes / 4)); note_launch();
+  } else {
+    k_copy1<<<grid, kBlock, 0, st>>>((uint8_t*)dst, (const uint8_t*)src, n_dev); note_launch();
+  }
+  PAMO_CUDA(cudaGetLastError());
+  return PAMO_OK;
+}
+
+pamo_status fill_dev4(void* p, const int* n_dev, int add, uint32_t v, int grid, cudaStream_t st) {
+  k_fill4<<<grid, kBlock, 0, st>>>((uint32_t*)p, n_dev, add, v); note_launch();
+  PAMO_CUDA(cudaGetLastError());
+  return PAMO_OK;
+}
+
+pamo_status fill_dev1(void* p, const int* n_dev, uint8_t v, int grid, cudaStream_t st) {
+  k_fill1<<<grid, kBlock, 0, st>>>((uint8_t*)p, n_dev, v); note_launch();
+  PAMO_CUDA(cudaGetLastError());
+  return PAMO_OK;
+}
+
+// vertex -> incident faces of the current mesh (device sizes)
 pamo_status build_vertex_faces(pamo_ctx* c) {
   cudaStream_t st = c->st;
-  PAMO_CUDA(cudaMemsetAsync(c->vcount, 0, sizeof(int32_t) * (c->nV + 1), st));
-  k_count_corners<<<grid_for(c->nF), kBlock, 0, st>>>(c->F, c->nF, c->vcount); note_launch();
-  PAMO_TRY(exclusive_scan_i32(c->vcount, c->vf_off, c->nV, c->scan_tmp, st));
-  PAMO_CUDA(cudaMemsetAsync(c->vcount, 0, sizeof(int32_t) * (c->nV + 1), st));
-  k_fill_corners<<<grid_for(c->nF), kBlock, 0, st>>>(c->F, c->nF, c->vf_off, c->vcount, c->vf_idx); note_launch();
-  k_sort_segments<<<grid_for(c->nV), kBlock, 0, st>>>(c->vf_off, c->nV, c->vf_idx); note_launch();
+  RoundCounters* dc = c->dc;
+  const int G = c->grid;
+  PAMO_TRY(fill_dev4(c->vcount, &dc->nV, 1, 0u, G, st));
+  k_count_corners<<<G, kBlock, 0, st>>>(c->F, &dc->nF, 0, c->vcount); note_launch();
+  PAMO_TRY(scan_dev_i32(c->vcount, &dc->nV, c->vf_off, c->scan_sums, G, st));
+  PAMO_TRY(fill_dev4(c->vcount, &dc->nV, 1, 0u, G, st));
+  k_fill_corners<<<G, kBlock, 0, st>>>(c->F, &dc->nF, 0, c->vf_off, c->vcount, c->vf_idx); note_launch();
+  k_sort_segments<<<G, kBlock, 0, st>>>(c->vf_off, &dc->nV, 0, c->vf_idx); note_launch();
   PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;
 }
@@ -445,29 +566,24 @@ pamo_status validate_mesh(pamo_ctx* c) {
   PAMO_CUDA(cudaGetLastError());
   PAMO_CUDA(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
   PAMO_CUDA(cudaStreamSynchronize(st));
+  PAMO_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
   if (hb & 8) { set_error("vertex with fewer than 3 incident faces (isolated or open)"); return PAMO_ENOTMANIFOLD; }
   if (hb & 16) { set_error("mesh is not closed, oriented and edge-manifold"); return PAMO_ENOTMANIFOLD; }
   if (hb & 32) { set_error("a vertex link is not a single cycle"); return PAMO_ENOTMANIFOLD; }
   return PAMO_OK;
 }
 
+// canonical edge list of the current mesh (device sizes); sets dc->nE
 pamo_status build_edges(pamo_ctx* c) {
   cudaStream_t st = c->st;
-  k_count_edges<<<grid_for(c->nV), kBlock, 0, st>>>(c->F, c->vf_off, c->vf_idx, c->nV, c->vcount); note_launch();
-  PAMO_TRY(exclusive_scan_i32(c->vcount, c->e_off, c->nV, c->scan_tmp, st));
-  k_write_edges<<<grid_for(c->nV), kBlock, 0, st>>>(c->F, c->vf_off, c->vf_idx, c->nV, c->e_off,
-                                                    c->E); note_launch();
+  RoundCounters* dc = c->dc;
+  const int G = c->grid;
+  k_count_edges<<<G, kBlock, 0, st>>>(c->F, c->vf_off, c->vf_idx, &dc->nV, c->vcount); note_launch();
+  PAMO_TRY(scan_dev_i32(c->vcount, &dc->nV, c->e_off, c->scan_sums, G, st));
+  k_write_edges<<<G, kBlock, 0, st>>>(c->F, c->vf_off, c->vf_idx, &dc->nV, c->e_off, c->Emax,
+                                      c->E); note_launch();
+  k_edge_total<<<1, 1, 0, st>>>(c->e_off, dc, c->Emax); note_launch();
   PAMO_CUDA(cudaGetLastError());
-  // a closed triangle mesh has exactly 3F/2 edges; anything else means the
-  // mesh is not closed and oriented, and later passes must not run
-  int32_t ne = 0;
-  PAMO_CUDA(cudaMemcpyAsync(&ne, c->e_off + c->nV, sizeof(int32_t), cudaMemcpyDeviceToHost, c->st));
-  PAMO_CUDA(cudaStreamSynchronize(c->st));
-  if ((int64_t)ne != (3 * c->nF) / 2) {
-    set_error("edge count is not 3F/2: the mesh is not a closed oriented manifold");
-    return PAMO_ENOTMANIFOLD;
-  }
-  c->nE = ne;
   return PAMO_OK;
 }
 
@@ -482,44 +598,41 @@ pamo_status init_quadrics(pamo_ctx* c) {
   return PAMO_OK;
 }
 
-pamo_status commit_compact(pamo_ctx* c, int64_t* n_undone) {
+// Commit M_s as the next M_1 when the last check was clean (device gate):
+// stable compaction, undone pairs, flags, dirty vertices.  The new sizes
+// become current in commit_sizes.
+pamo_status commit_compact(pamo_ctx* c) {
   cudaStream_t st = c->st;
+  RoundCounters* dc = c->dc;
+  const int G = c->grid;
+  k_commit_gate<<<1, 1, 0, st>>>(dc); note_launch();
   // vertices: new id = old id - (dead vertices before it)
-  PAMO_TRY(exclusive_scan_u8(c->vdead, c->dbuf, c->nV, c->scan_tmp, st));
-  k_compact_vertices<<<grid_for(c->nV), kBlock, 0, st>>>(c->pos_s, c->K_s, c->vdead, c->dbuf,
-                                                         c->nV, c->pos, c->K, c->vmap, c->ivmap); note_launch();
-  PAMO_CUDA(cudaGetLastError());
+  PAMO_TRY(scan_dev_u8(c->vdead, &dc->goV, c->dbuf, c->scan_sums, G, st));
+  k_compact_vertices<<<G, kBlock, 0, st>>>(c->pos_s, c->K_s, c->vdead, c->dbuf, &dc->goV, c->pos,
+                                           c->K, c->vmap, c->ivmap); note_launch();
   // faces, corners remapped
-  PAMO_TRY(exclusive_scan_u8(c->fdead, c->dbuf, c->nF, c->scan_tmp, st));
-  k_compact_faces<<<grid_for(c->nF), kBlock, 0, st>>>(c->F_s, c->fdead, c->dbuf, c->nF, c->vmap,
-                                                      c->F); note_launch();
-  PAMO_CUDA(cudaGetLastError());
-  int64_t nW = c->nW;
+  PAMO_TRY(scan_dev_u8(c->fdead, &dc->goF, c->dbuf, c->scan_sums, G, st));
+  k_compact_faces<<<G, kBlock, 0, st>>>(c->F_s, c->fdead, c->dbuf, &dc->goF, c->vmap, c->F); note_launch();
   // undone winners -> next round's flag candidates (sorted vertex pairs)
-  *n_undone = 0;
-  if (nW > 0) {
-    k_not<<<grid_for(nW), kBlock, 0, st>>>(c->standing, nW, c->alive_tmp); note_launch();
-    PAMO_TRY(exclusive_scan_u8(c->alive_tmp, c->wscan, nW, c->scan_tmp, st));
-    k_undone_pairs<<<grid_for(nW), kBlock, 0, st>>>(c->wlist, c->E, c->standing, c->wscan, nW,
-                                                    c->vmap, c->flags_next); note_launch();
-    PAMO_CUDA(cudaGetLastError());
-    int32_t hn = 0;
-    PAMO_CUDA(cudaMemcpyAsync(&hn, c->wscan + nW, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    PAMO_CUDA(cudaStreamSynchronize(st));
-    *n_undone = hn;
-  }
-  // dirty vertices of the next round (survivors and their neighbours), in the
-  // new numbering over the new faces
-  const int64_t committed = nW - *n_undone;
-  const int64_t nV_new = c->nV - committed, nF_new = c->nF - 2 * committed;
-  PAMO_CUDA(cudaMemsetAsync(c->vsurv, 0, nV_new, st));
-  PAMO_CUDA(cudaMemsetAsync(c->vdirty, 0, nV_new, st));
-  if (committed > 0) {
-    k_mark_survivors<<<grid_for(nW), kBlock, 0, st>>>(c->wlist, c->E, c->standing, nW, c->vmap,
-                                                      c->vsurv); note_launch();
-    k_mark_dirty<<<grid_for(nF_new), kBlock, 0, st>>>(c->F, nF_new, c->vsurv, c->vdirty); note_launch();
-    PAMO_CUDA(cudaGetLastError());
-  }
+  k_not<<<G, kBlock, 0, st>>>(c->standing, &dc->goW, c->alive_tmp); note_launch();
+  PAMO_TRY(scan_dev_u8(c->alive_tmp, &dc->goW, c->wscan, c->scan_sums, G, st));
+  k_commit_counts<<<1, 1, 0, st>>>(c->wscan, dc); note_launch();
+  k_undone_pairs<<<G, kBlock, 0, st>>>(c->wlist, c->E, c->standing, c->wscan, &dc->goW, c->vmap,
+                                       c->flags_next); note_launch();
+  k_flags_commit<<<G, kBlock, 0, st>>>(c->flags_next, c->flags, dc); note_launch();
+  // dirty vertices of the next round (survivors and their neighbours)
+  PAMO_TRY(fill_dev1(c->vsurv, &dc->goVn, 0, G, st));
+  PAMO_TRY(fill_dev1(c->vdirty, &dc->goVn, 0, G, st));
+  k_mark_survivors<<<G, kBlock, 0, st>>>(c->wlist, c->E, c->standing, &dc->goW, c->vmap, c->vsurv); note_launch();
+  k_mark_dirty<<<G, kBlock, 0, st>>>(c->F, &dc->goFn, c->vsurv, c->vdirty); note_launch();
+  PAMO_CUDA(cudaGetLastError());
+  return PAMO_OK;
+}
+
+// the new sizes become current (after everything that still needs the old ones)
+pamo_status commit_sizes(pamo_ctx* c) {
+  k_commit_sizes<<<1, 1, 0, c->st>>>(c->dc); note_launch();
+  PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;
 }
 

@@ -27,8 +27,9 @@ constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Byte layout of the scratch for the maximum sizes (256-byte aligned pieces).
 struct Layout {
-  size_t pos, F, dc, bbox, nodes, parent, flags, keys, vals, keys2, vals2, hist, aux, sums, total;
-  size_t nodes_b, parent_b, flags_b, kv_b, hist_b, aux_b;
+  size_t pos, F, dc, bbox, nodes, parent, flags, keys, vals, keys2, vals2, hist, aux, len, sums,
+      total;
+  size_t nodes_b, parent_b, flags_b, kv_b, hist_b, aux_b, sums_b;
 };
 
 constexpr size_t kTile = 4096;  // radix-sort tile (keys per block) of bvh.cu
@@ -37,11 +38,13 @@ constexpr size_t kTiles = (kMaxFaces + kTile - 1) / kTile;
 constexpr Layout make_layout() {
   Layout L{};
   L.nodes_b = sizeof(float) * 4 * 2 * (size_t)(2 * kMaxFaces);
-  L.parent_b = sizeof(int32_t) * (size_t)(2 * kMaxFaces);
+  L.parent_b = sizeof(int32_t) * (size_t)(2 * kMaxFaces + 1);
   L.flags_b = sizeof(int32_t) * (size_t)(kMaxFaces + 2);
   L.kv_b = sizeof(uint32_t) * (size_t)kMaxFaces;
   L.hist_b = sizeof(int32_t) * (size_t)(2 * 256 * kTiles + 2);
   L.aux_b = (size_t)kMaxFaces + 16;
+  // tile sums of the prefix scans (2048 items per tile), total after them
+  L.sums_b = sizeof(int32_t) * (size_t)((kMaxFaces + 2047) / 2048 + 1);
   size_t o = 0;
   L.pos = o; o += align256(sizeof(float) * 4 * (size_t)kMaxVertices);
   L.F = o; o += align256(sizeof(int) * 4 * (size_t)kMaxFaces);
@@ -56,7 +59,8 @@ constexpr Layout make_layout() {
   L.vals2 = o; o += align256(L.kv_b);
   L.hist = o; o += align256(L.hist_b);
   L.aux = o; o += align256(L.aux_b);
-  L.sums = o; o += align256(sizeof(int32_t) * (256 * kTiles / 2048 + 2));
+  L.len = o; o += align256(16);
+  L.sums = o; o += align256(L.sums_b);
   L.total = o;
   return L;
 }
@@ -115,7 +119,7 @@ extern "C" pamo_status pamo_check_self_intersections_noalloc(const float* d_V, i
     bvh_bytes((int)nF, &nb, &pb, &fb, &kvb, &hb, &ab, &hw);
     if (nb > kL.nodes_b || pb > kL.parent_b || fb > kL.flags_b || kvb > kL.kv_b ||
         hb > kL.hist_b || ab > kL.aux_b ||
-        (size_t)scan_sums_count(hw) * sizeof(int32_t) > kL.total - kL.sums) {
+        (size_t)scan_sums_count(hw > nF ? hw : nF) * sizeof(int32_t) > kL.sums_b) {
       set_error("internal: scratch layout smaller than the BVH needs");
       return PAMO_EINTERNAL;
     }
@@ -136,14 +140,17 @@ extern "C" pamo_status pamo_check_self_intersections_noalloc(const float* d_V, i
   b.vals2 = Buf{base + kL.vals2, kL.kv_b};
   b.hist = Buf{base + kL.hist, kL.hist_b};
   b.face_aux = Buf{base + kL.aux, kL.aux_b};
+  b.sort_len = Buf{base + kL.len, 16};
+  b.sums = Buf{base + kL.sums, kL.sums_b};
+  b.n_max = (int)nF;
   // the array keeps the previous call's contents: the counters must start at 0
   PAMO_CUDA(cudaMemsetAsync(dc, 0, sizeof(RoundCounters), st));
   PAMO_TRY(load_mesh(d_V, nV, d_F, nF, pos, F, st));
   float lo[3], hi[3];
   PAMO_TRY(mesh_bbox_into(pos, nV, (unsigned*)(base + kL.bbox), lo, hi, st));
-  PAMO_TRY(bvh_build_into(b, pos, F, (int)nF, lo, hi, (int32_t*)(base + kL.sums), st));
+  PAMO_TRY(bvh_build(b, pos, F, nullptr, nullptr, (int)nF, lo, hi, false, default_grid(), st));
   PAMO_TRY(bvh_check(b, pos, F, nullptr, nullptr, 1, nullptr, nullptr, 0, nullptr, dc, d_pairs,
-                     cap, st));
+                     cap, (int)nF, st));
   RoundCounters h;
   std::memset(&h, 0, sizeof(h));
   PAMO_CUDA(cudaMemcpyAsync(&h, dc, sizeof(h), cudaMemcpyDeviceToHost, st));

@@ -1,5 +1,8 @@
-// Deterministic device-wide exclusive prefix sums (reduce / scan-of-sums /
-// apply), used for CSR offsets, stream compaction and radix-sort histograms.
+// Deterministic device-wide exclusive prefix sums (tile sums / scan of the
+// tile sums / apply), used for CSR offsets, stream compaction and radix-sort
+// histograms.  The length can come from device memory, so that the scan can
+// sit inside a replayed CUDA graph whose sizes change from round to round;
+// blocks loop over tiles (grid-stride), so the grid is fixed.
 #include "common.cuh"
 
 namespace pamo {
@@ -7,7 +10,7 @@ namespace pamo {
 namespace {
 
 constexpr int kItems = 8;
-constexpr int kTile = kBlock * kItems;  // 2048 items per block
+constexpr int kTile = kBlock * kItems;  // 2048 items per tile
 
 __device__ __forceinline__ int warp_incl_scan(int v) {
   const int lane = threadIdx.x & 31;
@@ -41,34 +44,43 @@ __device__ __forceinline__ int block_excl_scan(int v, int& total) {
   return r;
 }
 
+__device__ __forceinline__ int tiles_of(int n) { return n > 0 ? (n + kTile - 1) / kTile : 1; }
+
 template <typename T>
-__global__ void k_tile_sums(const T* __restrict__ in, int64_t n, int32_t* __restrict__ sums) {
-  const int64_t base = (int64_t)blockIdx.x * kTile;
-  int s = 0;
-#pragma unroll
-  for (int i = 0; i < kItems; i++) {
-    int64_t j = base + (int64_t)i * kBlock + threadIdx.x;  // striped: coalesced
-    if (j < n) s += (int)in[j];
-  }
-  s = __reduce_add_sync(0xffffffffu, s);
+__global__ void k_tile_sums(const T* __restrict__ in, const int* n_dev, int n_host,
+                            int32_t* __restrict__ sums) {
+  const int n = dev_n(n_dev, n_host);
+  const int tiles = tiles_of(n);
   __shared__ int ws[kBlock / 32];
-  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int t = 0;
-    for (int w = 0; w < kBlock / 32; w++) t += ws[w];
-    sums[blockIdx.x] = t;
+  for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t base = (int64_t)tile * kTile;
+    int s = 0;
+#pragma unroll
+    for (int i = 0; i < kItems; i++) {
+      const int64_t j = base + (int64_t)i * kBlock + threadIdx.x;  // striped: coalesced
+      if (j < n) s += (int)in[j];
+    }
+    s = __reduce_add_sync(0xffffffffu, s);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int t = 0;
+      for (int w = 0; w < kBlock / 32; w++) t += ws[w];
+      sums[tile] = t;
+    }
+    __syncthreads();
   }
 }
 
-// single block: exclusive scan of sums[0..m) in place, total to sums[m]
-__global__ void k_scan_sums(int32_t* sums, int64_t m) {
+// single block: exclusive scan of the tile sums in place, total after them
+__global__ void k_scan_sums(int32_t* sums, const int* n_dev, int n_host) {
+  const int m = tiles_of(dev_n(n_dev, n_host));
   int carry = 0;
-  for (int64_t base = 0; base < m; base += kBlock) {
-    int64_t j = base + threadIdx.x;
-    int v = j < m ? sums[j] : 0;
+  for (int base = 0; base < m; base += kBlock) {
+    const int j = base + threadIdx.x;
+    const int v = j < m ? sums[j] : 0;
     int tot;
-    int ex = block_excl_scan(v, tot);
+    const int ex = block_excl_scan(v, tot);
     if (j < m) sums[j] = carry + ex;
     carry += tot;
   }
@@ -76,82 +88,92 @@ __global__ void k_scan_sums(int32_t* sums, int64_t m) {
 }
 
 template <typename T>
-__global__ void k_tile_apply(const T* __restrict__ in, int64_t n, const int32_t* __restrict__ sums,
-                             int32_t* __restrict__ out) {
+__global__ void k_tile_apply(const T* __restrict__ in, const int* n_dev, int n_host,
+                             const int32_t* __restrict__ sums, int32_t* __restrict__ out) {
   // blocked arrangement so that each thread owns kItems consecutive items
-  __shared__ int32_t tile[kTile];
-  const int64_t base = (int64_t)blockIdx.x * kTile;
+  __shared__ int32_t tile_buf[kTile];
+  const int n = dev_n(n_dev, n_host);
+  const int tiles = tiles_of(n);
+  for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t base = (int64_t)tile * kTile;
 #pragma unroll
-  for (int i = 0; i < kItems; i++) {
-    int64_t j = base + (int64_t)i * kBlock + threadIdx.x;
-    tile[i * kBlock + threadIdx.x] = j < n ? (int)in[j] : 0;
-  }
-  __syncthreads();
-  int v[kItems];
-  int s = 0;
+    for (int i = 0; i < kItems; i++) {
+      const int64_t j = base + (int64_t)i * kBlock + threadIdx.x;
+      tile_buf[i * kBlock + threadIdx.x] = j < n ? (int)in[j] : 0;
+    }
+    __syncthreads();
+    int v[kItems];
+    int s = 0;
 #pragma unroll
-  for (int i = 0; i < kItems; i++) {
-    v[i] = tile[threadIdx.x * kItems + i];
-    s += v[i];
-  }
-  int tot;
-  int ex = block_excl_scan(s, tot) + sums[blockIdx.x];
-  __syncthreads();
+    for (int i = 0; i < kItems; i++) {
+      v[i] = tile_buf[threadIdx.x * kItems + i];
+      s += v[i];
+    }
+    int tot;
+    int ex = block_excl_scan(s, tot) + sums[tile];
 #pragma unroll
-  for (int i = 0; i < kItems; i++) {
-    tile[threadIdx.x * kItems + i] = ex;
-    ex += v[i];
-  }
-  __syncthreads();
+    for (int i = 0; i < kItems; i++) {
+      tile_buf[threadIdx.x * kItems + i] = ex;
+      ex += v[i];
+    }
+    __syncthreads();
 #pragma unroll
-  for (int i = 0; i < kItems; i++) {
-    int64_t j = base + (int64_t)i * kBlock + threadIdx.x;
-    if (j < n) out[j] = tile[i * kBlock + threadIdx.x];
+    for (int i = 0; i < kItems; i++) {
+      const int64_t j = base + (int64_t)i * kBlock + threadIdx.x;
+      if (j < n) out[j] = tile_buf[i * kBlock + threadIdx.x];
+    }
+    __syncthreads();
   }
-  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
-    int64_t tiles = gridDim.x;
-    out[n] = sums[tiles];
-  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = sums[tiles];
 }
 
 template <typename T>
-pamo_status scan_impl(const T* in, int32_t* out, int64_t n, Buf& tmp, cudaStream_t st) {
-  int64_t tiles = (n + kTile - 1) / kTile;
-  if (tiles < 1) tiles = 1;
-  PAMO_TRY(buf_reserve(tmp, sizeof(int32_t) * (tiles + 1), st));
-  int32_t* sums = (int32_t*)tmp.p;
-  k_tile_sums<T><<<(unsigned)tiles, kBlock, 0, st>>>(in, n, sums); note_launch();
-  k_scan_sums<<<1, kBlock, 0, st>>>(sums, tiles); note_launch();
-  k_tile_apply<T><<<(unsigned)tiles, kBlock, 0, st>>>(in, n, sums, out); note_launch();
+pamo_status scan_launch(const T* in, const int* n_dev, int n_host, int32_t* out, int32_t* sums,
+                        int grid, cudaStream_t st) {
+  k_tile_sums<T><<<grid, kBlock, 0, st>>>(in, n_dev, n_host, sums); note_launch();
+  k_scan_sums<<<1, kBlock, 0, st>>>(sums, n_dev, n_host); note_launch();
+  k_tile_apply<T><<<grid, kBlock, 0, st>>>(in, n_dev, n_host, sums, out); note_launch();
   PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;
 }
 
-}  // namespace
-
-pamo_status exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, Buf& tmp,
-                               cudaStream_t st) {
-  return scan_impl<int32_t>(in, out, n, tmp, st);
+int eager_grid(int64_t n) {
+  int64_t t = (n + kTile - 1) / kTile;
+  return (int)(t < 1 ? 1 : (t > 4096 ? 4096 : t));
 }
+
+}  // namespace
 
 int64_t scan_sums_count(int64_t n) {
   int64_t tiles = (n + kTile - 1) / kTile;
   return (tiles < 1 ? 1 : tiles) + 1;
 }
 
-pamo_status exclusive_scan_i32_into(const int32_t* in, int32_t* out, int64_t n, int32_t* sums,
-                                    cudaStream_t st) {
-  int64_t tiles = scan_sums_count(n) - 1;
-  k_tile_sums<int32_t><<<(unsigned)tiles, kBlock, 0, st>>>(in, n, sums); note_launch();
-  k_scan_sums<<<1, kBlock, 0, st>>>(sums, tiles); note_launch();
-  k_tile_apply<int32_t><<<(unsigned)tiles, kBlock, 0, st>>>(in, n, sums, out); note_launch();
-  PAMO_CUDA(cudaGetLastError());
-  return PAMO_OK;
+pamo_status exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, Buf& tmp,
+                               cudaStream_t st) {
+  PAMO_TRY(buf_reserve(tmp, sizeof(int32_t) * scan_sums_count(n), st));
+  return scan_launch<int32_t>(in, nullptr, (int)n, out, (int32_t*)tmp.p, eager_grid(n), st);
 }
 
 pamo_status exclusive_scan_u8(const uint8_t* in, int32_t* out, int64_t n, Buf& tmp,
                               cudaStream_t st) {
-  return scan_impl<uint8_t>(in, out, n, tmp, st);
+  PAMO_TRY(buf_reserve(tmp, sizeof(int32_t) * scan_sums_count(n), st));
+  return scan_launch<uint8_t>(in, nullptr, (int)n, out, (int32_t*)tmp.p, eager_grid(n), st);
+}
+
+pamo_status exclusive_scan_i32_into(const int32_t* in, int32_t* out, int64_t n, int32_t* sums,
+                                    cudaStream_t st) {
+  return scan_launch<int32_t>(in, nullptr, (int)n, out, sums, eager_grid(n), st);
+}
+
+pamo_status scan_dev_i32(const int32_t* in, const int* n_dev, int32_t* out, int32_t* sums, int grid,
+                         cudaStream_t st) {
+  return scan_launch<int32_t>(in, n_dev, 0, out, sums, grid, st);
+}
+
+pamo_status scan_dev_u8(const uint8_t* in, const int* n_dev, int32_t* out, int32_t* sums, int grid,
+                        cudaStream_t st) {
+  return scan_launch<uint8_t>(in, n_dev, 0, out, sums, grid, st);
 }
 
 }  // namespace pamo

@@ -15,23 +15,35 @@ namespace pamo {
 
 namespace {
 
+#define GRID_STRIDE(i, n) \
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); \
+       i += (int64_t)gridDim.x * blockDim.x)
+
+__global__ void k_fill_vkey(unsigned long long* __restrict__ vkey, const RoundCounters* __restrict__ dc) {
+  const int nV = dc->nV;
+  GRID_STRIDE(v, nV) vkey[v] = ~0ull;
+}
+
 __global__ void k_vertex_min(const int2* __restrict__ E, const unsigned long long* __restrict__ key,
-                             int64_t nE, unsigned long long* __restrict__ vkey) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= nE) return;
-  const unsigned long long k = key[e];
-  if (k == ~0ull) return;
-  const int2 ab = E[e];
-  atomicMin(&vkey[ab.x], k);
-  atomicMin(&vkey[ab.y], k);
+                             const RoundCounters* __restrict__ dc,
+                             unsigned long long* __restrict__ vkey) {
+  const int nE = dc->nE;
+  GRID_STRIDE(e, nE) {
+    const unsigned long long k = key[e];
+    if (k == ~0ull) continue;
+    const int2 ab = E[e];
+    atomicMin(&vkey[ab.x], k);
+    atomicMin(&vkey[ab.y], k);
+  }
 }
 
 __global__ void k_select(const int2* __restrict__ E, const unsigned long long* __restrict__ key,
-                         int64_t nE, const unsigned long long* __restrict__ vkey,
+                         const RoundCounters* __restrict__ dc,
+                         const unsigned long long* __restrict__ vkey,
                          const int4* __restrict__ F, const int32_t* __restrict__ off,
                          const int32_t* __restrict__ idx, uint8_t* __restrict__ win) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= nE) return;
+  const int nE = dc->nE;
+  GRID_STRIDE(e, nE) {
   const unsigned long long k = key[e];
   uint8_t w = 0;
   if (k != ~0ull) {
@@ -51,27 +63,33 @@ __global__ void k_select(const int2* __restrict__ E, const unsigned long long* _
     }
   }
   win[e] = w;
+  }
 }
 
 __global__ void k_gather_winners(const uint8_t* __restrict__ win, const int32_t* __restrict__ scan,
-                                 int64_t nE, int32_t* __restrict__ wlist) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < nE && win[e]) wlist[scan[e]] = (int32_t)e;
+                                 RoundCounters* __restrict__ dc, int32_t* __restrict__ wlist) {
+  const int nE = dc->nE;
+  GRID_STRIDE(e, nE) {
+    if (win[e]) wlist[scan[e]] = (int32_t)e;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) dc->nW = scan[nE];
 }
 
 // Collapse winner w (edge a<b): survivor a takes vbar and K_a + K_b, b dies,
 // the two faces on ab die, the other faces around b swap b for a; every face
 // around a or b is tagged with w.  Regions of distinct winners share no face.
-__global__ void k_collapse(const int32_t* __restrict__ wlist, int64_t nW, const int2* __restrict__ E,
+__global__ void k_collapse(const int32_t* __restrict__ wlist, const RoundCounters* __restrict__ dc,
+                           const int2* __restrict__ E,
                            const float4* __restrict__ vbar, const double* __restrict__ K,
                            const int32_t* __restrict__ off, const int32_t* __restrict__ idx,
                            const int4* __restrict__ F, float4* __restrict__ pos_s,
                            double* __restrict__ K_s, int4* __restrict__ F_s,
                            uint8_t* __restrict__ fdead, uint8_t* __restrict__ vdead,
                            int32_t* __restrict__ ftag, uint8_t* __restrict__ standing,
-                           int32_t* __restrict__ qlist, int* __restrict__ qcount) {
-  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (w >= nW) return;
+                           uint8_t* __restrict__ undo, int32_t* __restrict__ qlist,
+                           int* __restrict__ qcount) {
+  const int nW = dc->nW;
+  GRID_STRIDE(w, nW) {
   const int e = wlist[w];
   const int a = E[e].x, b = E[e].y;
   pos_s[a] = vbar[e];
@@ -87,6 +105,7 @@ __global__ void k_collapse(const int32_t* __restrict__ wlist, int64_t nW, const 
   }
   vdead[b] = 1;
   standing[w] = 1;
+  undo[w] = 0;
   // the faces this collapse changes (alive ones) go to the query list as one
   // contiguous, spatially coherent run
   const int na = off[a + 1] - off[a], nb = off[b + 1] - off[b];
@@ -109,10 +128,11 @@ __global__ void k_collapse(const int32_t* __restrict__ wlist, int64_t nW, const 
     ftag[f] = (int32_t)w;
     qlist[q++] = f;
   }
+  }
 }
 
 // Undo every marked, still-standing collapse: its region returns to M_1.
-__global__ void k_undo(const int32_t* __restrict__ wlist, int64_t nW, const int2* __restrict__ E,
+__global__ void k_undo(const int32_t* __restrict__ wlist, const int2* __restrict__ E,
                        const float4* __restrict__ pos, const double* __restrict__ K,
                        const int32_t* __restrict__ off, const int32_t* __restrict__ idx,
                        const int4* __restrict__ F, float4* __restrict__ pos_s,
@@ -120,9 +140,12 @@ __global__ void k_undo(const int32_t* __restrict__ wlist, int64_t nW, const int2
                        uint8_t* __restrict__ fdead, uint8_t* __restrict__ vdead,
                        int32_t* __restrict__ ftag, uint8_t* __restrict__ standing,
                        uint8_t* __restrict__ undo, RoundCounters* __restrict__ dc) {
-  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (dc->cand_overflow) return;  // marks incomplete: the host reruns the fused check
+  const int nW = dc->nW;
   int n = 0;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nW;
+       base += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t w = base + threadIdx.x;
   if (w < nW && undo[w]) {
     undo[w] = 0;
     if (standing[w]) {
@@ -148,55 +171,63 @@ __global__ void k_undo(const int32_t* __restrict__ wlist, int64_t nW, const int2
       }
     }
   }
+  }
   n = __reduce_add_sync(0xffffffffu, n);
   if ((threadIdx.x & 31) == 0 && n) atomicAdd(&dc->n_undo, n);
+}
+
+// outcome of one check iteration: clean when nothing was undone (and the
+// candidate buffers held every pair)
+__global__ void k_check_result(RoundCounters* __restrict__ dc) {
+  // after an overflow the fused check recounts the pairs
+  if (!dc->cand_overflow) dc->pairs_total += dc->n_pairs;
+  const bool undone = dc->n_undo > 0;
+  dc->undo_iters += undone ? 1 : 0;
+  dc->clean = (!undone && !dc->cand_overflow) ? 1 : 0;
 }
 
 }  // namespace
 
 pamo_status select_winners(pamo_ctx* c) {
   cudaStream_t st = c->st;
-  PAMO_CUDA(cudaMemsetAsync(c->vkey, 0xff, sizeof(unsigned long long) * c->nV, st));
-  k_vertex_min<<<grid_for(c->nE), kBlock, 0, st>>>(c->E, c->key, c->nE, c->vkey); note_launch();
-  k_select<<<grid_for(c->nE), kBlock, 0, st>>>(c->E, c->key, c->nE, c->vkey, c->F, c->vf_off,
-                                               c->vf_idx, c->win); note_launch();
-  PAMO_TRY(exclusive_scan_u8(c->win, c->wscan, c->nE, c->scan_tmp, st));
-  k_gather_winners<<<grid_for(c->nE), kBlock, 0, st>>>(c->win, c->wscan, c->nE, c->wlist); note_launch();
+  const int G = c->grid;
+  k_fill_vkey<<<G, kBlock, 0, st>>>(c->vkey, c->dc); note_launch();
+  k_vertex_min<<<G, kBlock, 0, st>>>(c->E, c->key, c->dc, c->vkey); note_launch();
+  k_select<<<G, kBlock, 0, st>>>(c->E, c->key, c->dc, c->vkey, c->F, c->vf_off, c->vf_idx, c->win); note_launch();
+  PAMO_TRY(scan_dev_u8(c->win, &c->dc->nE, c->wscan, c->scan_sums, G, st));
+  k_gather_winners<<<G, kBlock, 0, st>>>(c->win, c->wscan, c->dc, c->wlist); note_launch();
   PAMO_CUDA(cudaGetLastError());
-  int32_t n = 0;
-  PAMO_CUDA(cudaMemcpyAsync(&n, c->wscan + c->nE, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  PAMO_CUDA(cudaStreamSynchronize(st));
-  c->nW = n;
   return PAMO_OK;
 }
 
 pamo_status collapse_winners(pamo_ctx* c) {
   cudaStream_t st = c->st;
+  RoundCounters* dc = c->dc;
+  const int G = c->grid;
   // M_s starts as a copy of M_1
-  PAMO_CUDA(cudaMemcpyAsync(c->pos_s, c->pos, sizeof(float4) * c->nV, cudaMemcpyDeviceToDevice, st));
-  PAMO_CUDA(cudaMemcpyAsync(c->K_s, c->K, sizeof(double) * 10 * c->nV, cudaMemcpyDeviceToDevice, st));
-  PAMO_CUDA(cudaMemcpyAsync(c->F_s, c->F, sizeof(int4) * c->nF, cudaMemcpyDeviceToDevice, st));
-  PAMO_CUDA(cudaMemsetAsync(c->fdead, 0, c->nF, st));
-  PAMO_CUDA(cudaMemsetAsync(c->vdead, 0, c->nV, st));
-  PAMO_CUDA(cudaMemsetAsync(c->ftag, 0xff, sizeof(int32_t) * c->nF, st));
-  PAMO_CUDA(cudaMemsetAsync(c->undo, 0, c->nW > 0 ? c->nW : 1, st));
-  PAMO_CUDA(cudaMemsetAsync(&c->dc->n_query, 0, sizeof(int), st));
-  if (c->nW > 0) {
-    k_collapse<<<grid_for(c->nW), kBlock, 0, st>>>(c->wlist, c->nW, c->E, c->vbar, c->K, c->vf_off,
-                                                   c->vf_idx, c->F, c->pos_s, c->K_s, c->F_s,
-                                                   c->fdead, c->vdead, c->ftag, c->standing,
-                                                   c->qlist, &c->dc->n_query); note_launch();
-    PAMO_CUDA(cudaGetLastError());
-  }
+  PAMO_TRY(copy_dev(c->pos_s, c->pos, &dc->nV, 0, sizeof(float4), G, st));
+  PAMO_TRY(copy_dev(c->K_s, c->K, &dc->nV, 0, 10 * sizeof(double), G, st));
+  PAMO_TRY(copy_dev(c->F_s, c->F, &dc->nF, 0, sizeof(int4), G, st));
+  PAMO_TRY(fill_dev1(c->fdead, &dc->nF, 0, G, st));
+  PAMO_TRY(fill_dev1(c->vdead, &dc->nV, 0, G, st));
+  PAMO_TRY(fill_dev4(c->ftag, &dc->nF, 0, 0xffffffffu, G, st));
+  k_collapse<<<G, kBlock, 0, st>>>(c->wlist, dc, c->E, c->vbar, c->K, c->vf_off, c->vf_idx, c->F,
+                                   c->pos_s, c->K_s, c->F_s, c->fdead, c->vdead, c->ftag,
+                                   c->standing, c->undo, c->qlist, &dc->n_query); note_launch();
+  PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;
 }
 
 pamo_status undo_marked(pamo_ctx* c) {
-  if (c->nW == 0) return PAMO_OK;
-  k_undo<<<grid_for(c->nW), kBlock, 0, c->st>>>(c->wlist, c->nW, c->E, c->pos, c->K, c->vf_off,
-                                                 c->vf_idx, c->F, c->pos_s, c->K_s, c->F_s,
-                                                 c->fdead, c->vdead, c->ftag, c->standing,
-                                                 c->undo, c->dc); note_launch();
+  k_undo<<<c->grid, kBlock, 0, c->st>>>(c->wlist, c->E, c->pos, c->K, c->vf_off, c->vf_idx, c->F,
+                                        c->pos_s, c->K_s, c->F_s, c->fdead, c->vdead, c->ftag,
+                                        c->standing, c->undo, c->dc); note_launch();
+  PAMO_CUDA(cudaGetLastError());
+  return PAMO_OK;
+}
+
+pamo_status check_result(pamo_ctx* c) {
+  k_check_result<<<1, 1, 0, c->st>>>(c->dc); note_launch();
   PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;
 }
