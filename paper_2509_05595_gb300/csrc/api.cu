@@ -28,12 +28,14 @@ pamo_status cuda_fail(cudaError_t e, const char* what) {
   return PAMO_ECUDA;
 }
 
-int default_grid() {
-  int dev = 0, sms = 152;
+int sm_count() {
+  int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) == cudaSuccess)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  return 4 * (sms > 0 ? sms : 152);
+  return sms > 0 ? sms : 152;
 }
+
+int default_grid() { return 4 * sm_count(); }
 
 pamo_status buf_reserve(Buf& b, size_t bytes, cudaStream_t st) {
   if (bytes <= b.bytes && b.p) return PAMO_OK;
@@ -329,6 +331,7 @@ namespace {
 
 // after a replay of graph slot g (stream synchronised)
 void graph_resolve(pamo_ctx* c, int g) {
+  c->gk_run += c->g_nodes[g];
   const long long* t = g < 2 ? c->gA_launch[g] : c->gB_launch;
   for (int cls = 0; cls < 8; cls++) {
     c->class_launches[cls] += t[cls];
@@ -476,11 +479,14 @@ pamo_status capture(pamo_ctx* c, int slot, cudaGraphExec_t* exec, Fn fn) {
   cudaGraph_t graph = nullptr;
   PAMO_CUDA(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
   g_capture_slot = slot;
+  const long long l0 = launch_count();
   const double bytes0 = c->bytes_model;
   double cb0[8];
   for (int i = 0; i < 8; i++) cb0[i] = c->class_bytes[i];
   pamo_status s = fn();
   g_capture_slot = -1;
+  c->g_nodes[slot] = launch_count() - l0;
+  c->gk_captured += c->g_nodes[slot];
   // bytes are counted per replay, not per capture
   c->bytes_model = bytes0;
   for (int i = 0; i < 8; i++) c->class_bytes[i] = cb0[i];
@@ -934,7 +940,7 @@ pamo_status pamo_ctx_run(pamo_ctx* c, int64_t target, pamo_stats* stats) {
   PAMO_CUDA(cudaEventCreate(&e0));
   PAMO_CUDA(cudaEventCreate(&e1));
   PAMO_CUDA(cudaEventRecord(e0, c->st));
-  const long long l0 = launch_count();
+  const long long l0 = launch_count() - c->gk_run + c->gk_captured;
   pamo_status s = run(c, target);
   PAMO_CUDA(cudaEventRecord(e1, c->st));
   PAMO_CUDA(cudaEventSynchronize(e1));
@@ -944,7 +950,8 @@ pamo_status pamo_ctx_run(pamo_ctx* c, int64_t target, pamo_stats* stats) {
   cudaEventDestroy(e1);
   kc_resolve(c);
   fill_stats(c, stats, ms);
-  if (stats) stats->launches = launch_count() - l0;
+  // kernels that ran: eager launches plus the kernel nodes of each replay
+  if (stats) stats->launches = launch_count() - c->gk_captured + c->gk_run - l0;
   join(c);
   if (s != PAMO_OK) return s;
   return (pamo_status)c->status;
@@ -987,7 +994,7 @@ pamo_status pamo_simplify(const float* d_V, int64_t nV, const int32_t* d_F, int6
     *nF_out = c->nF;
     kc_resolve(c);
     fill_stats(c, stats, ms);
-    if (stats) stats->launches = launch_count() - l0;
+    if (stats) stats->launches = launch_count() - c->gk_captured + c->gk_run - l0;
     s = (pamo_status)c->status;
   }
   cudaEventDestroy(e0);

@@ -647,7 +647,8 @@ pamo_status bvh_build(Bvh& b, const float4* pos, const int4* F, const uint8_t* f
     }
     unsigned* keys2 = (unsigned*)b.keys2.p;
     int32_t* vals2 = (int32_t*)b.vals2.p;
-    k_leaf_keys<<<grid, kBlock, 0, st>>>(pos, F, fdead, n_dev, n_host, lo[0], lo[1], lo[2], inv[0],
+    static const int g_keys = occ_grid(k_leaf_keys);
+    k_leaf_keys<<<g_keys, kBlock, 0, st>>>(pos, F, fdead, n_dev, n_host, lo[0], lo[1], lo[2], inv[0],
                                          inv[1], inv[2], keys, vals, (uint8_t*)b.face_aux.p); note_launch();
     const int tiles_max = (b.n_max + kSortTile - 1) / kSortTile;
     int32_t* hist = (int32_t*)b.hist.p;
@@ -666,7 +667,8 @@ pamo_status bvh_build(Bvh& b, const float4* pos, const int4* F, const uint8_t* f
     }
     // four passes: the sorted data is back in b.keys / b.vals
   }
-  k_karras<<<grid, kBlock, 0, st>>>(keys, vals, n_dev, n_host, (float*)b.nodes.p,
+  static const int g_karras = occ_grid(k_karras);
+  k_karras<<<g_karras, kBlock, 0, st>>>(keys, vals, n_dev, n_host, (float*)b.nodes.p,
                                     (int32_t*)b.parent.p); note_launch();
   PAMO_CUDA(cudaGetLastError());
   return bvh_refit(b, pos, F, fdead, n_dev, n_host, grid, st);
@@ -676,10 +678,12 @@ pamo_status bvh_refit(Bvh& b, const float4* pos, const int4* F, const uint8_t* f
                       const int* n_dev, int n_host, int grid, cudaStream_t st) {
   int32_t* fl = (int32_t*)b.flags.p;
   PAMO_CUDA(cudaMemsetAsync(fl, 0, sizeof(int32_t) * (size_t)(b.n_max + 2), st));
-  k_refit<<<grid, kBlock, 0, st>>>(pos, F, fdead, (const int32_t*)b.vals.p, n_dev, n_host,
+  static const int g_refit = occ_grid(k_refit);
+  static const int g_info = occ_grid(k_face_info);
+  k_refit<<<g_refit, kBlock, 0, st>>>(pos, F, fdead, (const int32_t*)b.vals.p, n_dev, n_host,
                                    (float*)b.nodes.p, (const int32_t*)b.parent.p, fl,
                                    fl + b.n_max + 1); note_launch();
-  k_face_info<<<grid, kBlock, 0, st>>>(pos, F, fdead, n_dev, n_host, (uint8_t*)b.face_aux.p); note_launch();
+  k_face_info<<<g_info, kBlock, 0, st>>>(pos, F, fdead, n_dev, n_host, (uint8_t*)b.face_aux.p); note_launch();
   PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;
 }
@@ -730,9 +734,11 @@ pamo_status bvh_check_split(Bvh& b, const float4* pos, const int4* F, const uint
     cb.c[r] = cand[r];
     cb.cap[r] = cap[r];
   }
-  k_traverse<<<grid, kBlock, 0, st>>>((const float*)b.nodes.p, n_dev, 0, pos, F, fdead, ftag,
+  static const int g_trav = occ_grid(k_traverse);
+  static const int g_pairs = occ_grid(k_pairs);
+  k_traverse<<<g_trav, kBlock, 0, st>>>((const float*)b.nodes.p, n_dev, 0, pos, F, fdead, ftag,
                                       query_all, qlist, qcount, cb, ncand, dc); note_launch();
-  k_pairs<<<grid, kBlock, 0, st>>>(cb, ncand, pos, F, (const uint8_t*)b.face_aux.p, ftag, undo,
+  k_pairs<<<g_pairs, kBlock, 0, st>>>(cb, ncand, pos, F, (const uint8_t*)b.face_aux.p, ftag, undo,
                                    dc); note_launch();
   PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;

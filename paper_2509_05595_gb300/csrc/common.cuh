@@ -38,6 +38,18 @@ pamo_status cuda_fail(cudaError_t e, const char* what);
 
 // fixed grid of the grid-stride kernels: 4 blocks per SM of the current device
 int default_grid();
+int sm_count();
+
+// Grid of a latency-bound grid-stride kernel: as many blocks of kBlock threads
+// as the SMs hold at once (one full wave), so that no block runs in a second,
+// partial wave.  Evaluated once per kernel (static at the call site).
+template <typename K>
+int occ_grid(K kernel) {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kBlock, 0) != cudaSuccess || b < 1)
+    b = 1;
+  return b * sm_count();
+}
 
 inline unsigned grid_for(int64_t n, int block = kBlock) {
   int64_t g = (n + block - 1) / block;
@@ -187,6 +199,9 @@ struct pamo_ctx {
   cudaGraphExec_t gB = nullptr;
   long long gA_launch[2][8] = {{0}}, gB_launch[8] = {0};
   cudaEvent_t gev[3][8][2] = {};  // per graph (A sort, A carry, B), class, begin/end
+  long long g_nodes[3] = {0, 0, 0};  // kernels in each graph
+  // kernels counted at capture (not run then) and kernels run by replays
+  long long gk_captured = 0, gk_run = 0;
   // --- per-kernel-class accounting (pamo_stats.class_*)
   long long kc_launch0[8] = {0};
   cudaEvent_t kc_open[8] = {nullptr};

@@ -542,8 +542,10 @@ pamo_status build_vertex_faces(pamo_ctx* c) {
   k_count_corners<<<G, kBlock, 0, st>>>(c->F, &dc->nF, 0, c->vcount); note_launch();
   PAMO_TRY(scan_dev_i32(c->vcount, &dc->nV, c->vf_off, c->scan_sums, G, st));
   PAMO_TRY(fill_dev4(c->vcount, &dc->nV, 1, 0u, G, st));
-  k_fill_corners<<<G, kBlock, 0, st>>>(c->F, &dc->nF, 0, c->vf_off, c->vcount, c->vf_idx); note_launch();
-  k_sort_segments<<<G, kBlock, 0, st>>>(c->vf_off, &dc->nV, 0, c->vf_idx); note_launch();
+  static const int g_fill = occ_grid(k_fill_corners);
+  static const int g_sort = occ_grid(k_sort_segments);
+  k_fill_corners<<<g_fill, kBlock, 0, st>>>(c->F, &dc->nF, 0, c->vf_off, c->vcount, c->vf_idx); note_launch();
+  k_sort_segments<<<g_sort, kBlock, 0, st>>>(c->vf_off, &dc->nV, 0, c->vf_idx); note_launch();
   PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;
 }
@@ -578,9 +580,11 @@ pamo_status build_edges(pamo_ctx* c) {
   cudaStream_t st = c->st;
   RoundCounters* dc = c->dc;
   const int G = c->grid;
-  k_count_edges<<<G, kBlock, 0, st>>>(c->F, c->vf_off, c->vf_idx, &dc->nV, c->vcount); note_launch();
+  static const int g_count = occ_grid(k_count_edges);
+  static const int g_write = occ_grid(k_write_edges);
+  k_count_edges<<<g_count, kBlock, 0, st>>>(c->F, c->vf_off, c->vf_idx, &dc->nV, c->vcount); note_launch();
   PAMO_TRY(scan_dev_i32(c->vcount, &dc->nV, c->e_off, c->scan_sums, G, st));
-  k_write_edges<<<G, kBlock, 0, st>>>(c->F, c->vf_off, c->vf_idx, &dc->nV, c->e_off, c->Emax,
+  k_write_edges<<<g_write, kBlock, 0, st>>>(c->F, c->vf_off, c->vf_idx, &dc->nV, c->e_off, c->Emax,
                                       c->E); note_launch();
   k_edge_total<<<1, 1, 0, st>>>(c->e_off, dc, c->Emax); note_launch();
   PAMO_CUDA(cudaGetLastError());

@@ -193,7 +193,8 @@ pamo_status select_winners(pamo_ctx* c) {
   const int G = c->grid;
   k_fill_vkey<<<G, kBlock, 0, st>>>(c->vkey, c->dc); note_launch();
   k_vertex_min<<<G, kBlock, 0, st>>>(c->E, c->key, c->dc, c->vkey); note_launch();
-  k_select<<<G, kBlock, 0, st>>>(c->E, c->key, c->dc, c->vkey, c->F, c->vf_off, c->vf_idx, c->win); note_launch();
+  static const int g_select = occ_grid(k_select);
+  k_select<<<g_select, kBlock, 0, st>>>(c->E, c->key, c->dc, c->vkey, c->F, c->vf_off, c->vf_idx, c->win); note_launch();
   PAMO_TRY(scan_dev_u8(c->win, &c->dc->nE, c->wscan, c->scan_sums, G, st));
   k_gather_winners<<<G, kBlock, 0, st>>>(c->win, c->wscan, c->dc, c->wlist); note_launch();
   PAMO_CUDA(cudaGetLastError());
@@ -211,7 +212,8 @@ pamo_status collapse_winners(pamo_ctx* c) {
   PAMO_TRY(fill_dev1(c->fdead, &dc->nF, 0, G, st));
   PAMO_TRY(fill_dev1(c->vdead, &dc->nV, 0, G, st));
   PAMO_TRY(fill_dev4(c->ftag, &dc->nF, 0, 0xffffffffu, G, st));
-  k_collapse<<<G, kBlock, 0, st>>>(c->wlist, dc, c->E, c->vbar, c->K, c->vf_off, c->vf_idx, c->F,
+  static const int g_collapse = occ_grid(k_collapse);
+  k_collapse<<<g_collapse, kBlock, 0, st>>>(c->wlist, dc, c->E, c->vbar, c->K, c->vf_off, c->vf_idx, c->F,
                                    c->pos_s, c->K_s, c->F_s, c->fdead, c->vdead, c->ftag,
                                    c->standing, c->undo, c->qlist, &dc->n_query); note_launch();
   PAMO_CUDA(cudaGetLastError());
