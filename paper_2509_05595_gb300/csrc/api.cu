@@ -109,7 +109,7 @@ void free_ctx_buffers(pamo_ctx* c) {
   release(c->vkey, st); release(c->win, st); release(c->wscan, st); release(c->wlist, st);
   release(c->standing, st); release(c->undo, st); release(c->ftag, st); release(c->qlist, st);
   release(c->fdead, st); release(c->vdead, st); release(c->vmap, st); release(c->dbuf, st);
-  release(c->alive_tmp, st); release(c->flags, st); release(c->flags_next, st);
+  release(c->flags, st); release(c->flags_next, st);
   release(c->dc, st);
   release(c->E_prev, st); release(c->e_off_prev, st); release(c->cbits, st);
   release(c->cbits_prev, st); release(c->vbar_prev, st); release(c->link, st);
@@ -213,7 +213,7 @@ pamo_status create(const float* d_V, int64_t nV, const int32_t* d_F, int64_t nF,
   A(win, c->Emax); A(wscan, c->Emax + 1); A(wlist, c->Emax); A(standing, c->Emax);
   A(undo, c->Emax); A(ftag, nF); A(qlist, nF);
   A(fdead, nF); A(vdead, nV); A(vmap, nV + 1);
-  A(dbuf, mx + 1); A(alive_tmp, mx); A(flags, c->Emax); A(flags_next, c->Emax); A(dc, 1);
+  A(dbuf, mx + 1); A(flags, c->Emax); A(flags_next, c->Emax); A(dc, 1);
   A(E_prev, c->Emax); A(e_off_prev, nV + 1); A(cbits, c->Emax); A(cbits_prev, c->Emax);
   A(vbar_prev, c->Emax); A(link, c->Emax); A(link_prev, c->Emax); A(ivmap, nV);
   A(vsurv, nV); A(vdirty, nV); A(dlist, c->Emax);
@@ -356,18 +356,10 @@ pamo_status sync_now(pamo_ctx* c) {
 
 // ---- the phases of a round (device sizes; capturable) ---------------------
 pamo_status phase_begin(pamo_ctx* c) {
-  cudaStream_t st = c->st;
-  RoundCounters* dc = c->dc;
-  const int G = c->grid;
   kc_begin(c, PAMO_KC_ADJACENCY);
-  PAMO_CUDA(cudaMemsetAsync((char*)dc + PAMO_ROUND_ZERO_OFFSET, 0,
-                            sizeof(RoundCounters) - PAMO_ROUND_ZERO_OFFSET, st));
-  // last round's edges and their costs become the reuse source
-  PAMO_TRY(copy_dev(c->E_prev, c->E, &dc->nE, 0, sizeof(int2), G, st));
-  PAMO_TRY(copy_dev(c->e_off_prev, c->e_off, &dc->nV_edges, 1, sizeof(int32_t), G, st));
-  PAMO_TRY(copy_dev(c->cbits_prev, c->cbits, &dc->nE, 0, sizeof(uint32_t), G, st));
-  PAMO_TRY(copy_dev(c->vbar_prev, c->vbar, &dc->nE, 0, sizeof(float4), G, st));
-  PAMO_TRY(copy_dev(c->link_prev, c->link, &dc->nE, 0, 1, G, st));
+  // the round's counters start at zero; last round's edges and their costs
+  // become the reuse source
+  PAMO_TRY(save_prev(c));
   PAMO_TRY(build_vertex_faces(c));
   PAMO_TRY(build_edges(c));
   const double nV = (double)c->nV, nF = (double)c->nF, nE = 1.5 * nF;
@@ -431,7 +423,6 @@ pamo_status phase_check(pamo_ctx* c) {
   RoundCounters* dc = c->dc;
   if (c->opt.check_mode == 3) return check_result(c);  // debug: no check
   kc_begin(c, PAMO_KC_QUERY);
-  PAMO_CUDA(cudaMemsetAsync(&dc->n_pairs, 0, 2 * sizeof(int), st));  // n_pairs, n_undo
   PAMO_TRY(bvh_check_split(c->bvh, c->pos_s, c->F_s, c->fdead, c->ftag, c->opt.check_mode == 1,
                            c->qlist, &dc->n_query, c->undo, dc, c->cand, c->cand_cap, dc->ncand,
                            &dc->nF, c->grid, st));

@@ -272,6 +272,16 @@ __device__ __forceinline__ void store_box(float* __restrict__ nodes, int p, int 
 // leaf boxes go into their parent's slot; then bottom-up unions: the second
 // child to arrive at a parent computes the parent's box and stores it in the
 // grandparent (no waiting; every thread stops at a first arrival or the root)
+// atomic add with acquire-release semantics at device scope
+__device__ __forceinline__ int add_acq_rel(int* p, int v) {
+  int old;
+  asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;"
+               : "=r"(old)
+               : "l"(p), "r"(v)
+               : "memory");
+  return old;
+}
+
 __global__ void k_refit(const float4* __restrict__ pos, const int4* __restrict__ F,
                         const uint8_t* __restrict__ fdead, const int32_t* __restrict__ vals,
                         const int* n_dev, int n_host, float* __restrict__ nodes,
@@ -290,7 +300,6 @@ __global__ void k_refit(const float4* __restrict__ pos, const int4* __restrict__
   }
   int ps = parent[n - 1 + j];
   store_box(nodes, ps >> 1, ps & 1, lo, hi);
-  __threadfence();
   // a radix tree over n leaves is at most n - 1 levels deep; the cap only
   // guards against a malformed tree
   for (int steps = 0;; steps++) {
@@ -299,8 +308,9 @@ __global__ void k_refit(const float4* __restrict__ pos, const int4* __restrict__
       atomicOr(overflow, 2);
       break;
     }
-    if (atomicAdd(&flags[p], 1) == 0) break;  // sibling not ready: it finishes
-    __threadfence();
+    // arrival count with release (our box store is visible before the count)
+    // and acquire (the sibling's box is visible to the second arrival)
+    if (add_acq_rel(&flags[p], 1) == 0) break;  // sibling not ready: it finishes
     const float4* q = reinterpret_cast<const float4*>(nodes + 16 * (size_t)p);
     const float4 a = __ldcg(q), b = __ldcg(q + 1), c = __ldcg(q + 2);
     ps = parent[p];
@@ -308,9 +318,19 @@ __global__ void k_refit(const float4* __restrict__ pos, const int4* __restrict__
     lo = make_float3(fminf(a.x, b.z), fminf(a.y, b.w), fminf(a.z, c.x));
     hi = make_float3(fmaxf(a.w, c.y), fmaxf(b.x, c.z), fmaxf(b.y, c.w));
     store_box(nodes, ps >> 1, ps & 1, lo, hi);
-    __threadfence();
   }
   }
+}
+
+// start of a split check: zero the pair / undo / candidate counters and fold
+// a refit overflow into the round's overflow word
+__global__ void k_check_begin(const int32_t* __restrict__ refit_overflow,
+                              RoundCounters* __restrict__ dc) {
+  dc->n_pairs = 0;
+  dc->n_undo = 0;
+  dc->ncand[0] = dc->ncand[1] = dc->ncand[2] = 0;
+  dc->cand_overflow = 0;
+  if (*refit_overflow) atomicOr(&dc->overflow, *refit_overflow);
 }
 
 __global__ void k_fold_overflow(const int32_t* __restrict__ src, int* __restrict__ dst) {
@@ -727,8 +747,7 @@ pamo_status bvh_check_split(Bvh& b, const float4* pos, const int4* F, const uint
                             const int* qcount, uint8_t* undo, RoundCounters* dc, int2* const cand[3],
                             const int64_t cap[3], int* ncand, const int* n_dev, int grid,
                             cudaStream_t st) {
-  k_fold_overflow<<<1, 1, 0, st>>>((const int32_t*)b.flags.p + b.n_max + 1, &dc->overflow); note_launch();
-  PAMO_CUDA(cudaMemsetAsync(ncand, 0, 4 * sizeof(int), st));  // ncand[3], cand_overflow
+  k_check_begin<<<1, 1, 0, st>>>((const int32_t*)b.flags.p + b.n_max + 1, dc); note_launch();
   CandBufs cb;
   for (int r = 0; r < 3; r++) {
     cb.c[r] = cand[r];

@@ -85,6 +85,9 @@ struct RoundCounters {
 };
 
 #define PAMO_ROUND_ZERO_OFFSET offsetof(::pamo::RoundCounters, link_rejects)
+static_assert((sizeof(RoundCounters) - PAMO_ROUND_ZERO_OFFSET) % 4 == 0 &&
+                  (sizeof(RoundCounters) - PAMO_ROUND_ZERO_OFFSET) / 4 <= 256,
+              "the round's counters are zeroed by one block, one word per thread");
 
 // Element count of a launch: the device value when n_dev is set, else n_host.
 __device__ __forceinline__ int dev_n(const int* n_dev, int n_host) {
@@ -180,7 +183,6 @@ struct pamo_ctx {
   uint8_t* vdead = nullptr;     // [nV0]
   int32_t* vmap = nullptr;      // [nV0+1]
   int32_t* dbuf = nullptr;      // [max(nV0,nF0)+1] dead-before scan
-  uint8_t* alive_tmp = nullptr; // [max(nV0,nF0)]
   // --- invalid-edge flags (sorted vertex pairs a<<32|b)
   unsigned long long* flags = nullptr;       // [Emax]
   unsigned long long* flags_next = nullptr;  // [Emax]
@@ -244,6 +246,9 @@ pamo_status scan_dev_i32(const int32_t* in, const int* n_dev, int32_t* out, int3
                          cudaStream_t st);
 pamo_status scan_dev_u8(const uint8_t* in, const int* n_dev, int32_t* out, int32_t* sums, int grid,
                         cudaStream_t st);
+// the same over the complement (counts the zero bytes)
+pamo_status scan_dev_u8_not(const uint8_t* in, const int* n_dev, int32_t* out, int32_t* sums,
+                            int grid, cudaStream_t st);
 
 // mesh.cu -------------------------------------------------------------------
 pamo_status mesh_bbox(const float4* pos, int64_t nV, float lo[3], float hi[3],
@@ -253,6 +258,7 @@ pamo_status mesh_bbox_into(const float4* pos, int64_t nV, unsigned* d_tmp, float
 pamo_status validate_mesh(pamo_ctx* c);
 pamo_status build_vertex_faces(pamo_ctx* c);
 pamo_status build_edges(pamo_ctx* c);
+pamo_status save_prev(pamo_ctx* c);
 pamo_status init_quadrics(pamo_ctx* c);
 pamo_status commit_compact(pamo_ctx* c);
 pamo_status commit_sizes(pamo_ctx* c);

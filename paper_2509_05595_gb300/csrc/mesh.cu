@@ -286,6 +286,26 @@ __global__ void k_edge_total(const int32_t* __restrict__ eoff, RoundCounters* __
   dc->nE = ne <= cap ? ne : (int)cap;
 }
 
+// start of a round: zero the round's counters (the words after the persistent
+// sizes) and make last round's edge data the reuse source of this round's costs
+__global__ void k_save_prev(RoundCounters* __restrict__ dc, const int2* __restrict__ E,
+                            const int32_t* __restrict__ e_off, const uint32_t* __restrict__ cbits,
+                            const float4* __restrict__ vbar, const uint8_t* __restrict__ link,
+                            int2* __restrict__ E_prev, int32_t* __restrict__ e_off_prev,
+                            uint32_t* __restrict__ cbits_prev, float4* __restrict__ vbar_prev,
+                            uint8_t* __restrict__ link_prev) {
+  const int nE = dc->nE, nO = dc->nV_edges + 1;
+  if (blockIdx.x == 0 && threadIdx.x < (sizeof(RoundCounters) - PAMO_ROUND_ZERO_OFFSET) / 4)
+    reinterpret_cast<int*>(reinterpret_cast<char*>(dc) + PAMO_ROUND_ZERO_OFFSET)[threadIdx.x] = 0;
+  GRID_STRIDE(i, nE) {
+    E_prev[i] = E[i];
+    cbits_prev[i] = cbits[i];
+    vbar_prev[i] = vbar[i];
+    link_prev[i] = link[i];
+  }
+  GRID_STRIDE(i, nO) e_off_prev[i] = e_off[i];
+}
+
 // ---- quadrics (Garland-Heckbert; Q_ab of Eq. 1) ---------------------------
 // plane of a face through its first corner, unit normal; coefficient order
 // xx xy xz xd yy yz yd zz zd dd
@@ -342,14 +362,8 @@ __global__ void k_vertex_quadrics(const double* __restrict__ q, const int32_t* _
   for (int i = 0; i < 10; i++) K[10 * v + i] = s[i];
 }
 
-// ---- commit (stable compaction), gated by the last check -------------------
-__global__ void k_commit_gate(RoundCounters* __restrict__ dc) {
-  const int go = dc->clean ? 1 : 0;
-  dc->go = go;
-  dc->goV = go ? dc->nV : 0;
-  dc->goF = go ? dc->nF : 0;
-  dc->goW = go ? dc->nW : 0;
-}
+// ---- commit (stable compaction), gated by the last check (the gate sizes
+// go/goV/goF/goW are set with the check's outcome) ---------------------------
 
 __global__ void k_compact_vertices(const float4* __restrict__ pos_s, const double* __restrict__ K_s,
                                    const uint8_t* __restrict__ vdead,
@@ -384,47 +398,46 @@ __global__ void k_compact_faces(const int4* __restrict__ F_s, const uint8_t* __r
   }
 }
 
-__global__ void k_not(const uint8_t* __restrict__ in, const int* n_dev, uint8_t* __restrict__ out) {
-  const int n = *n_dev;
-  GRID_STRIDE(i, n) out[i] = in[i] ? 0 : 1;
-}
-
-// committed / undone counts and the sizes of the committed mesh
-__global__ void k_commit_counts(const int32_t* __restrict__ wscan, RoundCounters* __restrict__ dc) {
-  if (!dc->go) {
-    dc->goVn = 0;
-    dc->goFn = 0;
-    return;
-  }
-  const int nund = wscan[dc->nW];
-  dc->nund = nund;
-  dc->committed = dc->nW - nund;
-  dc->goVn = dc->nV - dc->committed;
-  dc->goFn = dc->nF - 2 * dc->committed;
-}
-
-// flags of the next round: undone winners as remapped vertex pairs, in winner
-// (= ascending edge) order, which the monotone vertex map keeps sorted
+// Undone winners as remapped vertex pairs, in winner (= ascending edge) order,
+// which the monotone vertex map keeps sorted; uscan is the exclusive scan of
+// the undone marks (total at [nW]).  After a round that committed something
+// they are the next round's flags (Section 5.3) and go straight to flags; a
+// round without a commit keeps them in flags_next for the host merge.  Also
+// sets the committed / undone counts and the sizes of the committed mesh.
 __global__ void k_undone_pairs(const int32_t* __restrict__ wlist, const int2* __restrict__ E,
                                const uint8_t* __restrict__ standing, const int32_t* __restrict__ uscan,
-                               const int* n_dev, const int32_t* __restrict__ vmap,
-                               unsigned long long* __restrict__ out) {
-  const int nW = *n_dev;
+                               RoundCounters* __restrict__ dc, const int32_t* __restrict__ vmap,
+                               unsigned long long* __restrict__ flags,
+                               unsigned long long* __restrict__ flags_next) {
+  const int nW = dc->goW;  // 0 when the round does not commit
+  const int nund = dc->go ? uscan[dc->nW] : 0;
+  const int committed = dc->nW - nund;
+  unsigned long long* out = committed > 0 ? flags : flags_next;
   GRID_STRIDE(w, nW) {
     if (standing[w]) continue;
     const int2 e = E[wlist[w]];
     out[uscan[w]] = ((unsigned long long)(unsigned)vmap[e.x] << 32) | (unsigned)vmap[e.y];
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (!dc->go) {
+      dc->goVn = 0;
+      dc->goFn = 0;
+    } else {
+      dc->nund = nund;
+      dc->committed = committed;
+      dc->goVn = dc->nV - committed;
+      dc->goFn = dc->nF - 2 * committed;
+      if (committed > 0) dc->nflags = nund;
+    }
+  }
 }
 
-// after a round that committed something, the undone edges are the flags
-// (Section 5.3); a round without a commit is merged on the host
-__global__ void k_flags_commit(const unsigned long long* __restrict__ next,
-                               unsigned long long* __restrict__ flags, RoundCounters* __restrict__ dc) {
-  if (!dc->go || dc->committed == 0) return;
-  const int n = dc->nund;
-  GRID_STRIDE(i, n) flags[i] = next[i];
-  if (blockIdx.x == 0 && threadIdx.x == 0) dc->nflags = n;
+__global__ void k_clear2(uint8_t* __restrict__ a, uint8_t* __restrict__ b, const int* n_dev) {
+  const int n = *n_dev;
+  GRID_STRIDE(i, n) {
+    a[i] = 0;
+    b[i] = 0;
+  }
 }
 
 // survivors of committed collapses (new numbering)
@@ -575,6 +588,14 @@ pamo_status validate_mesh(pamo_ctx* c) {
   return PAMO_OK;
 }
 
+pamo_status save_prev(pamo_ctx* c) {
+  k_save_prev<<<c->grid, kBlock, 0, c->st>>>(c->dc, c->E, c->e_off, c->cbits, c->vbar, c->link,
+                                             c->E_prev, c->e_off_prev, c->cbits_prev, c->vbar_prev,
+                                             c->link_prev); note_launch();
+  PAMO_CUDA(cudaGetLastError());
+  return PAMO_OK;
+}
+
 // canonical edge list of the current mesh (device sizes); sets dc->nE
 pamo_status build_edges(pamo_ctx* c) {
   cudaStream_t st = c->st;
@@ -609,7 +630,6 @@ pamo_status commit_compact(pamo_ctx* c) {
   cudaStream_t st = c->st;
   RoundCounters* dc = c->dc;
   const int G = c->grid;
-  k_commit_gate<<<1, 1, 0, st>>>(dc); note_launch();
   // vertices: new id = old id - (dead vertices before it)
   PAMO_TRY(scan_dev_u8(c->vdead, &dc->goV, c->dbuf, c->scan_sums, G, st));
   k_compact_vertices<<<G, kBlock, 0, st>>>(c->pos_s, c->K_s, c->vdead, c->dbuf, &dc->goV, c->pos,
@@ -618,15 +638,11 @@ pamo_status commit_compact(pamo_ctx* c) {
   PAMO_TRY(scan_dev_u8(c->fdead, &dc->goF, c->dbuf, c->scan_sums, G, st));
   k_compact_faces<<<G, kBlock, 0, st>>>(c->F_s, c->fdead, c->dbuf, &dc->goF, c->vmap, c->F); note_launch();
   // undone winners -> next round's flag candidates (sorted vertex pairs)
-  k_not<<<G, kBlock, 0, st>>>(c->standing, &dc->goW, c->alive_tmp); note_launch();
-  PAMO_TRY(scan_dev_u8(c->alive_tmp, &dc->goW, c->wscan, c->scan_sums, G, st));
-  k_commit_counts<<<1, 1, 0, st>>>(c->wscan, dc); note_launch();
-  k_undone_pairs<<<G, kBlock, 0, st>>>(c->wlist, c->E, c->standing, c->wscan, &dc->goW, c->vmap,
+  PAMO_TRY(scan_dev_u8_not(c->standing, &dc->goW, c->wscan, c->scan_sums, G, st));
+  k_undone_pairs<<<G, kBlock, 0, st>>>(c->wlist, c->E, c->standing, c->wscan, dc, c->vmap, c->flags,
                                        c->flags_next); note_launch();
-  k_flags_commit<<<G, kBlock, 0, st>>>(c->flags_next, c->flags, dc); note_launch();
   // dirty vertices of the next round (survivors and their neighbours)
-  PAMO_TRY(fill_dev1(c->vsurv, &dc->goVn, 0, G, st));
-  PAMO_TRY(fill_dev1(c->vdirty, &dc->goVn, 0, G, st));
+  k_clear2<<<G, kBlock, 0, st>>>(c->vsurv, c->vdirty, &dc->goVn); note_launch();
   k_mark_survivors<<<G, kBlock, 0, st>>>(c->wlist, c->E, c->standing, &dc->goW, c->vmap, c->vsurv); note_launch();
   k_mark_dirty<<<G, kBlock, 0, st>>>(c->F, &dc->goFn, c->vsurv, c->vdirty); note_launch();
   PAMO_CUDA(cudaGetLastError());

@@ -46,7 +46,13 @@ __device__ __forceinline__ int block_excl_scan(int v, int& total) {
 
 __device__ __forceinline__ int tiles_of(int n) { return n > 0 ? (n + kTile - 1) / kTile : 1; }
 
-template <typename T>
+// value of item j: the element itself, or (kNot) 1 for a zero byte
+template <typename T, bool kNot>
+__device__ __forceinline__ int item(const T* __restrict__ in, int64_t j) {
+  return kNot ? (in[j] == 0 ? 1 : 0) : (int)in[j];
+}
+
+template <typename T, bool kNot>
 __global__ void k_tile_sums(const T* __restrict__ in, const int* n_dev, int n_host,
                             int32_t* __restrict__ sums) {
   const int n = dev_n(n_dev, n_host);
@@ -58,7 +64,7 @@ __global__ void k_tile_sums(const T* __restrict__ in, const int* n_dev, int n_ho
 #pragma unroll
     for (int i = 0; i < kItems; i++) {
       const int64_t j = base + (int64_t)i * kBlock + threadIdx.x;  // striped: coalesced
-      if (j < n) s += (int)in[j];
+      if (j < n) s += item<T, kNot>(in, j);
     }
     s = __reduce_add_sync(0xffffffffu, s);
     if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
@@ -87,7 +93,7 @@ __global__ void k_scan_sums(int32_t* sums, const int* n_dev, int n_host) {
   if (threadIdx.x == 0) sums[m] = carry;
 }
 
-template <typename T>
+template <typename T, bool kNot>
 __global__ void k_tile_apply(const T* __restrict__ in, const int* n_dev, int n_host,
                              const int32_t* __restrict__ sums, int32_t* __restrict__ out) {
   // blocked arrangement so that each thread owns kItems consecutive items
@@ -99,7 +105,7 @@ __global__ void k_tile_apply(const T* __restrict__ in, const int* n_dev, int n_h
 #pragma unroll
     for (int i = 0; i < kItems; i++) {
       const int64_t j = base + (int64_t)i * kBlock + threadIdx.x;
-      tile_buf[i * kBlock + threadIdx.x] = j < n ? (int)in[j] : 0;
+      tile_buf[i * kBlock + threadIdx.x] = j < n ? item<T, kNot>(in, j) : 0;
     }
     __syncthreads();
     int v[kItems];
@@ -127,12 +133,12 @@ __global__ void k_tile_apply(const T* __restrict__ in, const int* n_dev, int n_h
   if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = sums[tiles];
 }
 
-template <typename T>
+template <typename T, bool kNot = false>
 pamo_status scan_launch(const T* in, const int* n_dev, int n_host, int32_t* out, int32_t* sums,
                         int grid, cudaStream_t st) {
-  k_tile_sums<T><<<grid, kBlock, 0, st>>>(in, n_dev, n_host, sums); note_launch();
+  k_tile_sums<T, kNot><<<grid, kBlock, 0, st>>>(in, n_dev, n_host, sums); note_launch();
   k_scan_sums<<<1, kBlock, 0, st>>>(sums, n_dev, n_host); note_launch();
-  k_tile_apply<T><<<grid, kBlock, 0, st>>>(in, n_dev, n_host, sums, out); note_launch();
+  k_tile_apply<T, kNot><<<grid, kBlock, 0, st>>>(in, n_dev, n_host, sums, out); note_launch();
   PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;
 }
@@ -174,6 +180,11 @@ pamo_status scan_dev_i32(const int32_t* in, const int* n_dev, int32_t* out, int3
 pamo_status scan_dev_u8(const uint8_t* in, const int* n_dev, int32_t* out, int32_t* sums, int grid,
                         cudaStream_t st) {
   return scan_launch<uint8_t>(in, n_dev, 0, out, sums, grid, st);
+}
+
+pamo_status scan_dev_u8_not(const uint8_t* in, const int* n_dev, int32_t* out, int32_t* sums,
+                            int grid, cudaStream_t st) {
+  return scan_launch<uint8_t, true>(in, n_dev, 0, out, sums, grid, st);
 }
 
 }  // namespace pamo

@@ -131,6 +131,27 @@ __global__ void k_collapse(const int32_t* __restrict__ wlist, const RoundCounter
   }
 }
 
+__global__ void k_stage_ms(const RoundCounters* __restrict__ dc, const float4* __restrict__ pos,
+                           const double* __restrict__ K, const int4* __restrict__ F,
+                           float4* __restrict__ pos_s, double* __restrict__ K_s,
+                           int4* __restrict__ F_s, uint8_t* __restrict__ vdead,
+                           uint8_t* __restrict__ fdead, int32_t* __restrict__ ftag) {
+  const int nV = dc->nV, nF = dc->nF;
+  GRID_STRIDE(v, nV) {
+    pos_s[v] = pos[v];
+    const double2* src = reinterpret_cast<const double2*>(K + 10 * v);
+    double2* dst = reinterpret_cast<double2*>(K_s + 10 * v);
+#pragma unroll
+    for (int i = 0; i < 5; i++) dst[i] = src[i];
+    vdead[v] = 0;
+  }
+  GRID_STRIDE(f, nF) {
+    F_s[f] = F[f];
+    fdead[f] = 0;
+    ftag[f] = -1;
+  }
+}
+
 // Undo every marked, still-standing collapse: its region returns to M_1.
 __global__ void k_undo(const int32_t* __restrict__ wlist, const int2* __restrict__ E,
                        const float4* __restrict__ pos, const double* __restrict__ K,
@@ -183,7 +204,13 @@ __global__ void k_check_result(RoundCounters* __restrict__ dc) {
   if (!dc->cand_overflow) dc->pairs_total += dc->n_pairs;
   const bool undone = dc->n_undo > 0;
   dc->undo_iters += undone ? 1 : 0;
-  dc->clean = (!undone && !dc->cand_overflow) ? 1 : 0;
+  const int go = (!undone && !dc->cand_overflow) ? 1 : 0;
+  dc->clean = go;
+  // commit gate: the compaction that follows runs on these sizes (0 = no-op)
+  dc->go = go;
+  dc->goV = go ? dc->nV : 0;
+  dc->goF = go ? dc->nF : 0;
+  dc->goW = go ? dc->nW : 0;
 }
 
 }  // namespace
@@ -205,13 +232,9 @@ pamo_status collapse_winners(pamo_ctx* c) {
   cudaStream_t st = c->st;
   RoundCounters* dc = c->dc;
   const int G = c->grid;
-  // M_s starts as a copy of M_1
-  PAMO_TRY(copy_dev(c->pos_s, c->pos, &dc->nV, 0, sizeof(float4), G, st));
-  PAMO_TRY(copy_dev(c->K_s, c->K, &dc->nV, 0, 10 * sizeof(double), G, st));
-  PAMO_TRY(copy_dev(c->F_s, c->F, &dc->nF, 0, sizeof(int4), G, st));
-  PAMO_TRY(fill_dev1(c->fdead, &dc->nF, 0, G, st));
-  PAMO_TRY(fill_dev1(c->vdead, &dc->nV, 0, G, st));
-  PAMO_TRY(fill_dev4(c->ftag, &dc->nF, 0, 0xffffffffu, G, st));
+  // M_s starts as a copy of M_1: nothing dead, no face tagged
+  k_stage_ms<<<G, kBlock, 0, st>>>(dc, c->pos, c->K, c->F, c->pos_s, c->K_s, c->F_s, c->vdead,
+                                   c->fdead, c->ftag); note_launch();
   static const int g_collapse = occ_grid(k_collapse);
   k_collapse<<<g_collapse, kBlock, 0, st>>>(c->wlist, dc, c->E, c->vbar, c->K, c->vf_off, c->vf_idx, c->F,
                                    c->pos_s, c->K_s, c->F_s, c->fdead, c->vdead, c->ftag,
