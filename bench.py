@@ -168,6 +168,55 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def min_angles_deg(V, F):
+    """Smallest interior angle of every triangle, in degrees (float64)."""
+    P = np.asarray(V, np.float64)[np.asarray(F)]
+    out = np.full(len(F), 180.0)
+    for i in range(3):
+        u = P[:, (i + 1) % 3] - P[:, i]
+        w = P[:, (i + 2) % 3] - P[:, i]
+        den = np.linalg.norm(u, axis=1) * np.linalg.norm(w, axis=1)
+        cos = np.einsum("ij,ij->i", u, w) / np.where(den > 0, den, 1.0)
+        ang = np.degrees(np.arccos(np.clip(cos, -1.0, 1.0)))
+        out = np.minimum(out, np.where(den > 0, ang, 0.0))
+    return out
+
+
+ABLATION = {"full": (0.001, 0.005), "no_ce": (0.0, 0.005), "no_cs": (0.001, 0.0),
+            "no_ce_cs": (0.0, 0.0)}
+ALPHAS = (10.0, 5.0, 1.0)
+
+
+def run_ablation(args):
+    """Edge-cost ablation (the paper's bad-triangle study): each Eq. 1 term
+    switched off in turn, bad-triangle ratio (min angle below 10/5/1 degrees)
+    of the output on synthetic meshes, on the GPU path."""
+    import torch
+    import meshgen
+    import paper_2509_05595_gb300 as pamo
+    cases = []
+    Vb, Fb = meshgen.box_grid(32)
+    cases.append(("box_grid_32 to 10%", Vb, Fb, len(Fb) // 10))
+    Vt, Ft = meshgen.torus()
+    cases.append(("torus_64x32 to 10%", Vt, Ft, len(Ft) // 10))
+    Vs, Fs = meshgen.bumped_icosphere(7, 0)
+    cases.append(("bumped_icosphere_l7 to 1%", Vs, Fs, len(Fs) // 100))
+    res = {}
+    for name, V, F, target in cases:
+        Vd, Fd = torch.from_numpy(V).cuda(), torch.from_numpy(F).cuda()
+        res[name] = {}
+        for var, (w_e, w_s) in ABLATION.items():
+            opts = pamo.Options(w_e=w_e, w_s=w_s, validate_input=0)
+            pamo.pamo_simplify(Vd, Fd, target, options=opts)  # warm-up
+            Vo, Fo, st, status = pamo.pamo_simplify(Vd, Fd, target, options=opts)
+            m = min_angles_deg(Vo.cpu().numpy(), Fo.cpu().numpy())
+            res[name][var] = {"bad_pct": [round(100.0 * float((m < a).mean()), 3) for a in ALPHAS],
+                              "faces_out": int(len(Fo)), "status": status,
+                              "rounds": st["rounds"], "ms": round(st["ms_total"], 3)}
+    print(json.dumps({"ablation": "edge_cost_terms", "alpha_deg": list(ALPHAS),
+                      "data": "synthetic", "cases": res}), flush=True)
+
+
 def host_leg(pamo, torch, V, F, target, steps):
     """pamo_simplify_host from pinned host arrays: copies inside the timing."""
     hV = torch.from_numpy(V).pin_memory().numpy()
@@ -192,6 +241,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
+    ap.add_argument("--ablation", action="store_true",
+                    help="edge-cost ablation (bad-triangle ratios) instead of the benchmark")
     ap.add_argument("--level", type=int, default=8,
                     help="icosphere level of the workload (8 = the benchmark; smaller "
                          "levels only for profiling captures)")
@@ -202,6 +253,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.ablation:
+        if rank == 0:
+            run_ablation(args)
         return
 
     import torch
@@ -292,7 +347,7 @@ def main():
                        "l2": "flushed between steps (256 MiB write, outside the timed span)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "clocks": clk, "e2e": e2e,
-            "gpu_launches": int(launches // args.steps)}
+            "gpu_launches": int(launches)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_sample()
     if rank == 0:

@@ -67,6 +67,18 @@ typedef struct {
                               pamo_ctx_round_info / pamo_ctx_round_pairs */
   int32_t profile;         /* bit mask of PAMO_KC_* kernel classes to time with
                               CUDA events (0 = none; timing adds event records) */
+  int32_t exact_target;    /* 1 = stop at exactly the target face count where
+                              collapses allow it: a round whose winners would
+                              remove more faces than |F| - N_t collapses only
+                              the ceil((|F| - N_t) / 2) winners with the
+                              lowest keys. 0 (default) collapses every winner,
+                              as Algorithm 1 does, so |F| may end below N_t */
+  double max_cost;         /* target edge cost (Section 5.1 names it as the
+                              other termination criterion): an edge whose
+                              float cost exceeds it is not eligible, and the
+                              run ends with PAMO_OK once no edge is eligible
+                              and no flag is pending, even above N_t. Must be
+                              >= 0; default +infinity (off) */
 } pamo_options;
 
 /* Kernel classes reported in pamo_stats (index = bit of pamo_options.profile). */

@@ -137,11 +137,14 @@ class Result:
 
 def simplify(V, F, target, w_e=W_E, w_s=W_S, tolerance=TOLERANCE,
              max_rounds=100000, stall_limit=12, check_mode=CHECK_GRID,
-             keep_pairs=True):
+             keep_pairs=True, exact_target=0, max_cost=float("inf")):
+    """Algorithm 1 on the CPU.  exact_target / max_cost: the two termination
+    refinements of Section 5.1 (keep only the lowest-key winners needed to
+    reach N_t; edges costing more than max_cost are not eligible)."""
     V, F = _f32(V), _i32(F)
     L = lib()
-    w = np.array([w_e, w_s], np.float64)
-    iopt = np.array([tolerance, max_rounds, stall_limit, check_mode], np.int32)
+    w = np.array([w_e, w_s, max_cost], np.float64)
+    iopt = np.array([tolerance, max_rounds, stall_limit, check_mode, exact_target], np.int32)
     h = L.or_run(_ptr(V), len(V), _ptr(F), len(F), int(target), _ptr(w), _ptr(iopt))
     try:
         nv, nf = L.or_nv(h), L.or_nf(h)

@@ -38,6 +38,12 @@
 //   R10 flags: undone edges are invalid next round; after a round with no
 //      committed collapse the flags accumulate, cleared after `tolerance`
 //      such rounds.
+//   R14 target edge cost (Section 5.1 names it beside the face target): an
+//      edge whose float cost is above (float)max_cost is not eligible; the
+//      run ends normally when no edge is eligible and no flag is pending.
+//   R15 exact target: when a round's winners would remove more faces than
+//      |F| - N_t, only the ceil((|F| - N_t) / 2) winners with the lowest keys
+//      collapse (off by default: Algorithm 1 collapses every winner).
 //
 // Floating point: compiled with -ffp-contract=off (no implicit contraction),
 // IEEE double throughout the cost with explicit std::fma where the order says
@@ -488,7 +494,9 @@ static double tri_quality(const double* q0, const double* q1, const double* q2) 
 // ---------------------------------------------------------------------------
 struct Options {
   double w_e, w_s;
+  double max_cost;  // target edge cost (Section 5.1): +inf = off
   int32_t tolerance, max_rounds, stall_limit, check_mode;
+  int32_t exact_target;  // keep only the lowest-key winners needed for N_t
   // check_mode: 0 = changed faces vs all faces (cell grid),
   //             1 = changed faces vs all faces (brute force),
   //             2 = all face pairs, brute force (Algorithm 3 as printed),
@@ -875,6 +883,14 @@ static double input_scale(const float* V, int64_t nV) {
   return ext > 0.0 ? 1.0 / ext : 1.0;
 }
 
+static uint32_t float_bits_of_max_cost(double max_cost) {
+  if (!(max_cost < INFINITY)) return 0x7f800000u;  // +inf: every finite cost
+  float f = (float)max_cost;
+  uint32_t b;
+  std::memcpy(&b, &f, 4);
+  return b;
+}
+
 static void simplify(Mesh m, int64_t target, const Options& o, Run& run) {
   run.scale = input_scale(m.V.data(), m.nV);
   std::vector<int64_t> off;
@@ -898,11 +914,16 @@ static void simplify(Mesh m, int64_t target, const Options& o, Run& run) {
     std::vector<EdgeInfo> edges;
     analyse_edges(m, off, idx, run.scale, o, flags, edges);
     L.nE = (int64_t)edges.size();
+    // target edge cost (R14): an edge whose float cost exceeds (float)max_cost
+    // is not eligible; compared on the key's float bits (non-negative floats
+    // order as unsigned integers)
+    const uint32_t max_bits = float_bits_of_max_cost(o.max_cost);
     std::vector<char> elig(edges.size(), 0);
     for (size_t i = 0; i < edges.size(); i++) {
       if (!edges[i].link_ok) L.link_rejects++;
       if (edges[i].flagged) L.flagged++;
-      elig[i] = edges[i].link_ok && !edges[i].flagged && edges[i].key != ~0ull;
+      elig[i] = edges[i].link_ok && !edges[i].flagged && edges[i].key != ~0ull &&
+                (uint32_t)(edges[i].key >> 32) <= max_bits;
       if (elig[i]) L.eligible++;
     }
     // --- cost propagation onto the 1-ring triangles (push form, Sec. 5.1)
@@ -924,6 +945,19 @@ static void simplify(Mesh m, int64_t target, const Options& o, Run& run) {
           break;
         }
       if (win) winners.push_back((int32_t)i);
+    }
+    // exact-target mode (R15): when the winners would remove more faces than
+    // |F| - N_t, keep the ceil((|F| - N_t) / 2) lowest keys, in edge-id order
+    if (o.exact_target) {
+      const int64_t need = (m.nF - target + 1) / 2;
+      if ((int64_t)winners.size() > need) {
+        std::vector<int32_t> by_key = winners;
+        std::sort(by_key.begin(), by_key.end(),
+                  [&](int32_t x, int32_t y) { return edges[x].key < edges[y].key; });
+        by_key.resize(need);
+        std::sort(by_key.begin(), by_key.end());
+        winners.swap(by_key);
+      }
     }
     L.winners = (int64_t)winners.size();
     for (int32_t w : winners) {
@@ -1078,7 +1112,9 @@ static void simplify(Mesh m, int64_t target, const Options& o, Run& run) {
     run.logs.push_back(std::move(L));
     round++;
     if (stall_empty || zero_streak >= o.stall_limit) {
-      if (m.nF > target) run.status = 4;
+      // with a target edge cost, running out of eligible edges is the normal end
+      const bool cost_end = stall_empty && std::isfinite(o.max_cost);
+      if (m.nF > target && !cost_end) run.status = 4;
       break;
     }
   }
@@ -1095,6 +1131,8 @@ static Options to_options(const double* w, const int32_t* iopt) {
   o.max_rounds = iopt[1];
   o.stall_limit = iopt[2];
   o.check_mode = iopt[3];
+  o.exact_target = iopt[4];
+  o.max_cost = w[2];
   return o;
 }
 

@@ -42,7 +42,8 @@ class _Options(ctypes.Structure):
                 ("tolerance", ctypes.c_int32), ("max_rounds", ctypes.c_int32),
                 ("stall_limit", ctypes.c_int32), ("validate_input", ctypes.c_int32),
                 ("check_mode", ctypes.c_int32), ("record_rounds", ctypes.c_int32),
-                ("profile", ctypes.c_int32)]
+                ("profile", ctypes.c_int32), ("exact_target", ctypes.c_int32),
+                ("max_cost", ctypes.c_double)]
 
 
 class _Stats(ctypes.Structure):
@@ -68,6 +69,8 @@ class Options:
     check_mode: int = 0
     record_rounds: int = 0
     profile: int = 0
+    exact_target: int = 0
+    max_cost: float = float("inf")
 
     def c(self):
         return _Options(**{f.name: getattr(self, f.name) for f in fields(self)})

@@ -6,6 +6,8 @@
 //     -> M_1 <- M_s (stable compaction) and invalid-edge flags (Sec. 5.3).
 #include <algorithm>
 #include <atomic>
+#include <climits>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -165,6 +167,14 @@ pamo_status check_options(const pamo_options* o) {
     set_error("check_mode must be 0, 1 or 3");
     return PAMO_EINVAL;
   }
+  if (o->exact_target != 0 && o->exact_target != 1) {
+    set_error("exact_target must be 0 or 1");
+    return PAMO_EINVAL;
+  }
+  if (!(o->max_cost >= 0.0)) {
+    set_error("max_cost must be >= 0 (+infinity = no cost target)");
+    return PAMO_EINVAL;
+  }
   return PAMO_OK;
 }
 
@@ -239,6 +249,12 @@ pamo_status create(const float* d_V, int64_t nV, const int32_t* d_F, int64_t nF,
     std::memset(c->hc, 0, sizeof(RoundCounters));
     c->hc->nV = (int)nV;
     c->hc->nF = (int)nF;
+    // target edge cost as float bits (costs are keyed as floats, Section 5.1)
+    c->hc->max_bits = 0x7f800000u;
+    if (o.max_cost < INFINITY) {
+      const float f = (float)o.max_cost;
+      std::memcpy(&c->hc->max_bits, &f, 4);
+    }
     cudaError_t e = cudaMemcpyAsync(c->dc, c->hc, sizeof(RoundCounters), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) s = cuda_fail(e, "cudaMemcpyAsync");
   }
@@ -381,6 +397,8 @@ pamo_status phase_select(pamo_ctx* c) {
   const double nV = (double)c->nV, nF = (double)c->nF, nE = 1.5 * nF;
   kc_begin(c, PAMO_KC_SELECT);
   PAMO_TRY(select_winners(c));
+  // exact-target mode (a full run only: the per-round entry points have no N_t)
+  if (c->opt.exact_target && c->in_run) PAMO_TRY(trim_winners(c));
   // edges+keys read twice, vkey written and read, CSR+faces read, flags scanned
   kc_end(c, PAMO_KC_SELECT, nE * (2 * 16 + 1 + 1 + 4 + 1 + 4) + nV * (8 + 8 + 4) + nF * (16 + 12));
   return PAMO_OK;
@@ -621,7 +639,10 @@ pamo_status finish_round(pamo_ctx* c) {
   c->nF = h.nF;
   c->stage = 0;
   const bool stall_empty = (eligible == 0 && nflags_in == 0);
-  if (stall_empty || c->zero_streak >= c->opt.stall_limit) c->stalled = true;
+  if (stall_empty || c->zero_streak >= c->opt.stall_limit) {
+    c->stalled = true;
+    c->stall_empty = stall_empty;
+  }
   return PAMO_OK;
 }
 
@@ -751,7 +772,21 @@ pamo_status round_commit(pamo_ctx* c) {
   return finish_round(c);
 }
 
+pamo_status run_rounds(pamo_ctx* c, int64_t target);
+
 pamo_status run(pamo_ctx* c, int64_t target) {
+  c->in_run = true;
+  pamo_status s = run_rounds(c, target);
+  c->in_run = false;
+  return s;
+}
+
+pamo_status run_rounds(pamo_ctx* c, int64_t target) {
+  {  // N_t on the device (exact-target trimming reads it); pageable source,
+     // so the call returns once the value has been staged
+    const int t = (int)std::min<int64_t>(target, INT32_MAX);
+    PAMO_CUDA(cudaMemcpyAsync(&c->dc->target, &t, sizeof(int), cudaMemcpyHostToDevice, c->st));
+  }
   while (c->nF > target) {
     if (c->rounds >= c->opt.max_rounds) {
       c->status = PAMO_ESTALL;
@@ -763,7 +798,9 @@ pamo_status run(pamo_ctx* c, int64_t target) {
     }
     PAMO_TRY(graph_round(c));
     if (c->stalled) {
-      if (c->nF > target) c->status = PAMO_ESTALL;
+      // with a target edge cost, running out of eligible edges is the normal end
+      const bool cost_end = c->stall_empty && c->opt.max_cost < INFINITY;
+      if (c->nF > target && !cost_end) c->status = PAMO_ESTALL;
       break;
     }
   }
@@ -810,6 +847,8 @@ void pamo_default_options(pamo_options* o) {
   o->check_mode = 0;
   o->record_rounds = 0;
   o->profile = 0;
+  o->exact_target = 0;
+  o->max_cost = INFINITY;
 }
 
 const char* pamo_last_error(void) { return g_err.c_str(); }

@@ -67,7 +67,8 @@ struct RoundCounters {
   int nflags;               // entries of the invalid-edge flag list
   int have_prev;            // last round's edge costs can be reused
   int nV_edges;             // vertex count the edge offsets were built for
-  int pad0[2];
+  int target;               // N_t of the running simplification
+  unsigned max_bits;        // float bits of the target edge cost (0x7f800000 = off)
   // ---- zeroed at the start of every round (from link_rejects on)
   unsigned long long link_rejects, flagged, eligible;
   unsigned long long cost_tris;  // triangles produced, summed over evaluated edges
@@ -137,6 +138,8 @@ struct pamo_ctx {
   int undo_iters = 0;
   int64_t last_pairs = 0;              // intersecting pairs found this round
   bool stalled = false;
+  bool stall_empty = false;            // stopped because nothing was eligible
+  bool in_run = false;                 // inside pamo_simplify / pamo_ctx_run
   double scale = 1.0;                  // 1 / max bbox extent of the input
   float bb_lo[3], bb_hi[3];            // input bounding box (Morton frame)
   int stage = 0;                       // 0 idle, 1 costed, 2 selected, 3 collapsed, 4 checked
@@ -277,6 +280,8 @@ pamo_status edge_costs(pamo_ctx* c);
 
 // select.cu -----------------------------------------------------------------
 pamo_status select_winners(pamo_ctx* c);
+// exact-target mode: keep the ceil((nF - target) / 2) lowest-key winners
+pamo_status trim_winners(pamo_ctx* c);
 pamo_status collapse_winners(pamo_ctx* c);
 pamo_status undo_marked(pamo_ctx* c);
 pamo_status check_result(pamo_ctx* c);

@@ -105,6 +105,7 @@ __global__ void __launch_bounds__(kBlock) k_edge_reuse(
     int32_t* __restrict__ dlist, RoundCounters* __restrict__ dc) {
   const int nE = dc->nE;
   const int nflags = dc->nflags;
+  const unsigned max_bits = dc->max_bits;
   const bool all_dirty = !dc->have_prev;
   int link_bad = 0, flagged = 0, eligible = 0;
   const int lane = threadIdx.x & 31;
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(kBlock) k_edge_reuse(
                           is_flagged(flags, nflags,
                                      ((unsigned long long)(unsigned)ab.x << 32) | (unsigned)ab.y);
         unsigned long long k = ~0ull;
-        if (cb != 0xffffffffu && lk && !flag) {
+        if (cb != 0xffffffffu && cb <= max_bits && lk && !flag) {
           k = ((unsigned long long)cb << 32) | (unsigned long long)(uint32_t)e;
           eligible++;
         }
@@ -170,6 +171,7 @@ __global__ void __launch_bounds__(kBlock) k_edge_cost(
     RoundCounters* __restrict__ dc) {
   const int ndirty = dc->n_dirty;
   const int nflags = dc->nflags;
+  const unsigned max_bits = dc->max_bits;
   int link_bad = 0, flagged = 0, eligible = 0, ntri = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndirty;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -295,7 +297,7 @@ __global__ void __launch_bounds__(kBlock) k_edge_cost(
       cb = __float_as_uint(cf);
     }
     unsigned long long k = ~0ull;
-    if (cb != 0xffffffffu && link_ok && !flag) {
+    if (cb != 0xffffffffu && cb <= max_bits && link_ok && !flag) {
       k = ((unsigned long long)cb << 32) | (unsigned long long)(uint32_t)e;
       eligible++;
     }

@@ -213,7 +213,104 @@ __global__ void k_check_result(RoundCounters* __restrict__ dc) {
   dc->goW = go ? dc->nW : 0;
 }
 
+// Exact-target mode: when the winners would remove more faces than nF - N_t,
+// keep the need = ceil((nF - N_t) / 2) winners with the lowest keys, in edge
+// order.  One block: an MSB-first radix select (8 passes of 8 bits) finds the
+// need-th smallest key T (keys are unique: the low word is the edge id), then
+// an ordered in-place compaction keeps the winners with key <= T.  It runs at
+// most in the last round or two of a simplification; otherwise it returns at
+// once.
+constexpr int kTrimBlock = 1024;
+
+__device__ __forceinline__ int block_excl_scan_1024(int v, int& total) {
+  __shared__ int ws[kTrimBlock / 32 + 1];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) ws[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    const int w = ws[lane];  // kTrimBlock / 32 == 32 warps
+    int wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    ws[lane] = wi - w;
+    if (lane == 31) ws[32] = wi;
+  }
+  __syncthreads();
+  const int r = ws[wid] + inc - v;
+  total = ws[32];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kTrimBlock) k_trim(const unsigned long long* __restrict__ key,
+                                                     int32_t* __restrict__ wlist,
+                                                     RoundCounters* __restrict__ dc) {
+  const int nW = dc->nW;
+  const int excess = dc->nF - dc->target;
+  const int need = excess > 0 ? (excess + 1) / 2 : 0;
+  if (nW <= need) return;  // every winner is needed
+  __shared__ int hist[256];
+  __shared__ unsigned long long s_prefix;
+  __shared__ int s_rank;
+  unsigned long long prefix = 0, mask = 0;
+  int rank = need;  // 1-based rank of the wanted key among those matching prefix
+  for (int shift = 56; shift >= 0; shift -= 8) {
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    for (int w = threadIdx.x; w < nW; w += blockDim.x) {
+      const unsigned long long k = key[wlist[w]];
+      if ((k & mask) == prefix) atomicAdd(&hist[(int)((k >> shift) & 0xffu)], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int below = 0, d = 0;
+      for (; d < 255; d++) {
+        if (below + hist[d] >= rank) break;
+        below += hist[d];
+      }
+      s_prefix = prefix | ((unsigned long long)d << shift);
+      s_rank = rank - below;
+    }
+    __syncthreads();
+    prefix = s_prefix;
+    rank = s_rank;
+    mask |= 0xffull << shift;
+    __syncthreads();
+  }
+  const unsigned long long T = prefix;  // the need-th smallest key
+  int base = 0;
+  for (int start = 0; start < nW; start += blockDim.x) {
+    const int w = start + threadIdx.x;
+    int e = -1, keep = 0;
+    if (w < nW) {
+      e = wlist[w];
+      keep = key[e] <= T ? 1 : 0;
+    }
+    int total;
+    const int ex = block_excl_scan_1024(keep, total);  // synchronises: reads done
+    if (keep) wlist[base + ex] = e;  // base + ex <= w: never ahead of a read
+    base += total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) dc->nW = base;
+}
+
 }  // namespace
+
+pamo_status trim_winners(pamo_ctx* c) {
+  k_trim<<<1, kTrimBlock, 0, c->st>>>(c->key, c->wlist, c->dc); note_launch();
+  PAMO_CUDA(cudaGetLastError());
+  return PAMO_OK;
+}
 
 pamo_status select_winners(pamo_ctx* c) {
   cudaStream_t st = c->st;

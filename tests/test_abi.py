@@ -49,6 +49,7 @@ def test_library_loads_and_binding_resolves(libpath):
     o = pamo._Options()
     L.pamo_default_options(ctypes.byref(o))
     assert (o.w_e, o.w_s, o.tolerance) == (0.001, 0.005, 4)
+    assert (o.exact_target, o.max_cost) == (0, float("inf"))
     assert pamo.Options().c().tolerance == o.tolerance
 
 
@@ -58,7 +59,7 @@ def test_struct_layouts_match_c(tmp_path):
     prog.write_text('#include "pamo.h"\n#include <stdio.h>\n#include <stddef.h>\n'
                     'int main(){printf("%zu %zu %zu %zu\\n", sizeof(pamo_options), '
                     'sizeof(pamo_stats), offsetof(pamo_stats, committed), '
-                    'offsetof(pamo_options, record_rounds));return 0;}\n')
+                    'offsetof(pamo_options, max_cost));return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)],
                    check=True)
@@ -67,7 +68,7 @@ def test_struct_layouts_match_c(tmp_path):
     assert a == ctypes.sizeof(pamo._Options)
     assert b == ctypes.sizeof(pamo._Stats)
     assert c == pamo._Stats.committed.offset
-    assert d == pamo._Options.record_rounds.offset
+    assert d == pamo._Options.max_cost.offset
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

@@ -107,9 +107,10 @@ def _gpu_run(V, F, target, **opts):
     return Vo.cpu().numpy(), Fo.cpu().numpy(), rounds, stats, status
 
 
-def _assert_same_run(V, F, target, check_mode=oracle.CHECK_GRID, gpu_mode=0):
-    ref = oracle.simplify(V, F, target, check_mode=check_mode)
-    gV, gF, rounds, stats, status = _gpu_run(V, F, target, check_mode=gpu_mode)
+def _assert_same_run(V, F, target, check_mode=oracle.CHECK_GRID, gpu_mode=0, **opts):
+    """opts (w_e, w_s, exact_target, max_cost) go to both sides."""
+    ref = oracle.simplify(V, F, target, check_mode=check_mode, **opts)
+    gV, gF, rounds, stats, status = _gpu_run(V, F, target, check_mode=gpu_mode, **opts)
     assert len(rounds) == len(ref.rounds)
     for r, (g, o) in enumerate(zip(rounds, ref.rounds)):
         for k in oracle.ROUND_FIELDS:

@@ -1,0 +1,61 @@
+"""GPU parity of the option variants: the two termination refinements of
+Section 5.1 (exact target face count, target edge cost) and the Eq. 1
+ablation switches (w_e = 0, w_s = 0, both) of the edge-cost study.
+
+Same bar as the plain path: per-round collapse sets, counters, output
+connectivity and position bits identical to the oracle's.
+"""
+import numpy as np
+import pytest
+
+import meshgen
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from tests.test_gpu_parity import _assert_same_run  # noqa: E402
+
+
+@pytest.mark.parametrize("mesh", ["torus", "sphere5", "shells4", "shells4_stall"])
+def test_exact_target_bit_exact(mesh):
+    V, F, target = {
+        "torus": lambda: (*meshgen.mesh_config("torus_64x32")[:2], 1000),
+        "sphere5": lambda: (*meshgen.bumped_icosphere(5, 9), 2 * 1023),
+        "shells4": lambda: (*meshgen.nested_shells(4, check=False), 2400),
+        # the trimmed winners get undone near the end: a stall, on both sides
+        "shells4_stall": lambda: (*meshgen.nested_shells(4, check=False), 1400),
+    }[mesh]()
+    ref, stats = _assert_same_run(V, F, target, exact_target=1)
+    if ref.status == 0:
+        assert len(ref.F) == target  # even face counts: exactly N_t
+
+
+def test_exact_target_single_collapse_is_global_minimum():
+    V, F = meshgen.bumped_icosphere(4, 3)
+    ref, _ = _assert_same_run(V, F, len(F) - 2, exact_target=1)
+    T = oracle.edge_table(V, F)
+    e = int(np.argmin(T["key"]))
+    assert ref.rounds[0]["winners"] == 1
+    assert ref.rounds[0]["winner_pairs"].tolist() == [T["ab"][e].tolist()]
+
+
+@pytest.mark.parametrize("q", [0.0, 0.2, 0.6])
+def test_max_cost_bit_exact(q):
+    V, F = meshgen.bumped_icosphere(5, 4)
+    T = oracle.edge_table(V, F)
+    c = float(np.quantile(T["cost"], q)) if q > 0 else 0.0
+    ref, _ = _assert_same_run(V, F, 64, max_cost=c)
+    assert ref.status == 0  # the cost target ends the run normally
+    assert ref.rounds[-1]["eligible"] == 0
+
+
+@pytest.mark.parametrize("w_e,w_s", [(0.0, 0.005), (0.001, 0.0), (0.0, 0.0)])
+def test_cost_ablation_switches_bit_exact(w_e, w_s):
+    V, F = meshgen.bumped_icosphere(5, 2)
+    _assert_same_run(V, F, len(F) // 50, w_e=w_e, w_s=w_s)
+    Vt, Ft, target = meshgen.mesh_config("torus_64x32")
+    _assert_same_run(Vt, Ft, target, w_e=w_e, w_s=w_s)

@@ -150,3 +150,92 @@ def test_stall_on_tetrahedron_and_octahedron_to_tetrahedron():
     r = oracle.simplify(V, F, 4)
     assert r.status == 0 and len(r.F) == 4
     _check_mesh(r.V, r.F, 2, 1)
+
+
+# ------------------------------------------------ termination refinements
+# Section 5.1 names two termination criteria: a target face count (the default
+# above) and a target edge cost.  exact_target keeps only the winners needed to
+# land on N_t; max_cost makes costlier edges ineligible.
+def _same_rounds(a, b):
+    for k in oracle.ROUND_FIELDS:
+        if a[k] != b[k]:
+            return False
+    return all(np.array_equal(a[k], b[k])
+               for k in ("winner_pairs", "committed_pairs", "undone_pairs"))
+
+
+def test_exact_target_single_collapse_is_the_global_minimum():
+    # N_t = |F| - 2: one collapse is needed, so the trimmed round keeps the
+    # edge with the smallest key of the whole mesh (always a winner)
+    V, F = meshgen.bumped_icosphere(3, 7)
+    T = oracle.edge_table(V, F)
+    r = oracle.simplify(V, F, len(F) - 2, exact_target=1)
+    e = int(np.argmin(T["key"]))
+    assert len(r.rounds) == 1 and r.rounds[0]["winners"] == 1
+    assert r.rounds[0]["winner_pairs"].tolist() == [T["ab"][e].tolist()]
+    assert len(r.F) == len(F) - 2
+
+
+def test_exact_target_lands_on_target_and_only_trims_when_needed(torus_mesh):
+    V, F, _ = torus_mesh
+    target = 1000
+    plain = oracle.simplify(V, F, target)
+    exact = oracle.simplify(V, F, target, exact_target=1)
+    assert len(plain.F) < target           # Algorithm 1 overshoots here
+    assert exact.status == 0 and len(exact.F) == target
+    k = next(i for i, (a, b) in enumerate(zip(plain.rounds, exact.rounds))
+             if not _same_rounds(a, b))
+    a, b = plain.rounds[k], exact.rounds[k]
+    need = (b["nF"] - target + 1) // 2
+    assert b["winners"] == need < a["winners"]
+    kept = {tuple(p) for p in b["winner_pairs"].tolist()}
+    assert kept <= {tuple(p) for p in a["winner_pairs"].tolist()}
+    V2, F2 = exact.V, exact.F
+    assert is_closed_manifold(F2, len(V2)) and euler(F2, len(V2)) == 0
+
+
+def test_max_cost_round0_eligibility_and_normal_end(torus_mesh):
+    V, F, target = torus_mesh
+    T = oracle.edge_table(V, F)
+    finite = T["key"] != np.uint64(0xFFFFFFFFFFFFFFFF)
+    c = float(np.quantile(T["cost"][finite], 0.3))
+    r = oracle.simplify(V, F, 0, max_cost=c)
+    want = int((finite & (T["cost"].astype(np.float32) <= np.float32(c))).sum())
+    assert r.rounds[0]["eligible"] == want
+    assert r.status == 0 and len(r.F) > 0          # ended by the cost target
+    assert r.rounds[-1]["eligible"] == 0
+    assert is_closed_manifold(r.F, len(r.V)) and euler(r.F, len(r.V)) == 0
+    # nothing costs less than zero: max_cost = 0 stops at once, unchanged
+    z = oracle.simplify(V, F, target, max_cost=0.0)
+    assert z.status == 0 and len(z.rounds) == 1 and np.array_equal(z.F, F)
+    # +infinity is the default rule
+    d, i = oracle.simplify(V, F, target), oracle.simplify(V, F, target, max_cost=np.inf)
+    assert all(_same_rounds(a, b) for a, b in zip(d.rounds, i.rounds))
+
+
+def _bad_pct(V, F, alpha):
+    P = np.asarray(V, np.float64)[np.asarray(F)]
+    m = np.full(len(F), 180.0)
+    for i in range(3):
+        u = P[:, (i + 1) % 3] - P[:, i]
+        w = P[:, (i + 2) % 3] - P[:, i]
+        c = (u * w).sum(1) / (np.linalg.norm(u, axis=1) * np.linalg.norm(w, axis=1))
+        m = np.minimum(m, np.degrees(np.arccos(np.clip(c, -1, 1))))
+    return 100.0 * (m < alpha).mean()
+
+
+@pytest.mark.parametrize("mesh", ["box16", "torus"])
+def test_edge_cost_terms_reduce_bad_triangles(mesh):
+    # the edge-cost ablation of the paper: with both extra terms of Eq. 1 the
+    # output has the fewest triangles whose smallest angle is below 10 degrees,
+    # and QEM alone is clearly worse (flat regions, where QEM is constant)
+    V, F = meshgen.box_grid(16) if mesh == "box16" else meshgen.torus()
+    target = len(F) // 10
+    bad = {}
+    for name, (w_e, w_s) in {"full": (0.001, 0.005), "no_ce": (0.0, 0.005),
+                             "no_cs": (0.001, 0.0), "none": (0.0, 0.0)}.items():
+        r = oracle.simplify(V, F, target, w_e=w_e, w_s=w_s, keep_pairs=False)
+        assert is_closed_manifold(r.F, len(r.V))
+        bad[name] = _bad_pct(r.V, r.F, 10.0)
+    assert bad["full"] <= min(bad["no_ce"], bad["no_cs"], bad["none"])
+    assert bad["none"] >= bad["full"] + 2.0
