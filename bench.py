@@ -291,6 +291,7 @@ def main():
     barrier()
     torch.cuda.synchronize()
     times, dom_ms, dom_launch, dom_bytes, dom_flops, launches = [], 0.0, 0, 0.0, 0.0, 0
+    bytes_alg = 0.0
     out = None
     for _ in range(args.steps):
         flush.fill_(1)
@@ -306,6 +307,7 @@ def main():
         dom_bytes += st["class_bytes"][dom]
         dom_flops += st["class_flops"][dom]
         launches += st["launches"]
+        bytes_alg += st["bytes_model"]
         out = (Vo, Fo, st, status)
     torch.cuda.synchronize()
     barrier()
@@ -337,6 +339,11 @@ def main():
                 "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                 "peak_source": peak_kind, "launch_ms": avg_launch_ms, "class_share": share}
     Vo, Fo, st, status = out
+    # the whole pipeline against HBM: algorithmic bytes of every round / wall
+    hbm_peak, hbm_kind = peaks()
+    pipe_gbs = bytes_alg / args.steps / (ms_per_step * 1e-3) / 1e9
+    pipeline = {"bytes_alg_per_step": bytes_alg / args.steps, "achieved_gbs": pipe_gbs,
+                "peak_gbs": hbm_peak, "frac": pipe_gbs / hbm_peak, "peak_source": hbm_kind}
     line = {"metric": METRIC, "value": value, "unit": "Mfaces/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -346,7 +353,7 @@ def main():
                        "undo_iters_hist": st["undo_iters_hist"][:4],
                        "l2": "flushed between steps (256 MiB write, outside the timed span)",
                        "parallelism": f"replicas x{world}"},
-            "roofline": roof, "clocks": clk, "e2e": e2e,
+            "roofline": roof, "pipeline_hbm": pipeline, "clocks": clk, "e2e": e2e,
             "gpu_launches": int(launches)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_sample()
