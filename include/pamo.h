@@ -142,6 +142,33 @@ pamo_status pamo_simplify_host(const float* h_V, int64_t nV, const int32_t* h_F,
                                float* h_Vout, int64_t* nV_out, int32_t* h_Fout,
                                int64_t* nF_out, pamo_stats* stats);
 
+/* Simplify a batch of n_meshes closed manifold meshes in one pass (no
+ * counterpart in the paper, which simplifies one mesh at a time): every
+ * round of Algorithm 1 runs once over the disjoint union of all meshes, and
+ * each mesh keeps its own [0,1]^3 normalisation (Section 4 start), target,
+ * invalid-edge flags and tolerance count (Section 5.3) and termination, so
+ * the output of every mesh is bit-identical to pamo_simplify on that mesh.
+ *   d_V      device, [h_voff[n], 3] float32: the meshes' vertices, concatenated
+ *   h_voff   host, n + 1 int64 vertex offsets (h_voff[0] = 0)
+ *   d_F      device, [h_foff[n], 3] int32: the meshes' faces, concatenated;
+ *            each mesh's faces index its own vertices from 0
+ *   h_foff   host, n + 1 int64 face offsets (h_foff[0] = 0)
+ *   h_targets host, n target face counts (>= 0)
+ * Outputs: d_Vout / d_Fout (device, capacity of the inputs) hold the results
+ * in the same layout, with offsets in h_voff_out / h_foff_out (host, n + 1);
+ * h_status (host, n, may be NULL) gets PAMO_OK or PAMO_ESTALL per mesh and
+ * h_rounds (host, n, may be NULL) the rounds each mesh took.  Returns
+ * PAMO_ESTALL if any mesh stalled (all outputs still valid); PAMO_EINVAL for
+ * bad sizes, offsets, an index outside its mesh, or options.exact_target;
+ * PAMO_ENOTMANIFOLD as pamo_simplify.  Every mesh needs >= 4 vertices and an
+ * even face count >= 4; totals below 2^30.  Synchronous on return. */
+pamo_status pamo_simplify_batch(int32_t n_meshes, const float* d_V, const int64_t* h_voff,
+                                const int32_t* d_F, const int64_t* h_foff,
+                                const int64_t* h_targets, const pamo_options* opt, void* stream,
+                                float* d_Vout, int64_t* h_voff_out, int32_t* d_Fout,
+                                int64_t* h_foff_out, int32_t* h_status, int32_t* h_rounds,
+                                pamo_stats* stats);
+
 /* ---- per-round entry points (one round = one iteration of Algorithm 1's
  * while loop) over a context that owns the evolving mesh ---- */
 

@@ -91,6 +91,8 @@ def lib():
             "pamo_default_options": (None, [P]),
             "pamo_simplify": (ctypes.c_int, [P, i64, P, i64, i64, P, P, P, pi64, P, pi64, P]),
             "pamo_simplify_host": (ctypes.c_int, [P, i64, P, i64, i64, P, P, P, pi64, P, pi64, P]),
+            "pamo_simplify_batch": (ctypes.c_int, [i32, P, P, P, P, P, P, P, P, P, P, P, P, P,
+                                                   P]),
             "pamo_ctx_create": (ctypes.c_int, [P, i64, P, i64, P, P, ctypes.POINTER(P)]),
             "pamo_round_cost": (ctypes.c_int, [P]),
             "pamo_round_select": (ctypes.c_int, [P, pi64]),
@@ -174,6 +176,54 @@ def pamo_simplify(V, F, target_faces, options: Options | None = None, **kw):
                                _ptr(Fo), ctypes.byref(nf), ctypes.byref(st))
     _check(code, "pamo_simplify", ok=(PAMO_OK, PAMO_ESTALL))
     return Vo[: nv.value], Fo[: nf.value], _stats_dict(st), STATUS[code]
+
+
+def concat_meshes(meshes):
+    """Concatenate [(V, F), ...] (each F indexing its own V from 0) into the
+    batch layout: V [sum nV, 3], vertex offsets, F [sum nF, 3], face offsets."""
+    Vs = [np.ascontiguousarray(v, np.float32) for v, _ in meshes]
+    Fs = [np.ascontiguousarray(f, np.int32) for _, f in meshes]
+    voff = np.concatenate([[0], np.cumsum([len(v) for v in Vs])]).astype(np.int64)
+    foff = np.concatenate([[0], np.cumsum([len(f) for f in Fs])]).astype(np.int64)
+    return np.concatenate(Vs), voff, np.concatenate(Fs), foff
+
+
+def pamo_simplify_batch(V, voff, F, foff, targets, options: Options | None = None, **kw):
+    """Simplify many closed manifold meshes in one pass: every round runs once
+    over the whole batch and each mesh keeps its own normalisation, target,
+    flags and termination (each output equals that mesh simplified alone).
+
+    V: [sum nV, 3] float32 and F: [sum nF, 3] int32 concatenated (torch CUDA
+    tensors or array-likes; each mesh's faces index its own vertices from 0);
+    voff, foff: the M + 1 vertex / face offsets (host); targets: M face
+    targets.  Returns (V', voff', F', foff', status[M], rounds[M], stats)."""
+    import torch
+    o = options or Options(**kw)
+    V = _dev(V, torch.float32, 3)
+    F = _dev(F, torch.int32, 3)
+    voff = np.ascontiguousarray(voff, np.int64)
+    foff = np.ascontiguousarray(foff, np.int64)
+    M = len(voff) - 1
+    tg = np.ascontiguousarray(targets, np.int64)
+    if len(foff) != M + 1 or len(tg) != M:
+        raise ValueError("offsets need M + 1 entries and targets M")
+    Vo = torch.empty_like(V)
+    Fo = torch.empty_like(F)
+    vo = np.zeros(M + 1, np.int64)
+    fo = np.zeros(M + 1, np.int64)
+    status = np.zeros(M, np.int32)
+    rounds = np.zeros(M, np.int32)
+    st = _Stats()
+    opt = o.c()
+    code = lib().pamo_simplify_batch(
+        M, _ptr(V), voff.ctypes.data_as(ctypes.c_void_p), _ptr(F),
+        foff.ctypes.data_as(ctypes.c_void_p), tg.ctypes.data_as(ctypes.c_void_p),
+        ctypes.byref(opt), _stream(), _ptr(Vo), vo.ctypes.data_as(ctypes.c_void_p), _ptr(Fo),
+        fo.ctypes.data_as(ctypes.c_void_p), status.ctypes.data_as(ctypes.c_void_p),
+        rounds.ctypes.data_as(ctypes.c_void_p), ctypes.byref(st))
+    _check(code, "pamo_simplify_batch", ok=(PAMO_OK, PAMO_ESTALL))
+    return (Vo[: vo[-1]], vo, Fo[: fo[-1]], fo, [STATUS[int(x)] for x in status], rounds,
+            _stats_dict(st))
 
 
 def pamo_simplify_host(V, F, target_faces, options: Options | None = None, **kw):

@@ -117,6 +117,11 @@ void free_ctx_buffers(pamo_ctx* c) {
   release(c->cbits_prev, st); release(c->vbar_prev, st); release(c->link, st);
   release(c->link_prev, st); release(c->ivmap, st); release(c->vsurv, st); release(c->vdirty, st);
   release(c->dlist, st); release(c->scan_sums, st);
+  release(c->vmesh, st); release(c->vmesh_tmp, st); release(c->voff_d, st); release(c->foff_d, st);
+  release(c->mframe, st); release(c->mcost, st); release(c->mactive, st); release(c->mcount, st);
+  release(c->mvbase, st); release(c->flags_old, st);
+  if (c->mcount_h) cudaFreeHost(c->mcount_h);
+  c->mcount_h = nullptr;
   for (int r = 0; r < 3; r++) release(c->cand[r], st);
   buf_free(c->scan_tmp, st);
   buf_free(c->quad_tmp, st);
@@ -178,43 +183,40 @@ pamo_status check_options(const pamo_options* o) {
   return PAMO_OK;
 }
 
-pamo_status create(const float* d_V, int64_t nV, const int32_t* d_F, int64_t nF,
-                   const pamo_options* opt, cudaStream_t st, pamo_ctx** out) {
-  *out = nullptr;
-  if (!d_V || !d_F || nV < 4 || nF < 4) {
-    set_error("need device arrays and a closed mesh (nV >= 4, nF >= 4)");
-    return PAMO_EINVAL;
-  }
-  if (nF % 2 != 0 || nF >= (int64_t)1 << 30 || nV >= (int64_t)1 << 30) {
-    set_error("face count must be even (closed mesh) and sizes below 2^30");
-    return PAMO_EINVAL;
-  }
+// the context's stream (ordered after the caller's) and options
+pamo_status new_ctx(const pamo_options* opt, cudaStream_t st, pamo_ctx** out) {
   pamo_options o;
   if (opt) o = *opt;
   else pamo_default_options(&o);
   PAMO_TRY(check_options(&o));
   pamo_ctx* c = new pamo_ctx();
   c->ust = st;
-  {
-    cudaError_t e = cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventRecord(c->join_ev, st);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->st, c->join_ev, 0);
-    if (e != cudaSuccess) {
-      if (c->join_ev) cudaEventDestroy(c->join_ev);
-      if (c->st) cudaStreamDestroy(c->st);
-      delete c;
-      return cuda_fail(e, "context stream");
-    }
+  cudaError_t e = cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(c->join_ev, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->st, c->join_ev, 0);
+  if (e != cudaSuccess) {
+    if (c->join_ev) cudaEventDestroy(c->join_ev);
+    if (c->st) cudaStreamDestroy(c->st);
+    delete c;
+    return cuda_fail(e, "context stream");
   }
-  st = c->st;
   c->opt = o;
+  c->grid = default_grid();
+  c->sm_count = c->grid / 4;
+  *out = c;
+  return PAMO_OK;
+}
+
+// every buffer of a simplification of nV vertices and nF faces (sizes only
+// shrink, so nothing is allocated later); the batch arrays when n_mesh > 1
+pamo_status alloc_state(pamo_ctx* c, int64_t nV, int64_t nF) {
+  cudaStream_t st = c->st;
   c->nV0 = c->nV = nV;
   c->nF0 = c->nF = nF;
   c->Emax = (3 * nF) / 2 + 2;
-  c->grid = default_grid();
-  c->sm_count = c->grid / 4;
   const int64_t mx = std::max(nV, nF);
+  const int M = c->n_mesh;
   pamo_status s = PAMO_OK;
 #define A(ptr, n) if (s == PAMO_OK) s = alloc(&c->ptr, (size_t)(n), st)
   A(pos, nV); A(pos_s, nV); A(K, 10 * nV); A(K_s, 10 * nV); A(F, nF); A(F_s, nF);
@@ -238,28 +240,61 @@ pamo_status create(const float* d_V, int64_t nV, const int32_t* d_F, int64_t nF,
       for (int r = 0; r < 3; r++) c->cand_cap[r] = std::max<int64_t>(1, c->cand_cap[r] / d);
   }
   A(cand[0], c->cand_cap[0]); A(cand[1], c->cand_cap[1]); A(cand[2], c->cand_cap[2]);
+  if (M > 1) {
+    A(vmesh, nV); A(vmesh_tmp, nV); A(voff_d, M + 1); A(foff_d, M + 1);
+    A(mframe, 6 * (int64_t)M); A(mcost, 2 * (int64_t)M); A(mactive, M);
+    A(mcount, 3 * (int64_t)M); A(mvbase, M); A(flags_old, c->Emax);
+  }
 #undef A
+  c->bvh.n_mesh = M;
+  c->bvh.vmesh = c->vmesh;
+  c->bvh.mframe = c->mframe;
   if (s == PAMO_OK) s = bvh_alloc(c->bvh, (int)nF, st);
   if (s == PAMO_OK) {
     cudaError_t e = cudaMallocHost((void**)&c->hc, sizeof(RoundCounters));
     if (e != cudaSuccess) s = cuda_fail(e, "cudaMallocHost");
   }
-  if (s == PAMO_OK) s = load_mesh(d_V, nV, d_F, nF, c->pos, c->F, st);
-  if (s == PAMO_OK) {
-    std::memset(c->hc, 0, sizeof(RoundCounters));
-    c->hc->nV = (int)nV;
-    c->hc->nF = (int)nF;
-    // target edge cost as float bits (costs are keyed as floats, Section 5.1)
-    c->hc->max_bits = 0x7f800000u;
-    if (o.max_cost < INFINITY) {
-      const float f = (float)o.max_cost;
-      std::memcpy(&c->hc->max_bits, &f, 4);
-    }
-    cudaError_t e = cudaMemcpyAsync(c->dc, c->hc, sizeof(RoundCounters), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) s = cuda_fail(e, "cudaMemcpyAsync");
+  if (s == PAMO_OK && M > 1) {
+    cudaError_t e = cudaMallocHost((void**)&c->mcount_h, sizeof(int32_t) * 3 * (size_t)M);
+    if (e != cudaSuccess) s = cuda_fail(e, "cudaMallocHost");
   }
-  if (s == PAMO_OK && o.validate_input) s = validate_mesh(c);
-  if (s == PAMO_OK && !o.validate_input) s = build_vertex_faces(c);
+  return s;
+}
+
+// device counters at the start: sizes and the target edge cost
+pamo_status init_counters(pamo_ctx* c) {
+  std::memset(c->hc, 0, sizeof(RoundCounters));
+  c->hc->nV = (int)c->nV;
+  c->hc->nF = (int)c->nF;
+  // target edge cost as float bits (costs are keyed as floats, Section 5.1)
+  c->hc->max_bits = 0x7f800000u;
+  if (c->opt.max_cost < INFINITY) {
+    const float f = (float)c->opt.max_cost;
+    std::memcpy(&c->hc->max_bits, &f, 4);
+  }
+  PAMO_CUDA(cudaMemcpyAsync(c->dc, c->hc, sizeof(RoundCounters), cudaMemcpyHostToDevice, c->st));
+  return PAMO_OK;
+}
+
+pamo_status create(const float* d_V, int64_t nV, const int32_t* d_F, int64_t nF,
+                   const pamo_options* opt, cudaStream_t st, pamo_ctx** out) {
+  *out = nullptr;
+  if (!d_V || !d_F || nV < 4 || nF < 4) {
+    set_error("need device arrays and a closed mesh (nV >= 4, nF >= 4)");
+    return PAMO_EINVAL;
+  }
+  if (nF % 2 != 0 || nF >= (int64_t)1 << 30 || nV >= (int64_t)1 << 30) {
+    set_error("face count must be even (closed mesh) and sizes below 2^30");
+    return PAMO_EINVAL;
+  }
+  pamo_ctx* c = nullptr;
+  PAMO_TRY(new_ctx(opt, st, &c));
+  st = c->st;
+  pamo_status s = alloc_state(c, nV, nF);
+  if (s == PAMO_OK) s = load_mesh(d_V, nV, d_F, nF, c->pos, c->F, st);
+  if (s == PAMO_OK) s = init_counters(c);
+  if (s == PAMO_OK && c->opt.validate_input) s = validate_mesh(c);
+  if (s == PAMO_OK && !c->opt.validate_input) s = build_vertex_faces(c);
   if (s == PAMO_OK) s = mesh_bbox(c->pos, nV, c->bb_lo, c->bb_hi, c->scan_tmp, st);
   if (s == PAMO_OK) {
     // s = 1 / (largest extent of the input box), the [0,1]^3 normalisation
@@ -268,6 +303,103 @@ pamo_status create(const float* d_V, int64_t nV, const int32_t* d_F, int64_t nF,
     c->scale = ext > 0.0 ? 1.0 / ext : 1.0;
     s = init_quadrics(c);
   }
+  if (s != PAMO_OK) {
+    destroy_ctx(c);
+    return s;
+  }
+  *out = c;
+  return PAMO_OK;
+}
+
+// A batch: M meshes as one disjoint union.  h_voff / h_foff (host, M + 1
+// entries) delimit each mesh's vertices and faces in the concatenated input;
+// each mesh's faces index its own vertices from 0.
+pamo_status create_batch(int M, const float* d_V, const int64_t* h_voff, const int32_t* d_F,
+                         const int64_t* h_foff, const int64_t* h_targets,
+                         const pamo_options* opt, cudaStream_t st, pamo_ctx** out) {
+  *out = nullptr;
+  if (M < 1 || !d_V || !d_F || !h_voff || !h_foff || !h_targets) {
+    set_error("batch: need M >= 1, device arrays and host offsets and targets");
+    return PAMO_EINVAL;
+  }
+  if (h_voff[0] != 0 || h_foff[0] != 0) {
+    set_error("batch: offsets must start at 0");
+    return PAMO_EINVAL;
+  }
+  for (int m = 0; m < M; m++) {
+    const int64_t nv = h_voff[m + 1] - h_voff[m], nf = h_foff[m + 1] - h_foff[m];
+    if (nv < 4 || nf < 4 || nf % 2 != 0 || h_targets[m] < 0) {
+      set_error("batch: every mesh needs >= 4 vertices, an even face count >= 4 and a target >= 0");
+      return PAMO_EINVAL;
+    }
+  }
+  const int64_t nV = h_voff[M], nF = h_foff[M];
+  if (nF >= (int64_t)1 << 30 || nV >= (int64_t)1 << 30) {
+    set_error("batch: total sizes must stay below 2^30");
+    return PAMO_EINVAL;
+  }
+  if (opt && opt->exact_target) {
+    set_error("batch: exact_target is not supported");
+    return PAMO_EINVAL;
+  }
+  pamo_ctx* c = nullptr;
+  PAMO_TRY(new_ctx(opt, st, &c));
+  st = c->st;
+  c->n_mesh = M;
+  pamo_status s = alloc_state(c, nV, nF);
+  if (s == PAMO_OK) {
+    cudaError_t e = cudaMemcpyAsync(c->voff_d, h_voff, sizeof(int64_t) * (M + 1),
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->foff_d, h_foff, sizeof(int64_t) * (M + 1), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) s = cuda_fail(e, "cudaMemcpyAsync offsets");
+  }
+  if (s == PAMO_OK) s = init_counters(c);
+  if (s == PAMO_OK)
+    s = load_mesh_batch(d_V, nV, d_F, nF, c->voff_d, c->foff_d, M, c->pos, c->F, c->vmesh,
+                        &c->dc->bad, st);
+  if (s == PAMO_OK && c->opt.validate_input) s = validate_mesh(c);
+  if (s == PAMO_OK && !c->opt.validate_input) s = build_vertex_faces(c);
+  std::vector<float> lo(3 * (size_t)M), hi(3 * (size_t)M);
+  if (s == PAMO_OK) s = buf_reserve(c->scan_tmp, sizeof(unsigned) * 6 * (size_t)M, st);
+  if (s == PAMO_OK) s = mesh_bbox_batch(c->pos, c->voff_d, M, (unsigned*)c->scan_tmp.p, lo.data(),
+                                        hi.data(), st);
+  if (s == PAMO_OK) {
+    // per mesh: the [0,1]^3 scale of Eq. 1 and the Morton frame of the LBVH
+    std::vector<double> cost(2 * (size_t)M);
+    std::vector<float> frame(6 * (size_t)M);
+    for (int m = 0; m < M; m++) {
+      double ext = 0.0;
+      for (int k = 0; k < 3; k++)
+        ext = std::max(ext, (double)hi[3 * m + k] - (double)lo[3 * m + k]);
+      const double scale = ext > 0.0 ? 1.0 / ext : 1.0;
+      cost[2 * m] = scale * scale;
+      cost[2 * m + 1] = c->opt.w_e * scale;
+      for (int k = 0; k < 3; k++) {
+        const float e = hi[3 * m + k] - lo[3 * m + k];
+        frame[6 * m + k] = lo[3 * m + k];
+        frame[6 * m + 3 + k] = e > 0.f ? 1.0f / e : 0.0f;
+      }
+    }
+    c->m_nV.resize(M); c->m_nF.resize(M); c->m_target.resize(M); c->m_nflags.assign(M, 0);
+    c->m_hold.assign(M, 0); c->m_zero.assign(M, 0); c->m_status.assign(M, PAMO_OK);
+    c->m_rounds.assign(M, 0); c->m_active.assign(M, 1);
+    for (int m = 0; m < M; m++) {
+      c->m_nV[m] = h_voff[m + 1] - h_voff[m];
+      c->m_nF[m] = h_foff[m + 1] - h_foff[m];
+      c->m_target[m] = h_targets[m];
+      if (c->m_nF[m] <= c->m_target[m]) c->m_active[m] = 0;  // nothing to do
+    }
+    cudaError_t e = cudaMemcpyAsync(c->mcost, cost.data(), sizeof(double) * 2 * M,
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->mframe, frame.data(), sizeof(float) * 6 * M, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->mactive, c->m_active.data(), M, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host sources are locals
+    if (e != cudaSuccess) s = cuda_fail(e, "cudaMemcpyAsync batch tables");
+  }
+  if (s == PAMO_OK) s = init_quadrics(c);
   if (s != PAMO_OK) {
     destroy_ctx(c);
     return s;
@@ -361,6 +493,9 @@ void graph_resolve(pamo_ctx* c, int g) {
 
 pamo_status sync_out(pamo_ctx* c) {
   PAMO_CUDA(cudaMemcpyAsync(c->hc, c->dc, sizeof(RoundCounters), cudaMemcpyDeviceToHost, c->st));
+  if (c->n_mesh > 1)
+    PAMO_CUDA(cudaMemcpyAsync(c->mcount_h, c->mcount, sizeof(int32_t) * 3 * c->n_mesh,
+                              cudaMemcpyDeviceToHost, c->st));
   return PAMO_OK;
 }
 
@@ -562,8 +697,11 @@ pamo_status check_device_errors(pamo_ctx* c) {
   return PAMO_OK;
 }
 
+pamo_status finish_round_batch(pamo_ctx* c);
+
 // host bookkeeping once a round is committed (hc holds the device state)
 pamo_status finish_round(pamo_ctx* c) {
+  if (c->n_mesh > 1) return finish_round_batch(c);
   cudaStream_t st = c->st;
   const RoundCounters& h = *c->hc;
   const int64_t nV_in = c->nV, nF_in = c->nF, nE_in = h.nE, nW = h.nW;
@@ -643,6 +781,143 @@ pamo_status finish_round(pamo_ctx* c) {
     c->stalled = true;
     c->stall_empty = stall_empty;
   }
+  return PAMO_OK;
+}
+
+// Batch bookkeeping after a committed round: every mesh follows the rules of
+// a single simplification (Section 5.3 flags with their own tolerance count,
+// stall, target), so each output equals that mesh simplified alone.  The
+// device has the undone pairs of every mesh (flags_next) and last round's
+// flags in the new numbering (flags_old); the per-mesh merge is done here.
+pamo_status finish_round_batch(pamo_ctx* c) {
+  cudaStream_t st = c->st;
+  const RoundCounters& h = *c->hc;
+  const int M = c->n_mesh;
+  const int32_t* elig = c->mcount_h;
+  const int32_t* com = elig + M;
+  const int32_t* und = elig + 2 * M;
+  const int64_t nflags_in = c->nflags, nund = h.nund;
+  std::vector<unsigned long long> old(nflags_in), nw(nund);
+  if (nflags_in)
+    PAMO_CUDA(cudaMemcpyAsync(old.data(), c->flags_old, sizeof(unsigned long long) * nflags_in,
+                              cudaMemcpyDeviceToHost, st));
+  if (nund)
+    PAMO_CUDA(cudaMemcpyAsync(nw.data(), c->flags_next, sizeof(unsigned long long) * nund,
+                              cudaMemcpyDeviceToHost, st));
+  PAMO_CUDA(cudaStreamSynchronize(st));
+  // sizes and vertex bases of the committed union
+  std::vector<int64_t> vbase(M + 1, 0);
+  for (int m = 0; m < M; m++) {
+    c->m_nV[m] -= com[m];
+    c->m_nF[m] -= 2 * (int64_t)com[m];
+    vbase[m + 1] = vbase[m] + c->m_nV[m];
+  }
+  auto mesh_of = [&](unsigned long long p) {
+    const int64_t a = (int64_t)(p >> 32);
+    return (int)(std::upper_bound(vbase.begin(), vbase.end(), a) - vbase.begin()) - 1;
+  };
+  std::vector<unsigned long long> next;
+  next.reserve(nflags_in + nund);
+  size_t io = 0, in = 0;
+  bool active_changed = false;
+  const bool cost_target = c->opt.max_cost < INFINITY;
+  for (int m = 0; m < M; m++) {
+    std::vector<unsigned long long> om, nm;  // this mesh's old (valid) and new entries
+    for (; io < old.size() && (old[io] == ~0ull || mesh_of(old[io]) <= m); io++)
+      if (old[io] != ~0ull && mesh_of(old[io]) == m) om.push_back(old[io]);
+    for (; in < nw.size() && mesh_of(nw[in]) <= m; in++)
+      if (mesh_of(nw[in]) == m) nm.push_back(nw[in]);
+    if (!c->m_active[m]) continue;
+    std::vector<unsigned long long> fm;
+    if (com[m] > 0) {
+      c->m_hold[m] = 0;
+      c->m_zero[m] = 0;
+      fm.swap(nm);
+    } else {
+      c->m_hold[m]++;
+      c->m_zero[m]++;
+      std::merge(om.begin(), om.end(), nm.begin(), nm.end(), std::back_inserter(fm));
+      fm.erase(std::unique(fm.begin(), fm.end()), fm.end());
+      if (c->m_hold[m] >= c->opt.tolerance) {
+        fm.clear();
+        c->m_hold[m] = 0;
+      }
+    }
+    const bool stall_empty = elig[m] == 0 && c->m_nflags[m] == 0;
+    c->m_rounds[m]++;
+    if (stall_empty || c->m_zero[m] >= c->opt.stall_limit) {
+      const bool cost_end = stall_empty && cost_target;
+      c->m_status[m] = (c->m_nF[m] > c->m_target[m] && !cost_end) ? PAMO_ESTALL : PAMO_OK;
+      c->m_active[m] = 0;
+    } else if (c->m_nF[m] <= c->m_target[m]) {
+      c->m_active[m] = 0;  // reached N_t
+    }
+    if (!c->m_active[m]) {
+      active_changed = true;
+      fm.clear();
+    }
+    c->m_nflags[m] = (int64_t)fm.size();
+    next.insert(next.end(), fm.begin(), fm.end());
+  }
+  (void)und;
+  const int nf = (int)next.size();
+  if (nf)
+    PAMO_CUDA(cudaMemcpyAsync(c->flags, next.data(), sizeof(unsigned long long) * nf,
+                              cudaMemcpyHostToDevice, st));
+  PAMO_CUDA(cudaMemcpyAsync(&c->dc->nflags, &nf, sizeof(int), cudaMemcpyHostToDevice, st));
+  if (active_changed)
+    PAMO_CUDA(cudaMemcpyAsync(c->mactive, c->m_active.data(), M, cudaMemcpyHostToDevice, st));
+  PAMO_CUDA(cudaStreamSynchronize(st));
+  c->nflags = nf;
+  // totals over the batch
+  c->class_flops[PAMO_KC_COST] += 114.0 * h.n_dirty + 32.0 * (double)h.cost_tris;
+  c->committed_total += h.committed;
+  c->undone_total += h.nund;
+  c->link_total += (int64_t)h.link_rejects;
+  c->win_total += h.nW;
+  c->undo_hist[std::min(h.undo_iters, 7)]++;
+  c->undo_iters = h.undo_iters;
+  c->last_pairs = h.pairs_total;
+  c->rounds++;
+  c->nW = h.nW;
+  c->nE = h.nE;
+  c->nV = h.nV;
+  c->nF = h.nF;
+  c->stage = 0;
+  bool any = false;
+  for (int m = 0; m < M; m++) any |= c->m_active[m] != 0;
+  if (!any) c->stalled = true;  // every mesh is done
+  return PAMO_OK;
+}
+
+pamo_status graph_round(pamo_ctx* c);
+
+// the rounds of a batch: until every mesh has reached its target or stopped
+pamo_status run_batch(pamo_ctx* c) {
+  c->in_run = true;
+  const int M = c->n_mesh;
+  bool any = false;
+  for (int m = 0; m < M; m++) any |= c->m_active[m] != 0;
+  while (any) {
+    if (c->rounds >= c->opt.max_rounds) {
+      for (int m = 0; m < M; m++)
+        if (c->m_active[m]) {
+          c->m_active[m] = 0;
+          c->m_status[m] = PAMO_ESTALL;
+        }
+      break;
+    }
+    pamo_status s = graph_round(c);
+    if (s != PAMO_OK) {
+      c->in_run = false;
+      return s;
+    }
+    any = !c->stalled;
+  }
+  c->in_run = false;
+  c->status = PAMO_OK;
+  for (int m = 0; m < M; m++)
+    if (c->m_status[m] != PAMO_OK) c->status = PAMO_ESTALL;
   return PAMO_OK;
 }
 
@@ -1122,6 +1397,61 @@ pamo_status pamo_check_self_intersections(const float* d_V, int64_t nV, const in
   release(F, st);
   release(dc, st);
   cudaStreamSynchronize(st);
+  return s;
+}
+
+pamo_status pamo_simplify_batch(int32_t n_meshes, const float* d_V, const int64_t* h_voff,
+                                const int32_t* d_F, const int64_t* h_foff,
+                                const int64_t* h_targets, const pamo_options* opt, void* stream,
+                                float* d_Vout, int64_t* h_voff_out, int32_t* d_Fout,
+                                int64_t* h_foff_out, int32_t* h_status, int32_t* h_rounds,
+                                pamo_stats* stats) {
+  if (!d_Vout || !d_Fout || !h_voff_out || !h_foff_out) {
+    set_error("output arguments must not be NULL");
+    return PAMO_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  PAMO_CUDA(cudaEventCreate(&e0));
+  PAMO_CUDA(cudaEventCreate(&e1));
+  PAMO_CUDA(cudaEventRecord(e0, st));
+  pamo_ctx* c = nullptr;
+  const long long l0 = launch_count();
+  pamo_status s = create_batch(n_meshes, d_V, h_voff, d_F, h_foff, h_targets, opt, st, &c);
+  if (s == PAMO_OK) s = run_batch(c);
+  if (s == PAMO_OK) {
+    const int M = c->n_mesh;
+    std::vector<int32_t> vb(M);
+    h_voff_out[0] = 0;
+    h_foff_out[0] = 0;
+    for (int m = 0; m < M; m++) {
+      vb[m] = (int32_t)h_voff_out[m];
+      h_voff_out[m + 1] = h_voff_out[m] + c->m_nV[m];
+      h_foff_out[m + 1] = h_foff_out[m] + c->m_nF[m];
+      if (h_status) h_status[m] = c->m_status[m];
+      if (h_rounds) h_rounds[m] = c->m_rounds[m];
+    }
+    cudaError_t e = cudaMemcpyAsync(c->mvbase, vb.data(), sizeof(int32_t) * M,
+                                    cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) s = cuda_fail(e, "cudaMemcpyAsync vertex bases");
+  }
+  if (s == PAMO_OK)
+    s = store_mesh_batch(c->pos, c->nV, c->F, c->nF, c->vmesh, c->mvbase, d_Vout, d_Fout, c->st);
+  if (s == PAMO_OK) s = join(c);
+  if (s == PAMO_OK) {
+    float ms = 0.f;
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+    kc_resolve(c);
+    fill_stats(c, stats, ms);
+    if (stats) stats->launches = launch_count() - c->gk_captured + c->gk_run - l0;
+    s = (pamo_status)c->status;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (c) pamo_ctx_destroy(c);
   return s;
 }
 

@@ -51,20 +51,32 @@ __device__ __forceinline__ exact::FaceInfo unpack_info(uint8_t b) {
 #define GRID_STRIDE(i, n) \
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
 
+// Many meshes in one tree (a batch): the key of a leaf is (mesh id, Morton code
+// in that mesh's own frame), the mesh id in the high word hkeys, so the radix
+// tree separates the meshes before any spatial split and every mesh owns a
+// subtree (its root in mroot); mframe holds each mesh's frame (lo.xyz,
+// 1/extent.xyz).  With vmesh == nullptr there is one mesh and no high word.
 __global__ void k_leaf_keys(const float4* __restrict__ pos, const int4* __restrict__ F,
                             const uint8_t* __restrict__ fdead, const int* n_dev, int n_host,
                             float lx, float ly, float lz, float ix, float iy, float iz,
-                            unsigned* __restrict__ keys, int32_t* __restrict__ vals,
-                            uint8_t* __restrict__ info) {
+                            const int32_t* __restrict__ vmesh, const float* __restrict__ mframe,
+                            unsigned* __restrict__ keys, unsigned* __restrict__ hkeys,
+                            int32_t* __restrict__ vals, uint8_t* __restrict__ info) {
   const int n = dev_n(n_dev, n_host);
   GRID_STRIDE(f, n) {
   vals[f] = f;
+  const int4 t = F[f];
+  if (vmesh) {
+    const int m = vmesh[t.x];
+    hkeys[f] = (unsigned)m;
+    lx = mframe[6 * m]; ly = mframe[6 * m + 1]; lz = mframe[6 * m + 2];
+    ix = mframe[6 * m + 3]; iy = mframe[6 * m + 4]; iz = mframe[6 * m + 5];
+  }
   if (fdead && fdead[f]) {
     keys[f] = 1u << 30;
     info[f] = pack_info(exact::FaceInfo{0, 0});
     continue;
   }
-  const int4 t = F[f];
   const float4 a = pos[t.x], b = pos[t.y], c = pos[t.z];
   const float cx = 0.5f * (fminf(fminf(a.x, b.x), c.x) + fmaxf(fmaxf(a.x, b.x), c.x));
   const float cy = 0.5f * (fminf(fminf(a.y, b.y), c.y) + fmaxf(fmaxf(a.y, b.y), c.y));
@@ -100,6 +112,7 @@ __global__ void k_sort_len(const int* n_dev, int n_host, int* __restrict__ len) 
   *len = 256 * sort_tiles(dev_n(n_dev, n_host));
 }
 
+// keys: the array the digit of this pass is taken from (Morton or mesh word)
 __global__ void k_digit_hist(const unsigned* __restrict__ keys, const int* n_dev, int n_host,
                              int shift, int32_t* __restrict__ hist) {
   __shared__ int h[256];
@@ -120,10 +133,13 @@ __global__ void k_digit_hist(const unsigned* __restrict__ keys, const int* n_dev
   }
 }
 
+// moves (key, value[, high word]); the digit comes from the high word when
+// from_hi is set
 __global__ void __launch_bounds__(kBlock) k_digit_scatter(
-    const unsigned* __restrict__ keys, const int32_t* __restrict__ vals, const int* n_dev,
+    const unsigned* __restrict__ keys, const int32_t* __restrict__ vals,
+    const unsigned* __restrict__ hk, int from_hi, const int* n_dev,
     int n_host, int shift, const int32_t* __restrict__ offs, unsigned* __restrict__ okeys,
-    int32_t* __restrict__ ovals) {
+    int32_t* __restrict__ ovals, unsigned* __restrict__ ohk) {
   __shared__ int wcount[kBlock / 32][256];
   __shared__ int goff[256];
   const int n = dev_n(n_dev, n_host);
@@ -134,7 +150,7 @@ __global__ void __launch_bounds__(kBlock) k_digit_scatter(
   goff[threadIdx.x] = offs[threadIdx.x * tiles + tile];
   __syncthreads();
   const int base = tile * kSortTile + wid * (kSortItems * 32);
-  unsigned k[kSortItems];
+  unsigned k[kSortItems], h[kSortItems];
   int v[kSortItems], r[kSortItems];
   const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
@@ -143,7 +159,9 @@ __global__ void __launch_bounds__(kBlock) k_digit_scatter(
     const bool ok = j < n;
     k[i] = ok ? keys[j] : 0u;
     v[i] = ok ? vals[j] : 0;
-    const unsigned d = ok ? ((k[i] >> shift) & 0xffu) : (0x100u | lane);
+    h[i] = (ok && hk) ? hk[j] : 0u;
+    const unsigned src = from_hi ? h[i] : k[i];
+    const unsigned d = ok ? ((src >> shift) & 0xffu) : (0x100u | lane);
     const unsigned peers = __match_any_sync(0xffffffffu, d);
     int before = 0;
     if (ok) before = wcount[wid][d];
@@ -166,10 +184,11 @@ __global__ void __launch_bounds__(kBlock) k_digit_scatter(
   for (int i = 0; i < kSortItems; i++) {
     const int j = base + i * 32 + lane;
     if (j < n) {
-      const unsigned d = (k[i] >> shift) & 0xffu;
+      const unsigned d = ((from_hi ? h[i] : k[i]) >> shift) & 0xffu;
       const int p = goff[d] + wcount[wid][d] + r[i];
       okeys[p] = k[i];
       ovals[p] = v[i];
+      if (hk) ohk[p] = h[i];
     }
   }
   __syncthreads();
@@ -177,11 +196,18 @@ __global__ void __launch_bounds__(kBlock) k_digit_scatter(
 }
 
 // ---- Karras binary radix tree ---------------------------------------------
-__device__ __forceinline__ int delta(const unsigned* __restrict__ k, int n, int i, int j) {
+// common prefix length of the keys (high word, Morton word, then index for
+// equal keys), -1 outside [0, n)
+__device__ __forceinline__ int delta(const unsigned* __restrict__ k,
+                                     const unsigned* __restrict__ hk, int n, int i, int j) {
   if (j < 0 || j >= n) return -1;
+  if (hk) {
+    const unsigned ha = hk[i], hb = hk[j];
+    if (ha != hb) return __clz(ha ^ hb);
+  }
   const unsigned a = k[i], b = k[j];
-  if (a == b) return 32 + __clz(i ^ j);
-  return __clz(a ^ b);
+  if (a == b) return 64 + __clz(i ^ j);
+  return 32 + __clz(a ^ b);
 }
 
 // Node layout (64 bytes, internal nodes only): the boxes of both children and
@@ -191,25 +217,34 @@ __device__ __forceinline__ int delta(const unsigned* __restrict__ k, int n, int 
 //   ints 12, 13: left, right child (internal index >= 0, or ~face for a leaf)
 // parent[x] = (parent node << 1) | side for internal x in [0, n-1) and leaf
 // positions x = n-1+j; the root has -1.
-__global__ void k_karras(const unsigned* __restrict__ k, const int32_t* __restrict__ vals,
-                         const int* n_dev, int n_host, float* __restrict__ nodes,
-                         int32_t* __restrict__ parent) {
+// With high words (a batch), the node whose range is exactly one mesh's
+// leaves is that mesh's subtree root (mroot).
+__global__ void k_karras(const unsigned* __restrict__ k, const unsigned* __restrict__ hk,
+                         const int32_t* __restrict__ vals, const int* n_dev, int n_host,
+                         float* __restrict__ nodes, int32_t* __restrict__ parent,
+                         int32_t* __restrict__ mroot) {
   const int n = dev_n(n_dev, n_host);
   GRID_STRIDE(i, n - 1) {
-  const int d = (delta(k, n, i, i + 1) - delta(k, n, i, i - 1)) >= 0 ? 1 : -1;
-  const int dmin = delta(k, n, i, i - d);
+  const int d = (delta(k, hk, n, i, i + 1) - delta(k, hk, n, i, i - 1)) >= 0 ? 1 : -1;
+  const int dmin = delta(k, hk, n, i, i - d);
   int lmax = 2;
-  while (delta(k, n, i, i + lmax * d) > dmin) lmax <<= 1;
+  while (delta(k, hk, n, i, i + lmax * d) > dmin) lmax <<= 1;
   int l = 0;
   for (int t = lmax >> 1; t >= 1; t >>= 1)
-    if (delta(k, n, i, i + (l + t) * d) > dmin) l += t;
+    if (delta(k, hk, n, i, i + (l + t) * d) > dmin) l += t;
   const int j = i + l * d;
-  const int dnode = delta(k, n, i, j);
+  const int dnode = delta(k, hk, n, i, j);
   int s = 0;
   for (int div = 2;; div <<= 1) {
     const int t = (l + div - 1) / div;
-    if (delta(k, n, i, i + (s + t) * d) > dnode) s += t;
+    if (delta(k, hk, n, i, i + (s + t) * d) > dnode) s += t;
     if (t <= 1) break;
+  }
+  if (hk) {
+    const int first = min(i, j), last = max(i, j);
+    const unsigned m = hk[first];
+    if (hk[last] == m && (first == 0 || hk[first - 1] != m) && (last == n - 1 || hk[last + 1] != m))
+      mroot[m] = i;
   }
   const int g = i + s * d + (d < 0 ? -1 : 0);
   const bool lleaf = min(i, j) == g, rleaf = max(i, j) == g + 1;
@@ -231,24 +266,29 @@ __global__ void k_order_alive(const int32_t* __restrict__ vals, const int* n_dev
 }
 
 __global__ void k_order_write(const int32_t* __restrict__ vals, const unsigned* __restrict__ keys,
-                              const int* n_dev, const uint8_t* __restrict__ alive,
-                              const int32_t* __restrict__ pos, const int32_t* __restrict__ dead_before,
-                              int32_t* __restrict__ out, unsigned* __restrict__ okeys) {
+                              const unsigned* __restrict__ hk, const int* n_dev,
+                              const uint8_t* __restrict__ alive, const int32_t* __restrict__ pos,
+                              const int32_t* __restrict__ dead_before, int32_t* __restrict__ out,
+                              unsigned* __restrict__ okeys, unsigned* __restrict__ ohk) {
   const int n = *n_dev;
   GRID_STRIDE(i, n) {
     if (!alive[i]) continue;
     const int f = vals[i];
     out[pos[i]] = f - dead_before[f];
     okeys[pos[i]] = keys[i];
+    if (hk) ohk[pos[i]] = hk[i];
   }
 }
 
 __global__ void k_copy_order(const int32_t* __restrict__ vals2, const unsigned* __restrict__ keys2,
-                             const int* n_dev, int32_t* __restrict__ vals, unsigned* __restrict__ keys) {
-  const int n = *n_dev;
+                             const unsigned* __restrict__ hk2, const int* n_dev, int n_host,
+                             int32_t* __restrict__ vals, unsigned* __restrict__ keys,
+                             unsigned* __restrict__ hk) {
+  const int n = dev_n(n_dev, n_host);
   GRID_STRIDE(i, n) {
     vals[i] = vals2[i];
     keys[i] = keys2[i];
+    if (hk) hk[i] = hk2[i];
   }
 }
 
@@ -370,7 +410,7 @@ __global__ void __launch_bounds__(kBlock) k_query(
     const uint8_t* __restrict__ info, const int32_t* __restrict__ ftag, int query_all,
     const int32_t* __restrict__ qlist, const int* __restrict__ qcount,
     uint8_t* __restrict__ undo, RoundCounters* __restrict__ dc, int32_t* __restrict__ pairs_out,
-    int64_t cap) {
+    int64_t cap, const int32_t* __restrict__ vmesh, const int32_t* __restrict__ mroot) {
   const int n = dev_n(n_dev, n_host);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   int f;
@@ -402,8 +442,8 @@ __global__ void __launch_bounds__(kBlock) k_query(
   const exact::FaceInfo fiT = unpack_info(info[f]);
   int stack[kStack];
   int sp = 0;
-  int node = 0;
   if (n == 1) return;
+  int node = mroot ? mroot[vmesh[tv.x]] : 0;  // the query's own mesh
   // a tree has 2n - 1 nodes; the visit cap only guards against a malformed one
   for (int visits = 0;; visits++) {
     if (visits >= 2 * n) {
@@ -469,7 +509,8 @@ __global__ void __launch_bounds__(kBlock) k_traverse(
     const int4* __restrict__ F, const uint8_t* __restrict__ fdead,
     const int32_t* __restrict__ ftag, int query_all, const int32_t* __restrict__ qlist,
     const int* __restrict__ qcount, CandBufs cb, int* __restrict__ ncand,
-    RoundCounters* __restrict__ dc) {
+    RoundCounters* __restrict__ dc, const int32_t* __restrict__ vmesh,
+    const int32_t* __restrict__ mroot) {
   const int n = dev_n(n_dev, n_host);
   const int total = query_all ? n : *qcount;
   if (n < 2) return;
@@ -485,7 +526,7 @@ __global__ void __launch_bounds__(kBlock) k_traverse(
     const float3 hi = make_float3(fmaxf(fmaxf(a.x, b.x), c.x), fmaxf(fmaxf(a.y, b.y), c.y),
                                   fmaxf(fmaxf(a.z, b.z), c.z));
     int stack[kStack];
-    int sp = 0, node = 0;
+    int sp = 0, node = mroot ? mroot[vmesh[tv.x]] : 0;  // the query's own mesh
     for (int visits = 0;; visits++) {
       if (visits >= 2 * n) {
         atomicOr(&dc->overflow, 4);
@@ -635,6 +676,11 @@ pamo_status bvh_alloc(Bvh& b, int n_max, cudaStream_t st) {
   PAMO_TRY(buf_reserve(b.sort_len, 16, st));
   PAMO_TRY(buf_reserve(b.posn, sizeof(int32_t) * ((size_t)n_max + 1), st));
   PAMO_TRY(buf_reserve(b.sums, sizeof(int32_t) * scan_sums_count(hw > n_max ? hw : n_max), st));
+  if (b.n_mesh > 1) {
+    PAMO_TRY(buf_reserve(b.hkeys, kvb, st));
+    PAMO_TRY(buf_reserve(b.hkeys2, kvb, st));
+    PAMO_TRY(buf_reserve(b.mroot, sizeof(int32_t) * (size_t)b.n_mesh, st));
+  }
   b.n_max = n_max;
   return PAMO_OK;
 }
@@ -653,12 +699,13 @@ void bvh_bytes(int n, size_t* nodes, size_t* parent, size_t* flags, size_t* kv, 
 
 // Build over faces [0, n) (n from n_dev when set, else n_host) in the
 // preallocated buffers of b.  carry = true keeps the current leaf order and
-// Morton keys (see bvh_compact_order) and only rebuilds the hierarchy.
+// keys (see bvh_compact_order) and only rebuilds the hierarchy.
 pamo_status bvh_build(Bvh& b, const float4* pos, const int4* F, const uint8_t* fdead,
                       const int* n_dev, int n_host, const float lo[3], const float hi[3],
                       bool carry, int grid, cudaStream_t st) {
   unsigned* keys = (unsigned*)b.keys.p;
   int32_t* vals = (int32_t*)b.vals.p;
+  unsigned* hk = b.n_mesh > 1 ? (unsigned*)b.hkeys.p : nullptr;
   if (!carry) {
     float inv[3];
     for (int k = 0; k < 3; k++) {
@@ -667,29 +714,42 @@ pamo_status bvh_build(Bvh& b, const float4* pos, const int4* F, const uint8_t* f
     }
     unsigned* keys2 = (unsigned*)b.keys2.p;
     int32_t* vals2 = (int32_t*)b.vals2.p;
+    unsigned* hk2 = hk ? (unsigned*)b.hkeys2.p : nullptr;
     static const int g_keys = occ_grid(k_leaf_keys);
-    k_leaf_keys<<<g_keys, kBlock, 0, st>>>(pos, F, fdead, n_dev, n_host, lo[0], lo[1], lo[2], inv[0],
-                                         inv[1], inv[2], keys, vals, (uint8_t*)b.face_aux.p); note_launch();
+    k_leaf_keys<<<g_keys, kBlock, 0, st>>>(pos, F, fdead, n_dev, n_host, lo[0], lo[1], lo[2],
+                                           inv[0], inv[1], inv[2], hk ? b.vmesh : nullptr,
+                                           b.mframe, keys, hk, vals,
+                                           (uint8_t*)b.face_aux.p); note_launch();
     const int tiles_max = (b.n_max + kSortTile - 1) / kSortTile;
     int32_t* hist = (int32_t*)b.hist.p;
     int32_t* offs = hist + 256 * (tiles_max > 0 ? tiles_max : 1) + 1;
     int* len = (int*)b.sort_len.p;
     k_sort_len<<<1, 1, 0, st>>>(n_dev, n_host, len); note_launch();
-    for (int pass = 0; pass < 4; pass++) {
-      const int shift = 8 * pass;
-      k_digit_hist<<<grid, kBlock, 0, st>>>(keys, n_dev, n_host, shift, hist); note_launch();
+    // LSD: the four bytes of the Morton word, then the bytes of the mesh id
+    int hi_passes = 0;
+    for (int m = b.n_mesh - 1; m > 0; m >>= 8) hi_passes++;
+    for (int pass = 0; pass < 4 + hi_passes; pass++) {
+      const bool from_hi = pass >= 4;
+      const int shift = 8 * (from_hi ? pass - 4 : pass);
+      k_digit_hist<<<grid, kBlock, 0, st>>>(from_hi ? hk : keys, n_dev, n_host, shift, hist); note_launch();
       PAMO_TRY(scan_dev_i32(hist, len, offs, (int32_t*)b.sums.p, grid, st));
-      k_digit_scatter<<<grid, kBlock, 0, st>>>(keys, vals, n_dev, n_host, shift, offs, keys2,
-                                               vals2); note_launch();
+      k_digit_scatter<<<grid, kBlock, 0, st>>>(keys, vals, hk, from_hi ? 1 : 0, n_dev, n_host,
+                                               shift, offs, keys2, vals2, hk2); note_launch();
       PAMO_CUDA(cudaGetLastError());
-      unsigned* tk = keys; keys = keys2; keys2 = tk;
-      int32_t* tv = vals; vals = vals2; vals2 = tv;
+      std::swap(keys, keys2);
+      std::swap(vals, vals2);
+      std::swap(hk, hk2);
     }
-    // four passes: the sorted data is back in b.keys / b.vals
+    if (keys != (unsigned*)b.keys.p) {  // an odd number of passes: back to the primary buffers
+      k_copy_order<<<grid, kBlock, 0, st>>>(vals, keys, hk, n_dev, n_host, vals2, keys2, hk2); note_launch();
+      keys = keys2;
+      vals = vals2;
+      hk = hk2;
+    }
   }
   static const int g_karras = occ_grid(k_karras);
-  k_karras<<<g_karras, kBlock, 0, st>>>(keys, vals, n_dev, n_host, (float*)b.nodes.p,
-                                    (int32_t*)b.parent.p); note_launch();
+  k_karras<<<g_karras, kBlock, 0, st>>>(keys, hk, vals, n_dev, n_host, (float*)b.nodes.p,
+                                        (int32_t*)b.parent.p, (int32_t*)b.mroot.p); note_launch();
   PAMO_CUDA(cudaGetLastError());
   return bvh_refit(b, pos, F, fdead, n_dev, n_host, grid, st);
 }
@@ -715,10 +775,12 @@ pamo_status bvh_check(Bvh& b, const float4* pos, const int4* F, const uint8_t* f
   // fold a refit overflow into the round's overflow word
   k_fold_overflow<<<1, 1, 0, st>>>((const int32_t*)b.flags.p + b.n_max + 1, &dc->overflow); note_launch();
   const int64_t threads = query_all ? n_host : nq_max;
+  const bool many = b.n_mesh > 1;
   k_query<<<grid_for(threads), kBlock, 0, st>>>((const float*)b.nodes.p, nullptr, n_host, pos, F,
                                                 fdead, (const uint8_t*)b.face_aux.p, ftag,
                                                 query_all, qlist, qcount, undo, dc, pairs_out,
-                                                cap); note_launch();
+                                                cap, many ? b.vmesh : nullptr,
+                                                many ? (const int32_t*)b.mroot.p : nullptr); note_launch();
   PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;
 }
@@ -731,13 +793,18 @@ pamo_status bvh_compact_order(Bvh& b, const uint8_t* fdead, const int32_t* dead_
   // (rebuilt at the next refit) is only written for committed rounds
   uint8_t* alive = (uint8_t*)b.face_aux.p;
   int32_t* posn = (int32_t*)b.posn.p;
+  const bool many = b.n_mesh > 1;
   k_order_alive<<<grid, kBlock, 0, st>>>((const int32_t*)b.vals.p, n_old_dev, fdead, alive); note_launch();
   PAMO_TRY(scan_dev_u8(alive, n_old_dev, posn, (int32_t*)b.sums.p, grid, st));
   k_order_write<<<grid, kBlock, 0, st>>>((const int32_t*)b.vals.p, (const unsigned*)b.keys.p,
-                                         n_old_dev, alive, posn, dead_before, (int32_t*)b.vals2.p,
-                                         (unsigned*)b.keys2.p); note_launch();
+                                         many ? (const unsigned*)b.hkeys.p : nullptr, n_old_dev,
+                                         alive, posn, dead_before, (int32_t*)b.vals2.p,
+                                         (unsigned*)b.keys2.p,
+                                         many ? (unsigned*)b.hkeys2.p : nullptr); note_launch();
   k_copy_order<<<grid, kBlock, 0, st>>>((const int32_t*)b.vals2.p, (const unsigned*)b.keys2.p,
-                                        n_new_dev, (int32_t*)b.vals.p, (unsigned*)b.keys.p); note_launch();
+                                        many ? (const unsigned*)b.hkeys2.p : nullptr, n_new_dev, 0,
+                                        (int32_t*)b.vals.p, (unsigned*)b.keys.p,
+                                        many ? (unsigned*)b.hkeys.p : nullptr); note_launch();
   PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;
 }
@@ -753,10 +820,13 @@ pamo_status bvh_check_split(Bvh& b, const float4* pos, const int4* F, const uint
     cb.c[r] = cand[r];
     cb.cap[r] = cap[r];
   }
+  const bool many = b.n_mesh > 1;
   static const int g_trav = occ_grid(k_traverse);
   static const int g_pairs = occ_grid(k_pairs);
   k_traverse<<<g_trav, kBlock, 0, st>>>((const float*)b.nodes.p, n_dev, 0, pos, F, fdead, ftag,
-                                      query_all, qlist, qcount, cb, ncand, dc); note_launch();
+                                        query_all, qlist, qcount, cb, ncand, dc,
+                                        many ? b.vmesh : nullptr,
+                                        many ? (const int32_t*)b.mroot.p : nullptr); note_launch();
   k_pairs<<<g_pairs, kBlock, 0, st>>>(cb, ncand, pos, F, (const uint8_t*)b.face_aux.p, ftag, undo,
                                    dc); note_launch();
   PAMO_CUDA(cudaGetLastError());
@@ -776,6 +846,9 @@ void bvh_free(Bvh& b, cudaStream_t st) {
   buf_free(b.sort_len, st);
   buf_free(b.sums, st);
   buf_free(b.posn, st);
+  buf_free(b.hkeys, st);
+  buf_free(b.hkeys2, st);
+  buf_free(b.mroot, st);
 }
 
 pamo_status tri_batch(const float* P, const int32_t* idx, int64_t n, uint8_t* out,

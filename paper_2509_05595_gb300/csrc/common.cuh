@@ -110,6 +110,13 @@ struct Bvh {
   int n_max = 0;                 // capacity the buffers were allocated for
   Buf nodes, parent, flags, keys, vals, keys2, vals2, hist, face_aux, sort_len, sums;
   Buf posn;  // [n_max+1] new leaf positions of a compaction
+  // many meshes in one tree (a batch): the mesh id of each leaf (high key
+  // word, sorted order) and each mesh's subtree root; vmesh maps a vertex to
+  // its mesh and mframe holds each mesh's Morton frame (lo.xyz, 1/extent.xyz)
+  int n_mesh = 1;
+  Buf hkeys, hkeys2, mroot;
+  const int32_t* vmesh = nullptr;
+  const float* mframe = nullptr;
   // leaf order carried over rounds: valid when order_ok; re-sorted by Morton
   // code when the face count has halved since the last sort
   bool order_ok = false;
@@ -191,6 +198,23 @@ struct pamo_ctx {
   unsigned long long* flags_next = nullptr;  // [Emax]
   int64_t nflags = 0;
   int hold = 0, zero_streak = 0;
+  // --- batch (n_mesh > 1): the union of many meshes, each with its own
+  // normalisation, target, flags and termination
+  int n_mesh = 1;
+  int32_t* vmesh = nullptr;            // [nV0] vertex -> mesh
+  int32_t* vmesh_tmp = nullptr;        // [nV0] compaction scratch
+  int64_t* voff_d = nullptr;           // [M+1] input vertex offsets
+  int64_t* foff_d = nullptr;           // [M+1] input face offsets
+  float* mframe = nullptr;             // [M][6] Morton frame (lo, 1/extent)
+  double* mcost = nullptr;             // [M][2] s^2, w_e s of Eq. 1
+  uint8_t* mactive = nullptr;          // [M] the mesh still simplifies
+  int32_t* mcount = nullptr;           // [3M] eligible, committed, undone (per round)
+  int32_t* mcount_h = nullptr;         // pinned mirror
+  int32_t* mvbase = nullptr;           // [M] output vertex bases
+  unsigned long long* flags_old = nullptr;  // [Emax] last flags, committed numbering
+  std::vector<int64_t> m_nV, m_nF, m_target, m_nflags;
+  std::vector<int> m_hold, m_zero, m_status, m_rounds;
+  std::vector<uint8_t> m_active;
   // --- per-round counters
   pamo::RoundCounters* dc = nullptr;    // device
   pamo::RoundCounters* hc = nullptr;    // pinned host mirror
@@ -269,6 +293,15 @@ pamo_status load_mesh(const float* d_V, int64_t nV, const int32_t* d_F, int64_t 
                       float4* pos, int4* F, cudaStream_t st);
 pamo_status store_mesh(const float4* pos, int64_t nV, const int4* F, int64_t nF,
                        float* d_V, int32_t* d_F, cudaStream_t st);
+// batches: the union of M meshes (vertex / face offsets on the device)
+pamo_status load_mesh_batch(const float* d_V, int64_t nV, const int32_t* d_F, int64_t nF,
+                            const int64_t* d_voff, const int64_t* d_foff, int M, float4* pos,
+                            int4* F, int32_t* vmesh, int* d_bad, cudaStream_t st);
+pamo_status mesh_bbox_batch(const float4* pos, const int64_t* d_voff, int M, unsigned* d_out,
+                            float* lo, float* hi, cudaStream_t st);
+pamo_status store_mesh_batch(const float4* pos, int64_t nV, const int4* F, int64_t nF,
+                             const int32_t* vmesh, const int32_t* d_vbase, float* d_V,
+                             int32_t* d_F, cudaStream_t st);
 // copy (*n_dev + add) elements of elem_bytes; fill (*n_dev + add) words / bytes
 pamo_status copy_dev(void* dst, const void* src, const int* n_dev, int add, size_t elem_bytes,
                      int grid, cudaStream_t st);

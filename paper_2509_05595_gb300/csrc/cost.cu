@@ -70,6 +70,13 @@ __device__ __forceinline__ double quality(double x0, double y0, double z0, doubl
   return den > 0.0 ? (kTwoSqrt3 * sqrt(cr2)) / den : 0.0;
 }
 
+// per-mesh eligible counts of a batch: one atomic per group of lanes with the
+// same mesh (m < 0: nothing to count); every lane of the warp must call it
+__device__ __forceinline__ void count_by_mesh(int m, int32_t* __restrict__ melig) {
+  const unsigned peers = __match_any_sync(0xffffffffu, m);
+  if (m >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&melig[m], __popc(peers));
+}
+
 __device__ __forceinline__ int next_of(const int4& f, int v) {
   return f.x == v ? f.y : (f.y == v ? f.z : f.x);
 }
@@ -102,7 +109,9 @@ __global__ void __launch_bounds__(kBlock) k_edge_reuse(
     const float4* __restrict__ vbar_prev, const uint8_t* __restrict__ link_prev,
     const unsigned long long* __restrict__ flags, unsigned long long* __restrict__ key,
     float4* __restrict__ vbar, uint32_t* __restrict__ cbits, uint8_t* __restrict__ link,
-    int32_t* __restrict__ dlist, RoundCounters* __restrict__ dc) {
+    int32_t* __restrict__ dlist, RoundCounters* __restrict__ dc,
+    const int32_t* __restrict__ vmesh, const uint8_t* __restrict__ mactive,
+    int32_t* __restrict__ melig) {
   const int nE = dc->nE;
   const int nflags = dc->nflags;
   const unsigned max_bits = dc->max_bits;
@@ -114,6 +123,7 @@ __global__ void __launch_bounds__(kBlock) k_edge_reuse(
        base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t e = base + threadIdx.x;
     bool dirty = false;
+    int counted = -1;  // mesh of an eligible clean edge (batch)
     if (e < nE) {
       const int2 ab = E[e];
       dirty = all_dirty || vdirty[ab.x] || vdirty[ab.y];
@@ -133,16 +143,20 @@ __global__ void __launch_bounds__(kBlock) k_edge_reuse(
         const bool flag = nflags > 0 &&
                           is_flagged(flags, nflags,
                                      ((unsigned long long)(unsigned)ab.x << 32) | (unsigned)ab.y);
+        const int m = vmesh ? vmesh[ab.x] : 0;
+        const bool active = !vmesh || mactive[m];
         unsigned long long k = ~0ull;
-        if (cb != 0xffffffffu && cb <= max_bits && lk && !flag) {
+        if (cb != 0xffffffffu && cb <= max_bits && lk && !flag && active) {
           k = ((unsigned long long)cb << 32) | (unsigned long long)(uint32_t)e;
           eligible++;
+          counted = m;
         }
         key[e] = k;
         link_bad += !lk;
         flagged += flag;
       }
     }
+    if (vmesh) count_by_mesh(counted, melig);
     // dirty edges: warp-aggregated append to the work list
     const unsigned m = __ballot_sync(0xffffffffu, dirty);
     if (m) {
@@ -166,18 +180,27 @@ __global__ void __launch_bounds__(kBlock) k_edge_cost(
     const int32_t* __restrict__ dlist, const int2* __restrict__ E, const float4* __restrict__ pos,
     const double* __restrict__ Kv, const int4* __restrict__ F, const int32_t* __restrict__ off,
     const int32_t* __restrict__ idx, const unsigned long long* __restrict__ flags,
-    double s2, double wes, double ws, unsigned long long* __restrict__ key,
+    double s2_in, double wes_in, double ws, unsigned long long* __restrict__ key,
     float4* __restrict__ vbar, uint32_t* __restrict__ cbits, uint8_t* __restrict__ link,
-    RoundCounters* __restrict__ dc) {
+    RoundCounters* __restrict__ dc, const int32_t* __restrict__ vmesh,
+    const double* __restrict__ mcost, const uint8_t* __restrict__ mactive,
+    int32_t* __restrict__ melig) {
   const int ndirty = dc->n_dirty;
   const int nflags = dc->nflags;
   const unsigned max_bits = dc->max_bits;
   int link_bad = 0, flagged = 0, eligible = 0, ntri = 0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndirty;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  // block-uniform iterations: the per-mesh count is a warp-wide operation
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < ndirty;
+       base += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t i = base + threadIdx.x;
+  int counted = -1;
+  if (i < ndirty) {
     const int64_t e = dlist[i];
     const int2 ab = E[e];
     const int a = ab.x, b = ab.y;
+    const int m = vmesh ? vmesh[a] : 0;
+    // the mesh's own [0,1]^3 scale (a batch); one mesh: the arguments
+    const double s2 = vmesh ? mcost[2 * m] : s2_in, wes = vmesh ? mcost[2 * m + 1] : wes_in;
     const int a0 = off[a], a1 = off[a + 1], b0 = off[b], b1 = off[b + 1];
     // ---- link condition: exactly two common neighbours (the apexes of the
     // two faces on ab) and not both faces (a,c,d), (b,c,d) present
@@ -297,9 +320,10 @@ __global__ void __launch_bounds__(kBlock) k_edge_cost(
       cb = __float_as_uint(cf);
     }
     unsigned long long k = ~0ull;
-    if (cb != 0xffffffffu && cb <= max_bits && link_ok && !flag) {
+    if (cb != 0xffffffffu && cb <= max_bits && link_ok && !flag && (!vmesh || mactive[m])) {
       k = ((unsigned long long)cb << 32) | (unsigned long long)(uint32_t)e;
       eligible++;
+      counted = m;
     }
     key[e] = k;
     cbits[e] = cb;
@@ -307,6 +331,8 @@ __global__ void __launch_bounds__(kBlock) k_edge_cost(
     vbar[e] = make_float4(vx, vy, vz, 0.0f);
     link_bad += !link_ok;
     flagged += flag;
+  }
+  if (vmesh) count_by_mesh(counted, melig);
   }
   // block totals of the round counters
   link_bad = __reduce_add_sync(0xffffffffu, link_bad);
@@ -325,14 +351,17 @@ __global__ void __launch_bounds__(kBlock) k_edge_cost(
 
 pamo_status edge_costs(pamo_ctx* c) {
   const double s2 = c->scale * c->scale, wes = c->opt.w_e * c->scale;
+  const bool batch = c->n_mesh > 1;
   static const int g_reuse = occ_grid(k_edge_reuse);
   static const int g_cost = occ_grid(k_edge_cost);
   k_edge_reuse<<<g_reuse, kBlock, 0, c->st>>>(c->E, c->vdirty, c->ivmap, c->E_prev, c->e_off_prev,
                                         c->cbits_prev, c->vbar_prev, c->link_prev, c->flags,
-                                        c->key, c->vbar, c->cbits, c->link, c->dlist, c->dc); note_launch();
+                                        c->key, c->vbar, c->cbits, c->link, c->dlist, c->dc,
+                                        batch ? c->vmesh : nullptr, c->mactive, c->mcount); note_launch();
   k_edge_cost<<<g_cost, kBlock, 0, c->st>>>(c->dlist, c->E, c->pos, c->K, c->F, c->vf_off, c->vf_idx,
                                        c->flags, s2, wes, c->opt.w_s, c->key, c->vbar, c->cbits,
-                                       c->link, c->dc); note_launch();
+                                       c->link, c->dc, batch ? c->vmesh : nullptr, c->mcost,
+                                       c->mactive, c->mcount); note_launch();
   PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;
 }

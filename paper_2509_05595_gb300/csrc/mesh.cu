@@ -10,6 +10,7 @@
 // fixed grid; the commit kernels are gated by the "clean" result of the last
 // intersection check.
 #include <cstring>
+#include <vector>
 
 #include "common.cuh"
 
@@ -74,6 +75,120 @@ __global__ void k_bbox(const float4* __restrict__ pos, int64_t nV, unsigned* __r
       atomicMin(&out[k], lo[k]);
       atomicMax(&out[3 + k], hi[k]);
     }
+  }
+}
+
+// ---- batches: many meshes handled as one disjoint union --------------------
+// The vertices (faces) of mesh m are [off[m], off[m+1]) of the union; the
+// input faces of a mesh index its own vertices from 0.
+__device__ __forceinline__ int seg_of(const int64_t* __restrict__ off, int M, int64_t i) {
+  int lo = 0, hi = M - 1;  // the last m with off[m] <= i
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void k_load_batch(const float* __restrict__ V, int64_t nV, const int32_t* __restrict__ Fi,
+                             int64_t nF, const int64_t* __restrict__ voff,
+                             const int64_t* __restrict__ foff, int M, float4* __restrict__ pos,
+                             int4* __restrict__ F, int32_t* __restrict__ vmesh,
+                             int* __restrict__ bad) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nV) {
+    pos[i] = make_float4(V[3 * i], V[3 * i + 1], V[3 * i + 2], 0.0f);
+    vmesh[i] = seg_of(voff, M, i);
+  }
+  if (i < nF) {
+    const int m = seg_of(foff, M, i);
+    const int64_t base = voff[m], nv = voff[m + 1] - base;
+    int c[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      const int32_t x = Fi[3 * i + k];
+      if (x < 0 || x >= nv) {
+        atomicOr(bad, 1);
+        c[k] = (int)base;  // stays inside the mesh; the call fails with EINVAL
+      } else {
+        c[k] = (int)(base + x);
+      }
+    }
+    F[i] = make_int4(c[0], c[1], c[2], 0);
+  }
+}
+
+// bounding box of each mesh: one block per mesh, order-preserving encodings
+__global__ void k_mesh_bbox(const float4* __restrict__ pos, const int64_t* __restrict__ voff,
+                            unsigned* __restrict__ out) {
+  __shared__ unsigned red[6][kBlock / 32];
+  const int m = blockIdx.x;
+  unsigned lo[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, hi[3] = {0, 0, 0};
+  for (int64_t i = voff[m] + threadIdx.x; i < voff[m + 1]; i += blockDim.x) {
+    const float4 p = pos[i];
+    const float c[3] = {p.x, p.y, p.z};
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      const unsigned u = fkey(c[k]);
+      lo[k] = min(lo[k], u);
+      hi[k] = max(hi[k], u);
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    lo[k] = __reduce_min_sync(0xffffffffu, lo[k]);
+    hi[k] = __reduce_max_sync(0xffffffffu, hi[k]);
+    if (lane == 0) {
+      red[k][wid] = lo[k];
+      red[3 + k][wid] = hi[k];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    const int k = threadIdx.x;
+    unsigned r = red[k][0];
+    for (int w = 1; w < kBlock / 32; w++) r = k < 3 ? min(r, red[k][w]) : max(r, red[k][w]);
+    out[6 * m + k] = r;
+  }
+}
+
+// output faces in each mesh's own vertex numbering
+__global__ void k_store_batch(const float4* __restrict__ pos, int64_t nV,
+                              const int4* __restrict__ F, int64_t nF,
+                              const int32_t* __restrict__ vmesh, const int32_t* __restrict__ vbase,
+                              float* __restrict__ V, int32_t* __restrict__ Fo) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nV) {
+    const float4 p = pos[i];
+    V[3 * i] = p.x;
+    V[3 * i + 1] = p.y;
+    V[3 * i + 2] = p.z;
+  }
+  if (i < nF) {
+    const int4 f = F[i];
+    const int b = vbase[vmesh[f.x]];
+    Fo[3 * i] = f.x - b;
+    Fo[3 * i + 1] = f.y - b;
+    Fo[3 * i + 2] = f.z - b;
+  }
+}
+
+// last round's flags in the committed numbering (~0 where a vertex died); in a
+// batch the flags of meshes that committed nothing carry over, and the
+// vertices of other meshes may have moved
+__global__ void k_remap_flags(const unsigned long long* __restrict__ flags,
+                              const RoundCounters* __restrict__ dc,
+                              const int32_t* __restrict__ vmap,
+                              unsigned long long* __restrict__ out) {
+  if (!dc->go) return;
+  const int n = dc->nflags;
+  GRID_STRIDE(i, n) {
+    const unsigned long long p = flags[i];
+    const int a = vmap[(int)(p >> 32)], b = vmap[(int)(p & 0xffffffffu)];
+    out[i] = (a < 0 || b < 0) ? ~0ull
+                              : ((unsigned long long)(unsigned)a << 32) | (unsigned)b;
   }
 }
 
@@ -293,8 +408,10 @@ __global__ void k_save_prev(RoundCounters* __restrict__ dc, const int2* __restri
                             const float4* __restrict__ vbar, const uint8_t* __restrict__ link,
                             int2* __restrict__ E_prev, int32_t* __restrict__ e_off_prev,
                             uint32_t* __restrict__ cbits_prev, float4* __restrict__ vbar_prev,
-                            uint8_t* __restrict__ link_prev) {
+                            uint8_t* __restrict__ link_prev, int32_t* __restrict__ mcount,
+                            int mcount_n) {
   const int nE = dc->nE, nO = dc->nV_edges + 1;
+  GRID_STRIDE(i, mcount_n) mcount[i] = 0;
   if (blockIdx.x == 0 && threadIdx.x < (sizeof(RoundCounters) - PAMO_ROUND_ZERO_OFFSET) / 4)
     reinterpret_cast<int*>(reinterpret_cast<char*>(dc) + PAMO_ROUND_ZERO_OFFSET)[threadIdx.x] = 0;
   GRID_STRIDE(i, nE) {
@@ -369,7 +486,9 @@ __global__ void k_compact_vertices(const float4* __restrict__ pos_s, const doubl
                                    const uint8_t* __restrict__ vdead,
                                    const int32_t* __restrict__ dead_before, const int* n_dev,
                                    float4* __restrict__ pos, double* __restrict__ K,
-                                   int32_t* __restrict__ vmap, int32_t* __restrict__ ivmap) {
+                                   int32_t* __restrict__ vmap, int32_t* __restrict__ ivmap,
+                                   const int32_t* __restrict__ vmesh,
+                                   int32_t* __restrict__ vmesh_out) {
   const int nV = *n_dev;
   GRID_STRIDE(v, nV) {
     if (vdead[v]) {
@@ -380,6 +499,7 @@ __global__ void k_compact_vertices(const float4* __restrict__ pos_s, const doubl
     vmap[v] = (int32_t)n;
     ivmap[n] = (int32_t)v;
     pos[n] = pos_s[v];
+    if (vmesh) vmesh_out[n] = vmesh[v];
     const double2* src = reinterpret_cast<const double2*>(K_s + 10 * v);
     double2* dst = reinterpret_cast<double2*>(K + 10 * n);
 #pragma unroll
@@ -408,15 +528,33 @@ __global__ void k_undone_pairs(const int32_t* __restrict__ wlist, const int2* __
                                const uint8_t* __restrict__ standing, const int32_t* __restrict__ uscan,
                                RoundCounters* __restrict__ dc, const int32_t* __restrict__ vmap,
                                unsigned long long* __restrict__ flags,
-                               unsigned long long* __restrict__ flags_next) {
+                               unsigned long long* __restrict__ flags_next,
+                               const int32_t* __restrict__ vmesh, int32_t* __restrict__ mcount,
+                               int M) {
   const int nW = dc->goW;  // 0 when the round does not commit
   const int nund = dc->go ? uscan[dc->nW] : 0;
   const int committed = dc->nW - nund;
-  unsigned long long* out = committed > 0 ? flags : flags_next;
-  GRID_STRIDE(w, nW) {
-    if (standing[w]) continue;
-    const int2 e = E[wlist[w]];
-    out[uscan[w]] = ((unsigned long long)(unsigned)vmap[e.x] << 32) | (unsigned)vmap[e.y];
+  // a batch keeps every list apart for the per-mesh merge on the host
+  unsigned long long* out = (committed > 0 && !vmesh) ? flags : flags_next;
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nW;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t w = base + threadIdx.x;
+    int m = -1;
+    bool st = false;
+    if (w < nW) {
+      const int2 e = E[wlist[w]];
+      st = standing[w] != 0;
+      if (!st)
+        out[uscan[w]] = ((unsigned long long)(unsigned)vmap[e.x] << 32) | (unsigned)vmap[e.y];
+      if (vmesh) m = vmesh[e.x];
+    }
+    if (vmesh) {  // per-mesh committed / undone counts, one atomic per group of lanes
+      const int key = m < 0 ? -1 : (st ? m : M + m);
+      const unsigned peers = __match_any_sync(0xffffffffu, key);
+      if (key >= 0 && lane == __ffs(peers) - 1)
+        atomicAdd(&mcount[M + key], __popc(peers));  // [M, 2M) committed, [2M, 3M) undone
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (!dc->go) {
@@ -427,7 +565,7 @@ __global__ void k_undone_pairs(const int32_t* __restrict__ wlist, const int2* __
       dc->committed = committed;
       dc->goVn = dc->nV - committed;
       dc->goFn = dc->nF - 2 * committed;
-      if (committed > 0) dc->nflags = nund;
+      if (committed > 0 && !vmesh) dc->nflags = nund;
     }
   }
 }
@@ -480,13 +618,6 @@ pamo_status load_mesh(const float* d_V, int64_t nV, const int32_t* d_F, int64_t 
   return PAMO_OK;
 }
 
-pamo_status store_mesh(const float4* pos, int64_t nV, const int4* F, int64_t nF, float* d_V,
-                       int32_t* d_F, cudaStream_t st) {
-  k_store<<<grid_for(nV > nF ? nV : nF), kBlock, 0, st>>>(pos, nV, F, nF, d_V, d_F); note_launch();
-  PAMO_CUDA(cudaGetLastError());
-  return PAMO_OK;
-}
-
 static void decode_bbox(const unsigned out[6], float lo[3], float hi[3]) {
   for (int k = 0; k < 3; k++) {
     unsigned a = out[k], b = out[3 + k];
@@ -496,6 +627,52 @@ static void decode_bbox(const unsigned out[6], float lo[3], float hi[3]) {
     std::memcpy(&hi[k], &b, 4);
   }
 }
+
+pamo_status load_mesh_batch(const float* d_V, int64_t nV, const int32_t* d_F, int64_t nF,
+                            const int64_t* d_voff, const int64_t* d_foff, int M, float4* pos,
+                            int4* F, int32_t* vmesh, int* d_bad, cudaStream_t st) {
+  PAMO_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int), st));
+  k_load_batch<<<grid_for(nV > nF ? nV : nF), kBlock, 0, st>>>(d_V, nV, d_F, nF, d_voff, d_foff, M,
+                                                               pos, F, vmesh, d_bad); note_launch();
+  PAMO_CUDA(cudaGetLastError());
+  int hb = 0;
+  PAMO_CUDA(cudaMemcpyAsync(&hb, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PAMO_CUDA(cudaStreamSynchronize(st));
+  PAMO_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int), st));
+  if (hb) {
+    set_error("a face index is outside its mesh's vertex range");
+    return PAMO_EINVAL;
+  }
+  return PAMO_OK;
+}
+
+pamo_status mesh_bbox_batch(const float4* pos, const int64_t* d_voff, int M, unsigned* d_out,
+                            float* lo, float* hi, cudaStream_t st) {
+  k_mesh_bbox<<<M, kBlock, 0, st>>>(pos, d_voff, d_out); note_launch();
+  PAMO_CUDA(cudaGetLastError());
+  std::vector<unsigned> h(6 * (size_t)M);
+  PAMO_CUDA(cudaMemcpyAsync(h.data(), d_out, sizeof(unsigned) * 6 * M, cudaMemcpyDeviceToHost, st));
+  PAMO_CUDA(cudaStreamSynchronize(st));
+  for (int m = 0; m < M; m++) decode_bbox(&h[6 * (size_t)m], lo + 3 * (size_t)m, hi + 3 * (size_t)m);
+  return PAMO_OK;
+}
+
+pamo_status store_mesh_batch(const float4* pos, int64_t nV, const int4* F, int64_t nF,
+                             const int32_t* vmesh, const int32_t* d_vbase, float* d_V,
+                             int32_t* d_F, cudaStream_t st) {
+  k_store_batch<<<grid_for(nV > nF ? nV : nF), kBlock, 0, st>>>(pos, nV, F, nF, vmesh, d_vbase,
+                                                                d_V, d_F); note_launch();
+  PAMO_CUDA(cudaGetLastError());
+  return PAMO_OK;
+}
+
+pamo_status store_mesh(const float4* pos, int64_t nV, const int4* F, int64_t nF, float* d_V,
+                       int32_t* d_F, cudaStream_t st) {
+  k_store<<<grid_for(nV > nF ? nV : nF), kBlock, 0, st>>>(pos, nV, F, nF, d_V, d_F); note_launch();
+  PAMO_CUDA(cudaGetLastError());
+  return PAMO_OK;
+}
+
 
 // mesh_bbox with caller-provided device scratch (6 words); allocates nothing
 pamo_status mesh_bbox_into(const float4* pos, int64_t nV, unsigned* d_tmp, float lo[3], float hi[3],
@@ -591,7 +768,8 @@ pamo_status validate_mesh(pamo_ctx* c) {
 pamo_status save_prev(pamo_ctx* c) {
   k_save_prev<<<c->grid, kBlock, 0, c->st>>>(c->dc, c->E, c->e_off, c->cbits, c->vbar, c->link,
                                              c->E_prev, c->e_off_prev, c->cbits_prev, c->vbar_prev,
-                                             c->link_prev); note_launch();
+                                             c->link_prev, c->mcount,
+                                             c->n_mesh > 1 ? 3 * c->n_mesh : 0); note_launch();
   PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;
 }
@@ -632,15 +810,22 @@ pamo_status commit_compact(pamo_ctx* c) {
   const int G = c->grid;
   // vertices: new id = old id - (dead vertices before it)
   PAMO_TRY(scan_dev_u8(c->vdead, &dc->goV, c->dbuf, c->scan_sums, G, st));
+  const bool batch = c->n_mesh > 1;
   k_compact_vertices<<<G, kBlock, 0, st>>>(c->pos_s, c->K_s, c->vdead, c->dbuf, &dc->goV, c->pos,
-                                           c->K, c->vmap, c->ivmap); note_launch();
+                                           c->K, c->vmap, c->ivmap, batch ? c->vmesh : nullptr,
+                                           c->vmesh_tmp); note_launch();
   // faces, corners remapped
   PAMO_TRY(scan_dev_u8(c->fdead, &dc->goF, c->dbuf, c->scan_sums, G, st));
   k_compact_faces<<<G, kBlock, 0, st>>>(c->F_s, c->fdead, c->dbuf, &dc->goF, c->vmap, c->F); note_launch();
   // undone winners -> next round's flag candidates (sorted vertex pairs)
   PAMO_TRY(scan_dev_u8_not(c->standing, &dc->goW, c->wscan, c->scan_sums, G, st));
   k_undone_pairs<<<G, kBlock, 0, st>>>(c->wlist, c->E, c->standing, c->wscan, dc, c->vmap, c->flags,
-                                       c->flags_next); note_launch();
+                                       c->flags_next, batch ? c->vmesh : nullptr, c->mcount,
+                                       c->n_mesh); note_launch();
+  if (batch) {  // goVn is set by k_undone_pairs
+    k_remap_flags<<<G, kBlock, 0, st>>>(c->flags, dc, c->vmap, c->flags_old); note_launch();
+    PAMO_TRY(copy_dev(c->vmesh, c->vmesh_tmp, &dc->goVn, 0, sizeof(int32_t), G, st));
+  }
   // dirty vertices of the next round (survivors and their neighbours)
   k_clear2<<<G, kBlock, 0, st>>>(c->vsurv, c->vdirty, &dc->goVn); note_launch();
   k_mark_survivors<<<G, kBlock, 0, st>>>(c->wlist, c->E, c->standing, &dc->goW, c->vmap, c->vsurv); note_launch();
