@@ -79,6 +79,14 @@ typedef struct {
                               run ends with PAMO_OK once no edge is eligible
                               and no flag is pending, even above N_t. Must be
                               >= 0; default +infinity (off) */
+  /* Speed-only knobs (the results are identical for every value; chosen by
+   * pamo_autotune_batch or left at 0 for the defaults): */
+  int32_t grid_blocks_per_sm; /* blocks per SM of the bandwidth-bound
+                              grid-stride kernels (0 = 4; 1..32) */
+  int32_t resort_percent;  /* the LBVH keeps last round's compacted leaf order
+                              until the face count falls below this percent of
+                              the count at the last Morton sort (0 = 50;
+                              1..100, 100 = sort every round) */
 } pamo_options;
 
 /* Kernel classes reported in pamo_stats (index = bit of pamo_options.profile). */
@@ -168,6 +176,21 @@ pamo_status pamo_simplify_batch(int32_t n_meshes, const float* d_V, const int64_
                                 float* d_Vout, int64_t* h_voff_out, int32_t* d_Fout,
                                 int64_t* h_foff_out, int32_t* h_status, int32_t* h_rounds,
                                 pamo_stats* stats);
+
+/* Autotuner of the speed-only knobs for a batch (no counterpart in the
+ * paper): simplifies the given batch (arguments as pamo_simplify_batch) with
+ * a sequence of candidate settings -- coordinate descent over resort_percent
+ * in {25, 50, 75, 100}, then grid_blocks_per_sm in {2, 4, 8} -- timing each
+ * run with CUDA events, and writes the fastest into *best (a copy of *base
+ * with the two knobs set).  h_ms (host, may be NULL, capacity 8) receives
+ * the time of every trial and *n_trials their number.  Every trial produces
+ * the same meshes.  Synchronous; allocates only what pamo_simplify_batch
+ * allocates plus the trial outputs. */
+pamo_status pamo_autotune_batch(int32_t n_meshes, const float* d_V, const int64_t* h_voff,
+                                const int32_t* d_F, const int64_t* h_foff,
+                                const int64_t* h_targets, const pamo_options* base,
+                                void* stream, pamo_options* best, double* h_ms,
+                                int32_t* n_trials);
 
 /* ---- per-round entry points (one round = one iteration of Algorithm 1's
  * while loop) over a context that owns the evolving mesh ---- */

@@ -43,7 +43,8 @@ class _Options(ctypes.Structure):
                 ("stall_limit", ctypes.c_int32), ("validate_input", ctypes.c_int32),
                 ("check_mode", ctypes.c_int32), ("record_rounds", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("exact_target", ctypes.c_int32),
-                ("max_cost", ctypes.c_double)]
+                ("max_cost", ctypes.c_double), ("grid_blocks_per_sm", ctypes.c_int32),
+                ("resort_percent", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
@@ -71,6 +72,8 @@ class Options:
     profile: int = 0
     exact_target: int = 0
     max_cost: float = float("inf")
+    grid_blocks_per_sm: int = 0
+    resort_percent: int = 0
 
     def c(self):
         return _Options(**{f.name: getattr(self, f.name) for f in fields(self)})
@@ -93,6 +96,7 @@ def lib():
             "pamo_simplify_host": (ctypes.c_int, [P, i64, P, i64, i64, P, P, P, pi64, P, pi64, P]),
             "pamo_simplify_batch": (ctypes.c_int, [i32, P, P, P, P, P, P, P, P, P, P, P, P, P,
                                                    P]),
+            "pamo_autotune_batch": (ctypes.c_int, [i32, P, P, P, P, P, P, P, P, P, P]),
             "pamo_ctx_create": (ctypes.c_int, [P, i64, P, i64, P, P, ctypes.POINTER(P)]),
             "pamo_round_cost": (ctypes.c_int, [P]),
             "pamo_round_select": (ctypes.c_int, [P, pi64]),
@@ -224,6 +228,30 @@ def pamo_simplify_batch(V, voff, F, foff, targets, options: Options | None = Non
     _check(code, "pamo_simplify_batch", ok=(PAMO_OK, PAMO_ESTALL))
     return (Vo[: vo[-1]], vo, Fo[: fo[-1]], fo, [STATUS[int(x)] for x in status], rounds,
             _stats_dict(st))
+
+
+def pamo_autotune_batch(V, voff, F, foff, targets, options: Options | None = None, **kw):
+    """Choose the speed-only knobs (grid_blocks_per_sm, resort_percent) for a
+    batch by timing candidate runs on it.  Returns (Options, trial_ms)."""
+    import torch
+    o = options or Options(**kw)
+    V = _dev(V, torch.float32, 3)
+    F = _dev(F, torch.int32, 3)
+    voff = np.ascontiguousarray(voff, np.int64)
+    foff = np.ascontiguousarray(foff, np.int64)
+    tg = np.ascontiguousarray(targets, np.int64)
+    best = _Options()
+    ms = np.zeros(8, np.float64)
+    nt = ctypes.c_int32()
+    base = o.c()
+    code = lib().pamo_autotune_batch(
+        len(voff) - 1, _ptr(V), voff.ctypes.data_as(ctypes.c_void_p), _ptr(F),
+        foff.ctypes.data_as(ctypes.c_void_p), tg.ctypes.data_as(ctypes.c_void_p),
+        ctypes.byref(base), _stream(), ctypes.byref(best), ms.ctypes.data_as(ctypes.c_void_p),
+        ctypes.byref(nt))
+    _check(code, "pamo_autotune_batch")
+    chosen = Options(**{f.name: getattr(best, f.name) for f in fields(Options)})
+    return chosen, ms[: nt.value].tolist()
 
 
 def pamo_simplify_host(V, F, target_faces, options: Options | None = None, **kw):

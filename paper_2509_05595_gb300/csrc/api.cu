@@ -180,6 +180,11 @@ pamo_status check_options(const pamo_options* o) {
     set_error("max_cost must be >= 0 (+infinity = no cost target)");
     return PAMO_EINVAL;
   }
+  if (o->grid_blocks_per_sm < 0 || o->grid_blocks_per_sm > 32 || o->resort_percent < 0 ||
+      o->resort_percent > 100) {
+    set_error("grid_blocks_per_sm must be in 0..32 and resort_percent in 0..100");
+    return PAMO_EINVAL;
+  }
   return PAMO_OK;
 }
 
@@ -202,8 +207,8 @@ pamo_status new_ctx(const pamo_options* opt, cudaStream_t st, pamo_ctx** out) {
     return cuda_fail(e, "context stream");
   }
   c->opt = o;
-  c->grid = default_grid();
-  c->sm_count = c->grid / 4;
+  c->sm_count = sm_count();
+  c->grid = c->sm_count * (o.grid_blocks_per_sm > 0 ? o.grid_blocks_per_sm : 4);
   *out = c;
   return PAMO_OK;
 }
@@ -922,7 +927,11 @@ pamo_status run_batch(pamo_ctx* c) {
 }
 
 bool use_carry(pamo_ctx* c) {
-  return c->bvh.order_ok && 2 * c->nF > c->bvh.n_sorted && c->opt.check_mode != 3;
+  // keep the carried leaf order while the face count stays above resort% of
+  // the count at the last sort (Morton order only affects speed)
+  const int64_t pct = c->opt.resort_percent > 0 ? c->opt.resort_percent : 50;
+  return c->bvh.order_ok && 100 * c->nF > pct * (int64_t)c->bvh.n_sorted &&
+         pct < 100 && c->opt.check_mode != 3;
 }
 
 void note_build(pamo_ctx* c, bool carry) {
@@ -1124,6 +1133,8 @@ void pamo_default_options(pamo_options* o) {
   o->profile = 0;
   o->exact_target = 0;
   o->max_cost = INFINITY;
+  o->grid_blocks_per_sm = 0;
+  o->resort_percent = 0;
 }
 
 const char* pamo_last_error(void) { return g_err.c_str(); }
@@ -1410,6 +1421,25 @@ pamo_status pamo_simplify_batch(int32_t n_meshes, const float* d_V, const int64_
     set_error("output arguments must not be NULL");
     return PAMO_EINVAL;
   }
+  if (n_meshes == 1 && h_voff && h_foff && h_targets) {  // one mesh: the plain path
+    if (h_voff[0] != 0 || h_foff[0] != 0) {
+      set_error("batch: offsets must start at 0");
+      return PAMO_EINVAL;
+    }
+    pamo_stats local;
+    int64_t nvo = 0, nfo = 0;
+    pamo_status s = pamo_simplify(d_V, h_voff[1], d_F, h_foff[1], h_targets[0], opt, stream,
+                                  d_Vout, &nvo, d_Fout, &nfo, &local);
+    if (s != PAMO_OK && s != PAMO_ESTALL) return s;
+    h_voff_out[0] = 0;
+    h_voff_out[1] = nvo;
+    h_foff_out[0] = 0;
+    h_foff_out[1] = nfo;
+    if (h_status) h_status[0] = s;
+    if (h_rounds) h_rounds[0] = local.rounds;
+    if (stats) *stats = local;
+    return s;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   cudaEvent_t e0, e1;
   PAMO_CUDA(cudaEventCreate(&e0));
@@ -1453,6 +1483,87 @@ pamo_status pamo_simplify_batch(int32_t n_meshes, const float* d_V, const int64_
   cudaEventDestroy(e1);
   if (c) pamo_ctx_destroy(c);
   return s;
+}
+
+pamo_status pamo_autotune_batch(int32_t n_meshes, const float* d_V, const int64_t* h_voff,
+                                const int32_t* d_F, const int64_t* h_foff,
+                                const int64_t* h_targets, const pamo_options* base,
+                                void* stream, pamo_options* best, double* h_ms,
+                                int32_t* n_trials) {
+  if (!best || n_meshes < 1 || !h_voff || !h_foff || !h_targets) {
+    set_error("autotune: need the batch description and an output");
+    return PAMO_EINVAL;
+  }
+  pamo_options b;
+  if (base) b = *base;
+  else pamo_default_options(&b);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t nV = h_voff[n_meshes], nF = h_foff[n_meshes];
+  float* dVo = nullptr;
+  int32_t* dFo = nullptr;
+  pamo_status s = alloc(&dVo, 3 * nV, st);
+  if (s == PAMO_OK) s = alloc(&dFo, 3 * nF, st);
+  std::vector<int64_t> vo(n_meshes + 1), fo(n_meshes + 1);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (s == PAMO_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) {
+    set_error("autotune: cudaEventCreate");
+    s = PAMO_ECUDA;
+  }
+  auto trial = [&](const pamo_options& o, double* ms) -> pamo_status {
+    cudaEventRecord(e0, st);
+    pamo_status r = pamo_simplify_batch(n_meshes, d_V, h_voff, d_F, h_foff, h_targets, &o, stream,
+                                        dVo, vo.data(), dFo, fo.data(), nullptr, nullptr, nullptr);
+    if (r != PAMO_OK && r != PAMO_ESTALL) return r;
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    *ms = t;
+    return PAMO_OK;
+  };
+  int nt = 0;
+  double best_ms = 1e300, t = 0.0;
+  pamo_options cur = b;
+  cur.grid_blocks_per_sm = 4;
+  cur.resort_percent = 50;
+  pamo_options chosen = cur;
+  if (s == PAMO_OK) s = trial(cur, &t);  // warm-up (allocator pool, module load)
+  static const int kResort[4] = {25, 50, 75, 100};
+  for (int i = 0; i < 4 && s == PAMO_OK; i++) {
+    cur.resort_percent = kResort[i];
+    s = trial(cur, &t);
+    if (s == PAMO_OK) {
+      if (h_ms) h_ms[nt] = t;
+      nt++;
+      if (t < best_ms) {
+        best_ms = t;
+        chosen = cur;
+      }
+    }
+  }
+  static const int kGrid[2] = {2, 8};
+  cur = chosen;
+  for (int i = 0; i < 2 && s == PAMO_OK; i++) {
+    cur.grid_blocks_per_sm = kGrid[i];
+    s = trial(cur, &t);
+    if (s == PAMO_OK) {
+      if (h_ms) h_ms[nt] = t;
+      nt++;
+      if (t < best_ms) {
+        best_ms = t;
+        chosen = cur;
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  release(dVo, st);
+  release(dFo, st);
+  cudaStreamSynchronize(st);
+  if (s != PAMO_OK) return s;
+  *best = chosen;
+  if (n_trials) *n_trials = nt;
+  return PAMO_OK;
 }
 
 pamo_status pamo_tri_intersect_batch(const float* d_P, const int32_t* d_idx, int64_t n,

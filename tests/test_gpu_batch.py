@@ -101,3 +101,19 @@ def test_batch_rejects_bad_input():
     with pytest.raises(pamo.PamoError, match="EINVAL"):
         pamo.pamo_simplify_batch(torch.from_numpy(Vc), voff, torch.from_numpy(Fc), foff,
                                  [100, 100], exact_target=1)
+
+
+def test_autotune_picks_knobs_and_keeps_results():
+    meshes = [meshgen.bumped_icosphere(4, 12), meshgen.torus(48, 24, 1.0, 0.35, 0.002, 9),
+              meshgen.bumped_icosphere(3, 13)]
+    targets = [len(F) // 50 for _, F in meshes]
+    V, voff, F, foff = pamo.concat_meshes(meshes)
+    best, trials = pamo.pamo_autotune_batch(torch.from_numpy(V), voff, torch.from_numpy(F),
+                                            foff, targets)
+    assert len(trials) == 6 and all(t > 0 for t in trials)
+    assert best.resort_percent in (25, 50, 75, 100) and best.grid_blocks_per_sm in (2, 4, 8)
+    out, status, rounds, _ = _run_batch(meshes, targets, resort_percent=best.resort_percent,
+                                        grid_blocks_per_sm=best.grid_blocks_per_sm)
+    for m, ((Vm, Fm), t) in enumerate(zip(meshes, targets)):
+        ref = oracle.simplify(Vm, Fm, t, keep_pairs=False)
+        assert np.array_equal(out[m][1], ref.F) and np.array_equal(_bits(out[m][0]), _bits(ref.V))

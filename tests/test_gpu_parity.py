@@ -107,10 +107,13 @@ def _gpu_run(V, F, target, **opts):
     return Vo.cpu().numpy(), Fo.cpu().numpy(), rounds, stats, status
 
 
-def _assert_same_run(V, F, target, check_mode=oracle.CHECK_GRID, gpu_mode=0, **opts):
-    """opts (w_e, w_s, exact_target, max_cost) go to both sides."""
+def _assert_same_run(V, F, target, check_mode=oracle.CHECK_GRID, gpu_mode=0, gpu_only=None,
+                     **opts):
+    """opts (w_e, w_s, exact_target, max_cost) go to both sides; gpu_only
+    (speed-only knobs) to the GPU run alone."""
     ref = oracle.simplify(V, F, target, check_mode=check_mode, **opts)
-    gV, gF, rounds, stats, status = _gpu_run(V, F, target, check_mode=gpu_mode, **opts)
+    gV, gF, rounds, stats, status = _gpu_run(V, F, target, check_mode=gpu_mode, **opts,
+                                             **(gpu_only or {}))
     assert len(rounds) == len(ref.rounds)
     for r, (g, o) in enumerate(zip(rounds, ref.rounds)):
         for k in oracle.ROUND_FIELDS:

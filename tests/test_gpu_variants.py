@@ -59,3 +59,10 @@ def test_cost_ablation_switches_bit_exact(w_e, w_s):
     _assert_same_run(V, F, len(F) // 50, w_e=w_e, w_s=w_s)
     Vt, Ft, target = meshgen.mesh_config("torus_64x32")
     _assert_same_run(Vt, Ft, target, w_e=w_e, w_s=w_s)
+
+
+@pytest.mark.parametrize("knobs", [dict(resort_percent=100), dict(resort_percent=25),
+                                   dict(grid_blocks_per_sm=2), dict(grid_blocks_per_sm=8)])
+def test_speed_knobs_do_not_change_results(knobs):
+    V, F = meshgen.bumped_icosphere(5, 6)
+    _assert_same_run(V, F, len(F) // 100, **{"gpu_only": knobs})
