@@ -87,6 +87,14 @@ typedef struct {
                               until the face count falls below this percent of
                               the count at the last Morton sort (0 = 50;
                               1..100, 100 = sort every round) */
+  /* Learned proposal (no counterpart in the paper): a trained pamo_mlp (see
+   * below) that predicts, from 16 features of an eligible edge, that the
+   * intersection check would undo its collapse; such edges are deferred (hold
+   * no key) for the round, unless the previous round committed nothing.
+   * Every committed collapse still passes the exact check.  NULL = off
+   * (default); single-mesh calls only. */
+  const struct pamo_mlp* proposal;
+  float proposal_threshold; /* defer when the predicted probability exceeds it */
 } pamo_options;
 
 /* Kernel classes reported in pamo_stats (index = bit of pamo_options.profile). */
@@ -121,6 +129,7 @@ typedef struct {
    * edge 114 + 32 per produced triangle, counting +,-,*,/,sqrt as 1 and a
    * fused multiply-add as 2) */
   double class_flops[8];
+  int64_t deferred;            /* edges deferred by the learned proposal */
 } pamo_stats;
 
 typedef struct pamo_ctx pamo_ctx;
@@ -176,6 +185,41 @@ pamo_status pamo_simplify_batch(int32_t n_meshes, const float* d_V, const int64_
                                 float* d_Vout, int64_t* h_voff_out, int32_t* d_Fout,
                                 int64_t* h_foff_out, int32_t* h_status, int32_t* h_rounds,
                                 pamo_stats* stats);
+
+/* ---- the learned proposal's network (no counterpart in the paper) ----
+ * A per-edge MLP 16 -> 64 -> 64 -> 1 (ReLU, ReLU, logistic): BF16 weights
+ * (a BF16 copy of FP32 master weights), FP32 accumulation.  Parameters, flat:
+ * W1 [16][64] at 0, b1 [64] at 1024, W2 [64][64] at 1088, b2 [64] at 5184,
+ * W3 [64] at 5248, b3 at 5312 (W[i][j] maps input i to output j).  Inputs are
+ * the 16 edge features of pamo_ctx_winner_features, row-major float32. */
+#define PAMO_MLP_IN 16
+#define PAMO_MLP_HIDDEN 64
+#define PAMO_MLP_PARAMS 5313
+typedef struct pamo_mlp pamo_mlp;
+
+/* New network with all parameters zero (device memory, about 120 KB). */
+pamo_status pamo_mlp_create(pamo_mlp** out);
+void pamo_mlp_destroy(pamo_mlp* m);
+/* Set the FP32 master parameters (host, PAMO_MLP_PARAMS floats); refreshes
+ * the BF16 copy and resets the Adam state. */
+pamo_status pamo_mlp_set_params(pamo_mlp* m, const float* h_params);
+/* Read the master parameters and/or the BF16 copy (host, may be NULL). */
+pamo_status pamo_mlp_get_params(const pamo_mlp* m, float* h_params, uint16_t* h_bf16);
+/* Probabilities (device, n floats) for n feature rows (device, n x 16). */
+pamo_status pamo_mlp_forward(const pamo_mlp* m, const float* d_X, int64_t n, float* d_prob,
+                             void* stream);
+/* Gradient of the mean weighted binary cross-entropy
+ *   -(pos_weight y log p + (1 - y) log(1 - p))
+ * over n samples (d_X n x 16, d_y n labels in {0, 1}, device) with respect to
+ * the parameters, evaluated with the BF16 weights; kept in the model (see
+ * pamo_mlp_get_grad); *h_loss (host, may be NULL) gets the loss.
+ * Deterministic (fixed reduction order). */
+pamo_status pamo_mlp_grad(pamo_mlp* m, const float* d_X, const float* d_y, int64_t n,
+                          float pos_weight, void* stream, float* h_loss);
+pamo_status pamo_mlp_get_grad(const pamo_mlp* m, float* h_grad);
+/* One Adam step (Kingma & Ba 2015) with the last gradient. */
+pamo_status pamo_mlp_adam_step(pamo_mlp* m, float lr, float beta1, float beta2, float eps,
+                               void* stream);
 
 /* Autotuner of the speed-only knobs for a batch (no counterpart in the
  * paper): simplifies the given batch (arguments as pamo_simplify_batch) with
@@ -244,6 +288,14 @@ pamo_status pamo_ctx_round_info(const pamo_ctx* ctx, int64_t r, int64_t* out);
  * *n receives the total. */
 pamo_status pamo_ctx_round_pairs(const pamo_ctx* ctx, int64_t r, int32_t kind,
                                  int32_t* h_out, int64_t cap, int64_t* n);
+
+/* Training data of the learned proposal (no counterpart in the paper).
+ * After pamo_round_select: the 16 features of every winner of this round, in
+ * winner order (d_X: device, n_winners x 16 float32; see pamo_mlp).  After
+ * pamo_round_check_undo: 1 for each winner whose collapse stands, 0 for an
+ * undone one (d_out: device, n_winners bytes). */
+pamo_status pamo_ctx_winner_features(pamo_ctx* ctx, float* d_X);
+pamo_status pamo_ctx_winner_standing(pamo_ctx* ctx, uint8_t* d_out);
 
 /* Number of recorded rounds and the run status so far (PAMO_OK / ESTALL). */
 pamo_status pamo_ctx_rounds(const pamo_ctx* ctx, int64_t* rounds);

@@ -163,6 +163,18 @@ def nested_shells(level: int = 8, seeds=(0, 1), radii=(1.0, 0.99),
 nested_shells.last_min_gap = float("nan")
 
 
+def nested_shells_seeded(level: int, seed: int, **kw):
+    """Nested shells (nested_shells) for one seed of a seeded family: the outer
+    shell uses ``seed``; the inner one the first of seed + 4000 + 10007 k,
+    k = 0, 1, ..., for which the shells are disjoint."""
+    for k in range(64):
+        try:
+            return nested_shells(level, seeds=(seed, seed + 4000 + 10007 * k), check=True, **kw)
+        except ValueError:
+            continue
+    raise ValueError(f"no disjoint inner shell for seed {seed}")
+
+
 def tetrahedron():
     V = np.array([[1, 1, 1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1]], np.float32)
     F = np.array([[0, 1, 2], [0, 3, 1], [0, 2, 3], [1, 3, 2]], np.int32)

@@ -44,7 +44,8 @@ class _Options(ctypes.Structure):
                 ("check_mode", ctypes.c_int32), ("record_rounds", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("exact_target", ctypes.c_int32),
                 ("max_cost", ctypes.c_double), ("grid_blocks_per_sm", ctypes.c_int32),
-                ("resort_percent", ctypes.c_int32)]
+                ("resort_percent", ctypes.c_int32), ("proposal", ctypes.c_void_p),
+                ("proposal_threshold", ctypes.c_float)]
 
 
 class _Stats(ctypes.Structure):
@@ -55,7 +56,7 @@ class _Stats(ctypes.Structure):
                 ("ms_total", ctypes.c_double), ("bytes_model", ctypes.c_double),
                 ("launches", ctypes.c_int64), ("class_ms", ctypes.c_double * 8),
                 ("class_launches", ctypes.c_int64 * 8), ("class_bytes", ctypes.c_double * 8),
-                ("class_flops", ctypes.c_double * 8)]
+                ("class_flops", ctypes.c_double * 8), ("deferred", ctypes.c_int64)]
 
 
 @dataclass
@@ -74,9 +75,85 @@ class Options:
     max_cost: float = float("inf")
     grid_blocks_per_sm: int = 0
     resort_percent: int = 0
+    proposal: object = None        # an MLP (learned proposal) or None
+    proposal_threshold: float = 0.5
 
     def c(self):
-        return _Options(**{f.name: getattr(self, f.name) for f in fields(self)})
+        d = {f.name: getattr(self, f.name) for f in fields(self)}
+        p = d.pop("proposal")
+        o = _Options(**d)
+        o.proposal = p.handle.value if isinstance(p, MLP) else p
+        return o
+
+
+MLP_IN, MLP_HIDDEN, MLP_PARAMS = 16, 64, 5313
+
+
+class MLP:
+    """The learned proposal's network (pamo_mlp): 16 -> 64 -> 64 -> 1, BF16
+    weights over FP32 master weights, trained with the library's kernels."""
+
+    def __init__(self, params=None):
+        self.handle = ctypes.c_void_p()
+        _check(lib().pamo_mlp_create(ctypes.byref(self.handle)), "pamo_mlp_create")
+        if params is not None:
+            self.set_params(params)
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, np.float32)
+        if p.shape != (MLP_PARAMS,):
+            raise ValueError(f"expected {MLP_PARAMS} parameters")
+        _check(lib().pamo_mlp_set_params(self.handle, p.ctypes.data_as(ctypes.c_void_p)),
+               "pamo_mlp_set_params")
+
+    def get_params(self):
+        """(fp32 master parameters, bf16 copy as uint16 bit patterns)."""
+        p = np.zeros(MLP_PARAMS, np.float32)
+        b = np.zeros(MLP_PARAMS, np.uint16)
+        _check(lib().pamo_mlp_get_params(self.handle, p.ctypes.data_as(ctypes.c_void_p),
+                                         b.ctypes.data_as(ctypes.c_void_p)), "pamo_mlp_get_params")
+        return p, b
+
+    def forward(self, X):
+        import torch
+        X = _dev(X, torch.float32, MLP_IN)
+        out = torch.empty(X.shape[0], dtype=torch.float32, device="cuda")
+        _check(lib().pamo_mlp_forward(self.handle, _ptr(X), X.shape[0], _ptr(out), _stream()),
+               "pamo_mlp_forward")
+        return out
+
+    def grad(self, X, y, pos_weight=1.0):
+        """Loss (and the gradient, kept in the model) of the weighted BCE."""
+        import torch
+        X = _dev(X, torch.float32, MLP_IN)
+        y = _dev(y, torch.float32)
+        loss = ctypes.c_float()
+        _check(lib().pamo_mlp_grad(self.handle, _ptr(X), _ptr(y), X.shape[0],
+                                   ctypes.c_float(pos_weight), _stream(), ctypes.byref(loss)),
+               "pamo_mlp_grad")
+        return loss.value
+
+    def get_grad(self):
+        g = np.zeros(MLP_PARAMS, np.float32)
+        _check(lib().pamo_mlp_get_grad(self.handle, g.ctypes.data_as(ctypes.c_void_p)),
+               "pamo_mlp_get_grad")
+        return g
+
+    def adam_step(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        _check(lib().pamo_mlp_adam_step(self.handle, ctypes.c_float(lr), ctypes.c_float(beta1),
+                                        ctypes.c_float(beta2), ctypes.c_float(eps), _stream()),
+               "pamo_mlp_adam_step")
+
+    def close(self):
+        if self.handle:
+            lib().pamo_mlp_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def lib():
@@ -97,6 +174,17 @@ def lib():
             "pamo_simplify_batch": (ctypes.c_int, [i32, P, P, P, P, P, P, P, P, P, P, P, P, P,
                                                    P]),
             "pamo_autotune_batch": (ctypes.c_int, [i32, P, P, P, P, P, P, P, P, P, P]),
+            "pamo_ctx_winner_features": (ctypes.c_int, [P, P]),
+            "pamo_ctx_winner_standing": (ctypes.c_int, [P, P]),
+            "pamo_mlp_create": (ctypes.c_int, [ctypes.POINTER(P)]),
+            "pamo_mlp_destroy": (None, [P]),
+            "pamo_mlp_set_params": (ctypes.c_int, [P, P]),
+            "pamo_mlp_get_params": (ctypes.c_int, [P, P, P]),
+            "pamo_mlp_forward": (ctypes.c_int, [P, P, i64, P, P]),
+            "pamo_mlp_grad": (ctypes.c_int, [P, P, P, i64, ctypes.c_float, P, P]),
+            "pamo_mlp_get_grad": (ctypes.c_int, [P, P]),
+            "pamo_mlp_adam_step": (ctypes.c_int, [P, ctypes.c_float, ctypes.c_float,
+                                                  ctypes.c_float, ctypes.c_float, P]),
             "pamo_ctx_create": (ctypes.c_int, [P, i64, P, i64, P, P, ctypes.POINTER(P)]),
             "pamo_round_cost": (ctypes.c_int, [P]),
             "pamo_round_select": (ctypes.c_int, [P, pi64]),
@@ -157,7 +245,8 @@ def _stats_dict(s: _Stats):
                 winners=s.winners, nV_out=s.nV_out, nF_out=s.nF_out,
                 ms_total=s.ms_total, bytes_model=s.bytes_model, launches=s.launches,
                 class_ms=list(s.class_ms), class_launches=list(s.class_launches),
-                class_bytes=list(s.class_bytes), class_flops=list(s.class_flops))
+                class_bytes=list(s.class_bytes), class_flops=list(s.class_flops),
+                deferred=s.deferred)
 
 
 def pamo_simplify(V, F, target_faces, options: Options | None = None, **kw):
@@ -348,6 +437,21 @@ class Ctx:
         _check(lib().pamo_ctx_round_pairs(self._h, r, kind, out.ctypes.data_as(ctypes.c_void_p),
                                           n.value, ctypes.byref(n)), "pamo_ctx_round_pairs")
         return out[: n.value]
+
+    def winner_features(self, n_winners):
+        """[n_winners, 16] float32 features of this round's winners (after
+        round_select): the learned proposal's inputs."""
+        import torch
+        X = torch.empty((max(n_winners, 1), MLP_IN), dtype=torch.float32, device="cuda")
+        _check(lib().pamo_ctx_winner_features(self._h, _ptr(X)), "pamo_ctx_winner_features")
+        return X[:n_winners]
+
+    def winner_standing(self, n_winners):
+        """[n_winners] uint8: 1 where the collapse stands after the undo loop."""
+        import torch
+        s = torch.empty(max(n_winners, 1), dtype=torch.uint8, device="cuda")
+        _check(lib().pamo_ctx_winner_standing(self._h, _ptr(s)), "pamo_ctx_winner_standing")
+        return s[:n_winners]
 
     def run(self, target_faces):
         st = _Stats()

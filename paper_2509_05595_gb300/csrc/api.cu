@@ -120,6 +120,8 @@ void free_ctx_buffers(pamo_ctx* c) {
   release(c->vmesh, st); release(c->vmesh_tmp, st); release(c->voff_d, st); release(c->foff_d, st);
   release(c->mframe, st); release(c->mcost, st); release(c->mactive, st); release(c->mcount, st);
   release(c->mvbase, st); release(c->flags_old, st);
+  release(c->vnear, st); release(c->vnear_tmp, st); release(c->plist, st); release(c->pX, st);
+  release(c->pprob, st);
   if (c->mcount_h) cudaFreeHost(c->mcount_h);
   c->mcount_h = nullptr;
   for (int r = 0; r < 3; r++) release(c->cand[r], st);
@@ -233,7 +235,10 @@ pamo_status alloc_state(pamo_ctx* c, int64_t nV, int64_t nF) {
   A(dbuf, mx + 1); A(flags, c->Emax); A(flags_next, c->Emax); A(dc, 1);
   A(E_prev, c->Emax); A(e_off_prev, nV + 1); A(cbits, c->Emax); A(cbits_prev, c->Emax);
   A(vbar_prev, c->Emax); A(link, c->Emax); A(link_prev, c->Emax); A(ivmap, nV);
-  A(vsurv, nV); A(vdirty, nV); A(dlist, c->Emax);
+  A(vsurv, nV); A(vdirty, nV); A(dlist, c->Emax); A(vnear, nV); A(vnear_tmp, nV);
+  if (c->opt.proposal) {
+    A(plist, c->Emax); A(pX, 16 * c->Emax); A(pprob, c->Emax);
+  }
   A(scan_sums, scan_sums_count(std::max<int64_t>(c->Emax, mx + 1)));
   // candidate pairs of the split check: a changed face has at most 3
   // edge-neighbours; vertex-neighbours and other overlaps are bounded
@@ -251,9 +256,15 @@ pamo_status alloc_state(pamo_ctx* c, int64_t nV, int64_t nF) {
     A(mcount, 3 * (int64_t)M); A(mvbase, M); A(flags_old, c->Emax);
   }
 #undef A
+  if (s == PAMO_OK) {  // read by the proposal's features before the first check / commit
+    cudaError_t e = cudaMemsetAsync(c->vnear, 0, (size_t)nV, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->vsurv, 0, (size_t)nV, st);
+    if (e != cudaSuccess) s = cuda_fail(e, "cudaMemsetAsync");
+  }
   c->bvh.n_mesh = M;
   c->bvh.vmesh = c->vmesh;
   c->bvh.mframe = c->mframe;
+  c->bvh.vnear = c->vnear;
   if (s == PAMO_OK) s = bvh_alloc(c->bvh, (int)nF, st);
   if (s == PAMO_OK) {
     cudaError_t e = cudaMallocHost((void**)&c->hc, sizeof(RoundCounters));
@@ -271,6 +282,7 @@ pamo_status init_counters(pamo_ctx* c) {
   std::memset(c->hc, 0, sizeof(RoundCounters));
   c->hc->nV = (int)c->nV;
   c->hc->nF = (int)c->nF;
+  c->hc->last_committed = 1;
   // target edge cost as float bits (costs are keyed as floats, Section 5.1)
   c->hc->max_bits = 0x7f800000u;
   if (c->opt.max_cost < INFINITY) {
@@ -343,8 +355,8 @@ pamo_status create_batch(int M, const float* d_V, const int64_t* h_voff, const i
     set_error("batch: total sizes must stay below 2^30");
     return PAMO_EINVAL;
   }
-  if (opt && opt->exact_target) {
-    set_error("batch: exact_target is not supported");
+  if (opt && (opt->exact_target || opt->proposal)) {
+    set_error("batch: exact_target and the learned proposal are single-mesh options");
     return PAMO_EINVAL;
   }
   pamo_ctx* c = nullptr;
@@ -528,6 +540,7 @@ pamo_status phase_cost(pamo_ctx* c) {
   const double nV = (double)c->nV, nF = (double)c->nF, nE = 1.5 * nF;
   kc_begin(c, PAMO_KC_COST);
   PAMO_TRY(edge_costs(c));
+  if (c->opt.proposal) PAMO_TRY(propose(c));  // learned deferral of predicted rejects
   // E, positions, quadrics, CSR and faces read once; keys and placements written
   kc_end(c, PAMO_KC_COST, nE * (8 + 8 + 16) + nV * (16 + 80 + 4) + nF * (16 + 12));
   return PAMO_OK;
@@ -768,6 +781,7 @@ pamo_status finish_round(pamo_ctx* c) {
     c->rec.push_back(std::move(rec));
   }
   c->class_flops[PAMO_KC_COST] += 114.0 * h.n_dirty + 32.0 * (double)h.cost_tris;
+  c->deferred_total += h.deferred;
   c->committed_total += committed;
   c->undone_total += nund;
   c->link_total += info[3];
@@ -1104,6 +1118,7 @@ void fill_stats(const pamo_ctx* c, pamo_stats* s, double ms) {
   s->nF_out = c->nF;
   s->ms_total = ms;
   s->bytes_model = c->bytes_model;
+  s->deferred = c->deferred_total;
   for (int i = 0; i < 8; i++) {
     s->class_ms[i] = c->class_ms[i];
     s->class_launches[i] = c->class_launches[i];
@@ -1135,6 +1150,8 @@ void pamo_default_options(pamo_options* o) {
   o->max_cost = INFINITY;
   o->grid_blocks_per_sm = 0;
   o->resort_percent = 0;
+  o->proposal = nullptr;
+  o->proposal_threshold = 0.5f;
 }
 
 const char* pamo_last_error(void) { return g_err.c_str(); }
@@ -1241,6 +1258,31 @@ pamo_status pamo_ctx_round_pairs(const pamo_ctx* c, int64_t r, int32_t kind, int
   if (n) *n = m;
   if (h_out) std::memcpy(h_out, v.data(), sizeof(int32_t) * 2 * std::min(m, cap));
   return PAMO_OK;
+}
+
+pamo_status pamo_ctx_winner_features(pamo_ctx* c, float* d_X) {
+  CTX_GUARD(c);
+  if (c->stage != 2 || !d_X) {
+    set_error("pamo_ctx_winner_features: call after pamo_round_select, with an output");
+    return PAMO_EINVAL;
+  }
+  PAMO_TRY(enter(c));
+  PAMO_TRY(edge_features_list(c, c->wlist, &c->dc->nW, d_X, c->st));
+  PAMO_CUDA(cudaStreamSynchronize(c->st));
+  return join(c);
+}
+
+pamo_status pamo_ctx_winner_standing(pamo_ctx* c, uint8_t* d_out) {
+  CTX_GUARD(c);
+  if (c->stage != 4 || !d_out) {
+    set_error("pamo_ctx_winner_standing: call after pamo_round_check_undo, with an output");
+    return PAMO_EINVAL;
+  }
+  PAMO_TRY(enter(c));
+  if (c->nW > 0)
+    PAMO_CUDA(cudaMemcpyAsync(d_out, c->standing, (size_t)c->nW, cudaMemcpyDeviceToDevice, c->st));
+  PAMO_CUDA(cudaStreamSynchronize(c->st));
+  return join(c);
 }
 
 pamo_status pamo_ctx_rounds(const pamo_ctx* c, int64_t* rounds) {

@@ -584,7 +584,8 @@ __global__ void __launch_bounds__(kBlock) k_traverse(
 __global__ void __launch_bounds__(kBlock) k_pairs(
     CandBufs cb, const int* __restrict__ ncand, const float4* __restrict__ pos,
     const int4* __restrict__ F, const uint8_t* __restrict__ info,
-    const int32_t* __restrict__ ftag, uint8_t* __restrict__ undo, RoundCounters* __restrict__ dc) {
+    const int32_t* __restrict__ ftag, uint8_t* __restrict__ undo, RoundCounters* __restrict__ dc,
+    uint8_t* __restrict__ vnear) {
   const int n2 = min((int64_t)ncand[2], cb.cap[2]);
   const int n1 = min((int64_t)ncand[1], cb.cap[1]);
   const int n0 = min((int64_t)ncand[0], cb.cap[0]);
@@ -597,6 +598,10 @@ __global__ void __launch_bounds__(kBlock) k_pairs(
     const int2 p = i < n2 ? cb.c[2][i] : (i < n2 + n1 ? cb.c[1][i - n2] : cb.c[0][i - n2 - n1]);
     const int f = p.x, g = p.y;
     const int4 tv = F[f], cv = F[g];
+    if (vnear && i >= n2 + n1) {  // boxes of faces with no common vertex overlap
+      vnear[tv.x] = 1; vnear[tv.y] = 1; vnear[tv.z] = 1;
+      vnear[cv.x] = 1; vnear[cv.y] = 1; vnear[cv.z] = 1;
+    }
     const int ti[3] = {tv.x, tv.y, tv.z};
     const int ci[3] = {cv.x, cv.y, cv.z};
     float3 T[3], C[3];
@@ -828,7 +833,7 @@ pamo_status bvh_check_split(Bvh& b, const float4* pos, const int4* F, const uint
                                         many ? b.vmesh : nullptr,
                                         many ? (const int32_t*)b.mroot.p : nullptr); note_launch();
   k_pairs<<<g_pairs, kBlock, 0, st>>>(cb, ncand, pos, F, (const uint8_t*)b.face_aux.p, ftag, undo,
-                                   dc); note_launch();
+                                   dc, b.vnear); note_launch();
   PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;
 }

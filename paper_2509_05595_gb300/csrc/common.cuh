@@ -69,6 +69,8 @@ struct RoundCounters {
   int nV_edges;             // vertex count the edge offsets were built for
   int target;               // N_t of the running simplification
   unsigned max_bits;        // float bits of the target edge cost (0x7f800000 = off)
+  int last_committed;       // collapses committed by the last round (1 at the start)
+  int pad1;
   // ---- zeroed at the start of every round (from link_rejects on)
   unsigned long long link_rejects, flagged, eligible;
   unsigned long long cost_tris;  // triangles produced, summed over evaluated edges
@@ -83,6 +85,8 @@ struct RoundCounters {
   int goV, goF, goW;        // gated sizes for the commit (0 when not committing)
   int goVn, goFn;           // gated sizes of the committed mesh
   int sort_len;             // spare
+  int deferred;             // edges deferred by the learned proposal
+  int n_listed;             // eligible edges listed for the proposal
 };
 
 #define PAMO_ROUND_ZERO_OFFSET offsetof(::pamo::RoundCounters, link_rejects)
@@ -117,6 +121,7 @@ struct Bvh {
   Buf hkeys, hkeys2, mroot;
   const int32_t* vmesh = nullptr;
   const float* mframe = nullptr;
+  uint8_t* vnear = nullptr;  // marks vertices of non-adjacent overlapping pairs (may be null)
   // leaf order carried over rounds: valid when order_ok; re-sorted by Morton
   // code when the face count has halved since the last sort
   bool order_ok = false;
@@ -174,6 +179,13 @@ struct pamo_ctx {
   int32_t* ivmap = nullptr;            // [nV0] new vertex id -> previous id
   uint8_t* vsurv = nullptr;            // [nV0] survivor of a committed collapse
   uint8_t* vdirty = nullptr;           // [nV0] survivor or neighbour of one
+  uint8_t* vnear = nullptr;            // [nV0] near a non-adjacent face in the last check
+  uint8_t* vnear_tmp = nullptr;        // [nV0] compaction scratch
+  // learned proposal (when options.proposal is set)
+  int32_t* plist = nullptr;            // [Emax] eligible edges
+  float* pX = nullptr;                 // [Emax][16] their features
+  float* pprob = nullptr;              // [Emax] predicted probability of an undo
+  int64_t deferred_total = 0;
   int32_t* dlist = nullptr;            // [Emax] edges whose cost is recomputed
   bool have_prev = false;
   unsigned long long* key = nullptr;   // [Emax]
@@ -310,6 +322,13 @@ pamo_status fill_dev1(void* p, const int* n_dev, uint8_t v, int grid, cudaStream
 
 // cost.cu -------------------------------------------------------------------
 pamo_status edge_costs(pamo_ctx* c);
+
+// propose.cu / mlp.cu: the learned proposal
+pamo_status propose(pamo_ctx* c);
+pamo_status edge_features_list(pamo_ctx* c, const int32_t* list, const int* n_dev, float* X,
+                               cudaStream_t st);
+pamo_status mlp_forward_dev(const pamo_mlp* m, const float* X, const int* n_dev, float* prob,
+                            int64_t n_max, cudaStream_t st);
 
 // select.cu -----------------------------------------------------------------
 pamo_status select_winners(pamo_ctx* c);

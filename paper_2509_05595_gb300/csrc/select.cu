@@ -135,10 +135,12 @@ __global__ void k_stage_ms(const RoundCounters* __restrict__ dc, const float4* _
                            const double* __restrict__ K, const int4* __restrict__ F,
                            float4* __restrict__ pos_s, double* __restrict__ K_s,
                            int4* __restrict__ F_s, uint8_t* __restrict__ vdead,
-                           uint8_t* __restrict__ fdead, int32_t* __restrict__ ftag) {
+                           uint8_t* __restrict__ fdead, int32_t* __restrict__ ftag,
+                           uint8_t* __restrict__ vnear) {
   const int nV = dc->nV, nF = dc->nF;
   GRID_STRIDE(v, nV) {
     pos_s[v] = pos[v];
+    vnear[v] = 0;  // refilled by this round's check
     const double2* src = reinterpret_cast<const double2*>(K + 10 * v);
     double2* dst = reinterpret_cast<double2*>(K_s + 10 * v);
 #pragma unroll
@@ -331,7 +333,7 @@ pamo_status collapse_winners(pamo_ctx* c) {
   const int G = c->grid;
   // M_s starts as a copy of M_1: nothing dead, no face tagged
   k_stage_ms<<<G, kBlock, 0, st>>>(dc, c->pos, c->K, c->F, c->pos_s, c->K_s, c->F_s, c->vdead,
-                                   c->fdead, c->ftag); note_launch();
+                                   c->fdead, c->ftag, c->vnear); note_launch();
   static const int g_collapse = occ_grid(k_collapse);
   k_collapse<<<g_collapse, kBlock, 0, st>>>(c->wlist, dc, c->E, c->vbar, c->K, c->vf_off, c->vf_idx, c->F,
                                    c->pos_s, c->K_s, c->F_s, c->fdead, c->vdead, c->ftag,
