@@ -306,6 +306,136 @@ def run_batch_bench(args, world, rank):
         print(json.dumps(line), flush=True)
 
 
+def one_sided_hausdorff(Vo, Fo, V, F, k=16):
+    """max over the output's vertices and face centroids of the distance to
+    the input surface (exact point-to-triangle distance to the k input faces
+    whose centroids are nearest; float64)."""
+    from scipy.spatial import cKDTree
+    Vo, V = np.asarray(Vo, np.float64), np.asarray(V, np.float64)
+    Q = np.concatenate([Vo, Vo[np.asarray(Fo)].mean(1)])
+    T = V[np.asarray(F)]
+    _, cand = cKDTree(T.mean(1)).query(Q, k=min(k, len(F)))
+    A, B, C = T[cand, 0], T[cand, 1], T[cand, 2]
+    P = Q[:, None, :]
+    # closest point on triangle (Ericson, Real-Time Collision Detection, 5.1.5)
+    ab, ac, ap = B - A, C - A, P - A
+    d1, d2 = (ab * ap).sum(-1), (ac * ap).sum(-1)
+    bp = P - B
+    d3, d4 = (ab * bp).sum(-1), (ac * bp).sum(-1)
+    cp = P - C
+    d5, d6 = (ab * cp).sum(-1), (ac * cp).sum(-1)
+    va, vb, vc = d3 * d6 - d5 * d4, d5 * d2 - d1 * d6, d1 * d4 - d3 * d2
+    den = np.where(va + vb + vc == 0, 1.0, va + vb + vc)
+    v, w = vb / den, vc / den
+    X = A + ab * v[..., None] + ac * w[..., None]
+    def put(mask, val):
+        X[mask] = val[mask]
+    e_ab = (vc <= 0) & (d1 >= 0) & (d3 <= 0)
+    t = d1 / np.where(d1 - d3 == 0, 1.0, d1 - d3)
+    put(e_ab, A + ab * t[..., None])
+    e_ac = (vb <= 0) & (d2 >= 0) & (d6 <= 0)
+    t = d2 / np.where(d2 - d6 == 0, 1.0, d2 - d6)
+    put(e_ac, A + ac * t[..., None])
+    e_bc = (va <= 0) & ((d4 - d3) >= 0) & ((d5 - d6) >= 0)
+    t = (d4 - d3) / np.where((d4 - d3) + (d5 - d6) == 0, 1.0, (d4 - d3) + (d5 - d6))
+    put(e_bc, B + (C - B) * t[..., None])
+    put((d1 <= 0) & (d2 <= 0), A)
+    put((d3 >= 0) & (d4 <= d3), B)
+    put((d6 >= 0) & (d5 <= d6), C)
+    dist = np.linalg.norm(X - P, axis=-1).min(1)
+    return float(dist.max())
+
+
+def run_learned_bench(args, world, rank):
+    """The learned proposal against the plain method: labels logged by the
+    plain method on the near-contact family (nested shells, seeds 1000..),
+    the network trained by the library's kernels, then both methods on
+    held-out seeds (2000..): Mfaces/s, undo work, faces, self-intersections
+    and the one-sided Hausdorff distance to the input."""
+    import torch
+    import meshgen
+    import paper_2509_05595_gb300 as pamo
+    from paper_2509_05595_gb300 import proposal
+    t0 = time.perf_counter()
+    Xs, ys = [], []
+    for s in range(args.train_meshes):
+        V, F = meshgen.nested_shells_seeded(args.train_level, 1000 + s)
+        X, y = proposal.log_winners(V, F, len(F) // 100)
+        Xs.append(X)
+        ys.append(y)
+    X, y = torch.cat(Xs), torch.cat(ys)
+    t_log = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    # unweighted loss: calibrated probabilities, so a threshold is a probability
+    # of an undo (rejects are rare; a rebalanced loss would over-defer)
+    model, info = proposal.train(X, y, steps=args.train_steps, batch=8192, lr=2e-3,
+                                 pos_weight=1.0, log_every=max(1, args.train_steps // 10))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    thresholds = [float(t) for t in args.thresholds.split(",")]
+    arms = [("plain", None)] + [(f"learned@{t:g}", t) for t in thresholds]
+    res = {name: [] for name, _ in arms}
+    for s in range(args.eval_meshes):
+        V, F = meshgen.nested_shells_seeded(args.eval_level, 2000 + s)
+        Vd, Fd = torch.from_numpy(V).cuda(), torch.from_numpy(F).cuda()
+        target = len(F) // 100
+        for name, thr in arms:
+            opts = (pamo.Options(validate_input=0) if thr is None else
+                    pamo.Options(validate_input=0, proposal=model, proposal_threshold=thr))
+            pamo.pamo_simplify(Vd, Fd, target, options=opts)  # warm-up
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            Vo, Fo, st, status = pamo.pamo_simplify(Vd, Fd, target, options=opts)
+            e1.record(stream)
+            e1.synchronize()
+            nint, _ = pamo.pamo_check_self_intersections(Vo, Fo)
+            Vh, Fh = Vo.cpu().numpy(), Fo.cpu().numpy()
+            res[name].append(dict(ms=e0.elapsed_time(e1), faces_in=len(F), faces=len(Fh),
+                                  status=status, rounds=st["rounds"],
+                                  undone=st["undone"] - st["deferred"], deferred=st["deferred"],
+                                  undo_iters=sum(i * n for i, n in enumerate(st["undo_iters_hist"])),
+                                  intersections=int(nint),
+                                  hausdorff=one_sided_hausdorff(Vh, Fh, V, F)))
+
+    def agg(rows):
+        ms = sum(r["ms"] for r in rows)
+        return {"mfaces_s": sum(r["faces_in"] for r in rows) / (ms * 1e-3) / 1e6, "ms": ms,
+                "undo_iters": sum(r["undo_iters"] for r in rows),
+                "undone_by_check": sum(r["undone"] for r in rows),
+                "deferred": sum(r["deferred"] for r in rows),
+                "rounds": sum(r["rounds"] for r in rows),
+                "faces_out": sum(r["faces"] for r in rows),
+                "stalled": sum(r["status"] != "PAMO_OK" for r in rows),
+                "intersections": sum(r["intersections"] for r in rows),
+                "hausdorff_mean": float(np.mean([r["hausdorff"] for r in rows])),
+                "hausdorff_max": float(np.max([r["hausdorff"] for r in rows]))}
+    summary = {name: agg(rows) for name, rows in res.items()}
+    for name, _ in arms[1:]:
+        hd = [l["hausdorff"] / max(p["hausdorff"], 1e-30) for p, l in zip(res["plain"], res[name])]
+        summary[name]["hausdorff_ratio_mean"] = float(np.mean(hd))
+        summary[name]["hausdorff_ratio_max"] = float(np.max(hd))
+        summary[name]["speedup_vs_plain"] = summary["plain"]["ms"] / summary[name]["ms"]
+    best = max(arms[1:], key=lambda a: summary[a[0]]["mfaces_s"])[0]
+    line = {"metric": METRIC, "value": summary[best]["mfaces_s"], "unit": "Mfaces/s",
+            "n_gpus": world, "steps": args.eval_meshes, "warmup": 1,
+            "ms_per_step": summary[best]["ms"] / args.eval_meshes,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"learned proposal: nested shells L{args.eval_level} "
+                                   f"(seeds 2000..{2000 + args.eval_meshes - 1}) to 1%, one "
+                                   "call per mesh",
+                       "train": f"{args.train_meshes} nested shells L{args.train_level} "
+                                f"(seeds 1000..), {info['samples']} labels "
+                                f"({info['positives']} undone), {args.train_steps} Adam steps",
+                       "best_arm": best, "log_s": round(t_log, 1), "train_s": round(t_train, 1),
+                       "loss_first_last": [info["losses"][0], info["losses"][-1]]},
+            "arms": summary}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def host_leg(pamo, torch, V, F, target, steps):
     """pamo_simplify_host from pinned host arrays: copies inside the timing."""
     hV = torch.from_numpy(V).pin_memory().numpy()
@@ -330,7 +460,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
-    ap.add_argument("--workload", default="plain", choices=["plain", "batch"],
+    ap.add_argument("--train-meshes", type=int, default=64)
+    ap.add_argument("--train-level", type=int, default=6)
+    ap.add_argument("--train-steps", type=int, default=3000)
+    ap.add_argument("--eval-meshes", type=int, default=64)
+    ap.add_argument("--eval-level", type=int, default=6)
+    ap.add_argument("--thresholds", default="0.5,0.7,0.9")
+    ap.add_argument("--workload", default="plain", choices=["plain", "batch", "learned"],
                     help="plain: the L8 sphere (default); batch: many meshes per pass")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--ablation", action="store_true",
@@ -358,8 +494,8 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    if args.workload == "batch":
-        run_batch_bench(args, world, rank)
+    if args.workload in ("batch", "learned"):
+        (run_batch_bench if args.workload == "batch" else run_learned_bench)(args, world, rank)
         if world > 1:
             dist.destroy_process_group()
         return

@@ -88,11 +88,12 @@ typedef struct {
                               the count at the last Morton sort (0 = 50;
                               1..100, 100 = sort every round) */
   /* Learned proposal (no counterpart in the paper): a trained pamo_mlp (see
-   * below) that predicts, from 16 features of an eligible edge, that the
-   * intersection check would undo its collapse; such edges are deferred (hold
-   * no key) for the round, unless the previous round committed nothing.
-   * Every committed collapse still passes the exact check.  NULL = off
-   * (default); single-mesh calls only. */
+   * below) that predicts, from 16 features of a selected winner, that the
+   * intersection check would undo its collapse; such winners are deferred
+   * (not collapsed this round; winners are independent, so the others are
+   * unaffected), unless the previous round committed nothing.  Every
+   * committed collapse still passes the exact check.  NULL = off (default);
+   * single-mesh calls only. */
   const struct pamo_mlp* proposal;
   float proposal_threshold; /* defer when the predicted probability exceeds it */
 } pamo_options;
@@ -203,6 +204,9 @@ void pamo_mlp_destroy(pamo_mlp* m);
 /* Set the FP32 master parameters (host, PAMO_MLP_PARAMS floats); refreshes
  * the BF16 copy and resets the Adam state. */
 pamo_status pamo_mlp_set_params(pamo_mlp* m, const float* h_params);
+/* Standardise the inputs before the first layer: x' = (x - mu) / sd per
+ * feature (host, 16 floats each, sd > 0; FP32).  Default mu = 0, sd = 1. */
+pamo_status pamo_mlp_set_input_norm(pamo_mlp* m, const float* h_mu, const float* h_sd);
 /* Read the master parameters and/or the BF16 copy (host, may be NULL). */
 pamo_status pamo_mlp_get_params(const pamo_mlp* m, float* h_params, uint16_t* h_bf16);
 /* Probabilities (device, n floats) for n feature rows (device, n x 16). */

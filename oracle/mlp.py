@@ -40,10 +40,13 @@ def bf16_round(x):
     return r.astype(np.uint32).view(np.float32)
 
 
-def forward(p, X):
-    """Logits z, and the hidden activations, of rows X [n, 16]."""
+def forward(p, X, mu=None, sd=None):
+    """Logits z, and the hidden activations, of rows X [n, 16] (standardised
+    first as (X - mu) / sd when mu and sd are given)."""
     W1, b1, W2, b2, W3, b3 = unpack(p)
     X = np.asarray(X, np.float64)
+    if mu is not None:
+        X = (X - np.asarray(mu, np.float64)) / np.asarray(sd, np.float64)
     z1 = X @ W1 + b1
     h1 = np.maximum(z1, 0.0)
     z2 = h1 @ W2 + b2
@@ -52,8 +55,8 @@ def forward(p, X):
     return z, (X, z1, h1, z2, a2)
 
 
-def prob(p, X):
-    z, _ = forward(p, X)
+def prob(p, X, mu=None, sd=None):
+    z, _ = forward(p, X, mu, sd)
     return 1.0 / (1.0 + np.exp(-z))
 
 

@@ -106,6 +106,14 @@ class MLP:
         _check(lib().pamo_mlp_set_params(self.handle, p.ctypes.data_as(ctypes.c_void_p)),
                "pamo_mlp_set_params")
 
+    def set_input_norm(self, mu, sd):
+        """Standardise inputs as (x - mu) / sd before the first layer."""
+        mu = np.ascontiguousarray(mu, np.float32)
+        sd = np.ascontiguousarray(sd, np.float32)
+        _check(lib().pamo_mlp_set_input_norm(self.handle, mu.ctypes.data_as(ctypes.c_void_p),
+                                             sd.ctypes.data_as(ctypes.c_void_p)),
+               "pamo_mlp_set_input_norm")
+
     def get_params(self):
         """(fp32 master parameters, bf16 copy as uint16 bit patterns)."""
         p = np.zeros(MLP_PARAMS, np.float32)
@@ -179,6 +187,7 @@ def lib():
             "pamo_mlp_create": (ctypes.c_int, [ctypes.POINTER(P)]),
             "pamo_mlp_destroy": (None, [P]),
             "pamo_mlp_set_params": (ctypes.c_int, [P, P]),
+            "pamo_mlp_set_input_norm": (ctypes.c_int, [P, P, P]),
             "pamo_mlp_get_params": (ctypes.c_int, [P, P, P]),
             "pamo_mlp_forward": (ctypes.c_int, [P, P, i64, P, P]),
             "pamo_mlp_grad": (ctypes.c_int, [P, P, P, i64, ctypes.c_float, P, P]),

@@ -120,8 +120,8 @@ void free_ctx_buffers(pamo_ctx* c) {
   release(c->vmesh, st); release(c->vmesh_tmp, st); release(c->voff_d, st); release(c->foff_d, st);
   release(c->mframe, st); release(c->mcost, st); release(c->mactive, st); release(c->mcount, st);
   release(c->mvbase, st); release(c->flags_old, st);
-  release(c->vnear, st); release(c->vnear_tmp, st); release(c->plist, st); release(c->pX, st);
-  release(c->pprob, st);
+  release(c->vgap, st); release(c->vgap_tmp, st); release(c->pX, st);
+  release(c->pprob, st); release(c->pkeep, st);
   if (c->mcount_h) cudaFreeHost(c->mcount_h);
   c->mcount_h = nullptr;
   for (int r = 0; r < 3; r++) release(c->cand[r], st);
@@ -235,9 +235,9 @@ pamo_status alloc_state(pamo_ctx* c, int64_t nV, int64_t nF) {
   A(dbuf, mx + 1); A(flags, c->Emax); A(flags_next, c->Emax); A(dc, 1);
   A(E_prev, c->Emax); A(e_off_prev, nV + 1); A(cbits, c->Emax); A(cbits_prev, c->Emax);
   A(vbar_prev, c->Emax); A(link, c->Emax); A(link_prev, c->Emax); A(ivmap, nV);
-  A(vsurv, nV); A(vdirty, nV); A(dlist, c->Emax); A(vnear, nV); A(vnear_tmp, nV);
+  A(vsurv, nV); A(vdirty, nV); A(dlist, c->Emax); A(vgap, nV); A(vgap_tmp, nV);
   if (c->opt.proposal) {
-    A(plist, c->Emax); A(pX, 16 * c->Emax); A(pprob, c->Emax);
+    A(pX, 16 * c->Emax); A(pprob, c->Emax); A(pkeep, c->Emax);
   }
   A(scan_sums, scan_sums_count(std::max<int64_t>(c->Emax, mx + 1)));
   // candidate pairs of the split check: a changed face has at most 3
@@ -257,14 +257,14 @@ pamo_status alloc_state(pamo_ctx* c, int64_t nV, int64_t nF) {
   }
 #undef A
   if (s == PAMO_OK) {  // read by the proposal's features before the first check / commit
-    cudaError_t e = cudaMemsetAsync(c->vnear, 0, (size_t)nV, st);
+    cudaError_t e = cudaMemsetAsync(c->vgap, 0x7f, sizeof(uint32_t) * (size_t)nV, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->vsurv, 0, (size_t)nV, st);
     if (e != cudaSuccess) s = cuda_fail(e, "cudaMemsetAsync");
   }
   c->bvh.n_mesh = M;
   c->bvh.vmesh = c->vmesh;
   c->bvh.mframe = c->mframe;
-  c->bvh.vnear = c->vnear;
+  c->bvh.vgap = c->vgap;
   if (s == PAMO_OK) s = bvh_alloc(c->bvh, (int)nF, st);
   if (s == PAMO_OK) {
     cudaError_t e = cudaMallocHost((void**)&c->hc, sizeof(RoundCounters));
@@ -540,7 +540,6 @@ pamo_status phase_cost(pamo_ctx* c) {
   const double nV = (double)c->nV, nF = (double)c->nF, nE = 1.5 * nF;
   kc_begin(c, PAMO_KC_COST);
   PAMO_TRY(edge_costs(c));
-  if (c->opt.proposal) PAMO_TRY(propose(c));  // learned deferral of predicted rejects
   // E, positions, quadrics, CSR and faces read once; keys and placements written
   kc_end(c, PAMO_KC_COST, nE * (8 + 8 + 16) + nV * (16 + 80 + 4) + nF * (16 + 12));
   return PAMO_OK;
@@ -552,6 +551,7 @@ pamo_status phase_select(pamo_ctx* c) {
   PAMO_TRY(select_winners(c));
   // exact-target mode (a full run only: the per-round entry points have no N_t)
   if (c->opt.exact_target && c->in_run) PAMO_TRY(trim_winners(c));
+  if (c->opt.proposal) PAMO_TRY(propose(c));  // learned deferral of predicted rejects
   // edges+keys read twice, vkey written and read, CSR+faces read, flags scanned
   kc_end(c, PAMO_KC_SELECT, nE * (2 * 16 + 1 + 1 + 4 + 1 + 4) + nV * (8 + 8 + 4) + nF * (16 + 12));
   return PAMO_OK;

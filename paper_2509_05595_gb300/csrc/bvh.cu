@@ -382,6 +382,13 @@ __device__ __forceinline__ bool overlap(const float3& alo, const float3& ahi, fl
   return !(alo.x > bhx || blx > ahi.x || alo.y > bhy || bly > ahi.y || alo.z > bhz || blz > ahi.z);
 }
 
+__device__ __forceinline__ float3 sub3f(const float4& a, const float4& b) {
+  return make_float3(a.x - b.x, a.y - b.y, a.z - b.z);
+}
+__device__ __forceinline__ float3 cross3f(const float3& a, const float3& b) {
+  return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
 // one 64-byte node: which children overlap the query box, and their links
 struct NodeHits {
   bool l, r;
@@ -585,7 +592,7 @@ __global__ void __launch_bounds__(kBlock) k_pairs(
     CandBufs cb, const int* __restrict__ ncand, const float4* __restrict__ pos,
     const int4* __restrict__ F, const uint8_t* __restrict__ info,
     const int32_t* __restrict__ ftag, uint8_t* __restrict__ undo, RoundCounters* __restrict__ dc,
-    uint8_t* __restrict__ vnear) {
+    uint32_t* __restrict__ vgap) {
   const int n2 = min((int64_t)ncand[2], cb.cap[2]);
   const int n1 = min((int64_t)ncand[1], cb.cap[1]);
   const int n0 = min((int64_t)ncand[0], cb.cap[0]);
@@ -598,9 +605,27 @@ __global__ void __launch_bounds__(kBlock) k_pairs(
     const int2 p = i < n2 ? cb.c[2][i] : (i < n2 + n1 ? cb.c[1][i - n2] : cb.c[0][i - n2 - n1]);
     const int f = p.x, g = p.y;
     const int4 tv = F[f], cv = F[g];
-    if (vnear && i >= n2 + n1) {  // boxes of faces with no common vertex overlap
-      vnear[tv.x] = 1; vnear[tv.y] = 1; vnear[tv.z] = 1;
-      vnear[cv.x] = 1; vnear[cv.y] = 1; vnear[cv.z] = 1;
+    if (vgap && i >= n2 + n1) {
+      // boxes of faces with no common vertex overlap: each face's corners get
+      // the distance of the other face's centroid to its plane (a clearance
+      // estimate for the learned proposal; positive floats order as integers)
+      const float4 a0 = pos[tv.x], a1 = pos[tv.y], a2 = pos[tv.z];
+      const float4 b0 = pos[cv.x], b1 = pos[cv.y], b2 = pos[cv.z];
+      const float3 na = cross3f(sub3f(a1, a0), sub3f(a2, a0));
+      const float3 nb = cross3f(sub3f(b1, b0), sub3f(b2, b0));
+      const float3 ca = make_float3((a0.x + a1.x + a2.x) / 3.f, (a0.y + a1.y + a2.y) / 3.f,
+                                    (a0.z + a1.z + a2.z) / 3.f);
+      const float3 cb = make_float3((b0.x + b1.x + b2.x) / 3.f, (b0.y + b1.y + b2.y) / 3.f,
+                                    (b0.z + b1.z + b2.z) / 3.f);
+      const float la = sqrtf(na.x * na.x + na.y * na.y + na.z * na.z);
+      const float lb = sqrtf(nb.x * nb.x + nb.y * nb.y + nb.z * nb.z);
+      const float da = la > 0.f ? fabsf(na.x * (cb.x - a0.x) + na.y * (cb.y - a0.y) +
+                                        na.z * (cb.z - a0.z)) / la : 0.f;
+      const float db = lb > 0.f ? fabsf(nb.x * (ca.x - b0.x) + nb.y * (ca.y - b0.y) +
+                                        nb.z * (ca.z - b0.z)) / lb : 0.f;
+      const unsigned ua = __float_as_uint(da), ub = __float_as_uint(db);
+      atomicMin(&vgap[tv.x], ua); atomicMin(&vgap[tv.y], ua); atomicMin(&vgap[tv.z], ua);
+      atomicMin(&vgap[cv.x], ub); atomicMin(&vgap[cv.y], ub); atomicMin(&vgap[cv.z], ub);
     }
     const int ti[3] = {tv.x, tv.y, tv.z};
     const int ci[3] = {cv.x, cv.y, cv.z};
@@ -833,7 +858,7 @@ pamo_status bvh_check_split(Bvh& b, const float4* pos, const int4* F, const uint
                                         many ? b.vmesh : nullptr,
                                         many ? (const int32_t*)b.mroot.p : nullptr); note_launch();
   k_pairs<<<g_pairs, kBlock, 0, st>>>(cb, ncand, pos, F, (const uint8_t*)b.face_aux.p, ftag, undo,
-                                   dc, b.vnear); note_launch();
+                                   dc, b.vgap); note_launch();
   PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;
 }

@@ -121,7 +121,7 @@ struct Bvh {
   Buf hkeys, hkeys2, mroot;
   const int32_t* vmesh = nullptr;
   const float* mframe = nullptr;
-  uint8_t* vnear = nullptr;  // marks vertices of non-adjacent overlapping pairs (may be null)
+  uint32_t* vgap = nullptr;  // per-vertex clearance of non-adjacent overlapping pairs (may be null)
   // leaf order carried over rounds: valid when order_ok; re-sorted by Morton
   // code when the face count has halved since the last sort
   bool order_ok = false;
@@ -179,12 +179,14 @@ struct pamo_ctx {
   int32_t* ivmap = nullptr;            // [nV0] new vertex id -> previous id
   uint8_t* vsurv = nullptr;            // [nV0] survivor of a committed collapse
   uint8_t* vdirty = nullptr;           // [nV0] survivor or neighbour of one
-  uint8_t* vnear = nullptr;            // [nV0] near a non-adjacent face in the last check
-  uint8_t* vnear_tmp = nullptr;        // [nV0] compaction scratch
+  uint32_t* vgap = nullptr;            // [nV0] float bits: smallest distance to a
+                                       // non-adjacent face with an overlapping box
+                                       // in the last check (+inf: none)
+  uint32_t* vgap_tmp = nullptr;        // [nV0] compaction scratch
   // learned proposal (when options.proposal is set)
-  int32_t* plist = nullptr;            // [Emax] eligible edges
-  float* pX = nullptr;                 // [Emax][16] their features
+  float* pX = nullptr;                 // [Emax][16] winner features
   float* pprob = nullptr;              // [Emax] predicted probability of an undo
+  uint8_t* pkeep = nullptr;            // [Emax] winner not deferred
   int64_t deferred_total = 0;
   int32_t* dlist = nullptr;            // [Emax] edges whose cost is recomputed
   bool have_prev = false;

@@ -489,8 +489,8 @@ __global__ void k_compact_vertices(const float4* __restrict__ pos_s, const doubl
                                    int32_t* __restrict__ vmap, int32_t* __restrict__ ivmap,
                                    const int32_t* __restrict__ vmesh,
                                    int32_t* __restrict__ vmesh_out,
-                                   const uint8_t* __restrict__ vnear,
-                                   uint8_t* __restrict__ vnear_out) {
+                                   const uint32_t* __restrict__ vgap,
+                                   uint32_t* __restrict__ vgap_out) {
   const int nV = *n_dev;
   GRID_STRIDE(v, nV) {
     if (vdead[v]) {
@@ -502,7 +502,7 @@ __global__ void k_compact_vertices(const float4* __restrict__ pos_s, const doubl
     ivmap[n] = (int32_t)v;
     pos[n] = pos_s[v];
     if (vmesh) vmesh_out[n] = vmesh[v];
-    vnear_out[n] = vnear[v];
+    vgap_out[n] = vgap[v];
     const double2* src = reinterpret_cast<const double2*>(K_s + 10 * v);
     double2* dst = reinterpret_cast<double2*>(K + 10 * n);
 #pragma unroll
@@ -817,7 +817,7 @@ pamo_status commit_compact(pamo_ctx* c) {
   const bool batch = c->n_mesh > 1;
   k_compact_vertices<<<G, kBlock, 0, st>>>(c->pos_s, c->K_s, c->vdead, c->dbuf, &dc->goV, c->pos,
                                            c->K, c->vmap, c->ivmap, batch ? c->vmesh : nullptr,
-                                           c->vmesh_tmp, c->vnear, c->vnear_tmp); note_launch();
+                                           c->vmesh_tmp, c->vgap, c->vgap_tmp); note_launch();
   // faces, corners remapped
   PAMO_TRY(scan_dev_u8(c->fdead, &dc->goF, c->dbuf, c->scan_sums, G, st));
   k_compact_faces<<<G, kBlock, 0, st>>>(c->F_s, c->fdead, c->dbuf, &dc->goF, c->vmap, c->F); note_launch();
@@ -830,7 +830,7 @@ pamo_status commit_compact(pamo_ctx* c) {
     k_remap_flags<<<G, kBlock, 0, st>>>(c->flags, dc, c->vmap, c->flags_old); note_launch();
     PAMO_TRY(copy_dev(c->vmesh, c->vmesh_tmp, &dc->goVn, 0, sizeof(int32_t), G, st));
   }
-  PAMO_TRY(copy_dev(c->vnear, c->vnear_tmp, &dc->goVn, 0, 1, G, st));
+  PAMO_TRY(copy_dev(c->vgap, c->vgap_tmp, &dc->goVn, 0, sizeof(uint32_t), G, st));
   // dirty vertices of the next round (survivors and their neighbours)
   k_clear2<<<G, kBlock, 0, st>>>(c->vsurv, c->vdirty, &dc->goVn); note_launch();
   k_mark_survivors<<<G, kBlock, 0, st>>>(c->wlist, c->E, c->standing, &dc->goW, c->vmap, c->vsurv); note_launch();

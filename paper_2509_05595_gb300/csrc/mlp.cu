@@ -9,6 +9,10 @@
 //   W3 [64] at 5248, b3 at 5312; 5313 in all.  W[i][j] maps input i to
 //   output j.
 //
+// Inputs are standardised first, x' = (x - mu) * inv_sd (fp32, per feature;
+// identity by default), so that the BF16 first layer never has to absorb the
+// features' offsets and scales.
+//
 // Forward: one thread per sample, weights staged in shared memory as fp32
 // (converted from bf16 once per block).  Backward: one block per chunk of 64
 // samples keeps the activations of the chunk in shared memory and reduces
@@ -41,9 +45,17 @@ __device__ __forceinline__ float softplusf_(float x) {
   return x > 0.f ? x + log1pf(__expf(-x)) : log1pf(__expf(x));
 }
 
-__device__ __forceinline__ void load_weights(const __nv_bfloat16* __restrict__ pb, float* w) {
+// weights as fp32, then the 2 x 16 standardisation (mu, inv_sd) after them
+__device__ __forceinline__ void load_weights(const __nv_bfloat16* __restrict__ pb,
+                                             const float* __restrict__ norm, float* w) {
   for (int i = threadIdx.x; i < kParams; i += blockDim.x) w[i] = __bfloat162float(pb[i]);
+  for (int i = threadIdx.x; i < 2 * kIn; i += blockDim.x) w[kParams + i] = norm[i];
   __syncthreads();
+}
+
+__device__ __forceinline__ void standardise(const float* __restrict__ w, float* x) {
+#pragma unroll
+  for (int i = 0; i < kIn; i++) x[i] = (x[i] - w[kParams + i]) * w[kParams + kIn + i];
 }
 
 // logit of one sample; h1 (post-ReLU) and a2 (post-ReLU) optionally stored
@@ -87,12 +99,14 @@ __device__ __forceinline__ float forward_one(const float* __restrict__ w, const 
 }
 
 __global__ void __launch_bounds__(kBlock) k_mlp_forward(const __nv_bfloat16* __restrict__ pb,
+                                                        const float* __restrict__ norm,
                                                         const float* __restrict__ X,
                                                         const int* n_dev, int64_t n_host,
                                                         float* __restrict__ prob) {
-  __shared__ float w[kParams];
+  __shared__ float w[kParams + 2 * kIn];
   const int64_t n = n_dev ? (int64_t)*n_dev : n_host;
-  load_weights(pb, w);
+  if ((int64_t)blockIdx.x * blockDim.x >= n) return;  // no sample: skip the weight load
+  load_weights(pb, norm, w);
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
        s += (int64_t)gridDim.x * blockDim.x) {
     float x[kIn];
@@ -102,6 +116,7 @@ __global__ void __launch_bounds__(kBlock) k_mlp_forward(const __nv_bfloat16* __r
       const float4 v = xv[q];
       x[4 * q] = v.x; x[4 * q + 1] = v.y; x[4 * q + 2] = v.z; x[4 * q + 3] = v.w;
     }
+    standardise(w, x);
     prob[s] = sigmoidf_(forward_one<false>(w, x, nullptr, nullptr));
   }
 }
@@ -109,12 +124,13 @@ __global__ void __launch_bounds__(kBlock) k_mlp_forward(const __nv_bfloat16* __r
 // Weighted BCE over n samples: loss_s = -(pw y log p + (1 - y) log(1 - p)),
 // averaged; per-block partial gradients (and loss) into part[block][kParams+1].
 __global__ void __launch_bounds__(kChunk) k_mlp_grad(const __nv_bfloat16* __restrict__ pb,
+                                                     const float* __restrict__ norm,
                                                      const float* __restrict__ X,
                                                      const float* __restrict__ y, int64_t n,
                                                      float pos_weight, float* __restrict__ part) {
   extern __shared__ float sm[];
-  float* w = sm;                       // kParams
-  float* g = w + kParams;              // kParams + 1 (the loss last)
+  float* w = sm;                       // kParams + 2 kIn (weights, standardisation)
+  float* g = w + kParams + 2 * kIn;    // kParams + 1 (the loss last)
   float* Xs = g + kParams + 1;         // kChunk x kIn
   float* H1 = Xs + kChunk * kIn;       // kChunk x kH
   float* A2 = H1 + kChunk * kH;        // kChunk x kH
@@ -122,7 +138,7 @@ __global__ void __launch_bounds__(kChunk) k_mlp_grad(const __nv_bfloat16* __rest
   float* D1 = D2 + kChunk * kH;        // kChunk x kH
   float* d3 = D1 + kChunk * kH;        // kChunk
   float* ls = d3 + kChunk;             // kChunk: per-sample loss
-  load_weights(pb, w);
+  load_weights(pb, norm, w);
   for (int i = threadIdx.x; i <= kParams; i += blockDim.x) g[i] = 0.f;
   const float inv_n = 1.0f / (float)n;
   const int t = threadIdx.x;
@@ -133,8 +149,11 @@ __global__ void __launch_bounds__(kChunk) k_mlp_grad(const __nv_bfloat16* __rest
     // error, so they add nothing)
     float x[kIn];
 #pragma unroll
+    for (int i = 0; i < kIn; i++) x[i] = ok ? X[kIn * s + i] : 0.f;
+    standardise(w, x);
+#pragma unroll
     for (int i = 0; i < kIn; i++) {
-      x[i] = ok ? X[kIn * s + i] : 0.f;
+      if (!ok) x[i] = 0.f;
       Xs[t * kIn + i] = x[i];
     }
     const float z = forward_one<true>(w, x, H1 + t * kH, A2 + t * kH);
@@ -222,7 +241,8 @@ __global__ void k_to_bf16(const float* __restrict__ p, __nv_bfloat16* __restrict
 }
 
 size_t grad_smem_bytes() {
-  return sizeof(float) * ((size_t)2 * kParams + 1 + kChunk * kIn + 4 * kChunk * kH + 2 * kChunk);
+  return sizeof(float) *
+         ((size_t)2 * kParams + 2 * kIn + 1 + kChunk * kIn + 4 * kChunk * kH + 2 * kChunk);
 }
 
 }  // namespace
@@ -232,6 +252,7 @@ size_t grad_smem_bytes() {
 using namespace pamo;
 
 struct pamo_mlp {
+  float* norm = nullptr;           // [2][16] input standardisation (mu, 1/sd)
   float* p = nullptr;              // fp32 master weights
   __nv_bfloat16* pb = nullptr;     // bf16 working copy
   float* m = nullptr;              // Adam moments
@@ -246,7 +267,7 @@ namespace pamo {
 pamo_status mlp_forward_dev(const pamo_mlp* m, const float* X, const int* n_dev, float* prob,
                             int64_t n_host, cudaStream_t st) {
   static const int g = occ_grid(k_mlp_forward);
-  k_mlp_forward<<<g, kBlock, 0, st>>>(m->pb, X, n_dev, n_host, prob); note_launch();
+  k_mlp_forward<<<g, kBlock, 0, st>>>(m->pb, m->norm, X, n_dev, n_host, prob); note_launch();
   PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;
 }
@@ -262,6 +283,15 @@ pamo_status pamo_mlp_create(pamo_mlp** out) {
   }
   pamo_mlp* m = new pamo_mlp();
   cudaError_t e = cudaMalloc(&m->p, sizeof(float) * kParams);
+  if (e == cudaSuccess) e = cudaMalloc(&m->norm, sizeof(float) * 2 * kIn);
+  if (e == cudaSuccess) {
+    float id[2 * kIn];
+    for (int i = 0; i < kIn; i++) {
+      id[i] = 0.f;
+      id[kIn + i] = 1.f;
+    }
+    e = cudaMemcpy(m->norm, id, sizeof(id), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = cudaMalloc(&m->pb, sizeof(__nv_bfloat16) * kParams);
   if (e == cudaSuccess) e = cudaMalloc(&m->m, sizeof(float) * kParams);
   if (e == cudaSuccess) e = cudaMalloc(&m->v, sizeof(float) * kParams);
@@ -282,6 +312,7 @@ pamo_status pamo_mlp_create(pamo_mlp** out) {
 
 void pamo_mlp_destroy(pamo_mlp* m) {
   if (!m) return;
+  cudaFree(m->norm);
   cudaFree(m->p);
   cudaFree(m->pb);
   cudaFree(m->m);
@@ -303,6 +334,24 @@ pamo_status pamo_mlp_set_params(pamo_mlp* m, const float* h_params) {
   PAMO_CUDA(cudaMemset(m->v, 0, sizeof(float) * kParams));
   PAMO_CUDA(cudaDeviceSynchronize());
   m->step = 0;
+  return PAMO_OK;
+}
+
+pamo_status pamo_mlp_set_input_norm(pamo_mlp* m, const float* h_mu, const float* h_sd) {
+  if (!m || !h_mu || !h_sd) {
+    set_error("model, mu and sd required");
+    return PAMO_EINVAL;
+  }
+  float v[2 * kIn];
+  for (int i = 0; i < kIn; i++) {
+    if (!(h_sd[i] > 0.f)) {
+      set_error("standard deviations must be > 0");
+      return PAMO_EINVAL;
+    }
+    v[i] = h_mu[i];
+    v[kIn + i] = 1.0f / h_sd[i];
+  }
+  PAMO_CUDA(cudaMemcpy(m->norm, v, sizeof(v), cudaMemcpyHostToDevice));
   return PAMO_OK;
 }
 
@@ -342,7 +391,8 @@ pamo_status pamo_mlp_grad(pamo_mlp* m, const float* d_X, const float* d_y, int64
                                    (int)smem));
     attr = true;
   }
-  k_mlp_grad<<<kGradBlocks, kChunk, smem, st>>>(m->pb, d_X, d_y, n, pos_weight, m->part); note_launch();
+  k_mlp_grad<<<kGradBlocks, kChunk, smem, st>>>(m->pb, m->norm, d_X, d_y, n, pos_weight,
+                                                 m->part); note_launch();
   k_mlp_grad_reduce<<<(kParams + 1 + 255) / 256, 256, 0, st>>>(m->part, kGradBlocks, m->grad); note_launch();
   PAMO_CUDA(cudaGetLastError());
   if (h_loss) {

@@ -1,8 +1,10 @@
 // The learned proposal (no counterpart in the paper): per-edge features, and
-// the deferral of edges the network predicts the intersection check would
+// the deferral of winners the network predicts the intersection check would
 // reject (Sections 5.2-5.3 undo them; deferring skips the collapse, the
 // check and the undo for this round, and the edge competes again next
-// round).  Every collapse that is committed still passes the exact check.
+// round, invalid for the next round like an undone edge).  Winners are
+// independent, so deferring some leaves the others as they are.  Every
+// collapse that is committed still passes the exact check.
 //
 // Features of an edge e = (a, b) of the current mesh, with its placement v,
 // length l and cost (all float32; "produced" triangles are the faces around
@@ -10,11 +12,16 @@
 //   0 log10 of the cost (Eq. 1)          8 mean cos(old normal, new normal)
 //   1 log2 of s l (normalised length)    9 min C_ijk of the produced triangles
 //   2 |v - midpoint| / l                10 mean (1 - C_ijk)
-//   3 valence of a / 6                  11 produced triangles / 10
+//   3 valence of a / 6                  11 log2 of (largest distance of v to
+//                                          the planes of the old faces) /
+//                                          clearance (see 14), in [-10, 10]
 //   4 valence of b / 6                  12 log2 of the one-ring area / l^2
 //   5 (valence a + valence b - 4) / 6   13 new / old one-ring area
-//   6 cos of the dihedral across ab     14 a or b was near a non-adjacent face
-//   7 min cos(old normal, new normal)      in the last check (box overlap)
+//   6 cos of the dihedral across ab     14 log2 of the clearance / l: the
+//   7 min cos(old normal, new normal)      smallest plane distance to a
+//                                          non-adjacent face with an overlapping
+//                                          box in the last check (clamped to
+//                                          [-10, 10]; 10 when there is none)
 //                                       15 a or b survived a collapse last round
 #include "common.cuh"
 
@@ -43,7 +50,7 @@ __device__ __forceinline__ float tri_q(float3 u, float3 w, float3 n) {
 __device__ void edge_features(int e, const int2* __restrict__ E, const float4* __restrict__ pos,
                               const int4* __restrict__ F, const int32_t* __restrict__ off,
                               const int32_t* __restrict__ idx, const uint32_t* __restrict__ cbits,
-                              const float4* __restrict__ vbar, const uint8_t* __restrict__ vnear,
+                              const float4* __restrict__ vbar, const uint32_t* __restrict__ vgap,
                               const uint8_t* __restrict__ vsurv, float s, float* f) {
   const int2 ab = E[e];
   const int a = ab.x, b = ab.y;
@@ -53,6 +60,7 @@ __device__ void edge_features(int e, const int2* __restrict__ E, const float4* _
   const int va = off[a + 1] - off[a], vb = off[b + 1] - off[b];
   const float3 mid = make_float3(0.5f * (pa.x + pb.x), 0.5f * (pa.y + pb.y), 0.5f * (pa.z + pb.z));
   float mincos = 1.f, sumcos = 0.f, minq = 1.f, sumskin = 0.f, aold = 0.f, anew = 0.f;
+  float dmax = 0.f;  // how far v leaves the old surface
   int ntri = 0, nab = 0;
   float3 nab_n[2] = {make_float3(0.f, 0.f, 0.f), make_float3(0.f, 0.f, 0.f)};
   for (int pass = 0; pass < 2; pass++) {
@@ -64,7 +72,9 @@ __device__ void edge_features(int e, const int2* __restrict__ E, const float4* _
       if (pass == 1 && (t.x == a || t.y == a || t.z == a)) continue;  // counted from a
       const float3 q0 = f3(pos[t.x]), q1 = f3(pos[t.y]), q2 = f3(pos[t.z]);
       const float3 n_old = cross3(sub3(q1, q0), sub3(q2, q0));
-      aold += 0.5f * norm3(n_old);
+      const float lo_ = norm3(n_old);
+      aold += 0.5f * lo_;
+      if (lo_ > 0.f) dmax = fmaxf(dmax, fabsf(dot3f(n_old, sub3(v, q0))) / lo_);
       if (on_ab) {
         if (nab < 2) nab_n[nab] = n_old;
         nab++;
@@ -103,10 +113,11 @@ __device__ void edge_features(int e, const int2* __restrict__ E, const float4* _
   f[8] = sumcos / nt;
   f[9] = minq;
   f[10] = sumskin / nt;
-  f[11] = ntri / 10.f;
+  const float gap = __uint_as_float(min(vgap[a], vgap[b]));
+  f[11] = fminf(fmaxf(log2f(fmaxf(dmax, 1e-30f) / fmaxf(gap, 1e-30f)), -10.f), 10.f);
   f[12] = log2f(fmaxf(aold / (l * l), 1e-12f));
   f[13] = aold > 0.f ? anew / aold : 0.f;
-  f[14] = (vnear[a] | vnear[b]) ? 1.f : 0.f;
+  f[14] = fminf(fmaxf(log2f(fmaxf(gap, 1e-30f) / l), -10.f), 10.f);
   f[15] = (vsurv[a] | vsurv[b]) ? 1.f : 0.f;
 }
 
@@ -115,53 +126,35 @@ __global__ void k_features(const int32_t* __restrict__ list, const int* __restri
                            const int2* __restrict__ E, const float4* __restrict__ pos,
                            const int4* __restrict__ F, const int32_t* __restrict__ off,
                            const int32_t* __restrict__ idx, const uint32_t* __restrict__ cbits,
-                           const float4* __restrict__ vbar, const uint8_t* __restrict__ vnear,
+                           const float4* __restrict__ vbar, const uint32_t* __restrict__ vgap,
                            const uint8_t* __restrict__ vsurv, float s, float* __restrict__ X) {
   const int n = *n_dev;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int e = list ? list[i] : (int)i;
     float f[kF];
-    edge_features(e, E, pos, F, off, idx, cbits, vbar, vnear, vsurv, s, f);
+    edge_features(e, E, pos, F, off, idx, cbits, vbar, vgap, vsurv, s, f);
     float4* o = reinterpret_cast<float4*>(X + (int64_t)kF * i);
 #pragma unroll
     for (int q = 0; q < kF / 4; q++) o[q] = make_float4(f[4 * q], f[4 * q + 1], f[4 * q + 2], f[4 * q + 3]);
   }
 }
 
-// the eligible edges, listed for the proposal (in no particular order)
-__global__ void k_list_eligible(const unsigned long long* __restrict__ key,
-                                const RoundCounters* __restrict__ dc, int32_t* __restrict__ list,
-                                int* __restrict__ count) {
-  const int nE = dc->nE;
-  const int lane = threadIdx.x & 31;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nE;
-       base += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e = base + threadIdx.x;
-    const bool el = e < nE && key[e] != ~0ull;
-    const unsigned m = __ballot_sync(0xffffffffu, el);
-    int b0 = 0;
-    if (m && lane == __ffs(m) - 1) b0 = atomicAdd(count, __popc(m));
-    b0 = __shfl_sync(0xffffffffu, b0, __ffs(m ? m : 1u) - 1);
-    if (el) list[b0 + __popc(m & ((1u << lane) - 1u))] = (int32_t)e;
-  }
-}
-
-// deferral: predicted rejects hold no key this round (not after a round that
-// committed nothing, so that every edge keeps a chance and the stall rule of
-// Section 5.3 still ends a run)
-__global__ void k_defer(const int32_t* __restrict__ list, const int* __restrict__ count,
-                        const float* __restrict__ prob, float threshold,
-                        unsigned long long* __restrict__ key, RoundCounters* __restrict__ dc) {
-  if (dc->last_committed == 0) return;
-  const int n = *count;
+// deferral marks: a winner is kept unless the network predicts an undo (not
+// after a round that committed nothing, so that every winner keeps a chance
+// and the stall rule of Section 5.3 still ends a run).  A deferred winner is
+// not collapsed and counts as undone, so it is an invalid edge for the next
+// round like the undone ones (Section 5.3).
+__global__ void k_defer_mark(RoundCounters* __restrict__ dc, const float* __restrict__ prob,
+                             float threshold, uint8_t* __restrict__ keep) {
+  const int n = dc->nW;
+  const bool on = dc->last_committed != 0;
   int d = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    if (prob[i] > threshold) {
-      key[list[i]] = ~0ull;
-      d++;
-    }
+    const bool defer = on && prob[i] > threshold;
+    keep[i] = defer ? 0 : 1;
+    d += defer;
   }
   d = __reduce_add_sync(0xffffffffu, d);
   if ((threadIdx.x & 31) == 0 && d) atomicAdd(&dc->deferred, d);
@@ -173,22 +166,20 @@ pamo_status edge_features_list(pamo_ctx* c, const int32_t* list, const int* n_de
                                cudaStream_t st) {
   static const int g = occ_grid(k_features);
   k_features<<<g, kBlock, 0, st>>>(list, n_dev, c->E, c->pos, c->F, c->vf_off, c->vf_idx, c->cbits,
-                                   c->vbar, c->vnear, c->vsurv, (float)c->scale, X); note_launch();
+                                   c->vbar, c->vgap, c->vsurv, (float)c->scale, X); note_launch();
   PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;
 }
 
-// features + network + deferral over the eligible edges (device sizes)
+// features + network + deferral over this round's winners (device sizes)
 pamo_status propose(pamo_ctx* c) {
   cudaStream_t st = c->st;
   RoundCounters* dc = c->dc;
   const pamo_mlp* m = (const pamo_mlp*)c->opt.proposal;
-  PAMO_CUDA(cudaMemsetAsync(&dc->n_listed, 0, sizeof(int), st));
-  k_list_eligible<<<c->grid, kBlock, 0, st>>>(c->key, dc, c->plist, &dc->n_listed); note_launch();
-  PAMO_TRY(edge_features_list(c, c->plist, &dc->n_listed, c->pX, st));
-  PAMO_TRY(mlp_forward_dev(m, c->pX, &dc->n_listed, c->pprob, c->Emax, st));
-  k_defer<<<c->grid, kBlock, 0, st>>>(c->plist, &dc->n_listed, c->pprob, c->opt.proposal_threshold,
-                                      c->key, dc); note_launch();
+  const int G = c->grid;
+  PAMO_TRY(edge_features_list(c, c->wlist, &dc->nW, c->pX, st));
+  PAMO_TRY(mlp_forward_dev(m, c->pX, &dc->nW, c->pprob, c->Emax, st));
+  k_defer_mark<<<G, kBlock, 0, st>>>(dc, c->pprob, c->opt.proposal_threshold, c->pkeep); note_launch();
   PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;
 }

@@ -87,9 +87,14 @@ __global__ void k_collapse(const int32_t* __restrict__ wlist, const RoundCounter
                            uint8_t* __restrict__ fdead, uint8_t* __restrict__ vdead,
                            int32_t* __restrict__ ftag, uint8_t* __restrict__ standing,
                            uint8_t* __restrict__ undo, int32_t* __restrict__ qlist,
-                           int* __restrict__ qcount) {
+                           int* __restrict__ qcount, const uint8_t* __restrict__ keep) {
   const int nW = dc->nW;
   GRID_STRIDE(w, nW) {
+  if (keep && !keep[w]) {  // deferred by the learned proposal: treated as undone
+    standing[w] = 0;
+    undo[w] = 0;
+    continue;
+  }
   const int e = wlist[w];
   const int a = E[e].x, b = E[e].y;
   pos_s[a] = vbar[e];
@@ -136,11 +141,11 @@ __global__ void k_stage_ms(const RoundCounters* __restrict__ dc, const float4* _
                            float4* __restrict__ pos_s, double* __restrict__ K_s,
                            int4* __restrict__ F_s, uint8_t* __restrict__ vdead,
                            uint8_t* __restrict__ fdead, int32_t* __restrict__ ftag,
-                           uint8_t* __restrict__ vnear) {
+                           uint32_t* __restrict__ vgap) {
   const int nV = dc->nV, nF = dc->nF;
   GRID_STRIDE(v, nV) {
     pos_s[v] = pos[v];
-    vnear[v] = 0;  // refilled by this round's check
+    vgap[v] = 0x7f800000u;  // +inf; refilled by this round's check
     const double2* src = reinterpret_cast<const double2*>(K + 10 * v);
     double2* dst = reinterpret_cast<double2*>(K_s + 10 * v);
 #pragma unroll
@@ -333,11 +338,12 @@ pamo_status collapse_winners(pamo_ctx* c) {
   const int G = c->grid;
   // M_s starts as a copy of M_1: nothing dead, no face tagged
   k_stage_ms<<<G, kBlock, 0, st>>>(dc, c->pos, c->K, c->F, c->pos_s, c->K_s, c->F_s, c->vdead,
-                                   c->fdead, c->ftag, c->vnear); note_launch();
+                                   c->fdead, c->ftag, c->vgap); note_launch();
   static const int g_collapse = occ_grid(k_collapse);
   k_collapse<<<g_collapse, kBlock, 0, st>>>(c->wlist, dc, c->E, c->vbar, c->K, c->vf_off, c->vf_idx, c->F,
                                    c->pos_s, c->K_s, c->F_s, c->fdead, c->vdead, c->ftag,
-                                   c->standing, c->undo, c->qlist, &dc->n_query); note_launch();
+                                   c->standing, c->undo, c->qlist, &dc->n_query,
+                                   c->opt.proposal ? c->pkeep : nullptr); note_launch();
   PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;
 }

@@ -67,16 +67,6 @@ def log_winners(V, F, target, options: Options | None = None, max_rounds=400):
     return torch.cat(Xs), torch.cat(ys)
 
 
-def fold_normalisation(p, mu, sd):
-    """Parameters that take raw features, from ones trained on (x - mu) / sd."""
-    p = np.array(p, np.float64)
-    W1 = p[O_W1:O_B1].reshape(MLP_IN, H)
-    W1n = W1 / sd[:, None]
-    p[O_B1:O_W2] = p[O_B1:O_W2] - mu @ W1n
-    p[O_W1:O_B1] = W1n.ravel()
-    return p.astype(np.float32)
-
-
 def train(X, y, steps=2000, batch=8192, lr=2e-3, seed=0, pos_weight=None, log_every=0):
     """Train a network on (X, y) with weighted binary cross-entropy and Adam,
     all in the library's kernels; returns (MLP taking raw features, losses)."""
@@ -85,13 +75,13 @@ def train(X, y, steps=2000, batch=8192, lr=2e-3, seed=0, pos_weight=None, log_ev
     mu = Xh.mean(0)
     sd = Xh.std(0)
     sd[sd < 1e-6] = 1.0
-    Xn = ((X - torch.as_tensor(mu, dtype=torch.float32, device=X.device)) /
-          torch.as_tensor(sd, dtype=torch.float32, device=X.device)).contiguous()
+    X = X.contiguous()
     y = y.to(torch.float32).contiguous()
     npos = float(y.sum().item())
     nneg = float(len(y) - npos)
     pw = pos_weight if pos_weight is not None else max(1.0, nneg / max(npos, 1.0))
     m = MLP(he_init(seed))
+    m.set_input_norm(mu, sd)  # standardised in the kernels (FP32)
     rng = np.random.default_rng(seed + 1)
     n = len(y)
     losses = []
@@ -103,10 +93,8 @@ def train(X, y, steps=2000, batch=8192, lr=2e-3, seed=0, pos_weight=None, log_ev
             pos = 0
         idx = perm[pos:pos + batch]
         pos += batch
-        loss = m.grad(Xn.index_select(0, idx), y.index_select(0, idx), pw)
+        loss = m.grad(X.index_select(0, idx), y.index_select(0, idx), pw)
         m.adam_step(lr)
         if log_every and step % log_every == 0:
             losses.append(loss)
-    p, _ = m.get_params()
-    m.set_params(fold_normalisation(p, mu, sd))
     return m, dict(losses=losses, pos_weight=pw, positives=int(npos), samples=n)
