@@ -40,6 +40,12 @@ CLASS_NAMES = ("adjacency", "cost", "select", "collapse", "bvh", "query", "commi
 # chain probe measured 1.25 TFLOP/s)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
+# k_edge_cost DRAM bytes per evaluated edge: 32.17 MB for 491,520 edges in the ncu capture of
+# round 0 at L7 (profiles/top_kernels_bumped_icosphere_l7.md); the traffic of a launch grows
+# with the edges it evaluates, so a launch's traffic is this times its edge count
+COST_DRAM_BYTES_PER_EDGE = 32.168e6 / 491520
+COST_FP64_PIPE_BUSY = 0.827  # same capture
+
 
 def max_over_ranks(x, device=None):
     """Max of a float over all ranks (identity without a process group)."""
@@ -525,6 +531,7 @@ def main():
     torch.cuda.synchronize()
     times, dom_ms, dom_launch, dom_bytes, dom_flops, launches = [], 0.0, 0, 0.0, 0.0, 0
     bytes_alg = 0.0
+    cost_edges = 0
     out = None
     for _ in range(args.steps):
         flush.fill_(1)
@@ -541,6 +548,7 @@ def main():
         dom_flops += st["class_flops"][dom]
         launches += st["launches"]
         bytes_alg += st["bytes_model"]
+        cost_edges += st["cost_edges"]
         out = (Vo, Fo, st, status)
     torch.cuda.synchronize()
     barrier()
@@ -560,9 +568,14 @@ def main():
         # float64-ALU bound: algorithmic flops of the evaluated edges per launch
         flops_per_launch = dom_flops / max(dom_launch, 1)
         achieved = flops_per_launch / (avg_launch_ms * 1e-3) / 1e12 if avg_launch_ms > 0 else 0.0
+        # two launches per round in this class (reuse + cost): edges per k_edge_cost launch
+        edges_per_launch = cost_edges / max(dom_launch / 2, 1)
         roof = {"bound": "alu", "kernel_class": "cost", "achieved": achieved,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": None, "peak_source": "derived: float64 FMA units x clock",
+                "traffic": COST_DRAM_BYTES_PER_EDGE * edges_per_launch,
+                "traffic_note": "ncu DRAM bytes per edge (L7 round-0 capture) x edges per launch",
+                "ncu_fp64_pipe_busy": COST_FP64_PIPE_BUSY,
+                "peak_source": "derived: float64 FMA units x clock",
                 "launch_ms": avg_launch_ms, "class_share": share}
     else:
         peak, peak_kind = peaks()

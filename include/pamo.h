@@ -131,6 +131,7 @@ typedef struct {
    * fused multiply-add as 2) */
   double class_flops[8];
   int64_t deferred;            /* edges deferred by the learned proposal */
+  int64_t cost_edges;          /* edges whose Eq. 1 cost was evaluated (dirty edges) */
 } pamo_stats;
 
 typedef struct pamo_ctx pamo_ctx;

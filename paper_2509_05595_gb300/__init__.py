@@ -56,7 +56,8 @@ class _Stats(ctypes.Structure):
                 ("ms_total", ctypes.c_double), ("bytes_model", ctypes.c_double),
                 ("launches", ctypes.c_int64), ("class_ms", ctypes.c_double * 8),
                 ("class_launches", ctypes.c_int64 * 8), ("class_bytes", ctypes.c_double * 8),
-                ("class_flops", ctypes.c_double * 8), ("deferred", ctypes.c_int64)]
+                ("class_flops", ctypes.c_double * 8), ("deferred", ctypes.c_int64),
+                ("cost_edges", ctypes.c_int64)]
 
 
 @dataclass
@@ -255,7 +256,7 @@ def _stats_dict(s: _Stats):
                 ms_total=s.ms_total, bytes_model=s.bytes_model, launches=s.launches,
                 class_ms=list(s.class_ms), class_launches=list(s.class_launches),
                 class_bytes=list(s.class_bytes), class_flops=list(s.class_flops),
-                deferred=s.deferred)
+                deferred=s.deferred, cost_edges=s.cost_edges)
 
 
 def pamo_simplify(V, F, target_faces, options: Options | None = None, **kw):

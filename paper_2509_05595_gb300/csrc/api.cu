@@ -782,6 +782,7 @@ pamo_status finish_round(pamo_ctx* c) {
   }
   c->class_flops[PAMO_KC_COST] += 114.0 * h.n_dirty + 32.0 * (double)h.cost_tris;
   c->deferred_total += h.deferred;
+  c->cost_edges_total += h.n_dirty;
   c->committed_total += committed;
   c->undone_total += nund;
   c->link_total += info[3];
@@ -890,6 +891,7 @@ pamo_status finish_round_batch(pamo_ctx* c) {
   c->nflags = nf;
   // totals over the batch
   c->class_flops[PAMO_KC_COST] += 114.0 * h.n_dirty + 32.0 * (double)h.cost_tris;
+  c->cost_edges_total += h.n_dirty;
   c->committed_total += h.committed;
   c->undone_total += h.nund;
   c->link_total += (int64_t)h.link_rejects;
@@ -1119,6 +1121,7 @@ void fill_stats(const pamo_ctx* c, pamo_stats* s, double ms) {
   s->ms_total = ms;
   s->bytes_model = c->bytes_model;
   s->deferred = c->deferred_total;
+  s->cost_edges = c->cost_edges_total;
   for (int i = 0; i < 8; i++) {
     s->class_ms[i] = c->class_ms[i];
     s->class_launches[i] = c->class_launches[i];

@@ -188,6 +188,7 @@ struct pamo_ctx {
   float* pprob = nullptr;              // [Emax] predicted probability of an undo
   uint8_t* pkeep = nullptr;            // [Emax] winner not deferred
   int64_t deferred_total = 0;
+  int64_t cost_edges_total = 0;        // dirty edges evaluated by k_edge_cost
   int32_t* dlist = nullptr;            // [Emax] edges whose cost is recomputed
   bool have_prev = false;
   unsigned long long* key = nullptr;   // [Emax]
