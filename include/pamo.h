@@ -96,6 +96,11 @@ typedef struct {
    * single-mesh calls only. */
   const struct pamo_mlp* proposal;
   float proposal_threshold; /* defer when the predicted probability exceeds it */
+  int32_t recompute_quadrics; /* 1 = every round starts from the face-plane
+                              quadrics of the current mesh (summed in ascending
+                              face order) instead of carrying K_a + K_b through
+                              collapses (0, the default, standard QEM memory);
+                              Eq. 1 cites QEM without fixing this */
 } pamo_options;
 
 /* Kernel classes reported in pamo_stats (index = bit of pamo_options.profile). */

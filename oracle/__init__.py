@@ -39,7 +39,7 @@ def lib():
         L.or_orient2d_exact.restype = ctypes.c_int
         L.or_tri_intersect.restype = ctypes.c_int
         L.or_edge_table.restype = i64
-        L.or_edge_table.argtypes = [P, i64, P, i64, P, i64, P, P, P, P, P]
+        L.or_edge_table.argtypes = [P, i64, P, i64, P, i64, P, P, P, P, P, P]
         L.or_vertex_quadrics.argtypes = [P, i64, P, i64, P]
         L.or_run.restype = P
         L.or_run.argtypes = [P, i64, P, i64, i64, P, P]
@@ -107,7 +107,8 @@ def vertex_quadrics(V, F):
 
 
 def edge_table(V, F, w_e=W_E, w_s=W_S):
-    """Round-0 edge table: dict of arrays (ab, key, vbar, Q, l, Cs, cost, link_ok).
+    """Round-0 edge table: dict of arrays (ab, key, vbar, Q, l, Cs, cost, link_ok,
+    vsolve = the float64 placement before rounding, NaN where the fallback is taken).
 
     ``key`` is ~0 for ineligible edges."""
     V, F = _f32(V), _i32(F)
@@ -117,12 +118,14 @@ def edge_table(V, F, w_e=W_E, w_s=W_S):
     vbar = np.zeros((cap, 3), np.float32)
     terms = np.zeros((cap, 4), np.float64)
     bits = np.zeros(cap, np.int32)
+    vsolve = np.zeros((cap, 3), np.float64)
     w = np.array([w_e, w_s], np.float64)
     n = lib().or_edge_table(_ptr(V), len(V), _ptr(F), len(F), _ptr(w), cap,
-                            _ptr(ab), _ptr(key), _ptr(vbar), _ptr(terms), _ptr(bits))
+                            _ptr(ab), _ptr(key), _ptr(vbar), _ptr(terms), _ptr(bits),
+                            _ptr(vsolve))
     return dict(ab=ab[:n], key=key[:n], vbar=vbar[:n], Q=terms[:n, 0],
                 l=terms[:n, 1], Cs=terms[:n, 2], cost=terms[:n, 3],
-                link_ok=bits[:n].astype(bool))
+                link_ok=bits[:n].astype(bool), vsolve=vsolve[:n])
 
 
 class Result:
@@ -137,14 +140,15 @@ class Result:
 
 def simplify(V, F, target, w_e=W_E, w_s=W_S, tolerance=TOLERANCE,
              max_rounds=100000, stall_limit=12, check_mode=CHECK_GRID,
-             keep_pairs=True, exact_target=0, max_cost=float("inf")):
+             keep_pairs=True, exact_target=0, max_cost=float("inf"), recompute_quadrics=0):
     """Algorithm 1 on the CPU.  exact_target / max_cost: the two termination
     refinements of Section 5.1 (keep only the lowest-key winners needed to
     reach N_t; edges costing more than max_cost are not eligible)."""
     V, F = _f32(V), _i32(F)
     L = lib()
     w = np.array([w_e, w_s, max_cost], np.float64)
-    iopt = np.array([tolerance, max_rounds, stall_limit, check_mode, exact_target], np.int32)
+    iopt = np.array([tolerance, max_rounds, stall_limit, check_mode, exact_target,
+                     recompute_quadrics], np.int32)
     h = L.or_run(_ptr(V), len(V), _ptr(F), len(F), int(target), _ptr(w), _ptr(iopt))
     try:
         nv, nf = L.or_nv(h), L.or_nf(h)

@@ -41,6 +41,9 @@
 //   R14 target edge cost (Section 5.1 names it beside the face target): an
 //      edge whose float cost is above (float)max_cost is not eligible; the
 //      run ends normally when no edge is eligible and no flag is pending.
+//   R16 quadric memory (option): by default a collapse adds the two endpoint
+//      quadrics (R1); with recompute_quadrics every round starts from the
+//      face-plane quadrics of the current mesh instead.
 //   R15 exact target: when a round's winners would remove more faces than
 //      |F| - N_t, only the ceil((|F| - N_t) / 2) winners with the lowest keys
 //      collapse (off by default: Algorithm 1 collapses every winner).
@@ -497,6 +500,7 @@ struct Options {
   double max_cost;  // target edge cost (Section 5.1): +inf = off
   int32_t tolerance, max_rounds, stall_limit, check_mode;
   int32_t exact_target;  // keep only the lowest-key winners needed for N_t
+  int32_t recompute_quadrics;  // R16: vertex quadrics from the current faces every round
   // check_mode: 0 = changed faces vs all faces (cell grid),
   //             1 = changed faces vs all faces (brute force),
   //             2 = all face pairs, brute force (Algorithm 3 as printed),
@@ -507,6 +511,7 @@ struct EdgeInfo {
   int32_t a, b;          // a < b
   uint64_t key;          // ~0 when ineligible
   float vbar[3];
+  double vsolve[3];  // the float64 solve before rounding (NaN when the fallback is taken)
   double Q, l, Cs, cost;
   int32_t link_ok, flagged;
 };
@@ -644,12 +649,16 @@ static void edge_cost(const Mesh& m, const std::vector<int64_t>& off,
                                 std::max(std::fabs(K[2]), std::fabs(K[4]))),
                        std::max(std::fabs(K[5]), std::fabs(K[7])));
   double det = det3(K[0], K[1], K[2], K[1], K[4], K[5], K[2], K[5], K[7]);
+  e.vsolve[0] = e.vsolve[1] = e.vsolve[2] = std::numeric_limits<double>::quiet_NaN();
   bool solved = false;
   float v[3];
   if (mx != 0.0 && !(std::fabs(det) <= 1e-12 * ((mx * mx) * mx))) {
     double x = det3(r0, K[1], K[2], r1, K[4], K[5], r2, K[5], K[7]) / det;
     double y = det3(K[0], r0, K[2], K[1], r1, K[5], K[2], r2, K[7]) / det;
     double z = det3(K[0], K[1], r0, K[1], K[4], r1, K[2], K[5], r2) / det;
+    e.vsolve[0] = x;
+    e.vsolve[1] = y;
+    e.vsolve[2] = z;
     v[0] = (float)x;
     v[1] = (float)y;
     v[2] = (float)z;
@@ -910,6 +919,7 @@ static void simplify(Mesh m, int64_t target, const Options& o, Run& run) {
     L.nV = m.nV;
     L.nF = m.nF;
     vertex_faces(m, off, idx);
+    if (o.recompute_quadrics) init_quadrics(m, off, idx);  // R16
     // --- edge costs (Algorithm 1, first parallel loop; Eq. 1)
     std::vector<EdgeInfo> edges;
     analyse_edges(m, off, idx, run.scale, o, flags, edges);
@@ -1132,6 +1142,7 @@ static Options to_options(const double* w, const int32_t* iopt) {
   o.stall_limit = iopt[2];
   o.check_mode = iopt[3];
   o.exact_target = iopt[4];
+  o.recompute_quadrics = iopt[5];
   o.max_cost = w[2];
   return o;
 }
@@ -1185,7 +1196,7 @@ void or_vertex_quadrics(const float* V, int64_t nV, const int32_t* F, int64_t nF
 // receive endpoints, key, placement, the Eq. 1 terms and eligibility bits.
 int64_t or_edge_table(const float* V, int64_t nV, const int32_t* F, int64_t nF,
                       const double* w, int64_t cap, int32_t* ab, uint64_t* key,
-                      float* vbar, double* terms, int32_t* bits) {
+                      float* vbar, double* terms, int32_t* bits, double* vsolve) {
   Mesh m = to_mesh(V, nV, F, nF);
   std::vector<int64_t> off;
   std::vector<int32_t> idx;
@@ -1204,6 +1215,8 @@ int64_t or_edge_table(const float* V, int64_t nV, const int32_t* F, int64_t nF,
     bool elig = e.link_ok && e.key != ~0ull;
     key[i] = elig ? e.key : ~0ull;
     for (int k = 0; k < 3; k++) vbar[3 * i + k] = e.vbar[k];
+    if (vsolve)
+      for (int k = 0; k < 3; k++) vsolve[3 * i + k] = e.vsolve[k];
     terms[4 * i] = e.Q;
     terms[4 * i + 1] = e.l;
     terms[4 * i + 2] = e.Cs;

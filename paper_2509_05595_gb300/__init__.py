@@ -45,7 +45,7 @@ class _Options(ctypes.Structure):
                 ("profile", ctypes.c_int32), ("exact_target", ctypes.c_int32),
                 ("max_cost", ctypes.c_double), ("grid_blocks_per_sm", ctypes.c_int32),
                 ("resort_percent", ctypes.c_int32), ("proposal", ctypes.c_void_p),
-                ("proposal_threshold", ctypes.c_float)]
+                ("proposal_threshold", ctypes.c_float), ("recompute_quadrics", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
@@ -78,6 +78,7 @@ class Options:
     resort_percent: int = 0
     proposal: object = None        # an MLP (learned proposal) or None
     proposal_threshold: float = 0.5
+    recompute_quadrics: int = 0
 
     def c(self):
         d = {f.name: getattr(self, f.name) for f in fields(self)}

@@ -121,7 +121,7 @@ void free_ctx_buffers(pamo_ctx* c) {
   release(c->mframe, st); release(c->mcost, st); release(c->mactive, st); release(c->mcount, st);
   release(c->mvbase, st); release(c->flags_old, st);
   release(c->vgap, st); release(c->vgap_tmp, st); release(c->pX, st);
-  release(c->pprob, st); release(c->pkeep, st);
+  release(c->pprob, st); release(c->pkeep, st); release(c->qface, st);
   if (c->mcount_h) cudaFreeHost(c->mcount_h);
   c->mcount_h = nullptr;
   for (int r = 0; r < 3; r++) release(c->cand[r], st);
@@ -182,6 +182,10 @@ pamo_status check_options(const pamo_options* o) {
     set_error("max_cost must be >= 0 (+infinity = no cost target)");
     return PAMO_EINVAL;
   }
+  if (o->recompute_quadrics != 0 && o->recompute_quadrics != 1) {
+    set_error("recompute_quadrics must be 0 or 1");
+    return PAMO_EINVAL;
+  }
   if (o->grid_blocks_per_sm < 0 || o->grid_blocks_per_sm > 32 || o->resort_percent < 0 ||
       o->resort_percent > 100) {
     set_error("grid_blocks_per_sm must be in 0..32 and resort_percent in 0..100");
@@ -239,6 +243,7 @@ pamo_status alloc_state(pamo_ctx* c, int64_t nV, int64_t nF) {
   if (c->opt.proposal) {
     A(pX, 16 * c->Emax); A(pprob, c->Emax); A(pkeep, c->Emax);
   }
+  if (c->opt.recompute_quadrics) A(qface, 10 * nF);
   A(scan_sums, scan_sums_count(std::max<int64_t>(c->Emax, mx + 1)));
   // candidate pairs of the split check: a changed face has at most 3
   // edge-neighbours; vertex-neighbours and other overlaps are bounded
@@ -530,6 +535,7 @@ pamo_status phase_begin(pamo_ctx* c) {
   PAMO_TRY(save_prev(c));
   PAMO_TRY(build_vertex_faces(c));
   PAMO_TRY(build_edges(c));
+  if (c->opt.recompute_quadrics) PAMO_TRY(recompute_quadrics(c));
   const double nV = (double)c->nV, nF = (double)c->nF, nE = 1.5 * nF;
   // previous edge data copied; F read; CSR written and read back; edges written
   kc_end(c, PAMO_KC_ADJACENCY, 2 * nE * 29 + 16 * nF + 2 * (4 * nV + 12 * nF) + 8 * nE + 4 * nV);
@@ -1155,6 +1161,7 @@ void pamo_default_options(pamo_options* o) {
   o->resort_percent = 0;
   o->proposal = nullptr;
   o->proposal_threshold = 0.5f;
+  o->recompute_quadrics = 0;
 }
 
 const char* pamo_last_error(void) { return g_err.c_str(); }

@@ -201,6 +201,7 @@ struct pamo_ctx {
   uint8_t* undo = nullptr;      // [Emax] per winner slot
   int32_t* ftag = nullptr;      // [nF0] winner slot that rewrote the face
   int32_t* qlist = nullptr;     // [nF0] faces changed this round (query list)
+  double* qface = nullptr;      // [10 nF0] face-plane quadrics (recompute_quadrics)
   int2* cand[3] = {nullptr, nullptr, nullptr};  // candidate pairs by shared-vertex count
   int64_t cand_cap[3] = {0, 0, 0};
   int sm_count = 152;
@@ -302,6 +303,7 @@ pamo_status build_vertex_faces(pamo_ctx* c);
 pamo_status build_edges(pamo_ctx* c);
 pamo_status save_prev(pamo_ctx* c);
 pamo_status init_quadrics(pamo_ctx* c);
+pamo_status recompute_quadrics(pamo_ctx* c);
 pamo_status commit_compact(pamo_ctx* c);
 pamo_status commit_sizes(pamo_ctx* c);
 pamo_status load_mesh(const float* d_V, int64_t nV, const int32_t* d_F, int64_t nF,

@@ -427,9 +427,9 @@ __global__ void k_save_prev(RoundCounters* __restrict__ dc, const int2* __restri
 // plane of a face through its first corner, unit normal; coefficient order
 // xx xy xz xd yy yz yd zz zd dd
 __global__ void k_face_quadrics(const float4* __restrict__ pos, const int4* __restrict__ F,
-                                int64_t nF, double* __restrict__ q) {
-  int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= nF) return;
+                                const int* nF_dev, int64_t nF_host, double* __restrict__ q) {
+  const int64_t nF = nF_dev ? (int64_t)*nF_dev : nF_host;
+  GRID_STRIDE(f, nF) {
   int4 t = F[f];
   float4 p0 = pos[t.x], p1 = pos[t.y], p2 = pos[t.z];
   double ux = (double)p1.x - (double)p0.x, uy = (double)p1.y - (double)p0.y,
@@ -444,7 +444,7 @@ __global__ void k_face_quadrics(const float4* __restrict__ pos, const int4* __re
   if (len == 0.0) {
 #pragma unroll
     for (int i = 0; i < 10; i++) o[i] = 0.0;
-    return;
+    continue;
   }
   nx = nx / len;
   ny = ny / len;
@@ -460,13 +460,14 @@ __global__ void k_face_quadrics(const float4* __restrict__ pos, const int4* __re
   o[7] = nz * nz;
   o[8] = nz * d;
   o[9] = d * d;
+  }
 }
 
 __global__ void k_vertex_quadrics(const double* __restrict__ q, const int32_t* __restrict__ off,
-                                  const int32_t* __restrict__ idx, int64_t nV,
-                                  double* __restrict__ K) {
-  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= nV) return;
+                                  const int32_t* __restrict__ idx, const int* nV_dev,
+                                  int64_t nV_host, double* __restrict__ K) {
+  const int64_t nV = nV_dev ? (int64_t)*nV_dev : nV_host;
+  GRID_STRIDE(v, nV) {
   double s[10];
 #pragma unroll
   for (int i = 0; i < 10; i++) s[i] = 0.0;
@@ -477,6 +478,7 @@ __global__ void k_vertex_quadrics(const double* __restrict__ q, const int32_t* _
   }
 #pragma unroll
   for (int i = 0; i < 10; i++) K[10 * v + i] = s[i];
+  }
 }
 
 // ---- commit (stable compaction), gated by the last check (the gate sizes
@@ -798,10 +800,22 @@ pamo_status init_quadrics(pamo_ctx* c) {
   cudaStream_t st = c->st;
   PAMO_TRY(buf_reserve(c->quad_tmp, sizeof(double) * 10 * (size_t)c->nF, st));
   double* q = (double*)c->quad_tmp.p;
-  k_face_quadrics<<<grid_for(c->nF), kBlock, 0, st>>>(c->pos, c->F, c->nF, q); note_launch();
-  k_vertex_quadrics<<<grid_for(c->nV), kBlock, 0, st>>>(q, c->vf_off, c->vf_idx, c->nV, c->K); note_launch();
+  k_face_quadrics<<<grid_for(c->nF), kBlock, 0, st>>>(c->pos, c->F, nullptr, c->nF, q); note_launch();
+  k_vertex_quadrics<<<grid_for(c->nV), kBlock, 0, st>>>(q, c->vf_off, c->vf_idx, nullptr, c->nV,
+                                                        c->K); note_launch();
   PAMO_CUDA(cudaGetLastError());
   buf_free(c->quad_tmp, st);
+  return PAMO_OK;
+}
+
+// the option recompute_quadrics: vertex quadrics of M_1 from its current faces
+// (device sizes, every round, before the costs)
+pamo_status recompute_quadrics(pamo_ctx* c) {
+  cudaStream_t st = c->st;
+  k_face_quadrics<<<c->grid, kBlock, 0, st>>>(c->pos, c->F, &c->dc->nF, 0, c->qface); note_launch();
+  k_vertex_quadrics<<<c->grid, kBlock, 0, st>>>(c->qface, c->vf_off, c->vf_idx, &c->dc->nV, 0,
+                                                c->K); note_launch();
+  PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;
 }
 

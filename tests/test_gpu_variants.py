@@ -66,3 +66,13 @@ def test_cost_ablation_switches_bit_exact(w_e, w_s):
 def test_speed_knobs_do_not_change_results(knobs):
     V, F = meshgen.bumped_icosphere(5, 6)
     _assert_same_run(V, F, len(F) // 100, **{"gpu_only": knobs})
+
+
+@pytest.mark.parametrize("mesh", ["torus", "sphere5", "shells4"])
+def test_recompute_quadrics_bit_exact(mesh):
+    V, F, target = {
+        "torus": lambda: meshgen.mesh_config("torus_64x32"),
+        "sphere5": lambda: (*meshgen.bumped_icosphere(5, 3), 400),
+        "shells4": lambda: (*meshgen.nested_shells(4, check=False), 2400),
+    }[mesh]()
+    _assert_same_run(V, F, target, recompute_quadrics=1)

@@ -170,3 +170,28 @@ def test_link_condition_special_meshes():
     T = oracle.edge_table(V2, F2)
     bad = {tuple(x) for x in T["ab"][~T["link_ok"]].tolist()}
     assert bad == {(0, 2), (2, 4), (0, 4)}
+
+
+@pytest.mark.parametrize("mesh,tol", [("torus", 1e-10), ("sphere4", 1e-8), ("sphere6", 1e-5)])
+def test_placement_float64_error_statement(mesh, tol):
+    # SURVEY C-3: the float64 Cramer solve against a 50-digit solve of the same
+    # float64 system; the error grows with the conditioning of A (flatter
+    # neighbourhoods at finer levels) and is stated in the design notes
+    V, F = {"torus": lambda: meshgen.torus(),
+            "sphere4": lambda: meshgen.bumped_icosphere(4, 3),
+            "sphere6": lambda: meshgen.bumped_icosphere(6, 0)}[mesh]()
+    T = oracle.edge_table(V, F)
+    K = oracle.vertex_quadrics(V, F)
+    solved = np.where(~np.isnan(T["vsolve"][:, 0]))[0]
+    idx = np.random.default_rng(1).choice(solved, min(800, len(solved)), replace=False)
+    worst, flips = 0.0, 0
+    for i in idx:
+        a, b = T["ab"][i]
+        k = K[a] + K[b]
+        A = mpmath.matrix([[k[0], k[1], k[2]], [k[1], k[4], k[5]], [k[2], k[5], k[7]]])
+        v = mpmath.lu_solve(A, mpmath.matrix([-k[3], -k[6], -k[8]]))
+        vm = np.array([float(x) for x in v])
+        worst = max(worst, np.linalg.norm(T["vsolve"][i] - vm) / np.linalg.norm(vm))
+        flips += int((np.float32(vm) != T["vbar"][i]).any())
+    assert worst < tol
+    assert flips <= 0.1 * len(idx)

@@ -239,3 +239,22 @@ def test_edge_cost_terms_reduce_bad_triangles(mesh):
         bad[name] = _bad_pct(r.V, r.F, 10.0)
     assert bad["full"] <= min(bad["no_ce"], bad["no_cs"], bad["none"])
     assert bad["none"] >= bad["full"] + 2.0
+
+
+def test_recompute_quadrics_is_memoryless(torus_mesh):
+    # With recompute_quadrics (R16) a round's costs depend only on the current
+    # mesh (and the flags, empty while nothing is undone), so k rounds equal k
+    # fresh one-round runs chained, each starting from face-plane quadrics.
+    V, F, target = torus_mesh
+    Vk, Fk = V, F
+    for k in range(1, 6):
+        step = oracle.simplify(Vk, Fk, target, max_rounds=1, keep_pairs=False)
+        assert step.rounds[0]["undone"] == 0
+        Vk, Fk = step.V, step.F
+        full = oracle.simplify(V, F, target, max_rounds=k, keep_pairs=False, recompute_quadrics=1)
+        assert np.array_equal(full.F, Fk) and np.array_equal(full.V, Vk), k
+    # and it is a different rule from carrying K_a + K_b once collapses happened
+    carry = oracle.simplify(V, F, target, keep_pairs=False)
+    fresh = oracle.simplify(V, F, target, keep_pairs=False, recompute_quadrics=1)
+    assert not (np.array_equal(carry.F, fresh.F) and np.array_equal(carry.V, fresh.V))
+    assert is_closed_manifold(fresh.F, len(fresh.V)) and euler(fresh.F, len(fresh.V)) == 0
