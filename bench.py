@@ -516,6 +516,18 @@ def main():
         if world > 1:
             dist.barrier()
 
+    # rounds and their device times (one recorded run): the latency-bound tail
+    rc = pamo.Ctx(Vd, Fd, validate_input=0, record_rounds=1)
+    rc.run(target)
+    n_rounds, _ = rc.rounds()
+    per_round = [rc.round_info(r) for r in range(n_rounds)]
+    rc.close()
+    round_us = [r["us"] for r in per_round]
+    tail = [r for r in per_round if r["nF"] < 100000]
+    rounds_info = {"rounds": n_rounds, "round0_ms": round_us[0] / 1e3 if round_us else 0.0,
+                   "tail_rounds_below_100k_faces": len(tail),
+                   "tail_ms": sum(r["us"] for r in tail) / 1e3,
+                   "tail_share": sum(r["us"] for r in tail) / max(sum(round_us), 1)}
     # which class dominates: one profiled warm-up run with every class timed
     opts = pamo.Options(validate_input=0, profile=0xFF)
     _, _, st_prof, _ = pamo.pamo_simplify(Vd, Fd, target, options=opts)
@@ -597,6 +609,7 @@ def main():
             "config": {"workload": workload, "faces_in": int(len(F)), "target": int(target),
                        "faces_out": int(len(Fo)), "rounds": st["rounds"], "status": status,
                        "undo_iters_hist": st["undo_iters_hist"][:4],
+                       "round_times": rounds_info,
                        "l2": "flushed between steps (256 MiB write, outside the timed span)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "pipeline_hbm": pipeline, "clocks": clk, "e2e": e2e,

@@ -45,7 +45,10 @@ typedef enum {
   PAMO_ESTALL = 4,       /* stopped before the target; output is valid */
   PAMO_ETIMEOUT = 5,     /* a device-side bounded wait ran out */
   PAMO_ENOTMANIFOLD = 6, /* input is not a closed oriented manifold */
-  PAMO_EINTERNAL = 7     /* an internal capacity or consistency check failed */
+  PAMO_EINTERNAL = 7,    /* an internal capacity or consistency check failed */
+  PAMO_EINTERSECT = 8    /* options.check_input_intersections: the input
+                            mesh intersects itself (the method requires an
+                            intersection-free input, Section 5) */
 } pamo_status;
 
 /* Options.  pamo_default_options() fills the paper's defaults. */
@@ -96,6 +99,10 @@ typedef struct {
    * single-mesh calls only. */
   const struct pamo_mlp* proposal;
   float proposal_threshold; /* defer when the predicted probability exceeds it */
+  int32_t check_input_intersections; /* 1 = run the exact self-intersection
+                              check (Algorithm 3 over every face) on the input
+                              first and refuse a self-intersecting mesh with
+                              PAMO_EINTERSECT; 0 (default) trusts the caller */
   int32_t recompute_quadrics; /* 1 = every round starts from the face-plane
                               quadrics of the current mesh (summed in ascending
                               face order) instead of carrying K_a + K_b through
@@ -288,9 +295,11 @@ pamo_status pamo_ctx_sizes(const pamo_ctx* ctx, int64_t* nV, int64_t* nF,
 pamo_status pamo_ctx_export(pamo_ctx* ctx, float* d_V, int32_t* d_F,
                             uint64_t* d_keys, int32_t* d_edges);
 
-/* Per-round record (requires options.record_rounds).  out[11] receives
+/* Per-round record (requires options.record_rounds).  out[12] receives
  * nV nF nE link_rejects flagged eligible winners committed undone undo_iters
- * pairs_found of round r. */
+ * pairs_found of round r, and the round's device time in microseconds (its
+ * graph replays, CUDA events; 0 for rounds run by the per-round entry
+ * points). */
 pamo_status pamo_ctx_round_info(const pamo_ctx* ctx, int64_t r, int64_t* out);
 
 /* Vertex pairs (in round r's input numbering) of kind 0 = winners,

@@ -21,13 +21,13 @@ _lib = None
 
 STATUS = {0: "PAMO_OK", 1: "PAMO_EINVAL", 2: "PAMO_ENOMEM", 3: "PAMO_ECUDA",
           4: "PAMO_ESTALL", 5: "PAMO_ETIMEOUT", 6: "PAMO_ENOTMANIFOLD",
-          7: "PAMO_EINTERNAL"}
+          7: "PAMO_EINTERNAL", 8: "PAMO_EINTERSECT"}
 PAMO_OK, PAMO_ESTALL = 0, 4
 
 KERNEL_CLASSES = ("adjacency", "cost", "select", "collapse", "bvh", "query", "commit", "other")
 
 ROUND_FIELDS = ("nV", "nF", "nE", "link_rejects", "flagged", "eligible",
-                "winners", "committed", "undone", "undo_iters", "pairs_found")
+                "winners", "committed", "undone", "undo_iters", "pairs_found", "us")
 
 
 class PamoError(RuntimeError):
@@ -45,7 +45,9 @@ class _Options(ctypes.Structure):
                 ("profile", ctypes.c_int32), ("exact_target", ctypes.c_int32),
                 ("max_cost", ctypes.c_double), ("grid_blocks_per_sm", ctypes.c_int32),
                 ("resort_percent", ctypes.c_int32), ("proposal", ctypes.c_void_p),
-                ("proposal_threshold", ctypes.c_float), ("recompute_quadrics", ctypes.c_int32)]
+                ("proposal_threshold", ctypes.c_float),
+                ("check_input_intersections", ctypes.c_int32),
+                ("recompute_quadrics", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
@@ -78,6 +80,7 @@ class Options:
     resort_percent: int = 0
     proposal: object = None        # an MLP (learned proposal) or None
     proposal_threshold: float = 0.5
+    check_input_intersections: int = 0
     recompute_quadrics: int = 0
 
     def c(self):
@@ -435,7 +438,7 @@ class Ctx:
         return n.value, STATUS[code]
 
     def round_info(self, r):
-        out = np.zeros(11, np.int64)
+        out = np.zeros(12, np.int64)
         _check(lib().pamo_ctx_round_info(self._h, r, out.ctypes.data_as(ctypes.c_void_p)),
                "pamo_ctx_round_info")
         return dict(zip(ROUND_FIELDS, (int(x) for x in out)))

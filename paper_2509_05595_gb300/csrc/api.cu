@@ -156,6 +156,8 @@ pamo_status join(pamo_ctx* c) {
 void destroy_ctx(pamo_ctx* c) {
   free_ctx_buffers(c);
   cudaStreamSynchronize(c->st);
+  for (cudaEvent_t& e : c->round_ev)
+    if (e) cudaEventDestroy(e);
   if (c->join_ev) cudaEventDestroy(c->join_ev);
   cudaStreamDestroy(c->st);
   delete c;
@@ -180,6 +182,10 @@ pamo_status check_options(const pamo_options* o) {
   }
   if (!(o->max_cost >= 0.0)) {
     set_error("max_cost must be >= 0 (+infinity = no cost target)");
+    return PAMO_EINVAL;
+  }
+  if (o->check_input_intersections != 0 && o->check_input_intersections != 1) {
+    set_error("check_input_intersections must be 0 or 1");
     return PAMO_EINVAL;
   }
   if (o->recompute_quadrics != 0 && o->recompute_quadrics != 1) {
@@ -213,6 +219,10 @@ pamo_status new_ctx(const pamo_options* opt, cudaStream_t st, pamo_ctx** out) {
     return cuda_fail(e, "context stream");
   }
   c->opt = o;
+  if (o.record_rounds) {
+    cudaEventCreate(&c->round_ev[0]);
+    cudaEventCreate(&c->round_ev[1]);
+  }
   c->sm_count = sm_count();
   c->grid = c->sm_count * (o.grid_blocks_per_sm > 0 ? o.grid_blocks_per_sm : 4);
   *out = c;
@@ -298,6 +308,32 @@ pamo_status init_counters(pamo_ctx* c) {
   return PAMO_OK;
 }
 
+// options.check_input_intersections: Algorithm 3 over every face of the
+// input (exact); a pair means the input breaks the method's precondition
+pamo_status check_input(pamo_ctx* c, const float lo[3], const float hi[3]) {
+  cudaStream_t st = c->st;
+  RoundCounters* dc = c->dc;
+  PAMO_CUDA(cudaMemsetAsync(&dc->n_pairs, 0, sizeof(int), st));
+  PAMO_CUDA(cudaMemsetAsync(c->bvh.flags.p, 0, sizeof(int32_t) * (size_t)(c->bvh.n_max + 2), st));
+  PAMO_TRY(bvh_build(c->bvh, c->pos, c->F, nullptr, nullptr, (int)c->nF, lo, hi, false, c->grid, st));
+  PAMO_TRY(bvh_check(c->bvh, c->pos, c->F, nullptr, nullptr, 1, nullptr, nullptr, 0, nullptr, dc,
+                     nullptr, 0, (int)c->nF, st));
+  int h[2] = {0, 0};
+  PAMO_CUDA(cudaMemcpyAsync(h, &dc->n_pairs, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PAMO_CUDA(cudaMemcpyAsync(h + 1, &dc->overflow, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PAMO_CUDA(cudaStreamSynchronize(st));
+  PAMO_CUDA(cudaMemsetAsync(&dc->n_pairs, 0, sizeof(int), st));
+  if (h[1]) {
+    set_error("BVH traversal bound exceeded in the input check");
+    return PAMO_EINTERNAL;
+  }
+  if (h[0]) {
+    set_error("the input mesh intersects itself (" + std::to_string(h[0]) + " face pairs)");
+    return PAMO_EINTERSECT;
+  }
+  return PAMO_OK;
+}
+
 pamo_status create(const float* d_V, int64_t nV, const int32_t* d_F, int64_t nF,
                    const pamo_options* opt, cudaStream_t st, pamo_ctx** out) {
   *out = nullptr;
@@ -325,6 +361,7 @@ pamo_status create(const float* d_V, int64_t nV, const int32_t* d_F, int64_t nF,
     c->scale = ext > 0.0 ? 1.0 / ext : 1.0;
     s = init_quadrics(c);
   }
+  if (s == PAMO_OK && c->opt.check_input_intersections) s = check_input(c, c->bb_lo, c->bb_hi);
   if (s != PAMO_OK) {
     destroy_ctx(c);
     return s;
@@ -422,6 +459,10 @@ pamo_status create_batch(int M, const float* d_V, const int64_t* h_voff, const i
     if (e != cudaSuccess) s = cuda_fail(e, "cudaMemcpyAsync batch tables");
   }
   if (s == PAMO_OK) s = init_quadrics(c);
+  if (s == PAMO_OK && c->opt.check_input_intersections) {
+    float lo0[3] = {0.f, 0.f, 0.f}, hi0[3] = {1.f, 1.f, 1.f};  // per-mesh frames are used
+    s = check_input(c, lo0, hi0);
+  }
   if (s != PAMO_OK) {
     destroy_ctx(c);
     return s;
@@ -780,8 +821,10 @@ pamo_status finish_round(pamo_ctx* c) {
     PAMO_CUDA(cudaStreamSynchronize(st));
   }
   const int64_t eligible = (int64_t)h.eligible;
-  const int64_t info[11] = {nV_in, nF_in, nE_in, (int64_t)h.link_rejects, (int64_t)h.flagged,
-                            eligible, nW, committed, nund, h.undo_iters, h.pairs_total};
+  const int64_t info[12] = {nV_in, nF_in, nE_in, (int64_t)h.link_rejects, (int64_t)h.flagged,
+                            eligible, nW, committed, nund, h.undo_iters, h.pairs_total,
+                            c->last_round_us};
+  c->last_round_us = 0;
   if (c->opt.record_rounds) {
     std::memcpy(rec.info, info, sizeof(info));
     c->rec.push_back(std::move(rec));
@@ -971,6 +1014,8 @@ pamo_status graph_round(pamo_ctx* c) {
   const int slot = carry ? 1 : 0;
   if (!c->gA[slot]) PAMO_TRY(capture(c, slot, &c->gA[slot], [&] { return round_body(c, carry); }));
   note_build(c, carry);
+  const bool timed = c->opt.record_rounds && c->round_ev[0];
+  if (timed) PAMO_CUDA(cudaEventRecord(c->round_ev[0], st));
   PAMO_CUDA(cudaGraphLaunch(c->gA[slot], st));
   PAMO_CUDA(cudaStreamSynchronize(st));
   account_bytes(c, slot);
@@ -994,6 +1039,13 @@ pamo_status graph_round(pamo_ctx* c) {
       graph_resolve(c, 2);
     }
     PAMO_TRY(check_device_errors(c));
+  }
+  if (timed) {
+    PAMO_CUDA(cudaEventRecord(c->round_ev[1], st));
+    PAMO_CUDA(cudaEventSynchronize(c->round_ev[1]));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->round_ev[0], c->round_ev[1]);
+    c->last_round_us = (int64_t)(ms * 1000.0f);
   }
   return finish_round(c);
 }
@@ -1162,6 +1214,7 @@ void pamo_default_options(pamo_options* o) {
   o->proposal = nullptr;
   o->proposal_threshold = 0.5f;
   o->recompute_quadrics = 0;
+  o->check_input_intersections = 0;
 }
 
 const char* pamo_last_error(void) { return g_err.c_str(); }

@@ -129,7 +129,7 @@ struct Bvh {
 };
 
 struct RoundRecord {
-  int64_t info[11];
+  int64_t info[12];
   std::vector<int32_t> win, com, und;
 };
 
@@ -188,6 +188,8 @@ struct pamo_ctx {
   float* pprob = nullptr;              // [Emax] predicted probability of an undo
   uint8_t* pkeep = nullptr;            // [Emax] winner not deferred
   int64_t deferred_total = 0;
+  cudaEvent_t round_ev[2] = {nullptr, nullptr};  // device time of a round (records)
+  int64_t last_round_us = 0;
   int64_t cost_edges_total = 0;        // dirty edges evaluated by k_edge_cost
   int32_t* dlist = nullptr;            // [Emax] edges whose cost is recomputed
   bool have_prev = false;

@@ -76,3 +76,17 @@ def test_recompute_quadrics_bit_exact(mesh):
         "shells4": lambda: (*meshgen.nested_shells(4, check=False), 2400),
     }[mesh]()
     _assert_same_run(V, F, target, recompute_quadrics=1)
+
+
+def test_input_intersection_check_refuses_bad_input():
+    from tests.test_gpu_parity import pamo as _pamo
+    # seeds whose shells overlap (the generator's own disjointness check fails)
+    V, F = meshgen.nested_shells(4, seeds=(2000, 6000), check=False)
+    assert oracle.self_intersections(V, F)[1] > 0
+    with pytest.raises(_pamo.PamoError, match="EINTERSECT"):
+        _pamo.pamo_simplify(torch.from_numpy(V), torch.from_numpy(F), len(F) // 10,
+                            check_input_intersections=1)
+    Vg, Fg = meshgen.nested_shells_seeded(4, 2001)
+    Vo, Fo, st, status = _pamo.pamo_simplify(torch.from_numpy(Vg), torch.from_numpy(Fg),
+                                             len(Fg) // 10, check_input_intersections=1)
+    assert status in ("PAMO_OK", "PAMO_ESTALL") and st["rounds"] > 0  # accepted and run
