@@ -18,7 +18,7 @@
 //   * Section 5.2 / Algorithm 3 / supplementary Section 3: intersection check
 //     with the case analysis by the number of shared vertices.
 //   * Section 5.3: undo and the invalid-edge flags with tolerance 4.
-// Readings where the paper is silent (all listed in the design notes):
+// Readings where the paper is silent:
 //   R1 quadrics: unweighted face planes, vertex sums in ascending face order;
 //      a collapse adds the two endpoint quadrics.
 //   R2 placement: Cramer solve of A v = -b, singular if |det| <= 1e-12 m^3;
@@ -38,15 +38,22 @@
 //   R10 flags: undone edges are invalid next round; after a round with no
 //      committed collapse the flags accumulate, cleared after `tolerance`
 //      such rounds.
+//   R11 check scope: faces changed this round against all faces (the same
+//      pairs as all faces against all faces, the previous mesh being
+//      intersection-free).
+//   R12 an intersecting pair undoes the collapses that tagged either face.
+//   R13 evaluation order of Eq. 1: explicit std::fma in a fixed order;
+//      2A = sqrt(|u|^2 |w|^2 - (u.w)^2) clamped at 0, and the squared lengths
+//      sum to 2 (|u|^2 + |w|^2 - u.w), u, w the edges from the first corner.
 //   R14 target edge cost (Section 5.1 names it beside the face target): an
 //      edge whose float cost is above (float)max_cost is not eligible; the
 //      run ends normally when no edge is eligible and no flag is pending.
-//   R16 quadric memory (option): by default a collapse adds the two endpoint
-//      quadrics (R1); with recompute_quadrics every round starts from the
-//      face-plane quadrics of the current mesh instead.
 //   R15 exact target: when a round's winners would remove more faces than
 //      |F| - N_t, only the ceil((|F| - N_t) / 2) winners with the lowest keys
 //      collapse (off by default: Algorithm 1 collapses every winner).
+//   R16 quadric memory (option): by default a collapse adds the two endpoint
+//      quadrics (R1); with recompute_quadrics every round starts from the
+//      face-plane quadrics of the current mesh instead.
 //
 // Floating point: compiled with -ffp-contract=off (no implicit contraction),
 // IEEE double throughout the cost with explicit std::fma where the order says

@@ -174,9 +174,9 @@ def test_link_condition_special_meshes():
 
 @pytest.mark.parametrize("mesh,tol", [("torus", 1e-10), ("sphere4", 1e-8), ("sphere6", 1e-5)])
 def test_placement_float64_error_statement(mesh, tol):
-    # SURVEY C-3: the float64 Cramer solve against a 50-digit solve of the same
-    # float64 system; the error grows with the conditioning of A (flatter
-    # neighbourhoods at finer levels) and is stated in the design notes
+    # Precision of the placement (R2): the float64 Cramer solve against a
+    # 50-digit solve of the same float64 system; the error grows with the
+    # conditioning of A (flatter neighbourhoods at finer levels), bounded below
     V, F = {"torus": lambda: meshgen.torus(),
             "sphere4": lambda: meshgen.bumped_icosphere(4, 3),
             "sphere6": lambda: meshgen.bumped_icosphere(6, 0)}[mesh]()
