@@ -16,7 +16,7 @@ namespace pamo {
 
 namespace {
 
-constexpr double kTwoSqrt3 = 2.0 * 1.7320508075688772;
+constexpr double kSqrt3 = 1.7320508075688772;
 
 // float -> double on the integer pipe (exact for normal floats; zero,
 // subnormals, inf and NaN take the hardware conversion).  The float64 unit is
@@ -56,7 +56,16 @@ __device__ __forceinline__ double dot3(double ax, double ay, double az, double b
 
 // C_ijk = 4 sqrt(3) A / (l_ij^2 + l_jk^2 + l_ki^2), with u = q1 - q0, w = q2 - q0:
 // |u x w|^2 = |u|^2 |w|^2 - (u.w)^2 and the three squared lengths sum to
-// 2 (|u|^2 + |w|^2 - u.w)
+// 2 (|u|^2 + |w|^2 - u.w), so C_ijk = sqrt(3) |u x w| / (|u|^2 + |w|^2 - u.w).
+// This is bit-identical to (2 sqrt(3) |u x w|) / (2 (...)): the two factors
+// of 2 are exact and sqrt(3) |u x w| is never subnormal, so the rounded
+// quotient is the same, with one float64 multiply fewer.  Both operands are
+// finite for float32 inputs (squares of float32 differences stay far inside
+// float64 range), so their sign tests run on the integer bit patterns (a
+// finite double is > 0 iff its bits are > 0 as a signed integer), off the
+// float64 pipe.
+__device__ __forceinline__ bool pos_finite(double x) { return __double_as_longlong(x) > 0; }
+
 __device__ __forceinline__ double quality(double x0, double y0, double z0, double x1, double y1,
                                           double z1, double x2, double y2, double z2) {
   const double ux = x1 - x0, uy = y1 - y0, uz = z1 - z0;
@@ -65,9 +74,9 @@ __device__ __forceinline__ double quality(double x0, double y0, double z0, doubl
   const double b = dot3(wx, wy, wz, wx, wy, wz);
   const double c = dot3(ux, uy, uz, wx, wy, wz);
   double cr2 = __fma_rn(a, b, -(c * c));
-  if (!(cr2 > 0.0)) cr2 = 0.0;
-  const double den = 2.0 * ((a + b) - c);
-  return den > 0.0 ? (kTwoSqrt3 * sqrt(cr2)) / den : 0.0;
+  if (!pos_finite(cr2)) cr2 = 0.0;
+  const double half_den = (a + b) - c;
+  return pos_finite(half_den) ? (kSqrt3 * sqrt(cr2)) / half_den : 0.0;
 }
 
 // per-mesh eligible counts of a batch: one atomic per group of lanes with the
