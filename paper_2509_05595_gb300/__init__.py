@@ -219,6 +219,7 @@ def lib():
             "pamo_orient3d_batch": (ctypes.c_int, [P, i64, P, P]),
             "pamo_orient2d_batch": (ctypes.c_int, [P, i64, P, P]),
             "pamo_last_error": (ctypes.c_char_p, []),
+            "pamo_release_cached_memory": (ctypes.c_int, []),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -543,3 +544,9 @@ def pamo_orient2d_batch(P):
 
 def pamo_last_error():
     return lib().pamo_last_error().decode()
+
+
+def pamo_release_cached_memory():
+    """Return the device and pinned host memory the library keeps between
+    calls (and no live context uses) to the driver."""
+    _check(lib().pamo_release_cached_memory(), "pamo_release_cached_memory")

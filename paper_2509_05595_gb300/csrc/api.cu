@@ -11,7 +11,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <vector>
 
 #include "common.cuh"
 
@@ -39,6 +41,110 @@ int sm_count() {
 
 int default_grid() { return 4 * sm_count(); }
 
+// ---- memory -----------------------------------------------------------------
+// Device buffers come from a stream-ordered pool owned by the library (one per
+// device) whose release threshold keeps freed memory for the next call: a
+// simplification allocates its whole working set up front and frees it at the
+// end, and the default pool (threshold 0) would hand that memory back to the
+// driver at the next synchronisation and map it again for the next call.
+// Pinned host mirrors are recycled the same way.  pamo_release_cached_memory
+// returns what no live context uses.
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_mem_mu;
+cudaMemPool_t g_pools[kMaxDevices] = {};
+std::vector<std::pair<void*, size_t>> g_pinned;  // cached pinned host blocks
+constexpr size_t kPinnedCacheMax = 32;
+}  // namespace
+
+pamo_status device_pool(cudaMemPool_t* out) {
+  int dev = 0;
+  PAMO_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("device ordinal out of range for the memory pool table");
+    return PAMO_ECUDA;
+  }
+  std::lock_guard<std::mutex> lock(g_mem_mu);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    PAMO_CUDA(cudaMemPoolCreate(&pool, &props));
+    uint64_t keep = UINT64_MAX;
+    PAMO_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    g_pools[dev] = pool;
+  }
+  *out = g_pools[dev];
+  return PAMO_OK;
+}
+
+pamo_status device_alloc(void** p, size_t bytes, cudaStream_t st) {
+  *p = nullptr;
+  cudaMemPool_t pool = nullptr;
+  PAMO_TRY(device_pool(&pool));
+  cudaError_t e = cudaMallocFromPoolAsync(p, bytes > 0 ? bytes : 16, pool, st);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_fail(e, "cudaMallocFromPoolAsync");
+  }
+  return PAMO_OK;
+}
+
+// a pinned host block of at least `bytes` (the smallest cached one that fits)
+pamo_status pinned_get(void** p, size_t bytes) {
+  {
+    std::lock_guard<std::mutex> lock(g_mem_mu);
+    int best = -1;
+    for (int i = 0; i < (int)g_pinned.size(); i++)
+      if (g_pinned[i].second >= bytes && (best < 0 || g_pinned[i].second < g_pinned[best].second))
+        best = i;
+    if (best >= 0) {
+      *p = g_pinned[best].first;
+      g_pinned.erase(g_pinned.begin() + best);
+      return PAMO_OK;
+    }
+  }
+  cudaError_t e = cudaMallocHost(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_fail(e, "cudaMallocHost");
+  }
+  return PAMO_OK;
+}
+
+// back to the cache; the caller has synchronised every copy into the block
+void pinned_put(void* p, size_t bytes) {
+  if (!p) return;
+  {
+    std::lock_guard<std::mutex> lock(g_mem_mu);
+    if (g_pinned.size() < kPinnedCacheMax) {
+      g_pinned.emplace_back(p, bytes);
+      return;
+    }
+  }
+  cudaFreeHost(p);
+}
+
+pamo_status release_cached_memory() {
+  std::vector<std::pair<void*, size_t>> blocks;
+  cudaError_t first = cudaSuccess;
+  {
+    std::lock_guard<std::mutex> lock(g_mem_mu);
+    blocks.swap(g_pinned);
+    for (int d = 0; d < kMaxDevices; d++)
+      if (g_pools[d]) {
+        cudaError_t e = cudaMemPoolTrimTo(g_pools[d], 0);
+        if (first == cudaSuccess) first = e;
+      }
+  }
+  for (auto& b : blocks) cudaFreeHost(b.first);
+  if (first != cudaSuccess) return cuda_fail(first, "cudaMemPoolTrimTo");
+  return PAMO_OK;
+}
+
 pamo_status buf_reserve(Buf& b, size_t bytes, cudaStream_t st) {
   if (bytes <= b.bytes && b.p) return PAMO_OK;
   if (b.p) {
@@ -48,11 +154,7 @@ pamo_status buf_reserve(Buf& b, size_t bytes, cudaStream_t st) {
     b.bytes = 0;
   }
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMallocAsync(&b.p, bytes, st);
-  if (e != cudaSuccess) {
-    b.p = nullptr;
-    return cuda_fail(e, "cudaMallocAsync");
-  }
+  PAMO_TRY(device_alloc(&b.p, bytes, st));
   b.bytes = bytes;
   return PAMO_OK;
 }
@@ -67,12 +169,10 @@ namespace {
 
 template <typename T>
 pamo_status alloc(T** p, size_t count, cudaStream_t st) {
-  cudaError_t e = cudaMallocAsync((void**)p, sizeof(T) * (count > 0 ? count : 1), st);
-  if (e != cudaSuccess) {
-    *p = nullptr;
-    return cuda_fail(e, "cudaMallocAsync");
-  }
-  return PAMO_OK;
+  void* q = nullptr;
+  pamo_status s = device_alloc(&q, sizeof(T) * (count > 0 ? count : 1), st);
+  *p = (T*)q;
+  return s;
 }
 
 template <typename T>
@@ -122,13 +222,13 @@ void free_ctx_buffers(pamo_ctx* c) {
   release(c->mvbase, st); release(c->flags_old, st);
   release(c->vgap, st); release(c->vgap_tmp, st); release(c->pX, st);
   release(c->pprob, st); release(c->pkeep, st); release(c->qface, st);
-  if (c->mcount_h) cudaFreeHost(c->mcount_h);
+  pinned_put(c->mcount_h, sizeof(int32_t) * 3 * (size_t)c->n_mesh);
   c->mcount_h = nullptr;
   for (int r = 0; r < 3; r++) release(c->cand[r], st);
   buf_free(c->scan_tmp, st);
   buf_free(c->quad_tmp, st);
   bvh_free(c->bvh, st);
-  if (c->hc) cudaFreeHost(c->hc);
+  pinned_put(c->hc, sizeof(RoundCounters));
   c->hc = nullptr;
   for (auto& p : c->kc_pending) {
     c->ev_pool.push_back(p.second.first);
@@ -154,6 +254,8 @@ pamo_status join(pamo_ctx* c) {
 }
 
 void destroy_ctx(pamo_ctx* c) {
+  // no copy into the pinned mirrors may be in flight when they are recycled
+  cudaStreamSynchronize(c->st);
   free_ctx_buffers(c);
   cudaStreamSynchronize(c->st);
   for (cudaEvent_t& e : c->round_ev)
@@ -282,12 +384,10 @@ pamo_status alloc_state(pamo_ctx* c, int64_t nV, int64_t nF) {
   c->bvh.vgap = c->vgap;
   if (s == PAMO_OK) s = bvh_alloc(c->bvh, (int)nF, st);
   if (s == PAMO_OK) {
-    cudaError_t e = cudaMallocHost((void**)&c->hc, sizeof(RoundCounters));
-    if (e != cudaSuccess) s = cuda_fail(e, "cudaMallocHost");
+    s = pinned_get((void**)&c->hc, sizeof(RoundCounters));
   }
   if (s == PAMO_OK && M > 1) {
-    cudaError_t e = cudaMallocHost((void**)&c->mcount_h, sizeof(int32_t) * 3 * (size_t)M);
-    if (e != cudaSuccess) s = cuda_fail(e, "cudaMallocHost");
+    s = pinned_get((void**)&c->mcount_h, sizeof(int32_t) * 3 * (size_t)M);
   }
   return s;
 }
@@ -1218,6 +1318,8 @@ void pamo_default_options(pamo_options* o) {
 }
 
 const char* pamo_last_error(void) { return g_err.c_str(); }
+
+pamo_status pamo_release_cached_memory(void) { return release_cached_memory(); }
 
 pamo_status pamo_ctx_create(const float* d_V, int64_t nV, const int32_t* d_F, int64_t nF,
                             const pamo_options* opt, void* stream, pamo_ctx** out) {

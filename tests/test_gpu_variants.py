@@ -90,3 +90,24 @@ def test_input_intersection_check_refuses_bad_input():
     Vo, Fo, st, status = _pamo.pamo_simplify(torch.from_numpy(Vg), torch.from_numpy(Fg),
                                              len(Fg) // 10, check_input_intersections=1)
     assert status in ("PAMO_OK", "PAMO_ESTALL") and st["rounds"] > 0  # accepted and run
+
+
+def test_cached_memory_reuse_and_release_do_not_change_results():
+    """Back-to-back calls reuse the library's pooled device memory and pinned
+    mirrors (of other sizes too); releasing the cache between calls changes
+    nothing either."""
+    from tests.test_gpu_parity import pamo as _pamo
+    Vs, Fs = meshgen.bumped_icosphere(5, 7)
+    Vt, Ft, tt = meshgen.mesh_config("torus_64x32")
+    Vd, Fd = torch.from_numpy(Vs).cuda(), torch.from_numpy(Fs).cuda()
+    first = _pamo.pamo_simplify(Vd, Fd, len(Fs) // 20)
+    outs = []
+    for k in range(3):
+        _pamo.pamo_simplify(torch.from_numpy(Vt), torch.from_numpy(Ft), tt)  # other sizes
+        if k == 1:
+            _pamo.pamo_release_cached_memory()
+        outs.append(_pamo.pamo_simplify(Vd, Fd, len(Fs) // 20))
+    for o in outs:
+        assert o[3] == first[3] and o[2]["rounds"] == first[2]["rounds"]
+        assert torch.equal(o[0], first[0]) and torch.equal(o[1], first[1])
+    _pamo.pamo_release_cached_memory()
