@@ -852,12 +852,12 @@ pamo_status bvh_check_split(Bvh& b, const float4* pos, const int4* F, const uint
   }
   const bool many = b.n_mesh > 1;
   static const int g_trav = occ_grid(k_traverse);
-  static const int g_pairs = occ_grid(k_pairs);
+  static const int g_pairs = occ_grid(k_pairs, kItemBlock);
   k_traverse<<<g_trav, kBlock, 0, st>>>((const float*)b.nodes.p, n_dev, 0, pos, F, fdead, ftag,
                                         query_all, qlist, qcount, cb, ncand, dc,
                                         many ? b.vmesh : nullptr,
                                         many ? (const int32_t*)b.mroot.p : nullptr); note_launch();
-  k_pairs<<<g_pairs, kBlock, 0, st>>>(cb, ncand, pos, F, (const uint8_t*)b.face_aux.p, ftag, undo,
+  k_pairs<<<g_pairs, kItemBlock, 0, st>>>(cb, ncand, pos, F, (const uint8_t*)b.face_aux.p, ftag, undo,
                                    dc, b.vgap); note_launch();
   PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;

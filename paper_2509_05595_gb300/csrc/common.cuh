@@ -13,6 +13,10 @@
 namespace pamo {
 
 constexpr int kBlock = 256;
+// Blocks of the kernels with long per-item work (edge costs, the exact pair
+// test): small blocks spread a small round's items over every SM instead of
+// packing them into a few 256-thread blocks, at the same occupancy.
+constexpr int kItemBlock = 64;
 
 // ----------------------------------------------------------------------------
 // error plumbing: every host helper returns pamo_status; the message is kept
@@ -44,9 +48,9 @@ int sm_count();
 // as the SMs hold at once (one full wave), so that no block runs in a second,
 // partial wave.  Evaluated once per kernel (static at the call site).
 template <typename K>
-int occ_grid(K kernel) {
+int occ_grid(K kernel, int block = kBlock) {
   int b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kBlock, 0) != cudaSuccess || b < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, block, 0) != cudaSuccess || b < 1)
     b = 1;
   return b * sm_count();
 }

@@ -362,12 +362,12 @@ pamo_status edge_costs(pamo_ctx* c) {
   const double s2 = c->scale * c->scale, wes = c->opt.w_e * c->scale;
   const bool batch = c->n_mesh > 1;
   static const int g_reuse = occ_grid(k_edge_reuse);
-  static const int g_cost = occ_grid(k_edge_cost);
+  static const int g_cost = occ_grid(k_edge_cost, kItemBlock);
   k_edge_reuse<<<g_reuse, kBlock, 0, c->st>>>(c->E, c->vdirty, c->ivmap, c->E_prev, c->e_off_prev,
                                         c->cbits_prev, c->vbar_prev, c->link_prev, c->flags,
                                         c->key, c->vbar, c->cbits, c->link, c->dlist, c->dc,
                                         batch ? c->vmesh : nullptr, c->mactive, c->mcount); note_launch();
-  k_edge_cost<<<g_cost, kBlock, 0, c->st>>>(c->dlist, c->E, c->pos, c->K, c->F, c->vf_off, c->vf_idx,
+  k_edge_cost<<<g_cost, kItemBlock, 0, c->st>>>(c->dlist, c->E, c->pos, c->K, c->F, c->vf_off, c->vf_idx,
                                        c->flags, s2, wes, c->opt.w_s, c->key, c->vbar, c->cbits,
                                        c->link, c->dc, batch ? c->vmesh : nullptr, c->mcost,
                                        c->mactive, c->mcount); note_launch();
