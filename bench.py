@@ -40,11 +40,11 @@ CLASS_NAMES = ("adjacency", "cost", "select", "collapse", "bvh", "query", "commi
 # chain probe measured 1.25 TFLOP/s)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
-# k_edge_cost DRAM bytes per evaluated edge: 32.17 MB for 491,520 edges in the ncu capture of
+# k_edge_cost DRAM bytes per evaluated edge: 32.40 MB for 491,520 edges in the ncu capture of
 # round 0 at L7 (profiles/top_kernels_bumped_icosphere_l7.md); the traffic of a launch grows
 # with the edges it evaluates, so a launch's traffic is this times its edge count
-COST_DRAM_BYTES_PER_EDGE = 32.168e6 / 491520
-COST_FP64_PIPE_BUSY = 0.827  # same capture
+COST_DRAM_BYTES_PER_EDGE = 32.403e6 / 491520
+COST_FP64_PIPE_BUSY = 0.819  # same capture
 
 
 def max_over_ranks(x, device=None):
