@@ -36,9 +36,17 @@ CLASS_NAMES = ("adjacency", "cost", "select", "collapse", "bvh", "query", "commi
 
 
 # float64 FMA peak: 152 SMs x 2 FMA/clock/SM x 2 flop x 2.07 GHz (ncu reports a
-# float64 FMA peak of 304 thread-instructions per cycle on this GPU; an FMA
-# chain probe measured 1.25 TFLOP/s)
+# float64 FMA peak of 304 thread-instructions per cycle on this GPU;
+# pamo_measure_fp64 measures it live next to the division and root rates)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+# float64 operations of the edge-cost source (Eq. 1): per dirty edge, the
+# quadric sum, the 3x3 Cramer solve, the quadric at the placement, the edge
+# length and the cost (additions, multiplies, FMAs, min/max and compares: 85,
+# plus 3 divisions and 1 square root); per produced triangle, the quality term
+# (22, plus 1 division and 1 square root)
+COST_OPS_EDGE, COST_DIV_EDGE, COST_SQRT_EDGE = 85, 3, 1
+COST_OPS_TRI, COST_DIV_TRI, COST_SQRT_TRI = 22, 1, 1
 
 # k_edge_cost DRAM bytes per evaluated edge: 32.40 MB for 491,520 edges in the ncu capture of
 # round 0 at L7 (profiles/top_kernels_bumped_icosphere_l7.md); the traffic of a launch grows
@@ -533,6 +541,8 @@ def main():
     _, _, st_prof, _ = pamo.pamo_simplify(Vd, Fd, target, options=opts)
     dom = int(np.argmax(st_prof["class_ms"]))
     timed_opts = pamo.Options(validate_input=0, profile=1 << dom)
+    # float64 rates of this GPU (before the timed region)
+    fp64 = pamo.pamo_measure_fp64() if CLASS_NAMES[dom] == "cost" else None
     for _ in range(args.warmup):
         pamo.pamo_simplify(Vd, Fd, target, options=timed_opts)
     torch.cuda.synchronize()
@@ -582,6 +592,9 @@ def main():
         achieved = flops_per_launch / (avg_launch_ms * 1e-3) / 1e12 if avg_launch_ms > 0 else 0.0
         # two launches per round in this class (reuse + cost): edges per k_edge_cost launch
         edges_per_launch = cost_edges / max(dom_launch / 2, 1)
+        # produced triangles per launch, from the flop model (114 per edge + 32 per triangle)
+        flops_cost = flops_per_launch * 2  # the reuse launch has no flops
+        tris_per_launch = max(flops_cost - 114.0 * edges_per_launch, 0.0) / 32.0
         roof = {"bound": "alu", "kernel_class": "cost", "achieved": achieved,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                 "traffic": COST_DRAM_BYTES_PER_EDGE * edges_per_launch,
@@ -589,6 +602,24 @@ def main():
                 "ncu_fp64_pipe_busy": COST_FP64_PIPE_BUSY,
                 "peak_source": "derived: float64 FMA units x clock",
                 "launch_ms": avg_launch_ms, "class_share": share}
+        if fp64 is not None:
+            # the float64 pipe time the source's operations need at the measured
+            # rates, against the event-timed class time of a round (k_edge_reuse +
+            # k_edge_cost: two launches)
+            t_model = ((COST_OPS_EDGE * edges_per_launch + COST_OPS_TRI * tris_per_launch)
+                       / fp64["fma_per_s"]
+                       + (COST_DIV_EDGE * edges_per_launch + COST_DIV_TRI * tris_per_launch)
+                       / max(fp64["div_per_s"], 1.0)
+                       + (COST_SQRT_EDGE * edges_per_launch + COST_SQRT_TRI * tris_per_launch)
+                       / max(fp64["sqrt_per_s"], 1.0))
+            roof["fp64_measured"] = {"fma_tflops": 2 * fp64["fma_per_s"] / 1e12,
+                                     "div_per_s": fp64["div_per_s"],
+                                     "sqrt_per_s": fp64["sqrt_per_s"]}
+            roof["pipe_model"] = {"edges_per_launch": edges_per_launch,
+                                  "tris_per_launch": tris_per_launch,
+                                  "model_ms": t_model * 1e3,
+                                  "frac": (t_model * 1e3 / (2 * avg_launch_ms)
+                                           if avg_launch_ms else 0.0)}
     else:
         peak, peak_kind = peaks()
         bytes_per_launch = dom_bytes / max(dom_launch, 1)

@@ -373,6 +373,15 @@ pamo_status pamo_orient3d_batch(const float* d_P, int64_t n, int8_t* d_out,
 pamo_status pamo_orient2d_batch(const float* d_P, int64_t n, int8_t* d_out,
                                 void* stream);
 
+/* Measured float64 throughput of the current device (measurement support for
+ * the roofline of the edge cost, whose float64 arithmetic includes divisions
+ * and square roots that the hardware runs as instruction sequences).  Runs a
+ * few short probe kernels (about 0.1 s) on `stream` and synchronises it.
+ * h_rates (host, 3 doubles) receives fused multiply-adds per second,
+ * divisions per second and square roots per second over the whole GPU
+ * (divisions and roots timed beyond an identical loop without them). */
+pamo_status pamo_measure_fp64(void* stream, double* h_rates);
+
 /* Thread-local message of the last failing call ("" if none). */
 const char* pamo_last_error(void);
 

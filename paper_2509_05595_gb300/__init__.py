@@ -220,6 +220,7 @@ def lib():
             "pamo_orient2d_batch": (ctypes.c_int, [P, i64, P, P]),
             "pamo_last_error": (ctypes.c_char_p, []),
             "pamo_release_cached_memory": (ctypes.c_int, []),
+            "pamo_measure_fp64": (ctypes.c_int, [P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -544,6 +545,15 @@ def pamo_orient2d_batch(P):
 
 def pamo_last_error():
     return lib().pamo_last_error().decode()
+
+
+def pamo_measure_fp64():
+    """Measured float64 rates of the current GPU: dict of fused multiply-adds,
+    divisions and square roots per second."""
+    out = np.zeros(3, np.float64)
+    _check(lib().pamo_measure_fp64(_stream(), out.ctypes.data_as(ctypes.c_void_p)),
+           "pamo_measure_fp64")
+    return dict(fma_per_s=float(out[0]), div_per_s=float(out[1]), sqrt_per_s=float(out[2]))
 
 
 def pamo_release_cached_memory():
