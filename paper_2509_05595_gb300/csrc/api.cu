@@ -216,7 +216,8 @@ void free_ctx_buffers(pamo_ctx* c) {
   release(c->E_prev, st); release(c->e_off_prev, st); release(c->cbits, st);
   release(c->cbits_prev, st); release(c->vbar_prev, st); release(c->link, st);
   release(c->link_prev, st); release(c->ivmap, st); release(c->vsurv, st); release(c->vdirty, st);
-  release(c->dlist, st); release(c->scan_sums, st);
+  release(c->dlist, st); release(c->scan_sums, st); release(c->scan_sums2, st);
+  release(c->dbufF, st);
   release(c->vmesh, st); release(c->vmesh_tmp, st); release(c->voff_d, st); release(c->foff_d, st);
   release(c->mframe, st); release(c->mcost, st); release(c->mactive, st); release(c->mcount, st);
   release(c->mvbase, st); release(c->flags_old, st);
@@ -348,7 +349,7 @@ pamo_status alloc_state(pamo_ctx* c, int64_t nV, int64_t nF) {
   A(win, c->Emax); A(wscan, c->Emax + 1); A(wlist, c->Emax); A(standing, c->Emax);
   A(undo, c->Emax); A(ftag, nF); A(qlist, nF);
   A(fdead, nF); A(vdead, nV); A(vmap, nV + 1);
-  A(dbuf, mx + 1); A(flags, c->Emax); A(flags_next, c->Emax); A(dc, 1);
+  A(dbuf, mx + 1); A(dbufF, nF + 1); A(flags, c->Emax); A(flags_next, c->Emax); A(dc, 1);
   A(E_prev, c->Emax); A(e_off_prev, nV + 1); A(cbits, c->Emax); A(cbits_prev, c->Emax);
   A(vbar_prev, c->Emax); A(link, c->Emax); A(link_prev, c->Emax); A(ivmap, nV);
   A(vsurv, nV); A(vdirty, nV); A(dlist, c->Emax); A(vgap, nV); A(vgap_tmp, nV);
@@ -357,6 +358,8 @@ pamo_status alloc_state(pamo_ctx* c, int64_t nV, int64_t nF) {
   }
   if (c->opt.recompute_quadrics) A(qface, 10 * nF);
   A(scan_sums, scan_sums_count(std::max<int64_t>(c->Emax, mx + 1)));
+  c->scan_span = scan_sums_count(mx + 1);
+  A(scan_sums2, 3 * c->scan_span);
   // candidate pairs of the split check: a changed face has at most 3
   // edge-neighbours; vertex-neighbours and other overlaps are bounded
   // generously, and an overflow falls back to the fused check
@@ -376,6 +379,8 @@ pamo_status alloc_state(pamo_ctx* c, int64_t nV, int64_t nF) {
   if (s == PAMO_OK) {  // read by the proposal's features before the first check / commit
     cudaError_t e = cudaMemsetAsync(c->vgap, 0x7f, sizeof(uint32_t) * (size_t)nV, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->vsurv, 0, (size_t)nV, st);
+    // per-vertex counts start at zero (each use leaves them zeroed)
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->vcount, 0, sizeof(int32_t) * (size_t)(nV + 1), st);
     if (e != cudaSuccess) s = cuda_fail(e, "cudaMemsetAsync");
   }
   c->bvh.n_mesh = M;
@@ -757,7 +762,7 @@ pamo_status phase_commit(pamo_ctx* c) {
   kc_begin(c, PAMO_KC_COMMIT);
   PAMO_TRY(commit_compact(c));
   if (c->opt.check_mode != 3)
-    PAMO_TRY(bvh_compact_order(c->bvh, c->fdead, c->dbuf, &dc->goF, &dc->goFn, c->grid, c->st));
+    PAMO_TRY(bvh_compact_order(c->bvh, c->fdead, c->dbufF, &dc->goF, &dc->goFn, c->grid, c->st));
   PAMO_TRY(commit_sizes(c));
   // M_s read (positions, quadrics, faces, liveness), M_1 written, vertex map
   kc_end(c, PAMO_KC_COMMIT, (double)c->nV * (16 + 80 + 1 + 4) * 2 + (double)c->nF * (16 + 1 + 4) * 2);

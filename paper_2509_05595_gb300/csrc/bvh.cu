@@ -259,21 +259,15 @@ __global__ void k_karras(const unsigned* __restrict__ k, const unsigned* __restr
   }
 }
 
-__global__ void k_order_alive(const int32_t* __restrict__ vals, const int* n_dev,
-                              const uint8_t* __restrict__ fdead, uint8_t* __restrict__ alive) {
-  const int n = *n_dev;
-  GRID_STRIDE(i, n) alive[i] = fdead[vals[i]] ? 0 : 1;
-}
-
 __global__ void k_order_write(const int32_t* __restrict__ vals, const unsigned* __restrict__ keys,
                               const unsigned* __restrict__ hk, const int* n_dev,
-                              const uint8_t* __restrict__ alive, const int32_t* __restrict__ pos,
+                              const uint8_t* __restrict__ fdead, const int32_t* __restrict__ pos,
                               const int32_t* __restrict__ dead_before, int32_t* __restrict__ out,
                               unsigned* __restrict__ okeys, unsigned* __restrict__ ohk) {
   const int n = *n_dev;
   GRID_STRIDE(i, n) {
-    if (!alive[i]) continue;
     const int f = vals[i];
+    if (fdead[f]) continue;
     out[pos[i]] = f - dead_before[f];
     okeys[pos[i]] = keys[i];
     if (hk) ohk[pos[i]] = hk[i];
@@ -819,16 +813,13 @@ pamo_status bvh_compact_order(Bvh& b, const uint8_t* fdead, const int32_t* dead_
                               const int* n_old_dev, const int* n_new_dev, int grid,
                               cudaStream_t st) {
   // runs on every check outcome (sizes 0 when the round does not commit), so
-  // it must leave the tree intact: its own position buffer, and face info
-  // (rebuilt at the next refit) is only written for committed rounds
-  uint8_t* alive = (uint8_t*)b.face_aux.p;
-  int32_t* posn = (int32_t*)b.posn.p;
+  // it must leave the tree intact: the positions of the live leaves are in
+  // their own buffer (posn, scanned by the caller)
+  const int32_t* posn = (const int32_t*)b.posn.p;
   const bool many = b.n_mesh > 1;
-  k_order_alive<<<grid, kBlock, 0, st>>>((const int32_t*)b.vals.p, n_old_dev, fdead, alive); note_launch();
-  PAMO_TRY(scan_dev_u8(alive, n_old_dev, posn, (int32_t*)b.sums.p, grid, st));
   k_order_write<<<grid, kBlock, 0, st>>>((const int32_t*)b.vals.p, (const unsigned*)b.keys.p,
                                          many ? (const unsigned*)b.hkeys.p : nullptr, n_old_dev,
-                                         alive, posn, dead_before, (int32_t*)b.vals2.p,
+                                         fdead, posn, dead_before, (int32_t*)b.vals2.p,
                                          (unsigned*)b.keys2.p,
                                          many ? (unsigned*)b.hkeys2.p : nullptr); note_launch();
   k_copy_order<<<grid, kBlock, 0, st>>>((const int32_t*)b.vals2.p, (const unsigned*)b.keys2.p,

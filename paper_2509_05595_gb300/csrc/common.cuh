@@ -214,7 +214,8 @@ struct pamo_ctx {
   uint8_t* fdead = nullptr;     // [nF0]
   uint8_t* vdead = nullptr;     // [nV0]
   int32_t* vmap = nullptr;      // [nV0+1]
-  int32_t* dbuf = nullptr;      // [max(nV0,nF0)+1] dead-before scan
+  int32_t* dbuf = nullptr;      // [max(nV0,nF0)+1] dead-before scan (vertices)
+  int32_t* dbufF = nullptr;     // [nF0+1] dead-before scan of the faces
   // --- invalid-edge flags (sorted vertex pairs a<<32|b)
   unsigned long long* flags = nullptr;       // [Emax]
   unsigned long long* flags_next = nullptr;  // [Emax]
@@ -243,6 +244,8 @@ struct pamo_ctx {
   // --- scratch
   pamo::Buf scan_tmp, quad_tmp;
   int32_t* scan_sums = nullptr;  // tile sums of the device-sized scans
+  int32_t* scan_sums2 = nullptr; // three more tile-sum buffers (the commit's batched scans)
+  int64_t scan_span = 0;         // words per tile-sum buffer in scan_sums2
   int grid = 608;                // fixed grid of the per-round kernels
   pamo::Bvh bvh;
   // CUDA graphs of a round (A: full round, B: re-check after an undo); [carry]
@@ -298,6 +301,20 @@ pamo_status scan_dev_u8(const uint8_t* in, const int* n_dev, int32_t* out, int32
 // the same over the complement (counts the zero bytes)
 pamo_status scan_dev_u8_not(const uint8_t* in, const int* n_dev, int32_t* out, int32_t* sums,
                             int grid, cudaStream_t st);
+// Up to kMaxScanSegs independent byte scans in one set of three launches.
+// Item j of a segment is in[j] (in[gather[j]] when gather is set), counted as
+// itself or, with invert, as 1 for a zero byte; out[0..n] as above, n from
+// the device; each segment has its own tile-sum buffer.
+struct ScanSeg {
+  const uint8_t* in;
+  const int32_t* gather;
+  const int* n;
+  int32_t* out;
+  int32_t* sums;
+  int invert;
+};
+constexpr int kMaxScanSegs = 4;
+pamo_status scan_dev_u8_multi(const ScanSeg* segs, int count, int grid, cudaStream_t st);
 
 // mesh.cu -------------------------------------------------------------------
 pamo_status mesh_bbox(const float4* pos, int64_t nV, float lo[3], float hi[3],
@@ -380,6 +397,8 @@ pamo_status bvh_check_split(Bvh& b, const float4* pos, const int4* F, const uint
                             cudaStream_t st);
 // After a commit: keep the leaf order for the compacted faces (stable filter
 // of the current order through fdead / dead_before); sizes from the device.
+// b.posn must hold the exclusive scan of the live leaves (fdead[vals[i]] == 0,
+// i < *n_old_dev), which the commit computes with its other scans.
 pamo_status bvh_compact_order(Bvh& b, const uint8_t* fdead, const int32_t* dead_before,
                               const int* n_old_dev, const int* n_new_dev, int grid,
                               cudaStream_t st);

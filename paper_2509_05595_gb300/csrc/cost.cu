@@ -120,8 +120,16 @@ __global__ void __launch_bounds__(kBlock) k_edge_reuse(
     float4* __restrict__ vbar, uint32_t* __restrict__ cbits, uint8_t* __restrict__ link,
     int32_t* __restrict__ dlist, RoundCounters* __restrict__ dc,
     const int32_t* __restrict__ vmesh, const uint8_t* __restrict__ mactive,
-    int32_t* __restrict__ melig) {
+    int32_t* __restrict__ melig, unsigned long long* __restrict__ vkey) {
   const int nE = dc->nE;
+  // the per-vertex minima of the selection start from "no key" (nothing
+  // reads them before the selection)
+  {
+    const int nV = dc->nV;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nV;
+         v += (int64_t)gridDim.x * blockDim.x)
+      vkey[v] = ~0ull;
+  }
   const int nflags = dc->nflags;
   const unsigned max_bits = dc->max_bits;
   const bool all_dirty = !dc->have_prev;
@@ -366,7 +374,8 @@ pamo_status edge_costs(pamo_ctx* c) {
   k_edge_reuse<<<g_reuse, kBlock, 0, c->st>>>(c->E, c->vdirty, c->ivmap, c->E_prev, c->e_off_prev,
                                         c->cbits_prev, c->vbar_prev, c->link_prev, c->flags,
                                         c->key, c->vbar, c->cbits, c->link, c->dlist, c->dc,
-                                        batch ? c->vmesh : nullptr, c->mactive, c->mcount); note_launch();
+                                        batch ? c->vmesh : nullptr, c->mactive, c->mcount,
+                                        c->vkey); note_launch();
   k_edge_cost<<<g_cost, kItemBlock, 0, c->st>>>(c->dlist, c->E, c->pos, c->K, c->F, c->vf_off, c->vf_idx,
                                        c->flags, s2, wes, c->opt.w_s, c->key, c->vbar, c->cbits,
                                        c->link, c->dc, batch ? c->vmesh : nullptr, c->mcost,

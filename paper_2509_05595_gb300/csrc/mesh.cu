@@ -305,15 +305,18 @@ __global__ void k_count_corners(const int4* __restrict__ F, const int* nF_dev, i
   }
 }
 
+// each corner takes a slot of its vertex's segment by counting the vertex's
+// corner count down to zero (slot order is arbitrary: the segments are sorted
+// next), which leaves the counts zeroed
 __global__ void k_fill_corners(const int4* __restrict__ F, const int* nF_dev, int nF_host,
-                               const int32_t* __restrict__ off, int32_t* __restrict__ cur,
+                               const int32_t* __restrict__ off, int32_t* __restrict__ cnt,
                                int32_t* __restrict__ idx) {
   const int n = dev_n(nF_dev, nF_host);
   GRID_STRIDE(f, n) {
     const int4 t = F[f];
-    idx[off[t.x] + atomicAdd(&cur[t.x], 1)] = (int32_t)f;
-    idx[off[t.y] + atomicAdd(&cur[t.y], 1)] = (int32_t)f;
-    idx[off[t.z] + atomicAdd(&cur[t.z], 1)] = (int32_t)f;
+    idx[off[t.x] + atomicSub(&cnt[t.x], 1) - 1] = (int32_t)f;
+    idx[off[t.y] + atomicSub(&cnt[t.y], 1) - 1] = (int32_t)f;
+    idx[off[t.z] + atomicSub(&cnt[t.z], 1) - 1] = (int32_t)f;
   }
 }
 
@@ -366,11 +369,30 @@ __global__ void k_count_edges(const int4* __restrict__ F, const int32_t* __restr
   }
 }
 
+// the edge count; a closed triangle mesh has exactly 3F/2 edges, anything
+// else means a non-manifold mesh (the host reports it at the next sync)
+__device__ __forceinline__ void edge_total(const int32_t* __restrict__ eoff,
+                                           RoundCounters* __restrict__ dc, int64_t cap) {
+  const int ne = eoff[dc->nV];
+  dc->ne_actual = ne;
+  dc->nV_edges = dc->nV;
+  const int want = (3 * dc->nF) / 2;
+  if (ne != want || ne > cap) dc->bad |= 64;
+  dc->nE = ne <= cap ? ne : (int)cap;
+}
+
+// Each vertex writes its edges to higher-numbered neighbours, sorted, at its
+// offset; the per-vertex counts are zeroed for the next corner count (the
+// next round's vertices are a prefix of these), and one thread sets the
+// edge total (only the counters read it before the next kernel).
 __global__ void k_write_edges(const int4* __restrict__ F, const int32_t* __restrict__ off,
-                              const int32_t* __restrict__ idx, const int* nV_dev,
-                              const int32_t* __restrict__ eoff, int64_t cap, int2* __restrict__ E) {
-  const int nV = *nV_dev;
+                              const int32_t* __restrict__ idx, RoundCounters* __restrict__ dc,
+                              const int32_t* __restrict__ eoff, int64_t cap, int2* __restrict__ E,
+                              int32_t* __restrict__ cnt) {
+  const int nV = dc->nV;
+  if (blockIdx.x == 0 && threadIdx.x == 0) edge_total(eoff, dc, cap);
   GRID_STRIDE(v, nV) {
+    cnt[v] = 0;
     const int base = eoff[v];
     int n = 0;
     for (int s = off[v]; s < off[v + 1]; s++) {
@@ -387,18 +409,6 @@ __global__ void k_write_edges(const int4* __restrict__ F, const int32_t* __restr
       n++;
     }
   }
-}
-
-// the edge count; a closed triangle mesh has exactly 3F/2 edges, anything
-// else means a non-manifold mesh (the host reports it at the next sync)
-__global__ void k_edge_total(const int32_t* __restrict__ eoff, RoundCounters* __restrict__ dc,
-                             int64_t cap) {
-  const int ne = eoff[dc->nV];
-  dc->ne_actual = ne;
-  dc->nV_edges = dc->nV;
-  const int want = (3 * dc->nF) / 2;
-  if (ne != want || ne > cap) dc->bad |= 64;
-  dc->nE = ne <= cap ? ne : (int)cap;
 }
 
 // start of a round: zero the round's counters (the words after the persistent
@@ -575,11 +585,18 @@ __global__ void k_undone_pairs(const int32_t* __restrict__ wlist, const int2* __
   }
 }
 
-__global__ void k_clear2(uint8_t* __restrict__ a, uint8_t* __restrict__ b, const int* n_dev) {
+// clear two byte arrays over the new vertices, and move the per-vertex words
+// that the compaction wrote to scratch (clearance; a batch's vertex -> mesh
+// map, when set) back to their arrays
+__global__ void k_clear2(uint8_t* __restrict__ a, uint8_t* __restrict__ b, const int* n_dev,
+                         uint32_t* __restrict__ w0, const uint32_t* __restrict__ w0_src,
+                         int32_t* __restrict__ w1, const int32_t* __restrict__ w1_src) {
   const int n = *n_dev;
   GRID_STRIDE(i, n) {
     a[i] = 0;
     b[i] = 0;
+    w0[i] = w0_src[i];
+    if (w1) w1[i] = w1_src[i];
   }
 }
 
@@ -734,10 +751,10 @@ pamo_status build_vertex_faces(pamo_ctx* c) {
   cudaStream_t st = c->st;
   RoundCounters* dc = c->dc;
   const int G = c->grid;
-  PAMO_TRY(fill_dev4(c->vcount, &dc->nV, 1, 0u, G, st));
+  // vcount is zero here: zeroed at allocation, after each use as fill
+  // cursors below, and by k_write_edges after its use as edge counts
   k_count_corners<<<G, kBlock, 0, st>>>(c->F, &dc->nF, 0, c->vcount); note_launch();
   PAMO_TRY(scan_dev_i32(c->vcount, &dc->nV, c->vf_off, c->scan_sums, G, st));
-  PAMO_TRY(fill_dev4(c->vcount, &dc->nV, 1, 0u, G, st));
   static const int g_fill = occ_grid(k_fill_corners);
   static const int g_sort = occ_grid(k_sort_segments);
   k_fill_corners<<<g_fill, kBlock, 0, st>>>(c->F, &dc->nF, 0, c->vf_off, c->vcount, c->vf_idx); note_launch();
@@ -789,9 +806,8 @@ pamo_status build_edges(pamo_ctx* c) {
   static const int g_write = occ_grid(k_write_edges);
   k_count_edges<<<g_count, kBlock, 0, st>>>(c->F, c->vf_off, c->vf_idx, &dc->nV, c->vcount); note_launch();
   PAMO_TRY(scan_dev_i32(c->vcount, &dc->nV, c->e_off, c->scan_sums, G, st));
-  k_write_edges<<<g_write, kBlock, 0, st>>>(c->F, c->vf_off, c->vf_idx, &dc->nV, c->e_off, c->Emax,
-                                      c->E); note_launch();
-  k_edge_total<<<1, 1, 0, st>>>(c->e_off, dc, c->Emax); note_launch();
+  k_write_edges<<<g_write, kBlock, 0, st>>>(c->F, c->vf_off, c->vf_idx, dc, c->e_off, c->Emax,
+                                            c->E, c->vcount); note_launch();
   PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;
 }
@@ -826,27 +842,37 @@ pamo_status commit_compact(pamo_ctx* c) {
   cudaStream_t st = c->st;
   RoundCounters* dc = c->dc;
   const int G = c->grid;
-  // vertices: new id = old id - (dead vertices before it)
-  PAMO_TRY(scan_dev_u8(c->vdead, &dc->goV, c->dbuf, c->scan_sums, G, st));
+  // the commit's independent scans in one set of launches: dead vertices and
+  // dead faces before each (new id = old id - dead before it), undone winners
+  // (next round's flags), and the live leaves of the LBVH order
+  {
+    ScanSeg seg[4];
+    int ns = 0;
+    seg[ns++] = ScanSeg{c->vdead, nullptr, &dc->goV, c->dbuf, c->scan_sums, 0};
+    seg[ns++] = ScanSeg{c->fdead, nullptr, &dc->goF, c->dbufF, c->scan_sums2, 0};
+    seg[ns++] = ScanSeg{c->standing, nullptr, &dc->goW, c->wscan, c->scan_sums2 + c->scan_span, 1};
+    if (c->opt.check_mode != 3)
+      seg[ns++] = ScanSeg{c->fdead, (const int32_t*)c->bvh.vals.p, &dc->goF,
+                          (int32_t*)c->bvh.posn.p, c->scan_sums2 + 2 * c->scan_span, 1};
+    PAMO_TRY(scan_dev_u8_multi(seg, ns, G, st));
+  }
   const bool batch = c->n_mesh > 1;
   k_compact_vertices<<<G, kBlock, 0, st>>>(c->pos_s, c->K_s, c->vdead, c->dbuf, &dc->goV, c->pos,
                                            c->K, c->vmap, c->ivmap, batch ? c->vmesh : nullptr,
                                            c->vmesh_tmp, c->vgap, c->vgap_tmp); note_launch();
   // faces, corners remapped
-  PAMO_TRY(scan_dev_u8(c->fdead, &dc->goF, c->dbuf, c->scan_sums, G, st));
-  k_compact_faces<<<G, kBlock, 0, st>>>(c->F_s, c->fdead, c->dbuf, &dc->goF, c->vmap, c->F); note_launch();
+  k_compact_faces<<<G, kBlock, 0, st>>>(c->F_s, c->fdead, c->dbufF, &dc->goF, c->vmap, c->F); note_launch();
   // undone winners -> next round's flag candidates (sorted vertex pairs)
-  PAMO_TRY(scan_dev_u8_not(c->standing, &dc->goW, c->wscan, c->scan_sums, G, st));
   k_undone_pairs<<<G, kBlock, 0, st>>>(c->wlist, c->E, c->standing, c->wscan, dc, c->vmap, c->flags,
                                        c->flags_next, batch ? c->vmesh : nullptr, c->mcount,
                                        c->n_mesh); note_launch();
   if (batch) {  // goVn is set by k_undone_pairs
     k_remap_flags<<<G, kBlock, 0, st>>>(c->flags, dc, c->vmap, c->flags_old); note_launch();
-    PAMO_TRY(copy_dev(c->vmesh, c->vmesh_tmp, &dc->goVn, 0, sizeof(int32_t), G, st));
   }
-  PAMO_TRY(copy_dev(c->vgap, c->vgap_tmp, &dc->goVn, 0, sizeof(uint32_t), G, st));
-  // dirty vertices of the next round (survivors and their neighbours)
-  k_clear2<<<G, kBlock, 0, st>>>(c->vsurv, c->vdirty, &dc->goVn); note_launch();
+  // dirty vertices of the next round (survivors and their neighbours); the
+  // compacted clearance (and vertex -> mesh map) back from scratch
+  k_clear2<<<G, kBlock, 0, st>>>(c->vsurv, c->vdirty, &dc->goVn, c->vgap, c->vgap_tmp,
+                                 batch ? c->vmesh : nullptr, c->vmesh_tmp); note_launch();
   k_mark_survivors<<<G, kBlock, 0, st>>>(c->wlist, c->E, c->standing, &dc->goW, c->vmap, c->vsurv); note_launch();
   k_mark_dirty<<<G, kBlock, 0, st>>>(c->F, &dc->goFn, c->vsurv, c->vdirty); note_launch();
   PAMO_CUDA(cudaGetLastError());

@@ -19,11 +19,6 @@ namespace {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); \
        i += (int64_t)gridDim.x * blockDim.x)
 
-__global__ void k_fill_vkey(unsigned long long* __restrict__ vkey, const RoundCounters* __restrict__ dc) {
-  const int nV = dc->nV;
-  GRID_STRIDE(v, nV) vkey[v] = ~0ull;
-}
-
 __global__ void k_vertex_min(const int2* __restrict__ E, const unsigned long long* __restrict__ key,
                              const RoundCounters* __restrict__ dc,
                              unsigned long long* __restrict__ vkey) {
@@ -322,7 +317,7 @@ pamo_status trim_winners(pamo_ctx* c) {
 pamo_status select_winners(pamo_ctx* c) {
   cudaStream_t st = c->st;
   const int G = c->grid;
-  k_fill_vkey<<<G, kBlock, 0, st>>>(c->vkey, c->dc); note_launch();
+  // vkey was reset to "no key" by k_edge_reuse
   k_vertex_min<<<G, kBlock, 0, st>>>(c->E, c->key, c->dc, c->vkey); note_launch();
   static const int g_select = occ_grid(k_select);
   k_select<<<g_select, kBlock, 0, st>>>(c->E, c->key, c->dc, c->vkey, c->F, c->vf_off, c->vf_idx, c->win); note_launch();
