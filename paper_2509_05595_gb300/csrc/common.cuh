@@ -284,23 +284,13 @@ void kc_resolve(pamo_ctx* c);
 
 // scan.cu -------------------------------------------------------------------
 // Exclusive prefix sum of n int32 (or uint8 flags) into out[0..n]; out[n] is
-// the total.  Deterministic.  Eager forms take a host n (tmp grown as needed);
-// the _dev forms read n from device memory and use the caller's tile-sum
-// buffer (scan_sums_count(n_max) words) and a fixed grid.
+// the total.  Deterministic.  n is read from device memory; the caller gives
+// the tile-sum buffer (scan_sums_count(n_max) words) and a fixed grid.
 int64_t scan_sums_count(int64_t n);
-pamo_status exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, Buf& tmp,
-                               cudaStream_t st);
-pamo_status exclusive_scan_u8(const uint8_t* in, int32_t* out, int64_t n, Buf& tmp,
-                              cudaStream_t st);
-pamo_status exclusive_scan_i32_into(const int32_t* in, int32_t* out, int64_t n, int32_t* sums,
-                                    cudaStream_t st);
 pamo_status scan_dev_i32(const int32_t* in, const int* n_dev, int32_t* out, int32_t* sums, int grid,
                          cudaStream_t st);
 pamo_status scan_dev_u8(const uint8_t* in, const int* n_dev, int32_t* out, int32_t* sums, int grid,
                         cudaStream_t st);
-// the same over the complement (counts the zero bytes)
-pamo_status scan_dev_u8_not(const uint8_t* in, const int* n_dev, int32_t* out, int32_t* sums,
-                            int grid, cudaStream_t st);
 // Up to kMaxScanSegs independent byte scans in one set of three launches.
 // Item j of a segment is in[j] (in[gather[j]] when gather is set), counted as
 // itself or, with invert, as 1 for a zero byte; out[0..n] as above, n from
@@ -342,11 +332,6 @@ pamo_status mesh_bbox_batch(const float4* pos, const int64_t* d_voff, int M, uns
 pamo_status store_mesh_batch(const float4* pos, int64_t nV, const int4* F, int64_t nF,
                              const int32_t* vmesh, const int32_t* d_vbase, float* d_V,
                              int32_t* d_F, cudaStream_t st);
-// copy (*n_dev + add) elements of elem_bytes; fill (*n_dev + add) words / bytes
-pamo_status copy_dev(void* dst, const void* src, const int* n_dev, int add, size_t elem_bytes,
-                     int grid, cudaStream_t st);
-pamo_status fill_dev4(void* p, const int* n_dev, int add, uint32_t v, int grid, cudaStream_t st);
-pamo_status fill_dev1(void* p, const int* n_dev, uint8_t v, int grid, cudaStream_t st);
 
 // cost.cu -------------------------------------------------------------------
 pamo_status edge_costs(pamo_ctx* c);

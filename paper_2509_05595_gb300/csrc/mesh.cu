@@ -264,35 +264,6 @@ __global__ void k_check_vertices(const int4* __restrict__ F, const int32_t* __re
   if (steps != deg || cur != start) atomicOr(bad, 32);
 }
 
-// ---- utilities over device-sized ranges ------------------------------------
-// copies (*n_dev + add) * words words
-__global__ void k_copy16(uint4* __restrict__ dst, const uint4* __restrict__ src, const int* n_dev,
-                         int add, int words) {
-  const int64_t n = (int64_t)(*n_dev + add) * words;
-  GRID_STRIDE(i, n) dst[i] = src[i];
-}
-
-__global__ void k_copy4(uint32_t* __restrict__ dst, const uint32_t* __restrict__ src,
-                        const int* n_dev, int add, int words) {
-  const int64_t n = (int64_t)(*n_dev + add) * words;
-  GRID_STRIDE(i, n) dst[i] = src[i];
-}
-
-__global__ void k_copy1(uint8_t* __restrict__ dst, const uint8_t* __restrict__ src, const int* n_dev) {
-  const int64_t n = *n_dev;
-  GRID_STRIDE(i, n) dst[i] = src[i];
-}
-
-__global__ void k_fill4(uint32_t* __restrict__ p, const int* n_dev, int add, uint32_t v) {
-  const int64_t n = (int64_t)(*n_dev + add);
-  GRID_STRIDE(i, n) p[i] = v;
-}
-
-__global__ void k_fill1(uint8_t* __restrict__ p, const int* n_dev, uint8_t v) {
-  const int64_t n = *n_dev;
-  GRID_STRIDE(i, n) p[i] = v;
-}
-
 // ---- vertex -> faces ------------------------------------------------------
 __global__ void k_count_corners(const int4* __restrict__ F, const int* nF_dev, int nF_host,
                                 int32_t* __restrict__ cnt) {
@@ -717,33 +688,6 @@ pamo_status mesh_bbox(const float4* pos, int64_t nV, float lo[3], float hi[3], B
                       cudaStream_t st) {
   PAMO_TRY(buf_reserve(tmp, 64, st));
   return mesh_bbox_into(pos, nV, (unsigned*)tmp.p, lo, hi, st);
-}
-
-pamo_status copy_dev(void* dst, const void* src, const int* n_dev, int add, size_t elem_bytes,
-                     int grid, cudaStream_t st) {
-  if (elem_bytes % 16 == 0) {
-    k_copy16<<<grid, kBlock, 0, st>>>((uint4*)dst, (const uint4*)src, n_dev, add,
-                                      (int)(elem_bytes / 16)); note_launch();
-  } else if (elem_bytes % 4 == 0) {
-    k_copy4<<<grid, kBlock, 0, st>>>((uint32_t*)dst, (const uint32_t*)src, n_dev, add,
-                                     (int)(elem_bytes / 4)); note_launch();
-  } else {
-    k_copy1<<<grid, kBlock, 0, st>>>((uint8_t*)dst, (const uint8_t*)src, n_dev); note_launch();
-  }
-  PAMO_CUDA(cudaGetLastError());
-  return PAMO_OK;
-}
-
-pamo_status fill_dev4(void* p, const int* n_dev, int add, uint32_t v, int grid, cudaStream_t st) {
-  k_fill4<<<grid, kBlock, 0, st>>>((uint32_t*)p, n_dev, add, v); note_launch();
-  PAMO_CUDA(cudaGetLastError());
-  return PAMO_OK;
-}
-
-pamo_status fill_dev1(void* p, const int* n_dev, uint8_t v, int grid, cudaStream_t st) {
-  k_fill1<<<grid, kBlock, 0, st>>>((uint8_t*)p, n_dev, v); note_launch();
-  PAMO_CUDA(cudaGetLastError());
-  return PAMO_OK;
 }
 
 // vertex -> incident faces of the current mesh (device sizes)

@@ -257,33 +257,11 @@ __global__ void k_multi_tile_apply(ScanSegs g) {
   }
 }
 
-int eager_grid(int64_t n) {
-  int64_t t = (n + kTile - 1) / kTile;
-  return (int)(t < 1 ? 1 : (t > 4096 ? 4096 : t));
-}
-
 }  // namespace
 
 int64_t scan_sums_count(int64_t n) {
   int64_t tiles = (n + kTile - 1) / kTile;
   return (tiles < 1 ? 1 : tiles) + 1;
-}
-
-pamo_status exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, Buf& tmp,
-                               cudaStream_t st) {
-  PAMO_TRY(buf_reserve(tmp, sizeof(int32_t) * scan_sums_count(n), st));
-  return scan_launch<int32_t>(in, nullptr, (int)n, out, (int32_t*)tmp.p, eager_grid(n), st);
-}
-
-pamo_status exclusive_scan_u8(const uint8_t* in, int32_t* out, int64_t n, Buf& tmp,
-                              cudaStream_t st) {
-  PAMO_TRY(buf_reserve(tmp, sizeof(int32_t) * scan_sums_count(n), st));
-  return scan_launch<uint8_t>(in, nullptr, (int)n, out, (int32_t*)tmp.p, eager_grid(n), st);
-}
-
-pamo_status exclusive_scan_i32_into(const int32_t* in, int32_t* out, int64_t n, int32_t* sums,
-                                    cudaStream_t st) {
-  return scan_launch<int32_t>(in, nullptr, (int)n, out, sums, eager_grid(n), st);
 }
 
 pamo_status scan_dev_i32(const int32_t* in, const int* n_dev, int32_t* out, int32_t* sums, int grid,
@@ -294,11 +272,6 @@ pamo_status scan_dev_i32(const int32_t* in, const int* n_dev, int32_t* out, int3
 pamo_status scan_dev_u8(const uint8_t* in, const int* n_dev, int32_t* out, int32_t* sums, int grid,
                         cudaStream_t st) {
   return scan_launch<uint8_t>(in, n_dev, 0, out, sums, grid, st);
-}
-
-pamo_status scan_dev_u8_not(const uint8_t* in, const int* n_dev, int32_t* out, int32_t* sums,
-                            int grid, cudaStream_t st) {
-  return scan_launch<uint8_t, true>(in, n_dev, 0, out, sums, grid, st);
 }
 
 pamo_status scan_dev_u8_multi(const ScanSeg* segs, int count, int grid, cudaStream_t st) {
