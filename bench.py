@@ -313,7 +313,7 @@ def run_batch_bench(args, world, rank):
             "autotune": {"resort_percent": opts.resort_percent,
                          "grid_blocks_per_sm": opts.grid_blocks_per_sm,
                          "trials_ms": [round(t, 2) for t in trials],
-                         "trials": "resort 25/50/75/100 at 4 blocks/SM, then 2 and 8 blocks/SM"},
+                         "trials": "resort 25/50/75/100 at 6 blocks/SM, then 4 and 8 blocks/SM"},
             "clocks": clk,
             "gpu_launches": int(launches)}
     if rank == 0:

@@ -85,10 +85,10 @@ typedef struct {
   /* Speed-only knobs (the results are identical for every value; chosen by
    * pamo_autotune_batch or left at 0 for the defaults): */
   int32_t grid_blocks_per_sm; /* blocks per SM of the bandwidth-bound
-                              grid-stride kernels (0 = 4; 1..32) */
+                              grid-stride kernels (0 = 6; 1..32) */
   int32_t resort_percent;  /* the LBVH keeps last round's compacted leaf order
                               until the face count falls below this percent of
-                              the count at the last Morton sort (0 = 50;
+                              the count at the last Morton sort (0 = 25;
                               1..100, 100 = sort every round) */
   /* Learned proposal (no counterpart in the paper): a trained pamo_mlp (see
    * below) that predicts, from 16 features of a selected winner, that the
@@ -241,7 +241,7 @@ pamo_status pamo_mlp_adam_step(pamo_mlp* m, float lr, float beta1, float beta2, 
 /* Autotuner of the speed-only knobs for a batch (no counterpart in the
  * paper): simplifies the given batch (arguments as pamo_simplify_batch) with
  * a sequence of candidate settings -- coordinate descent over resort_percent
- * in {25, 50, 75, 100}, then grid_blocks_per_sm in {2, 4, 8} -- timing each
+ * in {25, 50, 75, 100}, then grid_blocks_per_sm in {4, 6, 8} -- timing each
  * run with CUDA events, and writes the fastest into *best (a copy of *base
  * with the two knobs set).  h_ms (host, may be NULL, capacity 8) receives
  * the time of every trial and *n_trials their number.  Every trial produces

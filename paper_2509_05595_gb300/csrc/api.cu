@@ -327,7 +327,7 @@ pamo_status new_ctx(const pamo_options* opt, cudaStream_t st, pamo_ctx** out) {
     cudaEventCreate(&c->round_ev[1]);
   }
   c->sm_count = sm_count();
-  c->grid = c->sm_count * (o.grid_blocks_per_sm > 0 ? o.grid_blocks_per_sm : 4);
+  c->grid = c->sm_count * (o.grid_blocks_per_sm > 0 ? o.grid_blocks_per_sm : 6);
   *out = c;
   return PAMO_OK;
 }
@@ -1099,7 +1099,7 @@ pamo_status run_batch(pamo_ctx* c) {
 bool use_carry(pamo_ctx* c) {
   // keep the carried leaf order while the face count stays above resort% of
   // the count at the last sort (Morton order only affects speed)
-  const int64_t pct = c->opt.resort_percent > 0 ? c->opt.resort_percent : 50;
+  const int64_t pct = c->opt.resort_percent > 0 ? c->opt.resort_percent : 25;
   return c->bvh.order_ok && 100 * c->nF > pct * (int64_t)c->bvh.n_sorted &&
          pct < 100 && c->opt.check_mode != 3;
 }
@@ -1736,8 +1736,8 @@ pamo_status pamo_autotune_batch(int32_t n_meshes, const float* d_V, const int64_
   int nt = 0;
   double best_ms = 1e300, t = 0.0;
   pamo_options cur = b;
-  cur.grid_blocks_per_sm = 4;
-  cur.resort_percent = 50;
+  cur.grid_blocks_per_sm = 6;
+  cur.resort_percent = 25;
   pamo_options chosen = cur;
   if (s == PAMO_OK) s = trial(cur, &t);  // warm-up (allocator pool, module load)
   static const int kResort[4] = {25, 50, 75, 100};
@@ -1753,7 +1753,7 @@ pamo_status pamo_autotune_batch(int32_t n_meshes, const float* d_V, const int64_
       }
     }
   }
-  static const int kGrid[2] = {2, 8};
+  static const int kGrid[2] = {4, 8};
   cur = chosen;
   for (int i = 0; i < 2 && s == PAMO_OK; i++) {
     cur.grid_blocks_per_sm = kGrid[i];

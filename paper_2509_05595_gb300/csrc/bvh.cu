@@ -46,11 +46,11 @@ __device__ __forceinline__ exact::FaceInfo unpack_info(uint8_t b) {
   return fi;
 }
 
-// leaf boxes (into the leaf half of the node array is done after sorting;
-// here: Morton keys, face ids and per-face predicate info)
 #define GRID_STRIDE(i, n) \
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
 
+// Morton keys of the face-box centres and the identity leaf order (the boxes
+// and the faces' predicate info are written by the refit, after the sort).
 // Many meshes in one tree (a batch): the key of a leaf is (mesh id, Morton code
 // in that mesh's own frame), the mesh id in the high word hkeys, so the radix
 // tree separates the meshes before any spatial split and every mesh owns a
@@ -61,7 +61,7 @@ __global__ void k_leaf_keys(const float4* __restrict__ pos, const int4* __restri
                             float lx, float ly, float lz, float ix, float iy, float iz,
                             const int32_t* __restrict__ vmesh, const float* __restrict__ mframe,
                             unsigned* __restrict__ keys, unsigned* __restrict__ hkeys,
-                            int32_t* __restrict__ vals, uint8_t* __restrict__ info) {
+                            int32_t* __restrict__ vals) {
   const int n = dev_n(n_dev, n_host);
   GRID_STRIDE(f, n) {
   vals[f] = f;
@@ -74,7 +74,6 @@ __global__ void k_leaf_keys(const float4* __restrict__ pos, const int4* __restri
   }
   if (fdead && fdead[f]) {
     keys[f] = 1u << 30;
-    info[f] = pack_info(exact::FaceInfo{0, 0});
     continue;
   }
   const float4 a = pos[t.x], b = pos[t.y], c = pos[t.z];
@@ -83,24 +82,6 @@ __global__ void k_leaf_keys(const float4* __restrict__ pos, const int4* __restri
   const float cz = 0.5f * (fminf(fminf(a.z, b.z), c.z) + fmaxf(fmaxf(a.z, b.z), c.z));
   keys[f] = (spread10(quant(cx, lx, ix)) << 2) | (spread10(quant(cy, ly, iy)) << 1) |
             spread10(quant(cz, lz, iz));
-  info[f] = pack_info(exact::face_info(make_float3(a.x, a.y, a.z), make_float3(b.x, b.y, b.z),
-                                       make_float3(c.x, c.y, c.z)));
-  }
-}
-
-__global__ void k_face_info(const float4* __restrict__ pos, const int4* __restrict__ F,
-                            const uint8_t* __restrict__ fdead, const int* n_dev, int n_host,
-                            uint8_t* __restrict__ info) {
-  const int n = dev_n(n_dev, n_host);
-  GRID_STRIDE(f, n) {
-    if (fdead && fdead[f]) {
-      info[f] = pack_info(exact::FaceInfo{0, 0});
-      continue;
-    }
-    const int4 t = F[f];
-    const float4 a = pos[t.x], b = pos[t.y], c = pos[t.z];
-    info[f] = pack_info(exact::face_info(make_float3(a.x, a.y, a.z), make_float3(b.x, b.y, b.z),
-                                         make_float3(c.x, c.y, c.z)));
   }
 }
 
@@ -286,15 +267,6 @@ __global__ void k_copy_order(const int32_t* __restrict__ vals2, const unsigned* 
   }
 }
 
-__device__ __forceinline__ void face_box(const float4* __restrict__ pos, const int4& t, float3& lo,
-                                         float3& hi) {
-  const float4 a = pos[t.x], b = pos[t.y], c = pos[t.z];
-  lo = make_float3(fminf(fminf(a.x, b.x), c.x), fminf(fminf(a.y, b.y), c.y),
-                   fminf(fminf(a.z, b.z), c.z));
-  hi = make_float3(fmaxf(fmaxf(a.x, b.x), c.x), fmaxf(fmaxf(a.y, b.y), c.y),
-                   fmaxf(fmaxf(a.z, b.z), c.z));
-}
-
 __device__ __forceinline__ void store_box(float* __restrict__ nodes, int p, int side,
                                           const float3& lo, const float3& hi) {
   float2* dst = reinterpret_cast<float2*>(nodes + 16 * (size_t)p + 6 * side);
@@ -305,7 +277,9 @@ __device__ __forceinline__ void store_box(float* __restrict__ nodes, int p, int 
 
 // leaf boxes go into their parent's slot; then bottom-up unions: the second
 // child to arrive at a parent computes the parent's box and stores it in the
-// grandparent (no waiting; every thread stops at a first arrival or the root)
+// grandparent (no waiting; every thread stops at a first arrival or the root).
+// Each leaf also writes its face's predicate info (dominant normal axis and
+// orientation, read by the exact pair test) from the corners it loaded.
 // atomic add with acquire-release semantics at device scope
 __device__ __forceinline__ int add_acq_rel(int* p, int v) {
   int old;
@@ -320,8 +294,23 @@ __global__ void k_refit(const float4* __restrict__ pos, const int4* __restrict__
                         const uint8_t* __restrict__ fdead, const int32_t* __restrict__ vals,
                         const int* n_dev, int n_host, float* __restrict__ nodes,
                         const int32_t* __restrict__ parent, int32_t* __restrict__ flags,
-                        int* __restrict__ overflow) {
+                        int* __restrict__ overflow, uint8_t* __restrict__ info) {
   const int n = dev_n(n_dev, n_host);
+  if (n == 1) {  // no internal node; the face's info only
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      const int f = vals[0];
+      if (fdead && fdead[f]) {
+        info[f] = pack_info(exact::FaceInfo{0, 0});
+      } else {
+        const int4 t = F[f];
+        const float4 a = pos[t.x], b = pos[t.y], c = pos[t.z];
+        info[f] = pack_info(exact::face_info(make_float3(a.x, a.y, a.z),
+                                             make_float3(b.x, b.y, b.z),
+                                             make_float3(c.x, c.y, c.z)));
+      }
+    }
+    return;
+  }
   if (n < 2) return;
   GRID_STRIDE(j, n) {
   const int f = vals[j];
@@ -329,8 +318,16 @@ __global__ void k_refit(const float4* __restrict__ pos, const int4* __restrict__
   if (fdead && fdead[f]) {
     lo = make_float3(INFINITY, INFINITY, INFINITY);
     hi = make_float3(-INFINITY, -INFINITY, -INFINITY);
+    info[f] = pack_info(exact::FaceInfo{0, 0});
   } else {
-    face_box(pos, F[f], lo, hi);
+    const int4 t = F[f];
+    const float4 a = pos[t.x], b = pos[t.y], c = pos[t.z];
+    lo = make_float3(fminf(fminf(a.x, b.x), c.x), fminf(fminf(a.y, b.y), c.y),
+                     fminf(fminf(a.z, b.z), c.z));
+    hi = make_float3(fmaxf(fmaxf(a.x, b.x), c.x), fmaxf(fmaxf(a.y, b.y), c.y),
+                     fmaxf(fmaxf(a.z, b.z), c.z));
+    info[f] = pack_info(exact::face_info(make_float3(a.x, a.y, a.z), make_float3(b.x, b.y, b.z),
+                                         make_float3(c.x, c.y, c.z)));
   }
   int ps = parent[n - 1 + j];
   store_box(nodes, ps >> 1, ps & 1, lo, hi);
@@ -742,8 +739,7 @@ pamo_status bvh_build(Bvh& b, const float4* pos, const int4* F, const uint8_t* f
     static const int g_keys = occ_grid(k_leaf_keys);
     k_leaf_keys<<<g_keys, kBlock, 0, st>>>(pos, F, fdead, n_dev, n_host, lo[0], lo[1], lo[2],
                                            inv[0], inv[1], inv[2], hk ? b.vmesh : nullptr,
-                                           b.mframe, keys, hk, vals,
-                                           (uint8_t*)b.face_aux.p); note_launch();
+                                           b.mframe, keys, hk, vals); note_launch();
     const int tiles_max = (b.n_max + kSortTile - 1) / kSortTile;
     int32_t* hist = (int32_t*)b.hist.p;
     int32_t* offs = hist + 256 * (tiles_max > 0 ? tiles_max : 1) + 1;
@@ -783,11 +779,9 @@ pamo_status bvh_refit(Bvh& b, const float4* pos, const int4* F, const uint8_t* f
   int32_t* fl = (int32_t*)b.flags.p;
   PAMO_CUDA(cudaMemsetAsync(fl, 0, sizeof(int32_t) * (size_t)(b.n_max + 2), st));
   static const int g_refit = occ_grid(k_refit);
-  static const int g_info = occ_grid(k_face_info);
   k_refit<<<g_refit, kBlock, 0, st>>>(pos, F, fdead, (const int32_t*)b.vals.p, n_dev, n_host,
                                    (float*)b.nodes.p, (const int32_t*)b.parent.p, fl,
-                                   fl + b.n_max + 1); note_launch();
-  k_face_info<<<g_info, kBlock, 0, st>>>(pos, F, fdead, n_dev, n_host, (uint8_t*)b.face_aux.p); note_launch();
+                                   fl + b.n_max + 1, (uint8_t*)b.face_aux.p); note_launch();
   PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;
 }

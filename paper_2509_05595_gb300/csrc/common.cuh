@@ -40,7 +40,7 @@ pamo_status cuda_fail(cudaError_t e, const char* what);
     if (s__ != PAMO_OK) return s__;              \
   } while (0)
 
-// fixed grid of the grid-stride kernels: 4 blocks per SM of the current device
+// fixed grid of the standalone intersection check's kernels: 4 blocks per SM
 int default_grid();
 int sm_count();
 
@@ -127,7 +127,8 @@ struct Bvh {
   const float* mframe = nullptr;
   uint32_t* vgap = nullptr;  // per-vertex clearance of non-adjacent overlapping pairs (may be null)
   // leaf order carried over rounds: valid when order_ok; re-sorted by Morton
-  // code when the face count has halved since the last sort
+  // code when the face count has fallen below resort_percent (default 25) of
+  // the count at the last sort
   bool order_ok = false;
   int n_sorted = 0;
 };

@@ -111,7 +111,7 @@ def test_autotune_picks_knobs_and_keeps_results():
     best, trials = pamo.pamo_autotune_batch(torch.from_numpy(V), voff, torch.from_numpy(F),
                                             foff, targets)
     assert len(trials) == 6 and all(t > 0 for t in trials)
-    assert best.resort_percent in (25, 50, 75, 100) and best.grid_blocks_per_sm in (2, 4, 8)
+    assert best.resort_percent in (25, 50, 75, 100) and best.grid_blocks_per_sm in (4, 6, 8)
     out, status, rounds, _ = _run_batch(meshes, targets, resort_percent=best.resort_percent,
                                         grid_blocks_per_sm=best.grid_blocks_per_sm)
     for m, ((Vm, Fm), t) in enumerate(zip(meshes, targets)):
