@@ -388,12 +388,12 @@ const char* pamo_last_error(void);
 /* Memory kept between calls.  Device buffers come from a stream-ordered pool
  * owned by the library (one per device, created on first use) that keeps the
  * memory freed by a finished call for the next one instead of returning it to
- * the driver, and the small pinned host mirrors of finished contexts are kept
+ * the CUDA driver, and the small pinned host mirrors of finished contexts are kept
  * for reuse, so back-to-back calls do not map, zero and unmap their working
  * set each time.  The library therefore holds, after a call returns, up to
  * the largest working set it has used on each device (roughly 0.8 KB per
  * input face).  This call returns everything that no live context uses to
- * the driver (device pools trimmed, cached pinned blocks freed).  It does not
+ * the CUDA driver (device pools trimmed, cached pinned blocks freed).  It does not
  * synchronise any stream; call it when no simplification is running. */
 pamo_status pamo_release_cached_memory(void);
 

@@ -558,5 +558,5 @@ def pamo_measure_fp64():
 
 def pamo_release_cached_memory():
     """Return the device and pinned host memory the library keeps between
-    calls (and no live context uses) to the driver."""
+    calls (and no live context uses) to the CUDA driver."""
     _check(lib().pamo_release_cached_memory(), "pamo_release_cached_memory")

@@ -46,7 +46,7 @@ int default_grid() { return 4 * sm_count(); }
 // device) whose release threshold keeps freed memory for the next call: a
 // simplification allocates its whole working set up front and frees it at the
 // end, and the default pool (threshold 0) would hand that memory back to the
-// driver at the next synchronisation and map it again for the next call.
+// CUDA driver at the next synchronisation and map it again for the next call.
 // Pinned host mirrors are recycled the same way.  pamo_release_cached_memory
 // returns what no live context uses.
 namespace {
