@@ -48,11 +48,11 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 COST_OPS_EDGE, COST_DIV_EDGE, COST_SQRT_EDGE = 85, 3, 1
 COST_OPS_TRI, COST_DIV_TRI, COST_SQRT_TRI = 22, 1, 1
 
-# k_edge_cost DRAM bytes per evaluated edge: 32.40 MB for 491,520 edges in the ncu capture of
+# k_edge_cost DRAM bytes per evaluated edge: 31.93 MB for 491,520 edges in the ncu capture of
 # round 0 at L7 (profiles/top_kernels_bumped_icosphere_l7.md); the traffic of a launch grows
 # with the edges it evaluates, so a launch's traffic is this times its edge count
-COST_DRAM_BYTES_PER_EDGE = 32.403e6 / 491520
-COST_FP64_PIPE_BUSY = 0.819  # same capture
+COST_DRAM_BYTES_PER_EDGE = 31.934e6 / 491520
+COST_FP64_PIPE_BUSY = 0.818  # same capture
 
 
 def max_over_ranks(x, device=None):
