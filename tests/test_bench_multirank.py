@@ -43,3 +43,38 @@ def test_two_rank_max_and_weak_value():
 def test_single_process_identity():
     assert bench.max_over_ranks(12.5) == 12.5
     assert bench.weak_value(1e6, 1, 1000.0) == pytest.approx(1.0)
+
+
+def _run_bench(args, env_extra=None):
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, **(env_extra or {}))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), *args], cwd=root,
+                       env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    return [json.loads(ln) for ln in lines]
+
+
+def test_reference_arm_line_keeps_the_contract():
+    """The reference arm (the CPU oracle on its bounded sample) prints one JSON
+    line with the contract's keys; no GPU is needed for it."""
+    (line,) = _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "0"])
+    assert line["impl"] == "reference" and line["unit"] == "Mfaces/s"
+    for k in ("metric", "value", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["value"] > 0 and line["steps"] == 1 and line["higher_is_better"] is True
+    assert line["config"]["workload"].startswith("bumped_icosphere_l8")
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
+    e2e = line["e2e"]
+    assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_reference_arm_other_ranks_print_nothing():
+    assert _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "0"],
+                      {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
