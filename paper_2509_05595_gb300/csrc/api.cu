@@ -107,10 +107,11 @@ pamo_status pinned_get(void** p, size_t bytes) {
       return PAMO_OK;
     }
   }
-  cudaError_t e = cudaMallocHost(p, bytes);
+  // portable: the cache may hand the block to a context on another device
+  cudaError_t e = cudaHostAlloc(p, bytes, cudaHostAllocPortable);
   if (e != cudaSuccess) {
     *p = nullptr;
-    return cuda_fail(e, "cudaMallocHost");
+    return cuda_fail(e, "cudaHostAlloc");
   }
   return PAMO_OK;
 }
@@ -144,6 +145,22 @@ pamo_status release_cached_memory() {
   if (first != cudaSuccess) return cuda_fail(first, "cudaMemPoolTrimTo");
   return PAMO_OK;
 }
+
+// two timing events, destroyed on every exit path
+struct EventPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  EventPair() = default;
+  EventPair(const EventPair&) = delete;
+  EventPair& operator=(const EventPair&) = delete;
+  ~EventPair() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+  cudaError_t create() {
+    cudaError_t e = cudaEventCreate(&a);
+    return e == cudaSuccess ? cudaEventCreate(&b) : e;
+  }
+};
 
 pamo_status buf_reserve(Buf& b, size_t bytes, cudaStream_t st) {
   if (bytes <= b.bytes && b.p) return PAMO_OK;
@@ -1464,18 +1481,19 @@ pamo_status pamo_ctx_rounds(const pamo_ctx* c, int64_t* rounds) {
 pamo_status pamo_ctx_run(pamo_ctx* c, int64_t target, pamo_stats* stats) {
   CTX_GUARD(c);
   PAMO_TRY(enter(c));
-  cudaEvent_t e0, e1;
-  PAMO_CUDA(cudaEventCreate(&e0));
-  PAMO_CUDA(cudaEventCreate(&e1));
-  PAMO_CUDA(cudaEventRecord(e0, c->st));
+  EventPair ev;
+  PAMO_CUDA(ev.create());
+  PAMO_CUDA(cudaEventRecord(ev.a, c->st));
   const long long l0 = launch_count() - c->gk_run + c->gk_captured;
   pamo_status s = run(c, target);
-  PAMO_CUDA(cudaEventRecord(e1, c->st));
-  PAMO_CUDA(cudaEventSynchronize(e1));
+  cudaError_t e = cudaEventRecord(ev.b, c->st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(ev.b);
+  if (e != cudaSuccess) {
+    join(c);
+    return cuda_fail(e, "pamo_ctx_run: synchronisation");
+  }
   float ms = 0.f;
-  cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  cudaEventElapsedTime(&ms, ev.a, ev.b);
   kc_resolve(c);
   fill_stats(c, stats, ms);
   // kernels that ran: eager launches plus the kernel nodes of each replay
@@ -1503,10 +1521,10 @@ pamo_status pamo_simplify(const float* d_V, int64_t nV, const int32_t* d_F, int6
     return PAMO_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  cudaEvent_t e0, e1;
-  PAMO_CUDA(cudaEventCreate(&e0));
-  PAMO_CUDA(cudaEventCreate(&e1));
-  PAMO_CUDA(cudaEventRecord(e0, st));
+  EventPair ev;
+  PAMO_CUDA(ev.create());
+  PAMO_CUDA(cudaEventRecord(ev.a, st));
+  cudaEvent_t e0 = ev.a, e1 = ev.b;
   pamo_ctx* c = nullptr;
   const long long l0 = launch_count();
   pamo_status s = create(d_V, nV, d_F, nF, opt, st, &c);
@@ -1514,9 +1532,12 @@ pamo_status pamo_simplify(const float* d_V, int64_t nV, const int32_t* d_F, int6
   if (s == PAMO_OK) s = store_mesh(c->pos, c->nV, c->F, c->nF, d_Vout, d_Fout, c->st);
   if (s == PAMO_OK) s = join(c);
   float ms = 0.f;
+  if (s == PAMO_OK) {  // the output copy's errors surface here
+    cudaError_t e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) s = cuda_fail(e, "pamo_simplify: final synchronisation");
+  }
   if (s == PAMO_OK) {
-    cudaEventRecord(e1, st);
-    cudaEventSynchronize(e1);
     cudaEventElapsedTime(&ms, e0, e1);
     *nV_out = c->nV;
     *nF_out = c->nF;
@@ -1525,8 +1546,6 @@ pamo_status pamo_simplify(const float* d_V, int64_t nV, const int32_t* d_F, int6
     if (stats) stats->launches = launch_count() - c->gk_captured + c->gk_run - l0;
     s = (pamo_status)c->status;
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   if (c) pamo_ctx_destroy(c);
   return s;
 }
@@ -1653,10 +1672,10 @@ pamo_status pamo_simplify_batch(int32_t n_meshes, const float* d_V, const int64_
     return s;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  cudaEvent_t e0, e1;
-  PAMO_CUDA(cudaEventCreate(&e0));
-  PAMO_CUDA(cudaEventCreate(&e1));
-  PAMO_CUDA(cudaEventRecord(e0, st));
+  EventPair ev;
+  PAMO_CUDA(ev.create());
+  PAMO_CUDA(cudaEventRecord(ev.a, st));
+  cudaEvent_t e0 = ev.a, e1 = ev.b;
   pamo_ctx* c = nullptr;
   const long long l0 = launch_count();
   pamo_status s = create_batch(n_meshes, d_V, h_voff, d_F, h_foff, h_targets, opt, st, &c);
@@ -1681,18 +1700,19 @@ pamo_status pamo_simplify_batch(int32_t n_meshes, const float* d_V, const int64_
   if (s == PAMO_OK)
     s = store_mesh_batch(c->pos, c->nV, c->F, c->nF, c->vmesh, c->mvbase, d_Vout, d_Fout, c->st);
   if (s == PAMO_OK) s = join(c);
+  if (s == PAMO_OK) {  // the output copy's errors surface here
+    cudaError_t e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) s = cuda_fail(e, "pamo_simplify_batch: final synchronisation");
+  }
   if (s == PAMO_OK) {
     float ms = 0.f;
-    cudaEventRecord(e1, st);
-    cudaEventSynchronize(e1);
     cudaEventElapsedTime(&ms, e0, e1);
     kc_resolve(c);
     fill_stats(c, stats, ms);
     if (stats) stats->launches = launch_count() - c->gk_captured + c->gk_run - l0;
     s = (pamo_status)c->status;
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   if (c) pamo_ctx_destroy(c);
   return s;
 }
