@@ -22,8 +22,11 @@
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Calls enqueue work on it; calls that return counts to host
  *     memory synchronise that stream before returning.
- *   - Internal scratch is allocated with cudaMallocAsync on `stream` and freed
- *     before the call returns (or by pamo_ctx_destroy for a context).
+ *   - Internal scratch comes from the library's stream-ordered memory pool and
+ *     goes back to it before the call returns (or in pamo_ctx_destroy for a
+ *     context); the pool keeps that memory for later calls until
+ *     pamo_release_cached_memory().  Work runs on a stream of the library's
+ *     own, ordered after `stream` on entry and joined back into it on exit.
  *   - Errors are reported by return code; nothing aborts.  pamo_last_error()
  *     returns a thread-local message for the last failing call.
  *   - Indices are int32: nF < 2^31 and the edge count (3 nF / 2) < 2^31.
