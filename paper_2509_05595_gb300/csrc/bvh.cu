@@ -1,9 +1,11 @@
 // Intersection check of Section 5.2 / Algorithm 3: a linear BVH over the
 // faces (Karras 2012: Morton codes of the face-box centres, a radix sort, the
 // binary radix tree built in parallel, boxes refitted bottom-up), queried
-// with the faces that changed this round; every candidate pair whose closed
-// boxes overlap goes straight to the exact narrow phase (exact.cuh), fused
-// into the traversal so no candidate list is stored.
+// with the faces that changed this round.  Candidate pairs (closed boxes
+// overlap) are written to three buckets by their number of shared vertices
+// (k_traverse) and tested by the exact narrow phase (exact.cuh) one thread per
+// pair (k_pairs), so a warp follows one branch of Algorithm 3; when a bucket
+// overflows, the fused traversal + narrow phase (k_query) reruns the check.
 //
 // Face boxes are the min/max of float32 corner coordinates, which is exact,
 // and overlap is tested on closed intervals, so the broad phase never drops a
