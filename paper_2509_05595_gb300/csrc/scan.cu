@@ -2,7 +2,9 @@
 // tile sums / apply), used for CSR offsets, stream compaction and radix-sort
 // histograms.  The length can come from device memory, so that the scan can
 // sit inside a replayed CUDA graph whose sizes change from round to round;
-// blocks loop over tiles (grid-stride), so the grid is fixed.
+// blocks loop over tiles (grid-stride), so the grid is fixed.  The
+// multi-segment form runs up to four independent byte scans (the commit's)
+// in one set of three launches over their concatenated tiles.
 #include "common.cuh"
 
 namespace pamo {
