@@ -82,7 +82,7 @@ __device__ __forceinline__ float forward_one(const float* __restrict__ w, const 
     float acc[16];
 #pragma unroll
     for (int k = 0; k < 16; k++) acc[k] = w[oB2 + j0 + k];
-#pragma unroll 8
+#pragma unroll  // constant indices keep h1 in registers
     for (int i = 0; i < kH; i++) {
       const float hi = h1[i];
 #pragma unroll
