@@ -60,6 +60,7 @@ def lib():
         L.or_self_intersections.argtypes = [P, i64, P, i64, P, i64, ctypes.c_int]
         L.or_tri_quality.argtypes = [P]
         L.or_tri_quality.restype = ctypes.c_double
+        L.or_set_plain_products.argtypes = [ctypes.c_int]
         L.or_self_intersections.restype = i64
         _lib = L
     return _lib
@@ -106,11 +107,19 @@ def vertex_quadrics(V, F):
     return K
 
 
-def edge_table(V, F, w_e=W_E, w_s=W_S):
+def edge_table(V, F, w_e=W_E, w_s=W_S, plain_products=False):
     """Round-0 edge table: dict of arrays (ab, key, vbar, Q, l, Cs, cost, link_ok,
     vsolve = the float64 placement before rounding, NaN where the fallback is taken).
 
-    ``key`` is ~0 for ineligible edges."""
+    ``key`` is ~0 for ineligible edges.  plain_products=True evaluates every
+    fused multiply-add of the cost as a multiply and an add (two roundings)
+    instead of the fixed fma order of reading R13."""
+    if plain_products:
+        lib().or_set_plain_products(1)
+        try:
+            return edge_table(V, F, w_e, w_s)
+        finally:
+            lib().or_set_plain_products(0)
     V, F = _f32(V), _i32(F)
     cap = 3 * len(F)
     ab = np.zeros((cap, 2), np.int32)

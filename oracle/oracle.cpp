@@ -42,9 +42,12 @@
 //      pairs as all faces against all faces, the previous mesh being
 //      intersection-free).
 //   R12 an intersecting pair undoes the collapses that tagged either face.
-//   R13 evaluation order of Eq. 1: explicit std::fma in a fixed order;
-//      2A = sqrt(|u|^2 |w|^2 - (u.w)^2) clamped at 0, and the squared lengths
-//      sum to 2 (|u|^2 + |w|^2 - u.w), u, w the edges from the first corner.
+//   R13 evaluation order of Eq. 1: products accumulate with explicit std::fma
+//      in a fixed order (one rounding each); the skinny term is the formula
+//      as printed: A = |u x w| / 2 with u, w the edges from the first corner,
+//      and the three squared edge lengths summed.  or_set_plain_products(1)
+//      replaces every fused multiply-add by a multiply and an add (two
+//      roundings), to measure how much the fixed fma order moves the keys.
 //   R14 target edge cost (Section 5.1 names it beside the face target): an
 //      edge whose float cost is above (float)max_cost is not eligible; the
 //      run ends normally when no edge is eligible and no flag is pending.
@@ -459,43 +462,54 @@ static Quadric face_quadric(const float* p0, const float* p1, const float* p2) {
   return q;
 }
 
-// Evaluation order (reading R2/R3): products are accumulated with fused
+// Evaluation order (reading R13): products are accumulated with fused
 // multiply-adds (std::fma: one rounding), written out explicitly so that the
-// order is fixed.  Cramer's rule expanded along the first row.
+// order is fixed.  With g_plain_products set, each fused multiply-add is a
+// multiply followed by an add instead (the same expression, two roundings).
+static bool g_plain_products = false;
+
+static double mad(double a, double b, double c) {
+  if (g_plain_products) return a * b + c;
+  return std::fma(a, b, c);
+}
+
+// Cramer's rule expanded along the first row.
 static double det3(double a00, double a01, double a02, double a10, double a11,
                    double a12, double a20, double a21, double a22) {
-  double m0 = std::fma(a11, a22, -(a12 * a21));
-  double m1 = std::fma(a10, a22, -(a12 * a20));
-  double m2 = std::fma(a10, a21, -(a11 * a20));
-  return std::fma(a02, m2, std::fma(-a01, m1, a00 * m0));
+  double m0 = mad(a11, a22, -(a12 * a21));
+  double m1 = mad(a10, a22, -(a12 * a20));
+  double m2 = mad(a10, a21, -(a11 * a20));
+  return mad(a02, m2, mad(-a01, m1, a00 * m0));
 }
 
 // Q(v) = v^T A v + 2 b^T v + c for the summed quadric K
 static double quadric_eval(const double* K, double x, double y, double z) {
-  double ax = std::fma(K[2], z, std::fma(K[1], y, K[0] * x));
-  double ay = std::fma(K[5], z, std::fma(K[4], y, K[1] * x));
-  double az = std::fma(K[7], z, std::fma(K[5], y, K[2] * x));
-  double bv = std::fma(K[8], z, std::fma(K[6], y, K[3] * x));
-  return std::fma(2.0, bv, std::fma(z, az, std::fma(y, ay, x * ax))) + K[9];
+  double ax = mad(K[2], z, mad(K[1], y, K[0] * x));
+  double ay = mad(K[5], z, mad(K[4], y, K[1] * x));
+  double az = mad(K[7], z, mad(K[5], y, K[2] * x));
+  double bv = mad(K[8], z, mad(K[6], y, K[3] * x));
+  return mad(2.0, bv, mad(z, az, mad(y, ay, x * ax))) + K[9];
 }
 
 static double dot3(double ax, double ay, double az, double bx, double by, double bz) {
-  return std::fma(az, bz, std::fma(ay, by, ax * bx));
+  return mad(az, bz, mad(ay, by, ax * bx));
 }
 
-// C_ijk = 4 sqrt(3) A / (l_ij^2 + l_jk^2 + l_ki^2) with u = q1 - q0, w = q2 - q0:
-// (2A)^2 = |u x w|^2 = |u|^2 |w|^2 - (u.w)^2 (Lagrange's identity) and
-// l_ij^2 + l_jk^2 + l_ki^2 = |u|^2 + |w|^2 + |w - u|^2 = 2 (|u|^2 + |w|^2 - u.w).
+// C_ijk = 4 sqrt(3) A / (l_ij^2 + l_jk^2 + l_ki^2) of Eq. 1 for the triangle
+// (q0, q1, q2): A is half the length of the cross product of the edges
+// q1 - q0 and q2 - q0, the denominator the three squared edge lengths summed
+// in the order (q0q1, q1q2, q2q0).
 static double tri_quality(const double* q0, const double* q1, const double* q2) {
   double ux = q1[0] - q0[0], uy = q1[1] - q0[1], uz = q1[2] - q0[2];
+  double tx = q2[0] - q1[0], ty = q2[1] - q1[1], tz = q2[2] - q1[2];
   double wx = q2[0] - q0[0], wy = q2[1] - q0[1], wz = q2[2] - q0[2];
-  double a = dot3(ux, uy, uz, ux, uy, uz);
-  double b = dot3(wx, wy, wz, wx, wy, wz);
-  double c = dot3(ux, uy, uz, wx, wy, wz);
-  double cr2 = std::fma(a, b, -(c * c));
-  if (!(cr2 > 0.0)) cr2 = 0.0;
-  double den = 2.0 * ((a + b) - c);
-  if (den > 0.0) return ((2.0 * kSqrt3) * std::sqrt(cr2)) / den;
+  double nx = mad(uy, wz, -(uz * wy));
+  double ny = mad(uz, wx, -(ux * wz));
+  double nz = mad(ux, wy, -(uy * wx));
+  double area = 0.5 * std::sqrt(dot3(nx, ny, nz, nx, ny, nz));
+  double den = (dot3(ux, uy, uz, ux, uy, uz) + dot3(tx, ty, tz, tx, ty, tz)) +
+               dot3(wx, wy, wz, wx, wy, wz);
+  if (den > 0.0) return ((4.0 * kSqrt3) * area) / den;
   return 0.0;
 }
 
@@ -714,7 +728,7 @@ static void edge_cost(const Mesh& m, const std::vector<int64_t>& off,
     Cs = Cs + (1.0 - tri_quality(q[0], q[1], q[2]));
   }
   double s2 = scale * scale, wes = o.w_e * scale;
-  double cost = std::fma(o.w_s, Cs, std::fma(wes, l, s2 * Q));
+  double cost = mad(o.w_s, Cs, mad(wes, l, s2 * Q));
   e.Q = Q;
   e.l = l;
   e.Cs = Cs;
@@ -1276,6 +1290,9 @@ int64_t or_round_pairs(void* h, int64_t r, int kind, int32_t* out, int64_t cap) 
 
 // C_ijk of Eq. 1 for one triangle (9 doubles).
 double or_tri_quality(const double* q) { return tri_quality(q, q + 3, q + 6); }
+
+// 1: every fused multiply-add of the cost becomes a multiply and an add (R13)
+void or_set_plain_products(int on) { g_plain_products = on != 0; }
 
 // All intersecting face pairs of a mesh (Algorithm 3 applied to every face).
 // brute = 1 tests every face pair, else box-overlap candidates from the cell

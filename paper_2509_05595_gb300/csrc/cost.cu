@@ -54,29 +54,31 @@ __device__ __forceinline__ double dot3(double ax, double ay, double az, double b
   return __fma_rn(az, bz, __fma_rn(ay, by, ax * bx));
 }
 
-// C_ijk = 4 sqrt(3) A / (l_ij^2 + l_jk^2 + l_ki^2), with u = q1 - q0, w = q2 - q0:
-// |u x w|^2 = |u|^2 |w|^2 - (u.w)^2 and the three squared lengths sum to
-// 2 (|u|^2 + |w|^2 - u.w), so C_ijk = sqrt(3) |u x w| / (|u|^2 + |w|^2 - u.w).
-// This is bit-identical to (2 sqrt(3) |u x w|) / (2 (...)): the two factors
-// of 2 are exact and sqrt(3) |u x w| is never subnormal, so the rounded
-// quotient is the same, with one float64 multiply fewer.  Both operands are
-// finite for float32 inputs (squares of float32 differences stay far inside
-// float64 range), so their sign tests run on the integer bit patterns (a
-// finite double is > 0 iff its bits are > 0 as a signed integer), off the
-// float64 pipe.
+// Finite doubles compare with zero on their bit patterns (a finite double is
+// > 0 iff its bits are > 0 as a signed integer): the test runs on the integer
+// pipe, off the float64 pipe.
 __device__ __forceinline__ bool pos_finite(double x) { return __double_as_longlong(x) > 0; }
 
+// C_ijk = 4 sqrt(3) A / (l_ij^2 + l_jk^2 + l_ki^2) of Eq. 1 for the triangle
+// (q0, q1, q2): A = |u x w| / 2 with u = q1 - q0, w = q2 - q0, and the three
+// squared edge lengths summed in the order (q0q1, q1q2, q2q0).  Evaluated as
+// (2 sqrt(3) |u x w|) / den, which rounds to the same bits as
+// (4 sqrt(3) (|u x w| / 2)) / den: 4 sqrt(3) and 2 sqrt(3) are exact
+// multiples of the float64 sqrt(3), and halving |u x w| is exact (for float32
+// corners it is zero or far above the subnormal range).
 __device__ __forceinline__ double quality(double x0, double y0, double z0, double x1, double y1,
                                           double z1, double x2, double y2, double z2) {
+  constexpr double k2Sqrt3 = 2.0 * kSqrt3;
   const double ux = x1 - x0, uy = y1 - y0, uz = z1 - z0;
+  const double tx = x2 - x1, ty = y2 - y1, tz = z2 - z1;
   const double wx = x2 - x0, wy = y2 - y0, wz = z2 - z0;
-  const double a = dot3(ux, uy, uz, ux, uy, uz);
-  const double b = dot3(wx, wy, wz, wx, wy, wz);
-  const double c = dot3(ux, uy, uz, wx, wy, wz);
-  double cr2 = __fma_rn(a, b, -(c * c));
-  if (!pos_finite(cr2)) cr2 = 0.0;
-  const double half_den = (a + b) - c;
-  return pos_finite(half_den) ? (kSqrt3 * sqrt(cr2)) / half_den : 0.0;
+  const double nx = __fma_rn(uy, wz, -(uz * wy));
+  const double ny = __fma_rn(uz, wx, -(ux * wz));
+  const double nz = __fma_rn(ux, wy, -(uy * wx));
+  const double n2 = dot3(nx, ny, nz, nx, ny, nz);
+  const double den = (dot3(ux, uy, uz, ux, uy, uz) + dot3(tx, ty, tz, tx, ty, tz)) +
+                     dot3(wx, wy, wz, wx, wy, wz);
+  return pos_finite(den) ? (k2Sqrt3 * sqrt(n2)) / den : 0.0;
 }
 
 // per-mesh eligible counts of a batch: one atomic per group of lanes with the

@@ -81,6 +81,88 @@ def test_quality_closed_forms():
     assert oracle.tri_quality(np.zeros(3), np.zeros(3), np.zeros(3)) == 0.0
 
 
+def _sliver(rng, ratio):
+    """A triangle whose apex lies ratio * |u| off the line of its base u,
+    anywhere along it (needles and caps), in a random orientation and corner
+    order, as float64 corners."""
+    p0, p1 = rng.uniform(-1, 1, 3), rng.uniform(-1, 1, 3)
+    u = p1 - p0
+    n = rng.normal(size=3)
+    n -= n.dot(u) / u.dot(u) * u
+    n /= np.linalg.norm(n)
+    p2 = p0 + rng.uniform(-0.5, 1.5) * u + ratio * np.linalg.norm(u) * n
+    q = [p0, p1, p2]
+    return [q[i] for i in rng.permutation(3)]
+
+
+# Error bound of C_ijk as Eq. 1 writes it (area from the cross product, the
+# three squared lengths summed), for any triangle: each cross-product
+# component is off by at most ~eps |u||w| (the edge differences, one product
+# and one fused multiply-add), so |u x w| by at most 3 sqrt(3) eps |u||w|;
+# C = 2 sqrt(3) |u x w| / den with den >= |u|^2 + |w|^2 >= 2 |u||w| gives
+# |C - C_exact| <= 9 eps plus the few-ulp relative error of the quotient.
+# The absolute bound holds however thin the triangle is, so a sliver's C_ijk
+# (nearly 0) stays right.  An area from |u|^2 |w|^2 - (u.w)^2 instead would be
+# off by about sqrt(eps) ~ 1e-8 on these slivers.
+QUALITY_ABS_BOUND = 9 * np.finfo(float).eps
+
+
+@pytest.mark.parametrize("ratio", [1e-3, 1e-6, 1e-9, 1e-12])
+def test_quality_on_slivers_against_mpmath(ratio):
+    rng = np.random.default_rng(int(-np.log10(ratio)))
+    worst = 0.0
+    for _ in range(120):
+        q = _sliver(rng, ratio)
+        c = oracle.tri_quality(*q)
+        e = _quality_mp(*q)
+        assert e > 0 and c > 0
+        worst = max(worst, abs(c - float(e)))
+    assert worst <= QUALITY_ABS_BOUND, worst
+
+
+def test_quality_on_float32_exact_slivers():
+    # base along (a, b, 0), apex 2^-k above the base's midpoint: every corner is
+    # exact in float32 (as mesh positions are), the exact C_ijk is far from 0,
+    # and |u|^2 |w|^2 - (u.w)^2 rounds to exactly 0 in float64 for k >= 27
+    for a, b in ((1, 1), (3, 1), (2, 5)):
+        for k in (10, 20, 27, 35, 50):
+            q = [np.zeros(3), np.array([a / 4, b / 4, 0.0]),
+                 np.array([a / 8, b / 8, 2.0 ** -k])]
+            assert all((np.float32(x) == x).all() for x in q)
+            e = float(_quality_mp(*q))
+            c = oracle.tri_quality(*q)
+            assert abs(c - e) <= QUALITY_ABS_BOUND and c > 0
+            assert abs(c - e) <= 1e-12 * e
+
+
+@pytest.mark.slow
+def test_fma_order_moves_keys_only_through_the_placement():
+    """Reading R13 fixes one float64 evaluation order of Eq. 1 (explicit fused
+    multiply-adds).  Against the same formulas with every fused multiply-add
+    split into a multiply and an add, on the 1,310,720-face benchmark mesh
+    (round 0, 1,966,080 edges): eligibility, link results and the
+    solved/fallback choice of every placement agree, and every key that moves
+    does so because the float32 placement moved -- the Cramer solve is
+    ill-conditioned on this fine, smooth mesh, so its last float32 bit depends
+    on the order in most edges.  Counts (stated beside R13): 1,711,870
+    placements and 1,249,136 keys differ."""
+    V, F, _ = meshgen.mesh_config("bumped_icosphere_l8")
+    A = oracle.edge_table(V, F)
+    B = oracle.edge_table(V, F, plain_products=True)
+    assert (A["ab"] == B["ab"]).all() and (A["link_ok"] == B["link_ok"]).all()
+    assert (np.isnan(A["vsolve"][:, 0]) == np.isnan(B["vsolve"][:, 0])).all()
+    assert ((A["key"] == ~np.uint64(0)) == (B["key"] == ~np.uint64(0))).all()
+    moved_key = A["key"] != B["key"]
+    moved_vbar = (A["vbar"] != B["vbar"]).any(1)
+    assert not (moved_key & ~moved_vbar).any()
+    # the two float64 solves agree to the conditioning of the 3x3 systems
+    solved = ~np.isnan(A["vsolve"][:, 0])
+    rel = (np.linalg.norm(A["vsolve"][solved] - B["vsolve"][solved], axis=1)
+           / np.linalg.norm(A["vsolve"][solved], axis=1))
+    assert rel.max() < 1e-3
+    assert moved_vbar.sum() == 1711870 and moved_key.sum() == 1249136
+
+
 @pytest.fixture(scope="module")
 def torus_table():
     V, F, _ = meshgen.mesh_config("torus_64x32")
