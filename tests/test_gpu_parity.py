@@ -108,10 +108,12 @@ def _gpu_run(V, F, target, **opts):
 
 
 def _assert_same_run(V, F, target, check_mode=oracle.CHECK_GRID, gpu_mode=0, gpu_only=None,
-                     **opts):
+                     ref=None, **opts):
     """opts (w_e, w_s, exact_target, max_cost) go to both sides; gpu_only
-    (speed-only knobs) to the GPU run alone."""
-    ref = oracle.simplify(V, F, target, check_mode=check_mode, **opts)
+    (speed-only knobs) to the GPU run alone; ref: an oracle run of the same
+    arguments made earlier."""
+    if ref is None:
+        ref = oracle.simplify(V, F, target, check_mode=check_mode, **opts)
     gV, gF, rounds, stats, status = _gpu_run(V, F, target, check_mode=gpu_mode, **opts,
                                              **(gpu_only or {}))
     assert len(rounds) == len(ref.rounds)
@@ -225,10 +227,58 @@ def test_self_intersection_check_matches_oracle():
     assert gn == 0
 
 
+def _deep_tree_soup(stack=1500):
+    """A triangle soup whose LBVH is as deep as Morton keys let it be: flat
+    triangles in the 30 cells whose Morton codes are single bits (a comb of
+    depth 30 in the radix tree), and a stack of `stack` parallel slanted
+    triangles inside cell (0, 0, 0) -- equal Morton keys, split by leaf index
+    below the comb -- whose boxes overlap about 500 deep but which never meet.
+    Two large triangles fix the box to [0, 1]^3.  All corners are exact in
+    float32."""
+    cell = 1.0 / 1023.0
+    tris = [[[0, 0, 0], [1, 0, 0], [0, 1, 0]], [[1, 1, 1], [0.5, 1, 1], [1, 0.5, 1]]]
+    for axis in range(3):
+        for j in range(10):
+            c = np.full(3, 0.25 * cell)
+            c[axis] = (2 ** j + 0.25) * cell
+            z = np.float32(c[2])
+            tris.append([[c[0], c[1], z], [c[0] + 0.25 * cell, c[1], z],
+                         [c[0], c[1] + 0.25 * cell, z]])
+    a, b, h = 2.0 ** -13, 2.0 ** -14, 2.0 ** -15
+    for i in range(stack):
+        x0, y0, z0 = 2.0 ** -12, 2.0 ** -12, 2.0 ** -12 + i * 2.0 ** -24
+        tris.append([[x0, y0, z0], [x0 + a, y0, z0 + b], [x0, y0 + a, z0 + h]])
+    V = np.asarray(tris, np.float32).reshape(-1, 3)
+    F = np.arange(len(V), dtype=np.int32).reshape(-1, 3)
+    return V, F
+
+
+def test_check_on_a_deep_tree_matches_oracle():
+    V, F = _deep_tree_soup()
+    pairs, n = oracle.self_intersections(V, F)
+    assert n == 0
+    gn, _ = pamo.pamo_check_self_intersections(torch.from_numpy(V), torch.from_numpy(F))
+    assert gn == 0
+    # and with one stacked triangle tilted through its neighbours
+    V2 = V.copy()
+    k = 3 * (2 + 30 + 700)
+    V2[k + 1, 2] += np.float32(2.0 ** -16)
+    pairs, n = oracle.self_intersections(V2, F)
+    gn, gp = pamo.pamo_check_self_intersections(torch.from_numpy(V2), torch.from_numpy(F))
+    assert gn == n > 0
+    assert {tuple(p) for p in gp.cpu().numpy().tolist()} == {tuple(p) for p in pairs.tolist()}
+
+
 # ---------------------------------------------------------------- full size
 @pytest.fixture(scope="module")
 def sphere_l8():
     return meshgen.mesh_config("bumped_icosphere_l8")
+
+
+@pytest.fixture(scope="module")
+def sphere_l8_ref(sphere_l8):
+    V, F, target = sphere_l8
+    return oracle.simplify(V, F, target)
 
 
 def test_full_size_round0_keys_bit_exact(sphere_l8):
@@ -239,14 +289,27 @@ def test_full_size_round0_keys_bit_exact(sphere_l8):
     assert (K == T["key"]).all()
 
 
-def test_full_size_run_properties(sphere_l8):
+def test_full_size_run_bit_exact(sphere_l8, sphere_l8_ref):
+    """The benchmark workload itself, 1,310,720 -> <= 13,107 faces: every
+    round's winner, committed and undone sets and counters, the output faces
+    and the position bits equal the oracle's (Algorithm 1, Eq. 1)."""
+    V, F, target = sphere_l8
+    ref, stats = _assert_same_run(V, F, target, ref=sphere_l8_ref)
+    assert len(ref.rounds) > 40 and len(ref.F) <= target
+
+
+def test_full_size_run_properties(sphere_l8, sphere_l8_ref):
     """1,310,720 -> <= 13,107 faces in the launch configuration the benchmark
-    times: manifold, genus 0, one component, under the target, and free of
+    times (pamo_simplify, validation off): bit-identical to the oracle,
+    manifold, genus 0, one component, under the target, and free of
     self-intersections by both the GPU check and the oracle's exact scan."""
     V, F, target = sphere_l8
     Vo, Fo, stats, status = pamo.pamo_simplify(torch.from_numpy(V), torch.from_numpy(F),
                                                target, validate_input=0)
     Vo, Fo = Vo.cpu().numpy(), Fo.cpu().numpy()
+    ref = sphere_l8_ref
+    assert np.array_equal(Fo, ref.F) and np.array_equal(_bits(Vo), _bits(ref.V))
+    assert stats["rounds"] == len(ref.rounds)
     assert status == "PAMO_OK" and len(Fo) <= target
     assert is_closed_manifold(Fo, len(Vo))
     assert euler(Fo, len(Vo)) == 2 and components(Fo, len(Vo)) == 1
@@ -277,14 +340,33 @@ def test_nested_shells_full_size_round0_keys(shells_l8):
     assert (K == T["key"]).all()
 
 
-def test_nested_shells_full_size_run_properties(shells_l8):
-    """2,621,440 faces -> 0.1 %: two closed manifold shells that nearly touch;
-    the output must stay manifold, keep both components and be free of
+@pytest.fixture(scope="module")
+def shells_l8_ref(shells_l8):
+    V, F, target = shells_l8
+    return oracle.simplify(V, F, target)
+
+
+def test_nested_shells_full_size_run_bit_exact(shells_l8, shells_l8_ref):
+    """The near-contact stress at full size, 2,621,440 faces -> 0.1 %: per-round
+    sets and counters (including the undo iterations of Section 5.3), output
+    faces and position bits equal the oracle's."""
+    V, F, target = shells_l8
+    ref, stats = _assert_same_run(V, F, target, ref=shells_l8_ref)
+    assert sum(d["undone"] for d in ref.rounds) > 0
+    assert stats["undone"] == sum(d["undone"] for d in ref.rounds)
+
+
+def test_nested_shells_full_size_run_properties(shells_l8, shells_l8_ref):
+    """2,621,440 faces -> 0.1 % through pamo_simplify (validation off): the
+    oracle's output, two closed manifold shells that nearly touch; the output
+    must stay manifold, keep both components and be free of
     self-intersections, checked by the GPU and by the oracle's exact scan."""
     V, F, target = shells_l8
     Vo, Fo, stats, status = pamo.pamo_simplify(torch.from_numpy(V), torch.from_numpy(F),
                                                target, validate_input=0)
     Vo, Fo = Vo.cpu().numpy(), Fo.cpu().numpy()
+    assert np.array_equal(Fo, shells_l8_ref.F)
+    assert np.array_equal(_bits(Vo), _bits(shells_l8_ref.V))
     assert status in ("PAMO_OK", "PAMO_ESTALL")
     if status == "PAMO_OK":
         assert len(Fo) <= target

@@ -86,10 +86,16 @@ def test_input_intersection_check_refuses_bad_input():
     with pytest.raises(_pamo.PamoError, match="EINTERSECT"):
         _pamo.pamo_simplify(torch.from_numpy(V), torch.from_numpy(F), len(F) // 10,
                             check_input_intersections=1)
+    # an intersection-free input is accepted and simplified exactly as the
+    # oracle does it (the input check changes nothing else)
     Vg, Fg = meshgen.nested_shells_seeded(4, 2001)
+    ref = oracle.simplify(Vg, Fg, len(Fg) // 10, keep_pairs=False)
     Vo, Fo, st, status = _pamo.pamo_simplify(torch.from_numpy(Vg), torch.from_numpy(Fg),
                                              len(Fg) // 10, check_input_intersections=1)
-    assert status in ("PAMO_OK", "PAMO_ESTALL") and st["rounds"] > 0  # accepted and run
+    assert status == ("PAMO_OK" if ref.status == 0 else "PAMO_ESTALL")
+    assert st["rounds"] == len(ref.rounds) > 0
+    assert np.array_equal(Fo.cpu().numpy(), ref.F)
+    assert np.array_equal(Vo.cpu().numpy().view(np.uint32), ref.V.view(np.uint32))
 
 
 def test_cached_memory_reuse_and_release_do_not_change_results():
