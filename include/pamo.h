@@ -332,7 +332,10 @@ void pamo_ctx_destroy(pamo_ctx* ctx);
 /* All intersecting face pairs of a mesh (LBVH broad phase, exact narrow
  * phase with the shared-vertex cases of supplementary Section 3).
  * *n_pairs (host) receives the count; d_pairs (nullable, device int32
- * [cap][2]) receives up to cap pairs (f < g), in no particular order. */
+ * [cap][2]) receives up to cap pairs (f < g), in no particular order.
+ * Every face index must lie in [0, nV): the call checks this first and
+ * returns PAMO_EINVAL, before anything reads the mesh, when one does not.
+ * Positions must be finite.  Synchronises `stream` before it returns. */
 pamo_status pamo_check_self_intersections(const float* d_V, int64_t nV,
                                           const int32_t* d_F, int64_t nF,
                                           void* stream, int64_t* n_pairs,
@@ -349,6 +352,8 @@ pamo_status pamo_check_self_intersections(const float* d_V, int64_t nV,
  *     4.1 MiB); every GPU that loads the library holds it until the process
  *     exits.  Limit: nF <= 32768 and nV <= 32768; larger meshes return
  *     PAMO_EINVAL with a message.
+ *   - Face indices outside [0, nV) return PAMO_EINVAL before the mesh is
+ *     read, as in pamo_check_self_intersections.
  *   - The first call on each device looks up that array's device address
  *     (cudaGetSymbolAddress) with the device current; make that first call
  *     before any stream capture.

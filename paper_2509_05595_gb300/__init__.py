@@ -500,13 +500,37 @@ def pamo_check_self_intersections(V, F, cap=1 << 20):
     return n.value, out[: min(n.value, cap)]
 
 
+def _require(t, name, dtype, cols):
+    """Check, without converting, that t is a contiguous CUDA tensor of dtype
+    and shape [n, cols] on the current device."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name}: expected a torch CUDA tensor, got {type(t).__name__}")
+    if not t.is_cuda:
+        raise ValueError(f"{name}: expected a CUDA tensor, got one on {t.device}")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name}: expected a tensor on cuda:{torch.cuda.current_device()}, "
+                         f"got {t.device}")
+    if t.dtype != dtype:
+        raise ValueError(f"{name}: expected {dtype}, got {t.dtype}")
+    if t.dim() != 2 or t.shape[1] != cols:
+        raise ValueError(f"{name}: expected shape [n, {cols}], got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous tensor")
+
+
 def pamo_check_self_intersections_noalloc(V, F, out):
     """pamo_check_self_intersections for callers that cannot allocate device
     memory during the call: the library uses its fixed internal scratch (at
     most 32,768 faces and vertices) and writes up to len(out) pairs into the
-    caller's int32 CUDA tensor out [cap, 2].  V, F must already be CUDA
-    tensors of the right dtype (float32 [nV,3], int32 [nF,3]); nothing is
-    converted or allocated here.  Returns the number of intersecting pairs."""
+    caller's int32 CUDA tensor out [cap, 2].  V, F must already be contiguous
+    CUDA tensors of the right dtype (float32 [nV,3], int32 [nF,3]) on the
+    current device; nothing is converted or allocated here, and anything else
+    raises ValueError.  Returns the number of intersecting pairs."""
+    import torch
+    _require(V, "V", torch.float32, 3)
+    _require(F, "F", torch.int32, 3)
+    _require(out, "out", torch.int32, 2)
     n = ctypes.c_int64()
     _check(lib().pamo_check_self_intersections_noalloc(
         _ptr(V), V.shape[0], _ptr(F), F.shape[0], _stream(), ctypes.byref(n), _ptr(out),

@@ -951,7 +951,7 @@ pamo_status finish_round(pamo_ctx* c) {
     std::memcpy(rec.info, info, sizeof(info));
     c->rec.push_back(std::move(rec));
   }
-  c->class_flops[PAMO_KC_COST] += 114.0 * h.n_dirty + 32.0 * (double)h.cost_tris;
+  c->class_flops[PAMO_KC_COST] += kCostFlopsEdge * h.n_dirty + kCostFlopsTri * (double)h.cost_tris;
   c->deferred_total += h.deferred;
   c->cost_edges_total += h.n_dirty;
   c->committed_total += committed;
@@ -1061,7 +1061,7 @@ pamo_status finish_round_batch(pamo_ctx* c) {
   PAMO_CUDA(cudaStreamSynchronize(st));
   c->nflags = nf;
   // totals over the batch
-  c->class_flops[PAMO_KC_COST] += 114.0 * h.n_dirty + 32.0 * (double)h.cost_tris;
+  c->class_flops[PAMO_KC_COST] += kCostFlopsEdge * h.n_dirty + kCostFlopsTri * (double)h.cost_tris;
   c->cost_edges_total += h.n_dirty;
   c->committed_total += h.committed;
   c->undone_total += h.nund;
@@ -1609,13 +1609,14 @@ pamo_status pamo_check_self_intersections(const float* d_V, int64_t nV, const in
   pamo_status s = alloc(&pos, nV, st);
   if (s == PAMO_OK) s = alloc(&F, nF, st);
   if (s == PAMO_OK) s = alloc(&dc, 1, st);
-  if (s == PAMO_OK) s = load_mesh(d_V, nV, d_F, nF, pos, F, st);
-  float lo[3], hi[3];
-  if (s == PAMO_OK) s = mesh_bbox(pos, nV, lo, hi, tmp, st);
   if (s == PAMO_OK) {
     cudaError_t e = cudaMemsetAsync(dc, 0, sizeof(RoundCounters), st);
     if (e != cudaSuccess) s = cuda_fail(e, "cudaMemsetAsync");
   }
+  // every face index is checked against [0, nV) before anything reads the mesh
+  if (s == PAMO_OK) s = load_mesh_checked(d_V, nV, d_F, nF, pos, F, &dc->bad, st);
+  float lo[3], hi[3];
+  if (s == PAMO_OK) s = mesh_bbox(pos, nV, lo, hi, tmp, st);
   if (s == PAMO_OK) s = bvh_alloc(b, (int)nF, st);
   if (s == PAMO_OK)
     s = bvh_build(b, pos, F, nullptr, nullptr, (int)nF, lo, hi, false, default_grid(), st);

@@ -19,8 +19,14 @@ namespace pamo {
 
 namespace {
 
-constexpr int kSortItems = 16;
-constexpr int kSortTile = kBlock * kSortItems;  // 4096 keys per block
+constexpr int kSortItems = kSortTile / kBlock;  // 4096 keys per block
+// Traversal stack.  Along any root-to-leaf path of the radix tree the common
+// prefix length of the node's key range grows strictly, and the prefixes are
+// drawn from at most 31 Morton bits (30 plus the dead-face bit) and, among
+// equal Morton keys, at most 31 bits of the leaf index (n < 2^30 faces): a
+// path has at most 62 internal nodes.  A query pushes at most one node per
+// level it descends, so 64 entries always suffice (in a batch each query
+// starts at its own mesh's subtree root, below the mesh-id levels).
 constexpr int kStack = 64;
 
 __device__ __forceinline__ unsigned spread10(unsigned x) {

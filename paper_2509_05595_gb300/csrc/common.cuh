@@ -18,6 +18,20 @@ constexpr int kBlock = 256;
 // packing them into a few 256-thread blocks, at the same occupancy.
 constexpr int kItemBlock = 64;
 
+// Tile sizes shared by the scans (scan.cu), the LBVH radix sort (bvh.cu) and
+// the fixed scratch layout of the allocation-free check (noalloc.cu).
+constexpr int kScanTile = kBlock * 8;   // items per block of a prefix scan
+constexpr int kSortTile = kBlock * 16;  // keys per block of a radix-sort pass
+
+// Algorithmic float64 flops of the edge cost (Eq. 1), for the roofline (a
+// fused multiply-add counts 2, a division or a square root 1): per evaluated
+// edge, the quadric sum, the 3x3 Cramer solve, the quadric at the placement,
+// the edge length and the weighted sum (114); per produced triangle, the
+// edge differences, the cross product and its length, the three squared
+// edge lengths, the quotient and the running sum of 1 - C_ijk (45).
+constexpr double kCostFlopsEdge = 114.0;
+constexpr double kCostFlopsTri = 45.0;
+
 // ----------------------------------------------------------------------------
 // error plumbing: every host helper returns pamo_status; the message is kept
 // per thread and surfaced by pamo_last_error().
@@ -322,6 +336,11 @@ pamo_status commit_compact(pamo_ctx* c);
 pamo_status commit_sizes(pamo_ctx* c);
 pamo_status load_mesh(const float* d_V, int64_t nV, const int32_t* d_F, int64_t nF,
                       float4* pos, int4* F, cudaStream_t st);
+// load_mesh that also checks every face index against [0, nV): synchronises
+// `st` once and returns PAMO_EINVAL before anything reads the mesh when an
+// index is out of range (d_bad: one device int of scratch)
+pamo_status load_mesh_checked(const float* d_V, int64_t nV, const int32_t* d_F, int64_t nF,
+                              float4* pos, int4* F, int* d_bad, cudaStream_t st);
 pamo_status store_mesh(const float4* pos, int64_t nV, const int4* F, int64_t nF,
                        float* d_V, int32_t* d_F, cudaStream_t st);
 // batches: the union of M meshes (vertex / face offsets on the device)

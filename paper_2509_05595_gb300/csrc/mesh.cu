@@ -22,11 +22,17 @@ namespace {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); \
        i += (int64_t)gridDim.x * blockDim.x)
 
+// bad (nullable): set to 1 when a face index lies outside [0, nV)
 __global__ void k_load(const float* __restrict__ V, int64_t nV, const int32_t* __restrict__ Fi,
-                       int64_t nF, float4* __restrict__ pos, int4* __restrict__ F) {
+                       int64_t nF, float4* __restrict__ pos, int4* __restrict__ F,
+                       int* __restrict__ bad) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < nV) pos[i] = make_float4(V[3 * i], V[3 * i + 1], V[3 * i + 2], 0.0f);
-  if (i < nF) F[i] = make_int4(Fi[3 * i], Fi[3 * i + 1], Fi[3 * i + 2], 0);
+  if (i < nF) {
+    const int a = Fi[3 * i], b = Fi[3 * i + 1], c = Fi[3 * i + 2];
+    if (bad && (a < 0 || b < 0 || c < 0 || a >= nV || b >= nV || c >= nV)) atomicOr(bad, 1);
+    F[i] = make_int4(a, b, c, 0);
+  }
 }
 
 __global__ void k_store(const float4* __restrict__ pos, int64_t nV, const int4* __restrict__ F,
@@ -607,8 +613,23 @@ __global__ void k_commit_sizes(RoundCounters* __restrict__ dc) {
 
 pamo_status load_mesh(const float* d_V, int64_t nV, const int32_t* d_F, int64_t nF, float4* pos,
                       int4* F, cudaStream_t st) {
-  k_load<<<grid_for(nV > nF ? nV : nF), kBlock, 0, st>>>(d_V, nV, d_F, nF, pos, F); note_launch();
+  k_load<<<grid_for(nV > nF ? nV : nF), kBlock, 0, st>>>(d_V, nV, d_F, nF, pos, F, nullptr); note_launch();
   PAMO_CUDA(cudaGetLastError());
+  return PAMO_OK;
+}
+
+pamo_status load_mesh_checked(const float* d_V, int64_t nV, const int32_t* d_F, int64_t nF,
+                              float4* pos, int4* F, int* d_bad, cudaStream_t st) {
+  PAMO_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int), st));
+  k_load<<<grid_for(nV > nF ? nV : nF), kBlock, 0, st>>>(d_V, nV, d_F, nF, pos, F, d_bad); note_launch();
+  PAMO_CUDA(cudaGetLastError());
+  int hb = 0;
+  PAMO_CUDA(cudaMemcpyAsync(&hb, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PAMO_CUDA(cudaStreamSynchronize(st));
+  if (hb) {
+    set_error("a face index is outside [0, nV)");
+    return PAMO_EINVAL;
+  }
   return PAMO_OK;
 }
 

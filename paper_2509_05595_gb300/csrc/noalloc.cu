@@ -27,13 +27,12 @@ constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Byte layout of the scratch for the maximum sizes (256-byte aligned pieces).
 struct Layout {
-  size_t pos, F, dc, bbox, nodes, parent, flags, keys, vals, keys2, vals2, hist, aux, len, sums,
-      total;
+  size_t pos, F, dc, bad, bbox, nodes, parent, flags, keys, vals, keys2, vals2, hist, aux, len,
+      sums, total;
   size_t nodes_b, parent_b, flags_b, kv_b, hist_b, aux_b, sums_b;
 };
 
-constexpr size_t kTile = 4096;  // radix-sort tile (keys per block) of bvh.cu
-constexpr size_t kTiles = (kMaxFaces + kTile - 1) / kTile;
+constexpr size_t kTiles = (kMaxFaces + kSortTile - 1) / kSortTile;  // radix-sort tiles
 
 constexpr Layout make_layout() {
   Layout L{};
@@ -43,12 +42,13 @@ constexpr Layout make_layout() {
   L.kv_b = sizeof(uint32_t) * (size_t)kMaxFaces;
   L.hist_b = sizeof(int32_t) * (size_t)(2 * 256 * kTiles + 2);
   L.aux_b = (size_t)kMaxFaces + 16;
-  // tile sums of the prefix scans (2048 items per tile), total after them
-  L.sums_b = sizeof(int32_t) * (size_t)((kMaxFaces + 2047) / 2048 + 1);
+  // tile sums of the prefix scans, total after them
+  L.sums_b = sizeof(int32_t) * (size_t)((kMaxFaces + kScanTile - 1) / kScanTile + 1);
   size_t o = 0;
   L.pos = o; o += align256(sizeof(float) * 4 * (size_t)kMaxVertices);
   L.F = o; o += align256(sizeof(int) * 4 * (size_t)kMaxFaces);
   L.dc = o; o += align256(sizeof(RoundCounters));
+  L.bad = o; o += align256(sizeof(int));
   L.bbox = o; o += align256(6 * sizeof(unsigned));
   L.nodes = o; o += align256(L.nodes_b);
   L.parent = o; o += align256(L.parent_b);
@@ -145,7 +145,8 @@ extern "C" pamo_status pamo_check_self_intersections_noalloc(const float* d_V, i
   b.n_max = (int)nF;
   // the array keeps the previous call's contents: the counters must start at 0
   PAMO_CUDA(cudaMemsetAsync(dc, 0, sizeof(RoundCounters), st));
-  PAMO_TRY(load_mesh(d_V, nV, d_F, nF, pos, F, st));
+  // every face index is checked against [0, nV) before anything reads the mesh
+  PAMO_TRY(load_mesh_checked(d_V, nV, d_F, nF, pos, F, (int*)(base + kL.bad), st));
   float lo[3], hi[3];
   PAMO_TRY(mesh_bbox_into(pos, nV, (unsigned*)(base + kL.bbox), lo, hi, st));
   PAMO_TRY(bvh_build(b, pos, F, nullptr, nullptr, (int)nF, lo, hi, false, default_grid(), st));

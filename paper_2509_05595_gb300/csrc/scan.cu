@@ -11,8 +11,8 @@ namespace pamo {
 
 namespace {
 
-constexpr int kItems = 8;
-constexpr int kTile = kBlock * kItems;  // 2048 items per tile
+constexpr int kItems = kScanTile / kBlock;
+constexpr int kTile = kScanTile;  // 2048 items per tile
 
 __device__ __forceinline__ int warp_incl_scan(int v) {
   const int lane = threadIdx.x & 31;

@@ -45,3 +45,17 @@ def test_default_options_match_the_library():
         if name == "proposal":
             continue
         assert getattr(o, name) == getattr(d, name), name
+
+
+def test_noalloc_check_rejects_host_arguments_before_any_call():
+    """The allocation-free check converts nothing: anything but CUDA tensors
+    is refused in Python, before the library is called."""
+    import pytest
+    torch = pytest.importorskip("torch")
+    V, F = meshgen.octahedron()
+    out = np.zeros((4, 2), np.int32)
+    with pytest.raises(ValueError, match="torch CUDA tensor"):
+        pamo.pamo_check_self_intersections_noalloc(V, F, out)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        pamo.pamo_check_self_intersections_noalloc(torch.from_numpy(V), torch.from_numpy(F),
+                                                  torch.from_numpy(out))

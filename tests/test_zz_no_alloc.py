@@ -5,8 +5,9 @@ device memory while they run (for example code whose device memory is owned
 and budgeted elsewhere): it uses a fixed scratch array inside the library.
 Here it must report exactly what pamo_check_self_intersections reports, on two
 calls in a row (the shared scratch keeps the previous call's contents, so the
-second call checks that nothing leaks between calls).  This file is collected
-last so that a -x run has executed every other test first.
+second call checks that nothing leaks between calls), take no device memory
+while it runs, and refuse bad face indices and wrongly typed arguments.  This
+file is collected last so that a -x run has executed every other test first.
 """
 import numpy as np
 import pytest
@@ -60,3 +61,51 @@ def test_noalloc_check_rejects_oversized_mesh():
     with pytest.raises(pamo.PamoError, match="EINVAL"):
         pamo.pamo_check_self_intersections_noalloc(torch.from_numpy(V).cuda(),
                                                   torch.from_numpy(F).cuda(), out)
+
+
+def test_noalloc_check_takes_no_device_memory():
+    """Free device memory is the same before and after repeated calls once the
+    library's cached pool memory has been handed back: nothing was allocated,
+    not even memory that the call would free again into the pool."""
+    out = torch.full((1 << 12, 2), -1, dtype=torch.int32, device="cuda")
+    V, F = _overlapping_spheres()
+    Vd, Fd = torch.from_numpy(V).cuda(), torch.from_numpy(F).cuda()
+    n0 = pamo.pamo_check_self_intersections_noalloc(Vd, Fd, out)  # set-up on this device
+    torch.cuda.synchronize()
+    pamo.pamo_release_cached_memory()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        assert pamo.pamo_check_self_intersections_noalloc(Vd, Fd, out) == n0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+
+
+def test_checks_reject_face_indices_out_of_range():
+    """A face index outside [0, nV) is refused with PAMO_EINVAL before the mesh
+    is read, by both checks; the next call works."""
+    V, F = meshgen.nested_shells(3, check=False)
+    out = torch.empty((64, 2), dtype=torch.int32, device="cuda")
+    Vd = torch.from_numpy(V).cuda()
+    for bad_index in (len(V), -1, 1 << 30):
+        Fb = F.copy()
+        Fb[17, 2] = bad_index
+        Fd = torch.from_numpy(Fb).cuda()
+        with pytest.raises(pamo.PamoError, match="EINVAL"):
+            pamo.pamo_check_self_intersections_noalloc(Vd, Fd, out)
+        with pytest.raises(pamo.PamoError, match="EINVAL"):
+            pamo.pamo_check_self_intersections(Vd, Fd)
+    Fd = torch.from_numpy(F).cuda()
+    assert pamo.pamo_check_self_intersections_noalloc(Vd, Fd, out) == 0
+
+
+def test_noalloc_check_rejects_wrong_tensors():
+    V, F = meshgen.nested_shells(3, check=False)
+    Vd, Fd = torch.from_numpy(V).cuda(), torch.from_numpy(F).cuda()
+    out = torch.empty((64, 2), dtype=torch.int32, device="cuda")
+    bad = [(Vd.double(), Fd, out), (Vd, Fd.long(), out), (Vd, Fd, out.reshape(-1)),
+           (Vd, Fd, out.t()), (Vd[:, :2], Fd, out), (Vd.t().contiguous().t(), Fd, out)]
+    for args in bad:
+        with pytest.raises(ValueError):
+            pamo.pamo_check_self_intersections_noalloc(*args)
