@@ -44,15 +44,20 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # quadric sum, the 3x3 Cramer solve, the quadric at the placement, the edge
 # length and the cost (additions, multiplies, FMAs, min/max and compares: 85,
 # plus 3 divisions and 1 square root); per produced triangle, the quality term
-# (22, plus 1 division and 1 square root)
+# (edge differences, cross product, squared lengths, sums: 32, plus 1 division
+# and 1 square root)
 COST_OPS_EDGE, COST_DIV_EDGE, COST_SQRT_EDGE = 85, 3, 1
-COST_OPS_TRI, COST_DIV_TRI, COST_SQRT_TRI = 22, 1, 1
+COST_OPS_TRI, COST_DIV_TRI, COST_SQRT_TRI = 32, 1, 1
+# algorithmic flops (FMA = 2, division and root = 1) per dirty edge and per
+# produced triangle; the library's class_flops use the same counts
+COST_FLOPS_EDGE, COST_FLOPS_TRI = 114.0, 45.0
 
-# k_edge_cost DRAM bytes per evaluated edge: 31.93 MB for 491,520 edges in the ncu capture of
-# round 0 at L7 (profiles/top_kernels_bumped_icosphere_l7.md); the traffic of a launch grows
-# with the edges it evaluates, so a launch's traffic is this times its edge count
-COST_DRAM_BYTES_PER_EDGE = 31.934e6 / 491520
-COST_FP64_PIPE_BUSY = 0.818  # same capture
+# k_edge_cost DRAM bytes per evaluated edge, from one ncu capture of the current kernel on
+# round 0 of the level-7 sphere (491,520 edges, all evaluated); the traffic of a launch grows
+# with the edges it evaluates, so a launch's traffic is this times its edge count.  None
+# (traffic reported as null) while no capture of the current kernel exists.
+COST_DRAM_BYTES_PER_EDGE = None
+COST_FP64_PIPE_BUSY = None  # same capture
 
 
 def max_over_ranks(x, device=None):
@@ -144,42 +149,101 @@ def make_workload(level=8):
     return V, F, target
 
 
-def cpu_oracle_sample(seconds_hint=True):
-    """The oracle (as it stands) on a bounded sample of the workload: the same
-    generator at level 7 (327,680 faces) to 1 %, single-threaded."""
+def host_cpu():
+    """Model name (lscpu) and core count of the host the oracle runs on."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    try:
+        nproc = len(os.sched_getaffinity(0))
+    except Exception:
+        nproc = os.cpu_count()
+    return {"cpu_model": model, "nproc": nproc}
+
+
+def _oracle_run(level, config=None):
+    """One oracle simplification (single-threaded); returns (seconds, faces in,
+    faces out, rounds).  level: icosphere level of the benchmark mesh, or
+    config: a named input recipe."""
     import meshgen
     import oracle
-    V, F = meshgen.bumped_icosphere(7, 0)
-    target = len(F) // 100
+    if config is not None:
+        V, F, target = meshgen.mesh_config(config)
+    else:
+        V, F, target = make_workload(level)
     t = time.perf_counter()
     r = oracle.simplify(V, F, target, keep_pairs=False)
-    dt = time.perf_counter() - t
-    return {"value": len(F) / dt / 1e6, "unit": "Mfaces/s", "cores": 1, "kind": "oracle",
-            "sample": f"bumped icosphere level 7 ({len(F)} faces) -> {target} faces, "
-                      f"{len(r.rounds)} rounds in {dt:.1f} s"}
+    return time.perf_counter() - t, len(F), len(r.F), len(r.rounds)
+
+
+def cpu_oracle_sample(level=8):
+    """The oracle (as it stands) on the benchmark workload itself: one
+    simplification of the level-8 sphere to 1 %, single-threaded."""
+    dt, nf, nout, rounds = _oracle_run(level)
+    return {"value": nf / dt / 1e6, "unit": "Mfaces/s", "cores": 1, "kind": "oracle",
+            "sample": f"the benchmark workload itself: bumped icosphere level {level} ({nf} "
+                      f"faces) -> {nout} faces, {rounds} rounds in {dt:.1f} s, one thread",
+            **host_cpu()}
 
 
 def run_reference(args, rank, world):
+    """The oracle as the reference arm: every step is one full simplification
+    of the benchmark workload (level-8 sphere to 1 %), single-threaded; the
+    steps run side by side in worker processes, one per host core, and the
+    value is the steps' faces over the wall time of all of them.  Warm-up
+    steps (untimed) load the library in every worker on the level-6 sphere."""
     if rank != 0:
         return
+    import multiprocessing as mp
     import oracle  # noqa: F401  (build happens on import)
-    vals = []
-    for _ in range(args.warmup if args.warmup < 1 else 1):
-        cpu_oracle_sample()
-    for _ in range(args.steps):
-        vals.append(cpu_oracle_sample())
-    v = statistics.median(x["value"] for x in vals)
+    level = args.level
+    V, F, target = make_workload(level)  # the cached input file the workers read
+    cpu = host_cpu()
+    procs = max(1, min(cpu["nproc"] or 1, args.steps))
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        pool.map(_oracle_run, [min(level, 6)] * max(args.warmup, procs))
+        t0 = time.perf_counter()
+        runs = pool.map(_oracle_run, [level] * args.steps, chunksize=1)
+        wall = time.perf_counter() - t0
+    nf = runs[0][1]
+    v = args.steps * nf / wall / 1e6
+    per_run = statistics.mean(r[0] for r in runs)
+    sample = (f"{args.steps} full simplifications of the benchmark workload (bumped icosphere "
+              f"level {level}, {nf} faces -> {runs[0][2]} faces, {runs[0][3]} rounds), one per "
+              f"worker process on {procs} host cores, {per_run:.1f} s each on average, "
+              f"{wall:.1f} s wall")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mfaces/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 327680 / (v * 1e6) * 1e3, "higher_is_better": True,
+            "ms_per_step": wall / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD + " (oracle runs the level-7 sample)",
-                       "target": "1%", "parallelism": "replicas"},
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": vals[0]["sample"],
-                             "value": v},
+            "config": {"workload": workload_name(level), "faces_in": int(nf),
+                       "target": int(target), "faces_out": int(runs[0][2]),
+                       "rounds": int(runs[0][3]),
+                       "parallelism": f"one simplification per host core x{procs}"},
+            "cpu_baseline": {"kind": "oracle", "cores": procs, "sample": sample, "value": v,
+                             **cpu},
             "e2e": {"value": v, "unit": "Mfaces/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
+    if level == 8:
+        # the near-contact configuration (nested shells level 8 to 0.1 %), once, end to end
+        dt3, nf3, nout3, rounds3 = _oracle_run(None, "nested_shells_l8")
+        line["oracle_nested_shells_l8"] = {
+            "value": nf3 / dt3 / 1e6, "unit": "Mfaces/s", "seconds": round(dt3, 1), "cores": 1,
+            "extrapolated": False,
+            "sample": f"nested shells level 8 ({nf3} faces) -> {nout3} faces, {rounds3} rounds, "
+                      "end to end"}
     print(json.dumps(line), flush=True)
+
+
+def workload_name(level):
+    return WORKLOAD if level == 8 else f"bumped_icosphere_l{level}"
 
 
 def min_angles_deg(V, F):
@@ -522,7 +586,7 @@ def main():
             dist.destroy_process_group()
         return
     V, F, target = make_workload(args.level)
-    workload = WORKLOAD if args.level == 8 else f"bumped_icosphere_l{args.level}"
+    workload = workload_name(args.level)
     Vd = torch.from_numpy(V).cuda()
     Fd = torch.from_numpy(F).cuda()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -600,15 +664,25 @@ def main():
         achieved = flops_per_launch / (avg_launch_ms * 1e-3) / 1e12 if avg_launch_ms > 0 else 0.0
         # two launches per round in this class (reuse + cost): edges per k_edge_cost launch
         edges_per_launch = cost_edges / max(dom_launch / 2, 1)
-        # produced triangles per launch, from the flop model (114 per edge + 32 per triangle)
+        # produced triangles per launch, from the flop model
         flops_cost = flops_per_launch * 2  # the reuse launch has no flops
-        tris_per_launch = max(flops_cost - 114.0 * edges_per_launch, 0.0) / 32.0
+        tris_per_launch = (max(flops_cost - COST_FLOPS_EDGE * edges_per_launch, 0.0)
+                           / COST_FLOPS_TRI)
+        # peak: the float64 FMA rate measured on this GPU just before the timed
+        # region (independent FMA chains over one full wave); the nominal
+        # figure from the unit count and clock when no measurement exists
+        if fp64 is not None:
+            peak = 2 * fp64["fma_per_s"] / 1e12
+            peak_source = "measured live: pamo_measure_fp64, independent float64 FMA chains"
+        else:
+            peak, peak_source = FP64_PEAK_TFLOPS, "derived: float64 FMA units x clock"
         roof = {"bound": "alu", "kernel_class": "cost", "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": COST_DRAM_BYTES_PER_EDGE * edges_per_launch,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": (COST_DRAM_BYTES_PER_EDGE * edges_per_launch
+                            if COST_DRAM_BYTES_PER_EDGE else None),
                 "traffic_note": "ncu DRAM bytes per edge (L7 round-0 capture) x edges per launch",
                 "ncu_fp64_pipe_busy": COST_FP64_PIPE_BUSY,
-                "peak_source": "derived: float64 FMA units x clock",
+                "peak_source": peak_source, "peak_nominal": FP64_PEAK_TFLOPS,
                 "launch_ms": avg_launch_ms, "class_share": share}
         if fp64 is not None:
             # the float64 pipe time the source's operations need at the measured
@@ -654,7 +728,7 @@ def main():
             "roofline": roof, "pipeline_hbm": pipeline, "clocks": clk, "e2e": e2e,
             "gpu_launches": int(launches)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_oracle_sample()
+        line["cpu_baseline"] = cpu_oracle_sample(args.level)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -59,22 +59,26 @@ def _run_bench(args, env_extra=None):
 
 
 def test_reference_arm_line_keeps_the_contract():
-    """The reference arm (the CPU oracle on its bounded sample) prints one JSON
-    line with the contract's keys; no GPU is needed for it."""
-    (line,) = _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "0"])
+    """The reference arm (the CPU oracle, steps side by side in worker
+    processes) prints one JSON line with the contract's keys; no GPU is needed
+    for it.  Level 5 keeps the test short (the benchmark is level 8)."""
+    (line,) = _run_bench(["--impl", "reference", "--steps", "2", "--warmup", "0",
+                          "--level", "5"])
     assert line["impl"] == "reference" and line["unit"] == "Mfaces/s"
     for k in ("metric", "value", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
               "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert k in line, k
-    assert line["value"] > 0 and line["steps"] == 1 and line["higher_is_better"] is True
-    assert line["config"]["workload"].startswith("bumped_icosphere_l8")
+    assert line["value"] > 0 and line["steps"] == 2 and line["higher_is_better"] is True
+    assert line["config"]["workload"] == "bumped_icosphere_l5"
+    assert line["config"]["faces_in"] == 20480 and line["config"]["target"] == 204
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
+    assert cb["nproc"] >= 1 and "cpu_model" in cb
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
 
 
 def test_reference_arm_other_ranks_print_nothing():
-    assert _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "0"],
+    assert _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "0", "--level", "5"],
                       {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
