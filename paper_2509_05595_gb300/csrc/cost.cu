@@ -195,7 +195,41 @@ __global__ void __launch_bounds__(kBlock) k_edge_reuse(
   }
 }
 
-__global__ void __launch_bounds__(kBlock) k_edge_cost(
+// Produced triangles of one warp's edges, flattened over the warp's lanes.
+// An edge produces val(a) + val(b) - 4 triangles on a closed manifold, and a
+// lane walking its own edge's two incidence lists meets the two faces on ab
+// at its own iterations, so a per-lane loop leaves about a third of the
+// float64 pipe's lane slots idle.  Instead each lane writes its produced face
+// ids (ascending) to shared memory, the warp evaluates 1 - C_ijk for all of
+// them 32 at a time, and each lane then adds up its own terms in the same
+// ascending order -- the same roundings as the per-lane loop.
+constexpr int kFlatCap = 320;  // produced triangles per warp; more: per-lane loop
+struct FlatTris {
+  double t[kFlatCap];               // 1 - C_ijk of each produced triangle
+  double vx[32], vy[32], vz[32];    // the owner edge's placement
+  int face[kFlatCap];
+  int a[32], b[32];
+  unsigned char own[kFlatCap];      // lane of the owner edge
+};
+
+// 1 - C_ijk of face t with corners a and b moved to (vx, vy, vz)
+__device__ __forceinline__ double skinny_term(const int4& t, int a, int b, double vx, double vy,
+                                              double vz, const float4* __restrict__ pos) {
+  double q[9];
+  const int cs[3] = {t.x, t.y, t.z};
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    if (cs[k] == a || cs[k] == b) {
+      q[3 * k] = vx; q[3 * k + 1] = vy; q[3 * k + 2] = vz;
+    } else {
+      const float4 p = pos[cs[k]];
+      q[3 * k] = f2d(p.x); q[3 * k + 1] = f2d(p.y); q[3 * k + 2] = f2d(p.z);
+    }
+  }
+  return 1.0 - quality(q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7], q[8]);
+}
+
+__global__ void __launch_bounds__(kItemBlock, 12) k_edge_cost(
     const int32_t* __restrict__ dlist, const int2* __restrict__ E, const float4* __restrict__ pos,
     const double* __restrict__ Kv, const int4* __restrict__ F, const int32_t* __restrict__ off,
     const int32_t* __restrict__ idx, const unsigned long long* __restrict__ flags,
@@ -204,23 +238,35 @@ __global__ void __launch_bounds__(kBlock) k_edge_cost(
     RoundCounters* __restrict__ dc, const int32_t* __restrict__ vmesh,
     const double* __restrict__ mcost, const uint8_t* __restrict__ mactive,
     int32_t* __restrict__ melig) {
+  __shared__ FlatTris flat[kItemBlock / 32];
+  FlatTris& S = flat[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
   const int ndirty = dc->n_dirty;
   const int nflags = dc->nflags;
   const unsigned max_bits = dc->max_bits;
   int link_bad = 0, flagged = 0, eligible = 0, ntri = 0;
-  // block-uniform iterations: the per-mesh count is a warp-wide operation
+  // block-uniform iterations: the triangle stage and the per-mesh count are
+  // warp-wide operations
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < ndirty;
        base += (int64_t)gridDim.x * blockDim.x) {
   const int64_t i = base + threadIdx.x;
+  const bool live = i < ndirty;
   int counted = -1;
-  if (i < ndirty) {
-    const int64_t e = dlist[i];
+  int64_t e = 0;
+  int a = 0, b = 0, m = 0, a0 = 0, a1 = 0, b0 = 0, b1 = 0, nt = 0;
+  double s2 = 0.0, wes = 0.0, Q = 0.0, l = 0.0;
+  float vx = 0.f, vy = 0.f, vz = 0.f;
+  bool link_ok = false, flag = false;
+  if (live) {
+    e = dlist[i];
     const int2 ab = E[e];
-    const int a = ab.x, b = ab.y;
-    const int m = vmesh ? vmesh[a] : 0;
+    a = ab.x;
+    b = ab.y;
+    m = vmesh ? vmesh[a] : 0;
     // the mesh's own [0,1]^3 scale (a batch); one mesh: the arguments
-    const double s2 = vmesh ? mcost[2 * m] : s2_in, wes = vmesh ? mcost[2 * m + 1] : wes_in;
-    const int a0 = off[a], a1 = off[a + 1], b0 = off[b], b1 = off[b + 1];
+    s2 = vmesh ? mcost[2 * m] : s2_in;
+    wes = vmesh ? mcost[2 * m + 1] : wes_in;
+    a0 = off[a]; a1 = off[a + 1]; b0 = off[b]; b1 = off[b + 1];
     // ---- link condition: exactly two common neighbours (the apexes of the
     // two faces on ab) and not both faces (a,c,d), (b,c,d) present
     int common = 0;
@@ -235,7 +281,9 @@ __global__ void __launch_bounds__(kBlock) k_edge_cost(
       }
       for (int j = b0; j < b1; j++) common += next_of(F[idx[j]], b) == x;
     }
-    bool link_ok = (common == 2) && (na == 2);
+    // the collapse produces every face around a or b but the na on ab
+    nt = (a1 - a0) + (b1 - b0) - 2 * na;
+    link_ok = (common == 2) && (na == 2);
     if (link_ok) {
       const int c = apex[0], d = apex[1];
       bool acd = false, bcd = false;
@@ -248,9 +296,8 @@ __global__ void __launch_bounds__(kBlock) k_edge_cost(
       }
       link_ok = !(acd && bcd);
     }
-    const bool flag =
-        nflags > 0 &&
-        is_flagged(flags, nflags, ((unsigned long long)(unsigned)a << 32) | (unsigned)b);
+    flag = nflags > 0 &&
+           is_flagged(flags, nflags, ((unsigned long long)(unsigned)a << 32) | (unsigned)b);
     // ---- Q_ab at the optimal placement (Cramer solve of A v = -b)
     double K[10];
     {
@@ -268,7 +315,6 @@ __global__ void __launch_bounds__(kBlock) k_edge_cost(
     const double mx = fmax(fmax(fmax(fabs(K[0]), fabs(K[1])), fmax(fabs(K[2]), fabs(K[4]))),
                            fmax(fabs(K[5]), fabs(K[7])));
     const double det = det3(K[0], K[1], K[2], K[1], K[4], K[5], K[2], K[5], K[7]);
-    float vx = 0.f, vy = 0.f, vz = 0.f;
     bool solved = false;
     if (mx != 0.0 && !(fabs(det) <= 1e-12 * ((mx * mx) * mx))) {
       const double x = det3(r0, K[1], K[2], r1, K[4], K[5], r2, K[5], K[7]) / det;
@@ -279,7 +325,6 @@ __global__ void __launch_bounds__(kBlock) k_edge_cost(
       vz = __double2float_rn(z);
       solved = isfinite(vx) && isfinite(vy) && isfinite(vz);
     }
-    double Q;
     if (solved) {
       Q = qeval(K, f2d(vx), f2d(vy), f2d(vz));
     } else {
@@ -297,15 +342,29 @@ __global__ void __launch_bounds__(kBlock) k_edge_cost(
     // ---- l_ab
     const double dx = f2d(pb.x) - f2d(pa.x), dy = f2d(pb.y) - f2d(pa.y),
                  dz = f2d(pb.z) - f2d(pa.z);
-    const double l = sqrt(dot3(dx, dy, dz, dx, dy, dz));
-    // ---- skinny term: faces around a or b, except the two on ab, ascending
-    // face id (merge of the two sorted incidence lists)
-    double Cs = 0.0;
-    const double vxd = f2d(vx), vyd = f2d(vy), vzd = f2d(vz);
-    {
-      int i = a0, j = b0;
+    l = sqrt(dot3(dx, dy, dz, dx, dy, dz));
+  }
+  // ---- skinny term: faces around a or b, except the two on ab, ascending
+  // face id (merge of the two sorted incidence lists)
+  int incl = nt;  // warp prefix of the produced-triangle counts
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += y;
+  }
+  const int T = __shfl_sync(0xffffffffu, incl, 31);
+  const int o = incl - nt;
+  const double vxd = f2d(vx), vyd = f2d(vy), vzd = f2d(vz);
+  double Cs = 0.0;
+  if (T <= kFlatCap) {  // warp-uniform
+    if (live) {
+      S.a[lane] = a;
+      S.b[lane] = b;
+      S.vx[lane] = vxd;
+      S.vy[lane] = vyd;
+      S.vz[lane] = vzd;
+      int i = a0, j = b0, k = o;
       while (i < a1 || j < b1) {
-        int f;
         const int fi = i < a1 ? idx[i] : 0x7fffffff;
         const int fj = j < b1 ? idx[j] : 0x7fffffff;
         if (fi == fj) {  // a face on edge ab: deleted by the collapse
@@ -313,24 +372,39 @@ __global__ void __launch_bounds__(kBlock) k_edge_cost(
           j++;
           continue;
         }
-        if (fi < fj) { f = fi; i++; }
-        else { f = fj; j++; }
-        const int4 t = F[f];
-        double q[9];
-        const int cs[3] = {t.x, t.y, t.z};
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-          if (cs[k] == a || cs[k] == b) {
-            q[3 * k] = vxd; q[3 * k + 1] = vyd; q[3 * k + 2] = vzd;
-          } else {
-            const float4 p = pos[cs[k]];
-            q[3 * k] = f2d(p.x); q[3 * k + 1] = f2d(p.y); q[3 * k + 2] = f2d(p.z);
-          }
-        }
-        Cs = Cs + (1.0 - quality(q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7], q[8]));
-        ntri++;
+        S.face[k] = fi < fj ? fi : fj;
+        S.own[k] = (unsigned char)lane;
+        k++;
+        if (fi < fj) i++;
+        else j++;
       }
     }
+    __syncwarp();
+    for (int s = lane; s < T; s += 32) {
+      const int L = S.own[s];
+      S.t[s] = skinny_term(F[S.face[s]], S.a[L], S.b[L], S.vx[L], S.vy[L], S.vz[L], pos);
+    }
+    __syncwarp();
+    for (int k = 0; k < nt; k++) Cs = Cs + S.t[o + k];
+    __syncwarp();  // the next iteration overwrites the warp's slots
+  } else if (live) {
+    int i = a0, j = b0;
+    while (i < a1 || j < b1) {
+      const int fi = i < a1 ? idx[i] : 0x7fffffff;
+      const int fj = j < b1 ? idx[j] : 0x7fffffff;
+      if (fi == fj) {
+        i++;
+        j++;
+        continue;
+      }
+      int f;
+      if (fi < fj) { f = fi; i++; }
+      else { f = fj; j++; }
+      Cs = Cs + skinny_term(F[f], a, b, vxd, vyd, vzd, pos);
+    }
+  }
+  if (live) {
+    ntri += nt;
     const double cost = __fma_rn(ws, Cs, __fma_rn(wes, l, s2 * Q));
     float cf = __double2float_rn(cost);
     uint32_t cb = 0xffffffffu;  // non-finite: never eligible
