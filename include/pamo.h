@@ -223,6 +223,12 @@ pamo_status pamo_mlp_set_params(pamo_mlp* m, const float* h_params);
 /* Standardise the inputs before the first layer: x' = (x - mu) / sd per
  * feature (host, 16 floats each, sd > 0; FP32).  Default mu = 0, sd = 1. */
 pamo_status pamo_mlp_set_input_norm(pamo_mlp* m, const float* h_mu, const float* h_sd);
+/* Fit that standardisation to training data: mu and sd are the mean and the
+ * population standard deviation of each feature over the n rows of d_X
+ * (device, n x 16 float32), computed on the device in float64 in a fixed
+ * order (deterministic); an sd below 1e-6 is taken as 1.  Synchronises
+ * `stream`. */
+pamo_status pamo_mlp_fit_input_norm(pamo_mlp* m, const float* d_X, int64_t n, void* stream);
 /* Read the master parameters and/or the BF16 copy (host, may be NULL). */
 pamo_status pamo_mlp_get_params(const pamo_mlp* m, float* h_params, uint16_t* h_bf16);
 /* Probabilities (device, n floats) for n feature rows (device, n x 16). */
@@ -318,6 +324,22 @@ pamo_status pamo_ctx_round_pairs(const pamo_ctx* ctx, int64_t r, int32_t kind,
  * undone one (d_out: device, n_winners bytes). */
 pamo_status pamo_ctx_winner_features(pamo_ctx* ctx, float* d_X);
 pamo_status pamo_ctx_winner_standing(pamo_ctx* ctx, uint8_t* d_out);
+
+/* A deferral schedule (no counterpart in the paper; the bound on what the
+ * learned proposal can save).  In round r of the context (0 = its first
+ * round) every winner whose vertex pair (a, b), a < b, in that round's input
+ * numbering, is listed in h_pairs[2*h_off[r] .. 2*h_off[r+1]) is not collapsed
+ * and counts as undone (an invalid edge of the next round, Section 5.3),
+ * exactly like a predicted reject.  Given the undone pairs of every round of a
+ * plain run (pamo_ctx_round_pairs, kind 2), the run repeats that plain run's
+ * output, round by round, without any undo iteration: what a perfect
+ * predictor of the intersection check would save.
+ *   h_off: host int64 [n_rounds + 1], ascending from 0; h_pairs: host int32
+ *   pairs [h_off[n_rounds]][2] (copied).  Rounds beyond n_rounds defer nothing.
+ *   Call before the context's first round, on a single-mesh context without a
+ *   learned proposal; otherwise PAMO_EINVAL. */
+pamo_status pamo_ctx_set_deferrals(pamo_ctx* ctx, const int64_t* h_off, int64_t n_rounds,
+                                   const int32_t* h_pairs);
 
 /* Number of recorded rounds and the run status so far (PAMO_OK / ESTALL). */
 pamo_status pamo_ctx_rounds(const pamo_ctx* ctx, int64_t* rounds);

@@ -119,6 +119,14 @@ class MLP:
                                              sd.ctypes.data_as(ctypes.c_void_p)),
                "pamo_mlp_set_input_norm")
 
+    def fit_input_norm(self, X):
+        """Standardise inputs by the per-feature mean and standard deviation of
+        the rows of X (computed by the library on the device)."""
+        import torch
+        X = _dev(X, torch.float32, MLP_IN)
+        _check(lib().pamo_mlp_fit_input_norm(self.handle, _ptr(X), X.shape[0], _stream()),
+               "pamo_mlp_fit_input_norm")
+
     def get_params(self):
         """(fp32 master parameters, bf16 copy as uint16 bit patterns)."""
         p = np.zeros(MLP_PARAMS, np.float32)
@@ -189,10 +197,12 @@ def lib():
             "pamo_autotune_batch": (ctypes.c_int, [i32, P, P, P, P, P, P, P, P, P, P]),
             "pamo_ctx_winner_features": (ctypes.c_int, [P, P]),
             "pamo_ctx_winner_standing": (ctypes.c_int, [P, P]),
+            "pamo_ctx_set_deferrals": (ctypes.c_int, [P, P, i64, P]),
             "pamo_mlp_create": (ctypes.c_int, [ctypes.POINTER(P)]),
             "pamo_mlp_destroy": (None, [P]),
             "pamo_mlp_set_params": (ctypes.c_int, [P, P]),
             "pamo_mlp_set_input_norm": (ctypes.c_int, [P, P, P]),
+            "pamo_mlp_fit_input_norm": (ctypes.c_int, [P, P, i64, P]),
             "pamo_mlp_get_params": (ctypes.c_int, [P, P, P]),
             "pamo_mlp_forward": (ctypes.c_int, [P, P, i64, P, P]),
             "pamo_mlp_grad": (ctypes.c_int, [P, P, P, i64, ctypes.c_float, P, P]),
@@ -468,6 +478,19 @@ class Ctx:
         s = torch.empty(max(n_winners, 1), dtype=torch.uint8, device="cuda")
         _check(lib().pamo_ctx_winner_standing(self._h, _ptr(s)), "pamo_ctx_winner_standing")
         return s[:n_winners]
+
+    def set_deferrals(self, rounds):
+        """Defer, in round r, the winners whose vertex pairs are rows of
+        rounds[r] (int [n, 2], a < b, that round's numbering): they are not
+        collapsed and count as undone.  Call before the first round."""
+        arrs = [np.ascontiguousarray(np.asarray(p, np.int32).reshape(-1, 2)) for p in rounds]
+        off = np.zeros(len(arrs) + 1, np.int64)
+        off[1:] = np.cumsum([len(a) for a in arrs])
+        pairs = (np.concatenate(arrs) if arrs and off[-1] else np.zeros((1, 2), np.int32))
+        pairs = np.ascontiguousarray(pairs, np.int32)
+        _check(lib().pamo_ctx_set_deferrals(self._h, off.ctypes.data_as(ctypes.c_void_p),
+                                            len(arrs), pairs.ctypes.data_as(ctypes.c_void_p)),
+               "pamo_ctx_set_deferrals")
 
     def run(self, target_faces):
         st = _Stats()

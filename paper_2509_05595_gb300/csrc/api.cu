@@ -240,6 +240,7 @@ void free_ctx_buffers(pamo_ctx* c) {
   release(c->mvbase, st); release(c->flags_old, st);
   release(c->vgap, st); release(c->vgap_tmp, st); release(c->pX, st);
   release(c->pprob, st); release(c->pkeep, st); release(c->qface, st);
+  release(c->dsched, st); release(c->rlist, st);
   pinned_put(c->mcount_h, sizeof(int32_t) * 3 * (size_t)c->n_mesh);
   c->mcount_h = nullptr;
   for (int r = 0; r < 3; r++) release(c->cand[r], st);
@@ -364,7 +365,7 @@ pamo_status alloc_state(pamo_ctx* c, int64_t nV, int64_t nF) {
   A(vf_off, nV + 1); A(vf_idx, 3 * nF); A(vcount, nV + 1);
   A(E, c->Emax); A(e_off, nV + 1); A(key, c->Emax); A(vbar, c->Emax); A(vkey, nV);
   A(win, c->Emax); A(wscan, c->Emax + 1); A(wlist, c->Emax); A(standing, c->Emax);
-  A(undo, c->Emax); A(ftag, nF); A(qlist, nF);
+  A(undo, c->Emax); A(ftag, nF); A(qlist, nF); A(rlist, nF);
   A(fdead, nF); A(vdead, nV); A(vmap, nV + 1);
   A(dbuf, mx + 1); A(dbufF, nF + 1); A(flags, c->Emax); A(flags_next, c->Emax); A(dc, 1);
   A(E_prev, c->Emax); A(e_off_prev, nV + 1); A(cbits, c->Emax); A(cbits_prev, c->Emax);
@@ -720,7 +721,8 @@ pamo_status phase_select(pamo_ctx* c) {
   PAMO_TRY(select_winners(c));
   // exact-target mode (a full run only: the per-round entry points have no N_t)
   if (c->opt.exact_target && c->in_run) PAMO_TRY(trim_winners(c));
-  if (c->opt.proposal) PAMO_TRY(propose(c));  // learned deferral of predicted rejects
+  if (c->sched_on) PAMO_TRY(defer_scheduled(c));  // a given deferral schedule
+  else if (c->opt.proposal) PAMO_TRY(propose(c));  // learned deferral of predicted rejects
   // edges+keys read twice, vkey written and read, CSR+faces read, flags scanned
   kc_end(c, PAMO_KC_SELECT, nE * (2 * 16 + 1 + 1 + 4 + 1 + 4) + nV * (8 + 8 + 4) + nF * (16 + 12));
   return PAMO_OK;
@@ -774,6 +776,27 @@ pamo_status phase_check(pamo_ctx* c) {
   return PAMO_OK;
 }
 
+// a check iteration after an undo: the restored faces against the standing
+// collapses' faces (no refit; see bvh_recheck_restored), undo, outcome
+pamo_status phase_recheck(pamo_ctx* c) {
+  cudaStream_t st = c->st;
+  RoundCounters* dc = c->dc;
+  if (c->opt.check_mode == 3) return check_result(c);  // debug: no check
+  if (c->opt.check_mode == 1) {  // all-faces mode re-checks everything
+    PAMO_TRY(phase_refit(c));
+    return phase_check(c);
+  }
+  kc_begin(c, PAMO_KC_QUERY);
+  PAMO_TRY(bvh_recheck_restored(c->bvh, c->pos_s, c->F_s, c->fdead, c->ftag, c->rlist, c->undo,
+                                dc, c->cand, c->cand_cap, dc->ncand, &dc->nF, st));
+  kc_end(c, PAMO_KC_QUERY, 0.0);
+  kc_begin(c, 7);
+  PAMO_TRY(undo_marked(c));  // skipped on the device if a bucket overflowed
+  PAMO_TRY(check_result(c));
+  kc_end(c, 7, 0.0);
+  return PAMO_OK;
+}
+
 pamo_status phase_commit(pamo_ctx* c) {
   RoundCounters* dc = c->dc;
   kc_begin(c, PAMO_KC_COMMIT);
@@ -786,13 +809,16 @@ pamo_status phase_commit(pamo_ctx* c) {
   return PAMO_OK;
 }
 
-// eager fallback after a candidate overflow: the fused check on the same
-// mesh state, undo, outcome, gated commit
+// eager fallback after a candidate overflow: the fused check of every
+// standing collapse's faces on the refitted tree of the current mesh state
+// (a whole re-check, so the restored faces waiting in rlist are covered),
+// undo, outcome, gated commit
 pamo_status fallback_check(pamo_ctx* c) {
   cudaStream_t st = c->st;
   RoundCounters* dc = c->dc;
   PAMO_CUDA(cudaMemsetAsync(&dc->n_pairs, 0, 2 * sizeof(int), st));
   PAMO_CUDA(cudaMemsetAsync(&dc->cand_overflow, 0, sizeof(int), st));
+  if (c->opt.check_mode != 3) PAMO_TRY(phase_refit(c));
   kc_begin(c, PAMO_KC_QUERY);
   PAMO_TRY(bvh_check(c->bvh, c->pos_s, c->F_s, c->fdead, c->ftag, c->opt.check_mode == 1, c->qlist,
                      &dc->n_query, c->nF, c->undo, dc, nullptr, 0, (int)c->nF, st));
@@ -845,8 +871,7 @@ pamo_status round_body(pamo_ctx* c, bool carry) {
 }
 
 pamo_status recheck_body(pamo_ctx* c) {
-  PAMO_TRY(phase_refit(c));
-  PAMO_TRY(phase_check(c));
+  PAMO_TRY(phase_recheck(c));
   PAMO_TRY(phase_commit(c));
   return sync_out(c);
 }
@@ -1130,8 +1155,25 @@ void note_build(pamo_ctx* c, bool carry) {
 
 // one round of Algorithm 1 through the captured graphs: one synchronisation
 // unless the check found intersections (then one per undo iteration)
+// this round's part of the deferral schedule to the device (before the round)
+pamo_status stage_schedule(pamo_ctx* c) {
+  if (!c->sched_on) return PAMO_OK;
+  const int64_t R = (int64_t)c->sched_off.size() - 1;
+  const int64_t r = c->rounds;
+  const int64_t b = r < R ? c->sched_off[r] : 0, e = r < R ? c->sched_off[r + 1] : 0;
+  const int n = (int)(e - b);
+  c->sched_n = n;
+  if (n > 0)
+    PAMO_CUDA(cudaMemcpyAsync(c->dsched, c->sched_keys.data() + b, sizeof(unsigned long long) * n,
+                              cudaMemcpyHostToDevice, c->st));
+  PAMO_CUDA(cudaMemcpyAsync(&c->dc->n_sched, &c->sched_n, sizeof(int), cudaMemcpyHostToDevice,
+                            c->st));
+  return PAMO_OK;
+}
+
 pamo_status graph_round(pamo_ctx* c) {
   cudaStream_t st = c->st;
+  PAMO_TRY(stage_schedule(c));
   const bool carry = use_carry(c);
   const int slot = carry ? 1 : 0;
   if (!c->gA[slot]) PAMO_TRY(capture(c, slot, &c->gA[slot], [&] { return round_body(c, carry); }));
@@ -1178,6 +1220,7 @@ pamo_status round_cost(pamo_ctx* c) {
     set_error("pamo_round_cost: previous round not committed");
     return PAMO_EINVAL;
   }
+  PAMO_TRY(stage_schedule(c));
   PAMO_TRY(phase_begin(c));
   PAMO_TRY(phase_cost(c));
   PAMO_TRY(sync_now(c));
@@ -1224,7 +1267,7 @@ pamo_status round_check_undo(pamo_ctx* c) {
       set_error("undo loop did not settle");
       return PAMO_EINTERNAL;
     }
-    PAMO_TRY(phase_check(c));
+    PAMO_TRY(it == 0 ? phase_check(c) : phase_recheck(c));
     PAMO_TRY(sync_now(c));
     if (c->hc->cand_overflow) {
       PAMO_TRY(fallback_check(c));
@@ -1233,7 +1276,6 @@ pamo_status round_check_undo(pamo_ctx* c) {
     kc_resolve(c);
     PAMO_TRY(check_device_errors(c));
     if (c->hc->clean) break;
-    PAMO_TRY(phase_refit(c));
   }
   c->undo_iters = c->hc->undo_iters;
   c->last_pairs = c->hc->pairs_total;
@@ -1470,6 +1512,56 @@ pamo_status pamo_ctx_winner_standing(pamo_ctx* c, uint8_t* d_out) {
     PAMO_CUDA(cudaMemcpyAsync(d_out, c->standing, (size_t)c->nW, cudaMemcpyDeviceToDevice, c->st));
   PAMO_CUDA(cudaStreamSynchronize(c->st));
   return join(c);
+}
+
+pamo_status pamo_ctx_set_deferrals(pamo_ctx* c, const int64_t* h_off, int64_t n_rounds,
+                                   const int32_t* h_pairs) {
+  CTX_GUARD(c);
+  if (n_rounds < 0 || (n_rounds > 0 && (!h_off || (h_off[n_rounds] > 0 && !h_pairs)))) {
+    set_error("pamo_ctx_set_deferrals: offsets (n_rounds + 1) and pairs required");
+    return PAMO_EINVAL;
+  }
+  if (c->rounds != 0 || c->stage != 0 || c->n_mesh > 1 || c->opt.proposal) {
+    set_error("pamo_ctx_set_deferrals: a single-mesh context without a learned proposal, "
+              "before its first round");
+    return PAMO_EINVAL;
+  }
+  std::vector<int64_t> off(h_off, h_off + n_rounds + 1);
+  int64_t widest = 0;
+  for (int64_t r = 0; r < n_rounds; r++) {
+    if (off[r + 1] < off[r] || off[0] != 0) {
+      set_error("pamo_ctx_set_deferrals: offsets must start at 0 and not decrease");
+      return PAMO_EINVAL;
+    }
+    widest = std::max(widest, off[r + 1] - off[r]);
+  }
+  if (widest > c->Emax) {
+    set_error("pamo_ctx_set_deferrals: more pairs in a round than the mesh has edges");
+    return PAMO_EINVAL;
+  }
+  std::vector<unsigned long long> keys(n_rounds > 0 ? (size_t)off[n_rounds] : 0);
+  for (size_t i = 0; i < keys.size(); i++) {
+    const int32_t a = h_pairs[2 * i], b = h_pairs[2 * i + 1];
+    if (a < 0 || b <= a) {
+      set_error("pamo_ctx_set_deferrals: pairs must be (a, b) with 0 <= a < b");
+      return PAMO_EINVAL;
+    }
+    keys[i] = ((unsigned long long)(unsigned)a << 32) | (unsigned)b;
+  }
+  for (int64_t r = 0; r < n_rounds; r++)
+    std::sort(keys.begin() + off[r], keys.begin() + off[r + 1]);
+  PAMO_TRY(enter(c));
+  pamo_status s = PAMO_OK;
+  if (!c->pkeep) s = alloc(&c->pkeep, (size_t)c->Emax, c->st);
+  if (s == PAMO_OK && c->dsched) release(c->dsched, c->st);
+  if (s == PAMO_OK) s = alloc(&c->dsched, (size_t)std::max<int64_t>(widest, 1), c->st);
+  if (s == PAMO_OK) {
+    c->sched_off.swap(off);
+    c->sched_keys.swap(keys);
+    c->sched_on = true;
+  }
+  pamo_status j = join(c);
+  return s != PAMO_OK ? s : j;
 }
 
 pamo_status pamo_ctx_rounds(const pamo_ctx* c, int64_t* rounds) {

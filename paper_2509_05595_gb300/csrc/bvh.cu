@@ -362,9 +362,14 @@ __global__ void k_refit(const float4* __restrict__ pos, const int4* __restrict__
 }
 
 // start of a split check: zero the pair / undo / candidate counters and fold
-// a refit overflow into the round's overflow word
+// a refit overflow into the round's overflow word; a re-check also moves its
+// query window to the faces the last undo restored
 __global__ void k_check_begin(const int32_t* __restrict__ refit_overflow,
-                              RoundCounters* __restrict__ dc) {
+                              RoundCounters* __restrict__ dc, int advance) {
+  if (advance) {
+    dc->rest_lo = dc->rest_mid;
+    dc->rest_mid = dc->rest_end;
+  }
   dc->n_pairs = 0;
   dc->n_undo = 0;
   dc->ncand[0] = dc->ncand[1] = dc->ncand[2] = 0;
@@ -549,6 +554,89 @@ __global__ void __launch_bounds__(kBlock) k_traverse(
           if (g == f) continue;
           const int tg = ftag ? ftag[g] : -1;
           if (query_all ? (g < f) : (tg >= 0 && g < f)) continue;
+          const int4 gv = F[g];
+          int s = 0;
+          s += (gv.x == tv.x) | (gv.x == tv.y) | (gv.x == tv.z);
+          s += (gv.y == tv.x) | (gv.y == tv.y) | (gv.y == tv.z);
+          s += (gv.z == tv.x) | (gv.z == tv.y) | (gv.z == tv.z);
+          const int r = s >= 2 ? 2 : s;
+          // warp-aggregated append into bucket r
+          const unsigned act = __activemask();
+          const unsigned peers = __match_any_sync(act, r);
+          const int leader = __ffs(peers) - 1;
+          const int lane = threadIdx.x & 31;
+          int base = 0;
+          if (lane == leader) base = atomicAdd(&ncand[r], __popc(peers));
+          base = __shfl_sync(peers, base, leader);
+          const int slot = base + __popc(peers & ((1u << lane) - 1u));
+          if (slot < cb.cap[r]) cb.c[r][slot] = make_int2(f, g);
+        } else if (next < 0) {
+          next = cn;
+        } else {
+          if (sp >= kStack) {
+            atomicOr(&dc->overflow, 1);
+            next = -2;
+            break;
+          }
+          stack[sp++] = cn;
+        }
+      }
+      if (next == -2) break;
+      if (next >= 0) {
+        node = next;
+      } else {
+        if (sp == 0) break;
+        node = stack[--sp];
+      }
+    }
+  }
+}
+
+// The re-check after an undo.  The previous mesh M_1 is intersection-free, so
+// a restored face (an M_1 face again) meets no unchanged or restored face, and
+// faces of standing collapses met no other in the last iteration (both
+// collapses would have been undone); every intersecting pair of this
+// iteration is therefore a restored face and a live face of a standing
+// collapse (ftag >= 0), found from the restored side.  The tree is the one
+// refitted for the first iteration: the standing faces have not moved since,
+// so their leaf boxes, and every ancestor's, still contain them (the stale
+// leaves of restored faces only add candidates that the tag test drops).
+// Each query also rewrites its face's predicate info for the pair test.
+__global__ void __launch_bounds__(kBlock) k_traverse_restored(
+    const float* __restrict__ nodes, const int* n_dev, const float4* __restrict__ pos,
+    const int4* __restrict__ F, const uint8_t* __restrict__ fdead,
+    const int32_t* __restrict__ ftag, const int32_t* __restrict__ rlist, CandBufs cb,
+    int* __restrict__ ncand, RoundCounters* __restrict__ dc, uint8_t* __restrict__ info,
+    const int32_t* __restrict__ vmesh, const int32_t* __restrict__ mroot) {
+  const int n = *n_dev;
+  const int lo = dc->rest_lo, hi = dc->rest_mid;
+  if (n < 2) return;
+  for (int i = lo + blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += gridDim.x * blockDim.x) {
+    const int f = rlist[i];
+    const int4 tv = F[f];
+    const float4 a = pos[tv.x], b = pos[tv.y], c = pos[tv.z];
+    info[f] = pack_info(exact::face_info(make_float3(a.x, a.y, a.z), make_float3(b.x, b.y, b.z),
+                                         make_float3(c.x, c.y, c.z)));
+    const float3 qlo = make_float3(fminf(fminf(a.x, b.x), c.x), fminf(fminf(a.y, b.y), c.y),
+                                   fminf(fminf(a.z, b.z), c.z));
+    const float3 qhi = make_float3(fmaxf(fmaxf(a.x, b.x), c.x), fmaxf(fmaxf(a.y, b.y), c.y),
+                                   fmaxf(fmaxf(a.z, b.z), c.z));
+    int stack[kStack];
+    int sp = 0, node = mroot ? mroot[vmesh[tv.x]] : 0;  // the query's own mesh
+    for (int visits = 0;; visits++) {
+      if (visits >= 2 * n) {
+        atomicOr(&dc->overflow, 4);
+        break;
+      }
+      const NodeHits h = visit(nodes, node, qlo, qhi);
+      int next = -1;
+#pragma unroll
+      for (int k = 0; k < 2; k++) {
+        if (!(k ? h.r : h.l)) continue;
+        const int cn = k ? h.R : h.L;
+        if (cn < 0) {
+          const int g = ~cn;
+          if (g == f || ftag[g] < 0 || fdead[g]) continue;
           const int4 gv = F[g];
           int s = 0;
           s += (gv.x == tv.x) | (gv.x == tv.y) | (gv.x == tv.z);
@@ -837,7 +925,7 @@ pamo_status bvh_check_split(Bvh& b, const float4* pos, const int4* F, const uint
                             const int* qcount, uint8_t* undo, RoundCounters* dc, int2* const cand[3],
                             const int64_t cap[3], int* ncand, const int* n_dev, int grid,
                             cudaStream_t st) {
-  k_check_begin<<<1, 1, 0, st>>>((const int32_t*)b.flags.p + b.n_max + 1, dc); note_launch();
+  k_check_begin<<<1, 1, 0, st>>>((const int32_t*)b.flags.p + b.n_max + 1, dc, 0); note_launch();
   CandBufs cb;
   for (int r = 0; r < 3; r++) {
     cb.c[r] = cand[r];
@@ -852,6 +940,30 @@ pamo_status bvh_check_split(Bvh& b, const float4* pos, const int4* F, const uint
                                         many ? (const int32_t*)b.mroot.p : nullptr); note_launch();
   k_pairs<<<g_pairs, kItemBlock, 0, st>>>(cb, ncand, pos, F, (const uint8_t*)b.face_aux.p, ftag, undo,
                                    dc, b.vgap); note_launch();
+  PAMO_CUDA(cudaGetLastError());
+  return PAMO_OK;
+}
+
+pamo_status bvh_recheck_restored(Bvh& b, const float4* pos, const int4* F, const uint8_t* fdead,
+                                 const int32_t* ftag, const int32_t* rlist, uint8_t* undo,
+                                 RoundCounters* dc, int2* const cand[3], const int64_t cap[3],
+                                 int* ncand, const int* n_dev, cudaStream_t st) {
+  k_check_begin<<<1, 1, 0, st>>>((const int32_t*)b.flags.p + b.n_max + 1, dc, 1); note_launch();
+  CandBufs cb;
+  for (int r = 0; r < 3; r++) {
+    cb.c[r] = cand[r];
+    cb.cap[r] = cap[r];
+  }
+  const bool many = b.n_mesh > 1;
+  static const int g_trav = occ_grid(k_traverse_restored);
+  static const int g_pairs = occ_grid(k_pairs, kItemBlock);
+  k_traverse_restored<<<g_trav, kBlock, 0, st>>>((const float*)b.nodes.p, n_dev, pos, F, fdead,
+                                                 ftag, rlist, cb, ncand, dc,
+                                                 (uint8_t*)b.face_aux.p,
+                                                 many ? b.vmesh : nullptr,
+                                                 many ? (const int32_t*)b.mroot.p : nullptr); note_launch();
+  k_pairs<<<g_pairs, kItemBlock, 0, st>>>(cb, ncand, pos, F, (const uint8_t*)b.face_aux.p, ftag,
+                                          undo, dc, b.vgap); note_launch();
   PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;
 }

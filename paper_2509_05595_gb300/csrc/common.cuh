@@ -88,7 +88,7 @@ struct RoundCounters {
   int target;               // N_t of the running simplification
   unsigned max_bits;        // float bits of the target edge cost (0x7f800000 = off)
   int last_committed;       // collapses committed by the last round (1 at the start)
-  int pad1;
+  int n_sched;              // scheduled deferrals of this round (pamo_ctx_set_deferrals)
   // ---- zeroed at the start of every round (from link_rejects on)
   unsigned long long link_rejects, flagged, eligible;
   unsigned long long cost_tris;  // triangles produced, summed over evaluated edges
@@ -105,6 +105,9 @@ struct RoundCounters {
   int sort_len;             // spare
   int deferred;             // edges deferred by the learned proposal
   int n_listed;             // eligible edges listed for the proposal
+  // faces restored by undos this round (rlist): [rest_lo, rest_mid) are the
+  // queries of the current re-check, rest_end the append position
+  int rest_lo, rest_mid, rest_end;
 };
 
 #define PAMO_ROUND_ZERO_OFFSET offsetof(::pamo::RoundCounters, link_rejects)
@@ -206,6 +209,14 @@ struct pamo_ctx {
   float* pX = nullptr;                 // [Emax][16] winner features
   float* pprob = nullptr;              // [Emax] predicted probability of an undo
   uint8_t* pkeep = nullptr;            // [Emax] winner not deferred
+  int32_t* rlist = nullptr;            // [nF] faces restored by this round's undos
+  // deferral schedule (pamo_ctx_set_deferrals): host keys (a << 32 | b, sorted
+  // within a round) with per-round offsets, and this round's keys on the device
+  std::vector<int64_t> sched_off;
+  std::vector<unsigned long long> sched_keys;
+  unsigned long long* dsched = nullptr;
+  int sched_n = 0;  // host source of this round's count
+  bool sched_on = false;
   int64_t deferred_total = 0;
   cudaEvent_t round_ev[2] = {nullptr, nullptr};  // device time of a round (records)
   int64_t last_round_us = 0;
@@ -358,6 +369,8 @@ pamo_status edge_costs(pamo_ctx* c);
 
 // propose.cu / mlp.cu: the learned proposal
 pamo_status propose(pamo_ctx* c);
+// marks the winners named by the deferral schedule for this round as deferred
+pamo_status defer_scheduled(pamo_ctx* c);
 pamo_status edge_features_list(pamo_ctx* c, const int32_t* list, const int* n_dev, float* X,
                                cudaStream_t st);
 pamo_status mlp_forward_dev(const pamo_mlp* m, const float* X, const int* n_dev, float* prob,
@@ -400,6 +413,15 @@ pamo_status bvh_check_split(Bvh& b, const float4* pos, const int4* F, const uint
                             const int* qcount, uint8_t* undo, RoundCounters* dc, int2* const cand[3],
                             const int64_t cap[3], int* ncand, const int* n_dev, int grid,
                             cudaStream_t st);
+// A re-check after an undo (every check iteration after the first): the
+// faces the last undo restored (rlist[dc->rest_lo, dc->rest_mid) once the
+// window is advanced) against the faces of standing collapses, on the tree as
+// it was refitted for the first iteration; same candidate buckets and exact
+// pair test as bvh_check_split.
+pamo_status bvh_recheck_restored(Bvh& b, const float4* pos, const int4* F, const uint8_t* fdead,
+                                 const int32_t* ftag, const int32_t* rlist, uint8_t* undo,
+                                 RoundCounters* dc, int2* const cand[3], const int64_t cap[3],
+                                 int* ncand, const int* n_dev, cudaStream_t st);
 // After a commit: keep the leaf order for the compacted faces (stable filter
 // of the current order through fdead / dead_before); sizes from the device.
 // b.posn must hold the exclusive scan of the live leaves (fdead[vals[i]] == 0,

@@ -240,6 +240,51 @@ __global__ void k_to_bf16(const float* __restrict__ p, __nv_bfloat16* __restrict
   if (i < kParams) pb[i] = __float2bfloat16_rn(p[i]);
 }
 
+// Input standardisation from the training data: per feature, the mean and
+// the population standard deviation over n rows, in float64 with a fixed
+// reduction order (deterministic), two passes (mean, then squared
+// deviations).  kNormBlocks blocks of 16 x 16 threads: thread (r, j) sums
+// feature j over rows b + kNormBlocks (r + 16 k); the 16 row lanes, then the
+// blocks, are summed in order.
+constexpr int kNormBlocks = 256;
+
+__global__ void __launch_bounds__(256) k_norm_pass(const float* __restrict__ X, int64_t n,
+                                                   const double* __restrict__ mean,
+                                                   double* __restrict__ part) {
+  __shared__ double acc[16][kIn];
+  const int j = threadIdx.x % kIn, r = threadIdx.x / kIn;
+  const double m = mean ? mean[j] : 0.0;
+  double s = 0.0;
+  for (int64_t i = blockIdx.x + (int64_t)kNormBlocks * r; i < n; i += (int64_t)kNormBlocks * 16) {
+    const double x = (double)X[kIn * i + j];
+    s = mean ? s + (x - m) * (x - m) : s + x;
+  }
+  acc[r][j] = s;
+  __syncthreads();
+  if (r == 0) {
+    double t = 0.0;
+    for (int q = 0; q < 16; q++) t += acc[q][j];
+    part[blockIdx.x * kIn + j] = t;
+  }
+}
+
+// sums the block partials in block order; first pass: mean; second: the
+// standardisation (mu, 1/sd), sd below 1e-6 taken as 1
+__global__ void k_norm_final(const double* __restrict__ part, int64_t n, double* __restrict__ mean,
+                             float* __restrict__ norm, int second) {
+  const int j = threadIdx.x;
+  if (j >= kIn) return;
+  double t = 0.0;
+  for (int b = 0; b < kNormBlocks; b++) t += part[b * kIn + j];
+  if (!second) {
+    mean[j] = t / (double)n;
+  } else {
+    const double sd = sqrt(t / (double)n);
+    norm[j] = (float)mean[j];
+    norm[kIn + j] = sd < 1e-6 ? 1.0f : (float)(1.0 / sd);
+  }
+}
+
 size_t grad_smem_bytes() {
   return sizeof(float) *
          ((size_t)2 * kParams + 2 * kIn + 1 + kChunk * kIn + 4 * kChunk * kH + 2 * kChunk);
@@ -352,6 +397,26 @@ pamo_status pamo_mlp_set_input_norm(pamo_mlp* m, const float* h_mu, const float*
     v[kIn + i] = 1.0f / h_sd[i];
   }
   PAMO_CUDA(cudaMemcpy(m->norm, v, sizeof(v), cudaMemcpyHostToDevice));
+  return PAMO_OK;
+}
+
+pamo_status pamo_mlp_fit_input_norm(pamo_mlp* m, const float* d_X, int64_t n, void* stream) {
+  if (!m || !d_X || n <= 0) {
+    set_error("model and at least one feature row required");
+    return PAMO_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  double* buf = nullptr;  // [kNormBlocks][16] partials, then [16] means
+  PAMO_CUDA(cudaMallocAsync((void**)&buf, sizeof(double) * (kNormBlocks + 1) * kIn, st));
+  double* mean = buf + kNormBlocks * kIn;
+  k_norm_pass<<<kNormBlocks, 256, 0, st>>>(d_X, n, nullptr, buf); note_launch();
+  k_norm_final<<<1, 32, 0, st>>>(buf, n, mean, m->norm, 0); note_launch();
+  k_norm_pass<<<kNormBlocks, 256, 0, st>>>(d_X, n, mean, buf); note_launch();
+  k_norm_final<<<1, 32, 0, st>>>(buf, n, mean, m->norm, 1); note_launch();
+  cudaError_t e = cudaGetLastError();
+  cudaFreeAsync(buf, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "pamo_mlp_fit_input_norm");
   return PAMO_OK;
 }
 

@@ -160,7 +160,38 @@ __global__ void k_defer_mark(RoundCounters* __restrict__ dc, const float* __rest
   if ((threadIdx.x & 31) == 0 && d) atomicAdd(&dc->deferred, d);
 }
 
+// scheduled deferrals: a winner whose vertex pair is in this round's sorted
+// schedule is not collapsed and counts as undone, like a predicted reject
+__global__ void k_defer_sched(RoundCounters* __restrict__ dc, const int32_t* __restrict__ wlist,
+                              const int2* __restrict__ E, const unsigned long long* __restrict__ sched,
+                              uint8_t* __restrict__ keep) {
+  const int n = dc->nW, ns = dc->n_sched;
+  int d = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int2 ab = E[wlist[i]];
+    const unsigned long long k = ((unsigned long long)(unsigned)ab.x << 32) | (unsigned)ab.y;
+    int lo = 0, hi = ns;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (sched[mid] < k) lo = mid + 1;
+      else hi = mid;
+    }
+    const bool defer = lo < ns && sched[lo] == k;
+    keep[i] = defer ? 0 : 1;
+    d += defer;
+  }
+  d = __reduce_add_sync(0xffffffffu, d);
+  if ((threadIdx.x & 31) == 0 && d) atomicAdd(&dc->deferred, d);
+}
+
 }  // namespace
+
+pamo_status defer_scheduled(pamo_ctx* c) {
+  k_defer_sched<<<c->grid, kBlock, 0, c->st>>>(c->dc, c->wlist, c->E, c->dsched, c->pkeep); note_launch();
+  PAMO_CUDA(cudaGetLastError());
+  return PAMO_OK;
+}
 
 pamo_status edge_features_list(pamo_ctx* c, const int32_t* list, const int* n_dev, float* X,
                                cudaStream_t st) {

@@ -154,7 +154,9 @@ __global__ void k_stage_ms(const RoundCounters* __restrict__ dc, const float4* _
   }
 }
 
-// Undo every marked, still-standing collapse: its region returns to M_1.
+// Undo every marked, still-standing collapse: its region returns to M_1, and
+// its faces (each once) are appended to rlist, the queries of the next
+// re-check.
 __global__ void k_undo(const int32_t* __restrict__ wlist, const int2* __restrict__ E,
                        const float4* __restrict__ pos, const double* __restrict__ K,
                        const int32_t* __restrict__ off, const int32_t* __restrict__ idx,
@@ -162,7 +164,8 @@ __global__ void k_undo(const int32_t* __restrict__ wlist, const int2* __restrict
                        double* __restrict__ K_s, int4* __restrict__ F_s,
                        uint8_t* __restrict__ fdead, uint8_t* __restrict__ vdead,
                        int32_t* __restrict__ ftag, uint8_t* __restrict__ standing,
-                       uint8_t* __restrict__ undo, RoundCounters* __restrict__ dc) {
+                       uint8_t* __restrict__ undo, RoundCounters* __restrict__ dc,
+                       int32_t* __restrict__ rlist) {
   if (dc->cand_overflow) return;  // marks incomplete: the host reruns the fused check
   const int nW = dc->nW;
   int n = 0;
@@ -183,13 +186,22 @@ __global__ void k_undo(const int32_t* __restrict__ wlist, const int2* __restrict
 #pragma unroll
       for (int i = 0; i < 5; i++) dst[i] = src[i];
       vdead[b] = 0;
+      // the region's faces: those around a, then those around b without a
+      int nr = off[a + 1] - off[a];
+      for (int s = off[b]; s < off[b + 1]; s++) {
+        const int4 t = F[idx[s]];
+        nr += !(t.x == a || t.y == a || t.z == a);
+      }
+      int q = atomicAdd(&dc->rest_end, nr);
       for (int pass = 0; pass < 2; pass++) {
         const int v = pass ? b : a;
         for (int s = off[v]; s < off[v + 1]; s++) {
           const int f = idx[s];
-          F_s[f] = F[f];
+          const int4 t = F[f];
+          F_s[f] = t;
           fdead[f] = 0;
           ftag[f] = -1;
+          if (pass == 0 || !(t.x == a || t.y == a || t.z == a)) rlist[q++] = f;
         }
       }
     }
@@ -338,7 +350,7 @@ pamo_status collapse_winners(pamo_ctx* c) {
   k_collapse<<<g_collapse, kBlock, 0, st>>>(c->wlist, dc, c->E, c->vbar, c->K, c->vf_off, c->vf_idx, c->F,
                                    c->pos_s, c->K_s, c->F_s, c->fdead, c->vdead, c->ftag,
                                    c->standing, c->undo, c->qlist, &dc->n_query,
-                                   c->opt.proposal ? c->pkeep : nullptr); note_launch();
+                                   (c->opt.proposal || c->sched_on) ? c->pkeep : nullptr); note_launch();
   PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;
 }
@@ -346,7 +358,7 @@ pamo_status collapse_winners(pamo_ctx* c) {
 pamo_status undo_marked(pamo_ctx* c) {
   k_undo<<<c->grid, kBlock, 0, c->st>>>(c->wlist, c->E, c->pos, c->K, c->vf_off, c->vf_idx, c->F,
                                         c->pos_s, c->K_s, c->F_s, c->fdead, c->vdead, c->ftag,
-                                        c->standing, c->undo, c->dc); note_launch();
+                                        c->standing, c->undo, c->dc, c->rlist); note_launch();
   PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;
 }

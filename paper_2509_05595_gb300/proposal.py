@@ -71,17 +71,13 @@ def train(X, y, steps=2000, batch=8192, lr=2e-3, seed=0, pos_weight=None, log_ev
     """Train a network on (X, y) with weighted binary cross-entropy and Adam,
     all in the library's kernels; returns (MLP taking raw features, losses)."""
     import torch
-    Xh = X.detach().cpu().numpy().astype(np.float64)
-    mu = Xh.mean(0)
-    sd = Xh.std(0)
-    sd[sd < 1e-6] = 1.0
     X = X.contiguous()
     y = y.to(torch.float32).contiguous()
     npos = float(y.sum().item())
     nneg = float(len(y) - npos)
     pw = pos_weight if pos_weight is not None else max(1.0, nneg / max(npos, 1.0))
     m = MLP(he_init(seed))
-    m.set_input_norm(mu, sd)  # standardised in the kernels (FP32)
+    m.fit_input_norm(X)  # mean / sd on the device; applied in the kernels (FP32)
     rng = np.random.default_rng(seed + 1)
     n = len(y)
     losses = []

@@ -126,3 +126,161 @@ def test_training_and_deferral_keep_the_output_valid():
     n_pairs, _ = pamo.pamo_check_self_intersections(Vo, Fo)
     assert n_pairs == 0
     assert st["deferred"] > 0
+
+
+def _plain_run_with_rounds(V, F, target):
+    c = pamo.Ctx(torch.from_numpy(V), torch.from_numpy(F), record_rounds=1)
+    st, status = c.run(target)
+    n, _ = c.rounds()
+    rounds = []
+    for r in range(n):
+        d = c.round_info(r)
+        d["committed_pairs"] = c.round_pairs(r, 1)
+        d["undone_pairs"] = c.round_pairs(r, 2)
+        rounds.append(d)
+    Vo, Fo = c.export()
+    c.close()
+    return Vo.cpu().numpy(), Fo.cpu().numpy(), st, status, rounds
+
+
+def test_perfect_deferral_replays_the_plain_run_without_undo_iterations():
+    """The bound on the learned proposal: deferring, in every round, exactly
+    the winners the plain run's check undid (pamo_ctx_set_deferrals) gives the
+    plain run's output and per-round committed / undone sets, with a single
+    clean check per round -- all the undo work a predictor could save."""
+    V, F = meshgen.nested_shells(5, check=False)
+    target = len(F) // 60
+    Vp, Fp, stp, sp, rp = _plain_run_with_rounds(V, F, target)
+    undone = [d["undone_pairs"] for d in rp]
+    assert sum(len(u) for u in undone) > 50 and stp["undo_iters_hist"][0] < stp["rounds"]
+    c = pamo.Ctx(torch.from_numpy(V), torch.from_numpy(F), record_rounds=1)
+    c.set_deferrals(undone)
+    st, status = c.run(target)
+    n, _ = c.rounds()
+    assert status == sp and n == len(rp)
+    for r in range(n):
+        d = c.round_info(r)
+        assert d["undo_iters"] == 0 and d["pairs_found"] == 0, r
+        assert d["winners"] == rp[r]["winners"] and d["committed"] == rp[r]["committed"], r
+        assert np.array_equal(c.round_pairs(r, 1), rp[r]["committed_pairs"]), r
+        assert np.array_equal(c.round_pairs(r, 2), rp[r]["undone_pairs"]), r
+    Vo, Fo = c.export()
+    c.close()
+    assert np.array_equal(Fo.cpu().numpy(), Fp)
+    assert np.array_equal(Vo.cpu().numpy().view(np.uint32), Vp.view(np.uint32))
+    assert st["deferred"] == sum(len(u) for u in undone)
+    assert st["undo_iters_hist"][0] == st["rounds"]
+
+
+def test_deferral_schedule_arguments():
+    V, F = meshgen.nested_shells(3, check=False)
+    c = pamo.Ctx(torch.from_numpy(V), torch.from_numpy(F))
+    with pytest.raises(pamo.PamoError, match="EINVAL"):
+        c.set_deferrals([np.array([[5, 3]])])          # a > b
+    c.round_cost()
+    with pytest.raises(pamo.PamoError, match="EINVAL"):  # after the first round began
+        c.set_deferrals([np.zeros((0, 2))])
+    c.close()
+
+
+def _features_cpu(V, F, ab, vbar, cost, scale):
+    """The 16 winner features restated in float32 numpy from their definition
+    (round 0: no clearance known yet, no survivor of an earlier round)."""
+    f32 = np.float32
+    P = V.astype(f32)
+    out = np.zeros((len(ab), 16), f32)
+    faces_of = [[] for _ in range(len(V))]
+    for fi, t in enumerate(F):
+        for x in t:
+            faces_of[x].append(fi)
+    for i, (a, b) in enumerate(ab):
+        pa, pb, v = P[a], P[b], vbar[i].astype(f32)
+        l = max(f32(np.linalg.norm(pb - pa)), f32(1e-30))
+        mincos, sumcos, minq, sumskin, aold, anew, dmax = f32(1), f32(0), f32(1), f32(0), f32(0), f32(0), f32(0)
+        ntri, nab = 0, []
+        seen = set()
+        for x in (a, b):
+            for fi in faces_of[x]:
+                if fi in seen:
+                    continue
+                seen.add(fi)
+                t = F[fi]
+                q = P[t]
+                n_old = np.cross(q[1] - q[0], q[2] - q[0]).astype(f32)
+                lo = f32(np.linalg.norm(n_old))
+                aold += f32(0.5) * lo
+                if lo > 0:
+                    dmax = max(dmax, f32(abs(np.dot(n_old, v - q[0])) / lo))
+                if a in t and b in t:
+                    nab.append(n_old)
+                    continue
+                r = np.array([v if c in (a, b) else P[c] for c in t], f32)
+                u, w = r[1] - r[0], r[2] - r[0]
+                n_new = np.cross(u, w).astype(f32)
+                ln = f32(np.linalg.norm(n_new))
+                c = f32(np.dot(n_new, n_old) / (ln * lo)) if ln > 0 and lo > 0 else f32(-1)
+                mincos = min(mincos, c)
+                sumcos += c
+                den = f32(np.dot(u, u) + np.dot(w, w) + np.dot(w - u, w - u))
+                qq = f32(3.4641016) * ln / den if den > 0 else f32(0)
+                minq = min(minq, qq)
+                sumskin += f32(1) - qq
+                anew += f32(0.5) * ln
+                ntri += 1
+        dih = f32(1)
+        if len(nab) == 2:
+            l0, l1 = np.linalg.norm(nab[0]), np.linalg.norm(nab[1])
+            dih = f32(np.dot(nab[0], nab[1]) / (l0 * l1)) if l0 > 0 and l1 > 0 else f32(-1)
+        va, vb = len(faces_of[a]), len(faces_of[b])
+        nt = f32(max(ntri, 1))
+        mid = f32(0.5) * (pa + pb)
+        gap = f32(np.inf)
+        out[i] = [np.log10(max(cost[i], 1e-12)), np.log2(max(scale * l, 1e-12)),
+                  np.linalg.norm(v - mid) / l, va / 6, vb / 6, (va + vb - 4) / 6, dih,
+                  mincos, sumcos / nt, minq, sumskin / nt,
+                  min(max(np.log2(max(dmax, 1e-30) / gap) if np.isfinite(gap) else -np.inf, -10), 10),
+                  np.log2(max(aold / (l * l), 1e-12)), anew / aold if aold > 0 else 0,
+                  min(max(np.log2(gap / l) if np.isfinite(gap) else np.inf, -10), 10), 0]
+    return out
+
+
+def test_winner_features_match_a_cpu_restatement():
+    """Every one of the 16 features of the round-0 winners, restated in float32
+    numpy from the definitions (the winners, their placements and costs from
+    the oracle), element by element."""
+    import oracle
+    V, F = meshgen.nested_shells(4, check=False)
+    c = pamo.Ctx(torch.from_numpy(V), torch.from_numpy(F))
+    c.round_cost()
+    nW = c.round_select()
+    X = c.winner_features(nW).cpu().numpy()
+    c.close()
+    ref = oracle.simplify(V, F, len(F) // 4, max_rounds=1)
+    pairs = ref.rounds[0]["winner_pairs"]   # edge order, as the GPU lists winners
+    assert len(pairs) == nW > 100
+    T = oracle.edge_table(V, F)
+    row = {tuple(p): i for i, p in enumerate(T["ab"].tolist())}
+    idx = np.array([row[tuple(p)] for p in pairs.tolist()])
+    cost = (T["key"][idx] >> np.uint64(32)).astype(np.uint32).view(np.float32)
+    scale = 1.0 / (V.astype(np.float64).max(0) - V.astype(np.float64).min(0)).max()
+    want = _features_cpu(V, F, pairs, T["vbar"][idx], cost, np.float32(scale))
+    assert np.allclose(X, want, rtol=2e-5, atol=2e-5), np.abs(X - want).max(0)
+
+
+def test_fitted_input_norm_matches_numpy_statistics():
+    """pamo_mlp_fit_input_norm (device, float64, fixed order) against numpy's
+    mean and population standard deviation: the fitted model and one given
+    numpy's statistics predict the same probabilities."""
+    rng = np.random.default_rng(9)
+    X = (rng.normal(size=(100003, 16)) * rng.uniform(0.01, 50, 16)
+         + rng.uniform(-100, 100, 16)).astype(np.float32)
+    X[:, 7] = 3.0  # a constant feature: sd taken as 1
+    p = proposal.he_init(4)
+    a, b = pamo.MLP(p), pamo.MLP(p)
+    a.fit_input_norm(torch.from_numpy(X))
+    Xd = X.astype(np.float64)
+    sd = Xd.std(0)
+    sd[sd < 1e-6] = 1.0
+    b.set_input_norm(Xd.mean(0).astype(np.float32), sd.astype(np.float32))
+    Q = torch.from_numpy(X[:5000])
+    assert torch.allclose(a.forward(Q), b.forward(Q), rtol=1e-5, atol=1e-6)
