@@ -314,9 +314,10 @@ def make_batch(count=256):
     return V, voff, F, foff, targets
 
 
-def run_batch_bench(args, world, rank):
+def run_batch_bench(args, world, rank, emit=True):
     """Many meshes per pass: the batched path against the same meshes run one
-    call at a time through the plain path (both device-resident, CUDA events)."""
+    call at a time through the plain path (both device-resident, CUDA events).
+    emit=False returns the line instead of printing it."""
     import torch
     import paper_2509_05595_gb300 as pamo
     V, voff, F, foff, targets = make_batch(args.batch_count)
@@ -380,19 +381,24 @@ def run_batch_bench(args, world, rank):
                          "trials": "resort 25/50/75/100 at 6 blocks/SM, then 4 and 8 blocks/SM"},
             "clocks": clk,
             "gpu_launches": int(launches)}
-    if rank == 0:
+    if rank == 0 and emit:
         print(json.dumps(line), flush=True)
+    return line
 
 
-def one_sided_hausdorff(Vo, Fo, V, F, k=16):
+def one_sided_hausdorff(Vo, Fo, V, F, k=16, tree=None, T=None):
     """max over the output's vertices and face centroids of the distance to
     the input surface (exact point-to-triangle distance to the k input faces
-    whose centroids are nearest; float64)."""
+    whose centroids are nearest; float64).  tree, T: a kd-tree of the input's
+    face centroids and its corner array, built once by the caller."""
     from scipy.spatial import cKDTree
-    Vo, V = np.asarray(Vo, np.float64), np.asarray(V, np.float64)
+    Vo = np.asarray(Vo, np.float64)
     Q = np.concatenate([Vo, Vo[np.asarray(Fo)].mean(1)])
-    T = V[np.asarray(F)]
-    _, cand = cKDTree(T.mean(1)).query(Q, k=min(k, len(F)))
+    if T is None:
+        T = np.asarray(V, np.float64)[np.asarray(F)]
+    if tree is None:
+        tree = cKDTree(T.mean(1))
+    _, cand = tree.query(Q, k=min(k, len(T)))
     A, B, C = T[cand, 0], T[cand, 1], T[cand, 2]
     P = Q[:, None, :]
     # closest point on triangle (Ericson, Real-Time Collision Detection, 5.1.5)
@@ -424,58 +430,130 @@ def one_sided_hausdorff(Vo, Fo, V, F, k=16):
     return float(dist.max())
 
 
-def run_learned_bench(args, world, rank):
-    """The learned proposal against the plain method: labels logged by the
-    plain method on the near-contact family (nested shells, seeds 1000..),
-    the network trained by the library's kernels, then both methods on
-    held-out seeds (2000..): Mfaces/s, undo work, faces, self-intersections
-    and the one-sided Hausdorff distance to the input."""
-    import torch
+def _shells_vertices(args):
+    """Worker: the vertices of one near-contact mesh (the faces are the same
+    for every seed of a level)."""
     import meshgen
+    level, seed = args
+    V, _ = meshgen.nested_shells_seeded(level, seed)
+    return V
+
+
+def _shells_stream(level, seeds, procs):
+    """(seed, V, F) for each seed, generated by `procs` worker processes."""
+    import multiprocessing as mp
+    import meshgen
+    _, F = meshgen.nested_shells(level, check=False)  # shared connectivity
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        for seed, V in zip(seeds, pool.imap(_shells_vertices, [(level, s) for s in seeds])):
+            yield seed, V, F
+
+
+class _Hausdorff:
+    """One-sided Hausdorff distance of outputs to one input mesh (kd-tree of
+    the input's face centroids built once, reused for every arm)."""
+
+    def __init__(self, V, F):
+        from scipy.spatial import cKDTree
+        self.V = np.asarray(V, np.float64)
+        self.T = self.V[np.asarray(F)]
+        self.tree = cKDTree(self.T.mean(1))
+
+    def __call__(self, Vo, Fo):
+        return one_sided_hausdorff(Vo, Fo, self.V, None, tree=self.tree, T=self.T)
+
+
+def run_learned_bench(args, world, rank):
+    """The learned proposal against the plain method, and the bound on any
+    such proposal: labels logged by the plain method on the near-contact
+    family (nested shells, seeds 1000..), negatives subsampled, the network
+    trained by the library's kernels; then, on held-out seeds (2000..), the
+    plain method, the perfect predictor (deferring exactly the winners the
+    plain run undid: the plain output with no undo iteration) and the network
+    at several thresholds: Mfaces/s, undo work, faces, self-intersections and
+    the one-sided Hausdorff distance to the input."""
+    import torch
     import paper_2509_05595_gb300 as pamo
     from paper_2509_05595_gb300 import proposal
+    procs = max(1, min(16, (host_cpu()["nproc"] or 2) - 1))
+    rng = np.random.default_rng(12345)
     t0 = time.perf_counter()
-    Xs, ys = [], []
-    for s in range(args.train_meshes):
-        V, F = meshgen.nested_shells_seeded(args.train_level, 1000 + s)
+    Xs, ys, n_all, n_pos = [], [], 0, 0
+    for seed, V, F in _shells_stream(args.train_level, range(1000, 1000 + args.train_meshes),
+                                     procs):
         X, y = proposal.log_winners(V, F, len(F) // 100)
-        Xs.append(X)
-        ys.append(y)
+        n_all += len(y)
+        n_pos += int(y.sum().item())
+        # every undone winner, a fixed fraction of the standing ones
+        keep = (y > 0.5) | torch.as_tensor(rng.random(len(y)) < args.neg_rate, device=y.device)
+        Xs.append(X[keep])
+        ys.append(y[keep])
     X, y = torch.cat(Xs), torch.cat(ys)
+    del Xs, ys
     t_log = time.perf_counter() - t0
     t0 = time.perf_counter()
-    # unweighted loss: calibrated probabilities, so a threshold is a probability
-    # of an undo (rejects are rare; a rebalanced loss would over-defer)
+    # negatives subsampled at rate r: positives weigh r so the probabilities
+    # stay calibrated (a threshold is a probability of an undo)
     model, info = proposal.train(X, y, steps=args.train_steps, batch=8192, lr=2e-3,
-                                 pos_weight=1.0, log_every=max(1, args.train_steps // 10))
+                                 pos_weight=args.neg_rate,
+                                 log_every=max(1, args.train_steps // 10))
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
     thresholds = [float(t) for t in args.thresholds.split(",")]
-    arms = [("plain", None)] + [(f"learned@{t:g}", t) for t in thresholds]
-    res = {name: [] for name, _ in arms}
-    for s in range(args.eval_meshes):
-        V, F = meshgen.nested_shells_seeded(args.eval_level, 2000 + s)
+    arms = ["plain", "ceiling"] + [f"learned@{t:g}" for t in thresholds]
+    res = {name: [] for name in arms}
+
+    def timed(fn):
+        fn()  # warm-up
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), out
+
+    for seed, V, F in _shells_stream(args.eval_level, range(2000, 2000 + args.eval_meshes), procs):
         Vd, Fd = torch.from_numpy(V).cuda(), torch.from_numpy(F).cuda()
         target = len(F) // 100
-        for name, thr in arms:
-            opts = (pamo.Options(validate_input=0) if thr is None else
-                    pamo.Options(validate_input=0, proposal=model, proposal_threshold=thr))
-            pamo.pamo_simplify(Vd, Fd, target, options=opts)  # warm-up
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            Vo, Fo, st, status = pamo.pamo_simplify(Vd, Fd, target, options=opts)
-            e1.record(stream)
-            e1.synchronize()
+        hd = _Hausdorff(V, F)
+        # the plain run's undone pairs per round: the perfect predictor's schedule
+        rc = pamo.Ctx(Vd, Fd, validate_input=0, record_rounds=1)
+        rc.run(target)
+        undone = [rc.round_pairs(r, 2) for r in range(rc.rounds()[0])]
+        rc.close()
+
+        def ceiling():
+            c = pamo.Ctx(Vd, Fd, validate_input=0)
+            c.set_deferrals(undone)
+            st, status = c.run(target)
+            Vo, Fo = c.export()
+            c.close()
+            return Vo, Fo, st, status
+
+        for name in arms:
+            if name == "plain":
+                fn = lambda: pamo.pamo_simplify(Vd, Fd, target, validate_input=0)  # noqa: E731
+            elif name == "ceiling":
+                fn = ceiling
+            else:
+                thr = float(name.split("@")[1])
+                fn = lambda thr=thr: pamo.pamo_simplify(  # noqa: E731
+                    Vd, Fd, target, validate_input=0, proposal=model, proposal_threshold=thr)
+            ms, (Vo, Fo, st, status) = timed(fn)
             nint, _ = pamo.pamo_check_self_intersections(Vo, Fo)
             Vh, Fh = Vo.cpu().numpy(), Fo.cpu().numpy()
-            res[name].append(dict(ms=e0.elapsed_time(e1), faces_in=len(F), faces=len(Fh),
-                                  status=status, rounds=st["rounds"],
-                                  undone=st["undone"] - st["deferred"], deferred=st["deferred"],
-                                  undo_iters=sum(i * n for i, n in enumerate(st["undo_iters_hist"])),
+            from tests.meshcheck import is_closed_manifold
+            res[name].append(dict(ms=ms, faces_in=len(F), faces=len(Fh), status=status,
+                                  rounds=st["rounds"], undone=st["undone"] - st["deferred"],
+                                  deferred=st["deferred"],
+                                  undo_iters=sum(i * n for i, n in
+                                                 enumerate(st["undo_iters_hist"])),
                                   intersections=int(nint),
-                                  hausdorff=one_sided_hausdorff(Vh, Fh, V, F)))
+                                  manifold=bool(is_closed_manifold(Fh, len(Vh))),
+                                  hausdorff=hd(Vh, Fh)))
 
     def agg(rows):
         ms = sum(r["ms"] for r in rows)
@@ -487,15 +565,16 @@ def run_learned_bench(args, world, rank):
                 "faces_out": sum(r["faces"] for r in rows),
                 "stalled": sum(r["status"] != "PAMO_OK" for r in rows),
                 "intersections": sum(r["intersections"] for r in rows),
+                "manifold": all(r["manifold"] for r in rows),
                 "hausdorff_mean": float(np.mean([r["hausdorff"] for r in rows])),
                 "hausdorff_max": float(np.max([r["hausdorff"] for r in rows]))}
     summary = {name: agg(rows) for name, rows in res.items()}
-    for name, _ in arms[1:]:
-        hd = [l["hausdorff"] / max(p["hausdorff"], 1e-30) for p, l in zip(res["plain"], res[name])]
-        summary[name]["hausdorff_ratio_mean"] = float(np.mean(hd))
-        summary[name]["hausdorff_ratio_max"] = float(np.max(hd))
+    for name in arms[1:]:
+        hdr = [l["hausdorff"] / max(p["hausdorff"], 1e-30) for p, l in zip(res["plain"], res[name])]
+        summary[name]["hausdorff_ratio_mean"] = float(np.mean(hdr))
+        summary[name]["hausdorff_ratio_max"] = float(np.max(hdr))
         summary[name]["speedup_vs_plain"] = summary["plain"]["ms"] / summary[name]["ms"]
-    best = max(arms[1:], key=lambda a: summary[a[0]]["mfaces_s"])[0]
+    best = max(arms[2:], key=lambda a: summary[a]["mfaces_s"])
     line = {"metric": METRIC, "value": summary[best]["mfaces_s"], "unit": "Mfaces/s",
             "n_gpus": world, "steps": args.eval_meshes, "warmup": 1,
             "ms_per_step": summary[best]["ms"] / args.eval_meshes,
@@ -505,9 +584,12 @@ def run_learned_bench(args, world, rank):
                                    f"(seeds 2000..{2000 + args.eval_meshes - 1}) to 1%, one "
                                    "call per mesh",
                        "train": f"{args.train_meshes} nested shells L{args.train_level} "
-                                f"(seeds 1000..), {info['samples']} labels "
-                                f"({info['positives']} undone), {args.train_steps} Adam steps",
-                       "best_arm": best, "log_s": round(t_log, 1), "train_s": round(t_train, 1),
+                                f"(seeds 1000..{1000 + args.train_meshes - 1}) to 1%: "
+                                f"{n_all} winners logged, {n_pos} undone; all undone and "
+                                f"{args.neg_rate:g} of the standing kept ({info['samples']} "
+                                f"samples); {args.train_steps} Adam steps",
+                       "best_learned_arm": best, "log_s": round(t_log, 1),
+                       "train_s": round(t_train, 1),
                        "loss_first_last": [info["losses"][0], info["losses"][-1]]},
             "arms": summary}
     if rank == 0:
@@ -546,11 +628,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
-    ap.add_argument("--train-meshes", type=int, default=64)
-    ap.add_argument("--train-level", type=int, default=6)
-    ap.add_argument("--train-steps", type=int, default=3000)
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched leg of the default line")
+    ap.add_argument("--train-meshes", type=int, default=512)
+    ap.add_argument("--train-level", type=int, default=8)
+    ap.add_argument("--train-steps", type=int, default=4000)
+    ap.add_argument("--neg-rate", type=float, default=0.05,
+                    help="fraction of the standing winners kept as training negatives")
     ap.add_argument("--eval-meshes", type=int, default=64)
-    ap.add_argument("--eval-level", type=int, default=6)
+    ap.add_argument("--eval-level", type=int, default=8)
     ap.add_argument("--thresholds", default="0.5,0.7,0.9")
     ap.add_argument("--workload", default="plain", choices=["plain", "batch", "learned"],
                     help="plain: the L8 sphere (default); batch: many meshes per pass")
@@ -727,6 +813,18 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "pipeline_hbm": pipeline, "clocks": clk, "e2e": e2e,
             "gpu_launches": int(launches)}
+    if not args.no_batch and args.level == 8:
+        # the batched path (many meshes per pass) on its own workload, beside
+        # the plain number: its throughput, the same meshes one call at a
+        # time, and the speed-up
+        b = run_batch_bench(args, world, rank, emit=False)
+        line["batch"] = {"value": b["value"], "unit": b["unit"], "ms_per_step": b["ms_per_step"],
+                         "steps": b["steps"], "workload": b["config"]["workload"],
+                         "meshes": b["config"]["meshes"], "faces_in": b["config"]["faces_in"],
+                         "stalled": b["config"]["stalled"],
+                         "plain_one_at_a_time": b["plain_one_at_a_time"],
+                         "speedup_vs_plain": b["speedup_vs_plain"], "autotune": b["autotune"],
+                         "clocks": b["clocks"], "gpu_launches": b["gpu_launches"]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_sample(args.level)
     if rank == 0:

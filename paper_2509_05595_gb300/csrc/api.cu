@@ -240,7 +240,7 @@ void free_ctx_buffers(pamo_ctx* c) {
   release(c->mvbase, st); release(c->flags_old, st);
   release(c->vgap, st); release(c->vgap_tmp, st); release(c->pX, st);
   release(c->pprob, st); release(c->pkeep, st); release(c->qface, st);
-  release(c->dsched, st); release(c->rlist, st);
+  release(c->dsched, st); release(c->dsched_off, st); release(c->rlist, st);
   pinned_put(c->mcount_h, sizeof(int32_t) * 3 * (size_t)c->n_mesh);
   c->mcount_h = nullptr;
   for (int r = 0; r < 3; r++) release(c->cand[r], st);
@@ -1155,25 +1155,8 @@ void note_build(pamo_ctx* c, bool carry) {
 
 // one round of Algorithm 1 through the captured graphs: one synchronisation
 // unless the check found intersections (then one per undo iteration)
-// this round's part of the deferral schedule to the device (before the round)
-pamo_status stage_schedule(pamo_ctx* c) {
-  if (!c->sched_on) return PAMO_OK;
-  const int64_t R = (int64_t)c->sched_off.size() - 1;
-  const int64_t r = c->rounds;
-  const int64_t b = r < R ? c->sched_off[r] : 0, e = r < R ? c->sched_off[r + 1] : 0;
-  const int n = (int)(e - b);
-  c->sched_n = n;
-  if (n > 0)
-    PAMO_CUDA(cudaMemcpyAsync(c->dsched, c->sched_keys.data() + b, sizeof(unsigned long long) * n,
-                              cudaMemcpyHostToDevice, c->st));
-  PAMO_CUDA(cudaMemcpyAsync(&c->dc->n_sched, &c->sched_n, sizeof(int), cudaMemcpyHostToDevice,
-                            c->st));
-  return PAMO_OK;
-}
-
 pamo_status graph_round(pamo_ctx* c) {
   cudaStream_t st = c->st;
-  PAMO_TRY(stage_schedule(c));
   const bool carry = use_carry(c);
   const int slot = carry ? 1 : 0;
   if (!c->gA[slot]) PAMO_TRY(capture(c, slot, &c->gA[slot], [&] { return round_body(c, carry); }));
@@ -1220,7 +1203,6 @@ pamo_status round_cost(pamo_ctx* c) {
     set_error("pamo_round_cost: previous round not committed");
     return PAMO_EINVAL;
   }
-  PAMO_TRY(stage_schedule(c));
   PAMO_TRY(phase_begin(c));
   PAMO_TRY(phase_cost(c));
   PAMO_TRY(sync_now(c));
@@ -1554,10 +1536,22 @@ pamo_status pamo_ctx_set_deferrals(pamo_ctx* c, const int64_t* h_off, int64_t n_
   pamo_status s = PAMO_OK;
   if (!c->pkeep) s = alloc(&c->pkeep, (size_t)c->Emax, c->st);
   if (s == PAMO_OK && c->dsched) release(c->dsched, c->st);
-  if (s == PAMO_OK) s = alloc(&c->dsched, (size_t)std::max<int64_t>(widest, 1), c->st);
+  if (s == PAMO_OK && c->dsched_off) release(c->dsched_off, c->st);
+  if (s == PAMO_OK) s = alloc(&c->dsched, std::max<size_t>(keys.size(), 1), c->st);
+  if (s == PAMO_OK) s = alloc(&c->dsched_off, (size_t)n_rounds + 1, c->st);
   if (s == PAMO_OK) {
-    c->sched_off.swap(off);
-    c->sched_keys.swap(keys);
+    cudaError_t e = cudaSuccess;
+    if (!keys.empty())
+      e = cudaMemcpyAsync(c->dsched, keys.data(), sizeof(unsigned long long) * keys.size(),
+                          cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->dsched_off, off.data(), sizeof(int64_t) * off.size(),
+                          cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);  // the host arrays are locals
+    if (e != cudaSuccess) s = cuda_fail(e, "pamo_ctx_set_deferrals: upload");
+  }
+  if (s == PAMO_OK) {
+    c->n_sched = (int)n_rounds;
     c->sched_on = true;
   }
   pamo_status j = join(c);

@@ -88,7 +88,7 @@ struct RoundCounters {
   int target;               // N_t of the running simplification
   unsigned max_bits;        // float bits of the target edge cost (0x7f800000 = off)
   int last_committed;       // collapses committed by the last round (1 at the start)
-  int n_sched;              // scheduled deferrals of this round (pamo_ctx_set_deferrals)
+  int round_no;             // rounds started (k_save_prev counts them)
   // ---- zeroed at the start of every round (from link_rejects on)
   unsigned long long link_rejects, flagged, eligible;
   unsigned long long cost_tris;  // triangles produced, summed over evaluated edges
@@ -210,12 +210,11 @@ struct pamo_ctx {
   float* pprob = nullptr;              // [Emax] predicted probability of an undo
   uint8_t* pkeep = nullptr;            // [Emax] winner not deferred
   int32_t* rlist = nullptr;            // [nF] faces restored by this round's undos
-  // deferral schedule (pamo_ctx_set_deferrals): host keys (a << 32 | b, sorted
-  // within a round) with per-round offsets, and this round's keys on the device
-  std::vector<int64_t> sched_off;
-  std::vector<unsigned long long> sched_keys;
+  // deferral schedule (pamo_ctx_set_deferrals) on the device: keys
+  // (a << 32 | b, sorted within a round) and n_sched + 1 round offsets
   unsigned long long* dsched = nullptr;
-  int sched_n = 0;  // host source of this round's count
+  int64_t* dsched_off = nullptr;
+  int n_sched = 0;
   bool sched_on = false;
   int64_t deferred_total = 0;
   cudaEvent_t round_ev[2] = {nullptr, nullptr};  // device time of a round (records)

@@ -398,6 +398,7 @@ __global__ void k_save_prev(RoundCounters* __restrict__ dc, const int2* __restri
                             uint8_t* __restrict__ link_prev, int32_t* __restrict__ mcount,
                             int mcount_n) {
   const int nE = dc->nE, nO = dc->nV_edges + 1;
+  if (blockIdx.x == 0 && threadIdx.x == 0) dc->round_no++;  // outside the zeroed words
   GRID_STRIDE(i, mcount_n) mcount[i] = 0;
   if (blockIdx.x == 0 && threadIdx.x < (sizeof(RoundCounters) - PAMO_ROUND_ZERO_OFFSET) / 4)
     reinterpret_cast<int*>(reinterpret_cast<char*>(dc) + PAMO_ROUND_ZERO_OFFSET)[threadIdx.x] = 0;

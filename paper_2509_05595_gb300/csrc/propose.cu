@@ -161,11 +161,15 @@ __global__ void k_defer_mark(RoundCounters* __restrict__ dc, const float* __rest
 }
 
 // scheduled deferrals: a winner whose vertex pair is in this round's sorted
-// schedule is not collapsed and counts as undone, like a predicted reject
+// part of the schedule is not collapsed and counts as undone, like a
+// predicted reject
 __global__ void k_defer_sched(RoundCounters* __restrict__ dc, const int32_t* __restrict__ wlist,
-                              const int2* __restrict__ E, const unsigned long long* __restrict__ sched,
+                              const int2* __restrict__ E, const unsigned long long* __restrict__ keys,
+                              const int64_t* __restrict__ off, int rounds,
                               uint8_t* __restrict__ keep) {
-  const int n = dc->nW, ns = dc->n_sched;
+  const int n = dc->nW, r = dc->round_no - 1;
+  const unsigned long long* sched = keys + (r < rounds ? off[r] : 0);
+  const int ns = r < rounds ? (int)(off[r + 1] - off[r]) : 0;
   int d = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -188,7 +192,8 @@ __global__ void k_defer_sched(RoundCounters* __restrict__ dc, const int32_t* __r
 }  // namespace
 
 pamo_status defer_scheduled(pamo_ctx* c) {
-  k_defer_sched<<<c->grid, kBlock, 0, c->st>>>(c->dc, c->wlist, c->E, c->dsched, c->pkeep); note_launch();
+  k_defer_sched<<<c->grid, kBlock, 0, c->st>>>(c->dc, c->wlist, c->E, c->dsched, c->dsched_off,
+                                                c->n_sched, c->pkeep); note_launch();
   PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;
 }
