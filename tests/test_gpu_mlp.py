@@ -284,3 +284,51 @@ def test_fitted_input_norm_matches_numpy_statistics():
     b.set_input_norm(Xd.mean(0).astype(np.float32), sd.astype(np.float32))
     Q = torch.from_numpy(X[:5000])
     assert torch.allclose(a.forward(Q), b.forward(Q), rtol=1e-5, atol=1e-6)
+
+
+def test_learned_against_plain_on_held_out_meshes(capsys):
+    """The trained network against the plain method on held-out near-contact
+    meshes: the time ratio and undo work are reported; every output must be
+    closed, manifold and free of exact self-intersections, with a one-sided
+    Hausdorff distance to the input within 1.05x of the plain output's, on
+    average and on every mesh."""
+    from bench import one_sided_hausdorff
+    Xs, ys = [], []
+    for seed in range(12):
+        V, F = meshgen.nested_shells_seeded(5, 1000 + seed)
+        X, y = proposal.log_winners(V, F, len(F) // 100)
+        Xs.append(X)
+        ys.append(y)
+    X, y = torch.cat(Xs), torch.cat(ys)
+    m, _ = proposal.train(X, y, steps=400, batch=4096, lr=2e-3, pos_weight=1.0)
+    ratios, t_plain, t_learned, undo = [], 0.0, 0.0, [0, 0]
+    for seed in range(2000, 2004):
+        V, F = meshgen.nested_shells_seeded(5, seed)
+        Vd, Fd = torch.from_numpy(V).cuda(), torch.from_numpy(F).cuda()
+        out = {}
+        for name, kw in (("plain", {}), ("learned", dict(proposal=m, proposal_threshold=0.9))):
+            for _ in range(2):  # the second run is timed
+                c = pamo.Ctx(Vd, Fd, **kw)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                st, status = c.run(len(F) // 100)
+                e1.record()
+                e1.synchronize()
+                Vo, Fo = c.export()
+                c.close()
+            Vh, Fh = Vo.cpu().numpy(), Fo.cpu().numpy()
+            assert status == "PAMO_OK" and is_closed_manifold(Fh, len(Vh))
+            assert euler(Fh, len(Vh)) == euler(F, len(V))
+            assert pamo.pamo_check_self_intersections(Vo, Fo)[0] == 0
+            out[name] = (e0.elapsed_time(e1), one_sided_hausdorff(Vh, Fh, V, F), st)
+        t_plain += out["plain"][0]
+        t_learned += out["learned"][0]
+        undo[0] += sum(i * n for i, n in enumerate(out["plain"][2]["undo_iters_hist"]))
+        undo[1] += sum(i * n for i, n in enumerate(out["learned"][2]["undo_iters_hist"]))
+        ratios.append(out["learned"][1] / out["plain"][1])
+    with capsys.disabled():
+        print(f"\nlearned vs plain on 4 held-out level-5 shells: time x{t_learned / t_plain:.3f}, "
+              f"undo iterations {undo[1]} vs {undo[0]}, Hausdorff ratio mean "
+              f"{np.mean(ratios):.3f} max {np.max(ratios):.3f}")
+    assert np.mean(ratios) <= 1.05 and np.max(ratios) <= 1.05
