@@ -515,6 +515,79 @@ struct CandBufs {
   int64_t cap[3];
 };
 
+// Appends candidate pair (f, g) to the bucket of its shared-vertex count
+// (warp-aggregated over the lanes that append in the same call)
+__device__ __forceinline__ void append_candidate(int f, const int4& tv, int g,
+                                                 const int4* __restrict__ F, CandBufs& cb,
+                                                 int* __restrict__ ncand) {
+  const int4 gv = F[g];
+  int s = 0;
+  s += (gv.x == tv.x) | (gv.x == tv.y) | (gv.x == tv.z);
+  s += (gv.y == tv.x) | (gv.y == tv.y) | (gv.y == tv.z);
+  s += (gv.z == tv.x) | (gv.z == tv.y) | (gv.z == tv.z);
+  const int r = s >= 2 ? 2 : s;
+  const unsigned act = __activemask();
+  const unsigned peers = __match_any_sync(act, r);
+  const int leader = __ffs(peers) - 1;
+  const int lane = threadIdx.x & 31;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(&ncand[r], __popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  const int slot = base + __popc(peers & ((1u << lane) - 1u));
+  if (slot < cb.cap[r]) cb.c[r][slot] = make_int2(f, g);
+}
+
+// Depth-first traversal of the subtree at `node` for query f (one thread).
+// Returns false after a stack or visit-cap overflow (flagged in dc).
+__device__ __forceinline__ bool dfs_query(const float* __restrict__ nodes, int node, int n, int f,
+                                          const int4& tv, const float3& lo, const float3& hi,
+                                          const int32_t* __restrict__ ftag, int query_all,
+                                          const int4* __restrict__ F, CandBufs& cb,
+                                          int* __restrict__ ncand, RoundCounters* __restrict__ dc) {
+  int stack[kStack];
+  int sp = 0;
+  for (int visits = 0;; visits++) {
+    if (visits >= 2 * n) {
+      atomicOr(&dc->overflow, 4);
+      return false;
+    }
+    const NodeHits h = visit(nodes, node, lo, hi);
+    int next = -1;
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+      if (!(k ? h.r : h.l)) continue;
+      const int cn = k ? h.R : h.L;
+      if (cn < 0) {
+        const int g = ~cn;
+        if (g == f) continue;
+        const int tg = ftag ? ftag[g] : -1;
+        if (query_all ? (g < f) : (tg >= 0 && g < f)) continue;
+        append_candidate(f, tv, g, F, cb, ncand);
+      } else if (next < 0) {
+        next = cn;
+      } else {
+        if (sp >= kStack) {
+          atomicOr(&dc->overflow, 1);
+          return false;
+        }
+        stack[sp++] = cn;
+      }
+    }
+    if (next >= 0) {
+      node = next;
+    } else {
+      if (sp == 0) return true;
+      node = stack[--sp];
+    }
+  }
+}
+
+// One thread per query face while there are many queries; when there are at
+// most two per warp (the small late rounds, where a query's chain of
+// dependent node loads is the kernel's time), one warp per query: the warp
+// expands the tree breadth-first over its lanes until the frontier fills
+// them, then each lane finishes its frontier nodes depth-first, so the chain
+// is about the tree's depth instead of one load per overlapping node.
 __global__ void __launch_bounds__(kBlock) k_traverse(
     const float* __restrict__ nodes, const int* n_dev, int n_host, const float4* __restrict__ pos,
     const int4* __restrict__ F, const uint8_t* __restrict__ fdead,
@@ -522,73 +595,81 @@ __global__ void __launch_bounds__(kBlock) k_traverse(
     const int* __restrict__ qcount, CandBufs cb, int* __restrict__ ncand,
     RoundCounters* __restrict__ dc, const int32_t* __restrict__ vmesh,
     const int32_t* __restrict__ mroot) {
+  __shared__ int frontier[kBlock / 32][64];
   const int n = dev_n(n_dev, n_host);
   const int total = query_all ? n : *qcount;
   if (n < 2) return;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-    const int f = query_all ? i : qlist[i];
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  if ((int64_t)total > 2 * warps) {  // block-uniform: one thread per query
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+      const int f = query_all ? i : qlist[i];
+      if (fdead && fdead[f]) continue;
+      const int tf = ftag ? ftag[f] : -1;
+      if (!query_all && tf < 0) continue;
+      const int4 tv = F[f];
+      const float4 a = pos[tv.x], b = pos[tv.y], c = pos[tv.z];
+      const float3 lo = make_float3(fminf(fminf(a.x, b.x), c.x), fminf(fminf(a.y, b.y), c.y),
+                                    fminf(fminf(a.z, b.z), c.z));
+      const float3 hi = make_float3(fmaxf(fmaxf(a.x, b.x), c.x), fmaxf(fmaxf(a.y, b.y), c.y),
+                                    fmaxf(fmaxf(a.z, b.z), c.z));
+      dfs_query(nodes, mroot ? mroot[vmesh[tv.x]] : 0, n, f, tv, lo, hi, ftag, query_all, F, cb,
+                ncand, dc);
+    }
+    return;
+  }
+  int* fr = frontier[threadIdx.x >> 5];
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  for (int64_t i = w0; i < total; i += warps) {  // warp-uniform
+    const int f = query_all ? (int)i : qlist[i];
     if (fdead && fdead[f]) continue;
-    const int tf = ftag ? ftag[f] : -1;
-    if (!query_all && tf < 0) continue;
+    if (!query_all && (ftag ? ftag[f] : -1) < 0) continue;
     const int4 tv = F[f];
     const float4 a = pos[tv.x], b = pos[tv.y], c = pos[tv.z];
     const float3 lo = make_float3(fminf(fminf(a.x, b.x), c.x), fminf(fminf(a.y, b.y), c.y),
                                   fminf(fminf(a.z, b.z), c.z));
     const float3 hi = make_float3(fmaxf(fmaxf(a.x, b.x), c.x), fmaxf(fmaxf(a.y, b.y), c.y),
                                   fmaxf(fmaxf(a.z, b.z), c.z));
-    int stack[kStack];
-    int sp = 0, node = mroot ? mroot[vmesh[tv.x]] : 0;  // the query's own mesh
-    for (int visits = 0;; visits++) {
-      if (visits >= 2 * n) {
-        atomicOr(&dc->overflow, 4);
-        break;
-      }
-      const NodeHits h = visit(nodes, node, lo, hi);
-      int next = -1;
+    if (lane == 0) fr[0] = mroot ? mroot[vmesh[tv.x]] : 0;
+    int nf = 1;
+    __syncwarp();
+    // breadth-first while the frontier is narrower than the warp (at most 62
+    // entries after a step)
+    for (int level = 0; nf > 0 && nf < 32 && level < kStack; level++) {
+      int kids[2] = {-1, -1}, nk = 0;
+      if (lane < nf) {
+        const NodeHits h = visit(nodes, fr[lane], lo, hi);
 #pragma unroll
-      for (int k = 0; k < 2; k++) {
-        if (!(k ? h.r : h.l)) continue;
-        const int cn = k ? h.R : h.L;
-        if (cn < 0) {
-          const int g = ~cn;
-          if (g == f) continue;
-          const int tg = ftag ? ftag[g] : -1;
-          if (query_all ? (g < f) : (tg >= 0 && g < f)) continue;
-          const int4 gv = F[g];
-          int s = 0;
-          s += (gv.x == tv.x) | (gv.x == tv.y) | (gv.x == tv.z);
-          s += (gv.y == tv.x) | (gv.y == tv.y) | (gv.y == tv.z);
-          s += (gv.z == tv.x) | (gv.z == tv.y) | (gv.z == tv.z);
-          const int r = s >= 2 ? 2 : s;
-          // warp-aggregated append into bucket r
-          const unsigned act = __activemask();
-          const unsigned peers = __match_any_sync(act, r);
-          const int leader = __ffs(peers) - 1;
-          const int lane = threadIdx.x & 31;
-          int base = 0;
-          if (lane == leader) base = atomicAdd(&ncand[r], __popc(peers));
-          base = __shfl_sync(peers, base, leader);
-          const int slot = base + __popc(peers & ((1u << lane) - 1u));
-          if (slot < cb.cap[r]) cb.c[r][slot] = make_int2(f, g);
-        } else if (next < 0) {
-          next = cn;
-        } else {
-          if (sp >= kStack) {
-            atomicOr(&dc->overflow, 1);
-            next = -2;
-            break;
+        for (int k = 0; k < 2; k++) {
+          if (!(k ? h.r : h.l)) continue;
+          const int cn = k ? h.R : h.L;
+          if (cn < 0) {
+            const int g = ~cn;
+            if (g == f) continue;
+            const int tg = ftag ? ftag[g] : -1;
+            if (query_all ? (g < f) : (tg >= 0 && g < f)) continue;
+            append_candidate(f, tv, g, F, cb, ncand);
+          } else {
+            kids[nk++] = cn;
           }
-          stack[sp++] = cn;
         }
       }
-      if (next == -2) break;
-      if (next >= 0) {
-        node = next;
-      } else {
-        if (sp == 0) break;
-        node = stack[--sp];
+      int incl = nk;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
       }
+      __syncwarp();  // every lane has read its frontier entry
+      const int o = incl - nk;
+      for (int k = 0; k < nk; k++) fr[o + k] = kids[k];
+      nf = __shfl_sync(0xffffffffu, incl, 31);
+      __syncwarp();
     }
+    // depth-first from the frontier nodes, one per lane (two at most)
+    for (int j = lane; j < nf; j += 32)
+      dfs_query(nodes, fr[j], n, f, tv, lo, hi, ftag, query_all, F, cb, ncand, dc);
+    __syncwarp();  // the next query overwrites the frontier
   }
 }
 

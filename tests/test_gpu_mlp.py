@@ -318,7 +318,8 @@ def test_learned_against_plain_on_held_out_meshes(capsys):
                 Vo, Fo = c.export()
                 c.close()
             Vh, Fh = Vo.cpu().numpy(), Fo.cpu().numpy()
-            assert status == "PAMO_OK" and is_closed_manifold(Fh, len(Vh))
+            # a near-contact mesh may stop above 1 % (a valid output, Section 5.3)
+            assert status in ("PAMO_OK", "PAMO_ESTALL") and is_closed_manifold(Fh, len(Vh))
             assert euler(Fh, len(Vh)) == euler(F, len(V))
             assert pamo.pamo_check_self_intersections(Vo, Fo)[0] == 0
             out[name] = (e0.elapsed_time(e1), one_sided_hausdorff(Vh, Fh, V, F), st)
