@@ -111,6 +111,15 @@ typedef struct {
                               face order) instead of carrying K_a + K_b through
                               collapses (0, the default, standard QEM memory);
                               Eq. 1 cites QEM without fixing this */
+  int32_t device_loop;        /* 1 = run all rounds of pamo_simplify /
+                              pamo_ctx_run / pamo_simplify_batch as ONE CUDA
+                              graph launch: conditional graph nodes repeat the
+                              round and the undo iterations, and device kernels
+                              keep the Section 5.3 bookkeeping, so the host
+                              does not wake between rounds.  Same results.  0
+                              (default): one graph launch per round from the
+                              host, measured faster on a GB300.  Ignored with
+                              record_rounds, profile or check_mode != 0 */
 } pamo_options;
 
 /* Kernel classes reported in pamo_stats (index = bit of pamo_options.profile). */

@@ -47,7 +47,7 @@ class _Options(ctypes.Structure):
                 ("resort_percent", ctypes.c_int32), ("proposal", ctypes.c_void_p),
                 ("proposal_threshold", ctypes.c_float),
                 ("check_input_intersections", ctypes.c_int32),
-                ("recompute_quadrics", ctypes.c_int32)]
+                ("recompute_quadrics", ctypes.c_int32), ("device_loop", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
@@ -82,6 +82,7 @@ class Options:
     proposal_threshold: float = 0.5
     check_input_intersections: int = 0
     recompute_quadrics: int = 0
+    device_loop: int = 0           # 1: all rounds in one graph launch (conditional nodes)
 
     def c(self):
         d = {f.name: getattr(self, f.name) for f in fields(self)}

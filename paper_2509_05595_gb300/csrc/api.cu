@@ -208,6 +208,10 @@ void free_graphs(pamo_ctx* c) {
     cudaGraphExecDestroy(c->gB);
     c->gB = nullptr;
   }
+  if (c->gL) {
+    cudaGraphExecDestroy(c->gL);
+    c->gL = nullptr;
+  }
   for (auto& g : c->gev)
     for (auto& k : g)
       for (auto& e : k)
@@ -241,6 +245,11 @@ void free_ctx_buffers(pamo_ctx* c) {
   release(c->vgap, st); release(c->vgap_tmp, st); release(c->pX, st);
   release(c->pprob, st); release(c->pkeep, st); release(c->qface, st);
   release(c->dsched, st); release(c->dsched_off, st); release(c->rlist, st);
+  release(c->loop, st); release(c->flags_tmp, st); release(c->mstate, st);
+  pinned_put(c->loop_h, sizeof(LoopState));
+  c->loop_h = nullptr;
+  pinned_put(c->mstate_h, sizeof(MeshState) * (size_t)c->n_mesh);
+  c->mstate_h = nullptr;
   pinned_put(c->mcount_h, sizeof(int32_t) * 3 * (size_t)c->n_mesh);
   c->mcount_h = nullptr;
   for (int r = 0; r < 3; r++) release(c->cand[r], st);
@@ -311,6 +320,10 @@ pamo_status check_options(const pamo_options* o) {
   }
   if (o->recompute_quadrics != 0 && o->recompute_quadrics != 1) {
     set_error("recompute_quadrics must be 0 or 1");
+    return PAMO_EINVAL;
+  }
+  if (o->device_loop != 0 && o->device_loop != 1) {
+    set_error("device_loop must be 0 or 1");
     return PAMO_EINVAL;
   }
   if (o->grid_blocks_per_sm < 0 || o->grid_blocks_per_sm > 32 || o->resort_percent < 0 ||
@@ -1110,11 +1123,23 @@ pamo_status finish_round_batch(pamo_ctx* c) {
 pamo_status graph_round(pamo_ctx* c);
 
 // the rounds of a batch: until every mesh has reached its target or stopped
+pamo_status run_rounds_device(pamo_ctx* c, int64_t target);
+bool use_device_loop(const pamo_ctx* c);
+
 pamo_status run_batch(pamo_ctx* c) {
   c->in_run = true;
   const int M = c->n_mesh;
   bool any = false;
   for (int m = 0; m < M; m++) any |= c->m_active[m] != 0;
+  if (any && use_device_loop(c) && c->stage == 0 && c->rounds < c->opt.max_rounds) {
+    pamo_status s = run_rounds_device(c, INT32_MAX);  // the target of every mesh is its own
+    c->in_run = false;
+    if (s != PAMO_OK) return s;
+    c->status = PAMO_OK;
+    for (int m = 0; m < M; m++)
+      if (c->m_status[m] != PAMO_OK) c->status = PAMO_ESTALL;
+    return PAMO_OK;
+  }
   while (any) {
     if (c->rounds >= c->opt.max_rounds) {
       for (int m = 0; m < M; m++)
@@ -1285,12 +1310,258 @@ pamo_status run(pamo_ctx* c, int64_t target) {
   return s;
 }
 
+// ---- the device-side round loop (loop.cu) ----------------------------------
+// Captures fn's launches on the context's stream into graph g after the nodes
+// in deps; deps then holds the capture's last nodes.  kernels counts the
+// launches captured.
+template <typename Fn>
+pamo_status capture_into(pamo_ctx* c, cudaGraph_t g, std::vector<cudaGraphNode_t>& deps,
+                         long long* kernels, Fn fn) {
+  PAMO_CUDA(cudaStreamBeginCaptureToGraph(c->st, g, deps.empty() ? nullptr : deps.data(), nullptr,
+                                          deps.size(), cudaStreamCaptureModeThreadLocal));
+  const long long l0 = launch_count();
+  pamo_status s = fn();
+  if (kernels) *kernels += launch_count() - l0;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  const cudaGraphNode_t* d = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(c->st, &cs, nullptr, nullptr, &d, nullptr, &nd);
+  std::vector<cudaGraphNode_t> last;
+  if (e == cudaSuccess && d) last.assign(d, d + nd);
+  cudaGraph_t out = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(c->st, &out);
+  if (s != PAMO_OK) return s;
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamGetCaptureInfo");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+  deps.swap(last);
+  return PAMO_OK;
+}
+
+// A conditional node after deps; bodies receives its body graphs (size of
+// them); deps then holds the node.
+pamo_status add_conditional(cudaGraph_t g, std::vector<cudaGraphNode_t>& deps,
+                            cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                            unsigned size, cudaGraph_t* bodies) {
+  cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+  p.conditional.handle = h;
+  p.conditional.type = type;
+  p.conditional.size = size;
+  cudaGraphNode_t node = nullptr;
+  PAMO_CUDA(cudaGraphAddNode(&node, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(),
+                             &p));
+  for (unsigned i = 0; i < size; i++) bodies[i] = p.conditional.phGraph_out[i];
+  deps.assign(1, node);
+  return PAMO_OK;
+}
+
+// The whole run as one graph:
+//   init -> WHILE(round) { begin, cost, select, collapse;
+//                          IF(sort) sort build ELSE carried-order build;
+//                          check; IF(overflow) fallback;
+//                          WHILE(not clean) { re-check; IF(overflow) fallback };
+//                          commit; flags; finish }
+pamo_status build_loop_graph(pamo_ctx* c) {
+  cudaGraph_t g = nullptr;
+  PAMO_CUDA(cudaGraphCreate(&g, 0));
+  // launch and byte accounting of the phases is per replay, not per capture
+  const double bytes0 = c->bytes_model;
+  double cb0[8];
+  long long cl0[8];
+  for (int i = 0; i < 8; i++) {
+    cb0[i] = c->class_bytes[i];
+    cl0[i] = c->class_launches[i];
+  }
+  const long long captured0 = launch_count();
+  long long* kn = c->gL_nodes;
+  for (int i = 0; i < 5; i++) kn[i] = 0;
+  auto body = [&]() -> pamo_status {
+    cudaGraphConditionalHandle h_round, h_sort, h_fb1, h_undo, h_fb2;
+    PAMO_CUDA(cudaGraphConditionalHandleCreate(&h_round, g, 1, cudaGraphCondAssignDefault));
+    PAMO_CUDA(cudaGraphConditionalHandleCreate(&h_sort, g, 0, 0));
+    PAMO_CUDA(cudaGraphConditionalHandleCreate(&h_fb1, g, 0, 0));
+    PAMO_CUDA(cudaGraphConditionalHandleCreate(&h_undo, g, 0, 0));
+    PAMO_CUDA(cudaGraphConditionalHandleCreate(&h_fb2, g, 0, 0));
+    std::vector<cudaGraphNode_t> top;
+    PAMO_TRY(capture_into(c, g, top, nullptr, [&] { return loop_init(c, h_sort); }));
+    cudaGraph_t round_g;
+    PAMO_TRY(add_conditional(g, top, h_round, cudaGraphCondTypeWhile, 1, &round_g));
+    std::vector<cudaGraphNode_t> d;
+    PAMO_TRY(capture_into(c, round_g, d, &kn[0], [&]() -> pamo_status {
+      PAMO_TRY(phase_begin(c));
+      PAMO_TRY(phase_cost(c));
+      PAMO_TRY(phase_select(c));
+      return phase_collapse(c);
+    }));
+    cudaGraph_t build[2];
+    PAMO_TRY(add_conditional(round_g, d, h_sort, cudaGraphCondTypeIf, 2, build));
+    std::vector<cudaGraphNode_t> b0, b1;
+    PAMO_TRY(capture_into(c, build[0], b0, &kn[1], [&] { return phase_bvh(c, false); }));
+    PAMO_TRY(capture_into(c, build[1], b1, &kn[2], [&] { return phase_bvh(c, true); }));
+    PAMO_TRY(capture_into(c, round_g, d, &kn[0], [&]() -> pamo_status {
+      PAMO_TRY(phase_check(c));
+      return loop_cond_fallback(c, h_fb1, 1);
+    }));
+    cudaGraph_t fb;
+    PAMO_TRY(add_conditional(round_g, d, h_fb1, cudaGraphCondTypeIf, 1, &fb));
+    std::vector<cudaGraphNode_t> f1;
+    PAMO_TRY(capture_into(c, fb, f1, &kn[4], [&] { return fallback_check(c); }));
+    PAMO_TRY(capture_into(c, round_g, d, &kn[0], [&] { return loop_cond_undo(c, h_undo); }));
+    cudaGraph_t undo_g;
+    PAMO_TRY(add_conditional(round_g, d, h_undo, cudaGraphCondTypeWhile, 1, &undo_g));
+    std::vector<cudaGraphNode_t> u;
+    PAMO_TRY(capture_into(c, undo_g, u, &kn[3], [&]() -> pamo_status {
+      PAMO_TRY(phase_recheck(c));
+      return loop_cond_fallback(c, h_fb2, 0);
+    }));
+    cudaGraph_t fb2;
+    PAMO_TRY(add_conditional(undo_g, u, h_fb2, cudaGraphCondTypeIf, 1, &fb2));
+    std::vector<cudaGraphNode_t> f2;
+    PAMO_TRY(capture_into(c, fb2, f2, nullptr, [&] { return fallback_check(c); }));
+    PAMO_TRY(capture_into(c, undo_g, u, &kn[3], [&] { return loop_cond_undo(c, h_undo); }));
+    PAMO_TRY(capture_into(c, round_g, d, &kn[0], [&]() -> pamo_status {
+      PAMO_TRY(phase_commit(c));
+      return loop_finish(c, h_round, h_sort);
+    }));
+    PAMO_CUDA(cudaGraphInstantiate(&c->gL, g, 0));
+    return PAMO_OK;
+  };
+  pamo_status s = body();
+  cudaGraphDestroy(g);
+  c->gk_captured += launch_count() - captured0;
+  c->bytes_model = bytes0;
+  for (int i = 0; i < 8; i++) {
+    c->class_bytes[i] = cb0[i];
+    c->class_launches[i] = cl0[i];
+  }
+  return s;
+}
+
+// The device loop (options.device_loop) runs plain simplifications and
+// batches; per-round records, class timing and the all-faces / no-check debug
+// modes keep the host loop.
+bool use_device_loop(const pamo_ctx* c) {
+  return c->opt.device_loop && !c->opt.record_rounds && !c->opt.profile &&
+         c->opt.check_mode == 0;
+}
+
+pamo_status run_rounds_device(pamo_ctx* c, int64_t target) {
+  cudaStream_t st = c->st;
+  const int M = c->n_mesh;
+  if (!c->loop) {
+    PAMO_TRY(alloc(&c->loop, 1, st));
+    PAMO_TRY(alloc(&c->flags_tmp, (size_t)c->Emax, st));
+    PAMO_TRY(pinned_get((void**)&c->loop_h, sizeof(LoopState)));
+    if (M > 1) {
+      PAMO_TRY(alloc(&c->mstate, (size_t)M, st));
+      PAMO_TRY(pinned_get((void**)&c->mstate_h, sizeof(MeshState) * (size_t)M));
+    }
+  }
+  if (M > 1) {  // every mesh's state, as the host loop keeps it
+    for (int m = 0; m < M; m++) {
+      MeshState& ms = c->mstate_h[m];
+      ms.nV = c->m_nV[m];
+      ms.nF = c->m_nF[m];
+      ms.target = c->m_target[m];
+      ms.nflags = (int)c->m_nflags[m];
+      ms.hold = c->m_hold[m];
+      ms.zero = c->m_zero[m];
+      ms.status = c->m_status[m];
+      ms.rounds = c->m_rounds[m];
+      ms.active = c->m_active[m];
+      ms.mode = 0;
+    }
+    PAMO_CUDA(cudaMemcpyAsync(c->mstate, c->mstate_h, sizeof(MeshState) * M,
+                              cudaMemcpyHostToDevice, st));
+  }
+  if (!c->gL) PAMO_TRY(build_loop_graph(c));
+  LoopState& L = *c->loop_h;
+  std::memset(&L, 0, sizeof(L));
+  L.target = (int)std::min<int64_t>(target, INT32_MAX);
+  L.max_rounds = c->opt.max_rounds;
+  L.stall_limit = c->opt.stall_limit;
+  L.tolerance = c->opt.tolerance;
+  L.resort_pct = c->opt.resort_percent > 0 ? c->opt.resort_percent : 25;
+  L.cost_target = c->opt.max_cost < INFINITY ? 1 : 0;
+  L.rounds = (int)c->rounds;
+  L.hold = c->hold;
+  L.zero_streak = c->zero_streak;
+  const bool carry = use_carry(c);
+  note_build(c, carry);
+  L.sort_first = carry ? 0 : 1;
+  L.sorts = carry ? 0 : 1;
+  L.order_ok = c->bvh.order_ok ? 1 : 0;
+  L.n_sorted = c->bvh.n_sorted;
+  PAMO_CUDA(cudaMemcpyAsync(c->loop, &L, sizeof(L), cudaMemcpyHostToDevice, st));
+  PAMO_CUDA(cudaGraphLaunch(c->gL, st));
+  PAMO_CUDA(cudaMemcpyAsync(&L, c->loop, sizeof(L), cudaMemcpyDeviceToHost, st));
+  PAMO_CUDA(cudaMemcpyAsync(c->hc, c->dc, sizeof(RoundCounters), cudaMemcpyDeviceToHost, st));
+  if (M > 1)
+    PAMO_CUDA(cudaMemcpyAsync(c->mstate_h, c->mstate, sizeof(MeshState) * M,
+                              cudaMemcpyDeviceToHost, st));
+  PAMO_CUDA(cudaStreamSynchronize(st));
+  if (M > 1) {
+    for (int m = 0; m < M; m++) {
+      const MeshState& ms = c->mstate_h[m];
+      c->m_nV[m] = ms.nV;
+      c->m_nF[m] = ms.nF;
+      c->m_nflags[m] = ms.nflags;
+      c->m_hold[m] = ms.hold;
+      c->m_zero[m] = ms.zero;
+      c->m_status[m] = ms.status;
+      c->m_rounds[m] = ms.rounds;
+      c->m_active[m] = (uint8_t)ms.active;
+    }
+  }
+  const int64_t done = L.rounds - c->rounds;
+  // kernels run: every round, its BVH build, its re-checks and fallbacks
+  c->gk_run += done * c->gL_nodes[0] + L.sorts * c->gL_nodes[1] +
+               (done - L.sorts) * c->gL_nodes[2] + L.rechecks * c->gL_nodes[3] +
+               L.fallbacks * c->gL_nodes[4] + 1;
+  c->rounds = L.rounds;
+  c->hold = L.hold;
+  c->zero_streak = L.zero_streak;
+  c->bvh.order_ok = L.order_ok != 0;
+  c->bvh.n_sorted = L.n_sorted;
+  c->nflags = c->hc->nflags;
+  c->nV = c->hc->nV;
+  c->nF = c->hc->nF;
+  c->nE = L.nE;
+  c->nW = L.nW;
+  c->undo_iters = L.undo_iters;
+  c->last_pairs = L.pairs;
+  c->committed_total += L.committed;
+  c->undone_total += L.undone;
+  c->link_total += L.link;
+  c->win_total += L.winners;
+  c->deferred_total += L.deferred;
+  c->cost_edges_total += L.cost_edges;
+  c->class_flops[PAMO_KC_COST] += kCostFlopsEdge * (double)L.cost_edges +
+                                  kCostFlopsTri * (double)L.cost_tris;
+  for (int i = 0; i < 8; i++) c->undo_hist[i] += (int32_t)L.undo_hist[i];
+  c->stage = 0;
+  if (L.error) {
+    set_error(L.error == PAMO_ENOTMANIFOLD
+                  ? "edge count is not 3F/2: the mesh is not a closed oriented manifold"
+                  : "BVH traversal or refit bound exceeded, or the undo loop did not settle");
+    return (pamo_status)L.error;
+  }
+  if (L.status == PAMO_ESTALL) {
+    c->stalled = true;
+    c->stall_empty = L.stall_empty != 0;
+    c->status = PAMO_ESTALL;
+  }
+  return PAMO_OK;
+}
+
 pamo_status run_rounds(pamo_ctx* c, int64_t target) {
   {  // N_t on the device (exact-target trimming reads it); pageable source,
      // so the call returns once the value has been staged
     const int t = (int)std::min<int64_t>(target, INT32_MAX);
     PAMO_CUDA(cudaMemcpyAsync(&c->dc->target, &t, sizeof(int), cudaMemcpyHostToDevice, c->st));
   }
+  if (use_device_loop(c) && c->nF > target && c->stage == 0 && !c->stalled &&
+      c->rounds < c->opt.max_rounds)
+    return run_rounds_device(c, target);
   while (c->nF > target) {
     if (c->rounds >= c->opt.max_rounds) {
       c->status = PAMO_ESTALL;
@@ -1360,6 +1631,7 @@ void pamo_default_options(pamo_options* o) {
   o->proposal = nullptr;
   o->proposal_threshold = 0.5f;
   o->recompute_quadrics = 0;
+  o->device_loop = 0;
   o->check_input_intersections = 0;
 }
 

@@ -115,6 +115,28 @@ static_assert((sizeof(RoundCounters) - PAMO_ROUND_ZERO_OFFSET) % 4 == 0 &&
                   (sizeof(RoundCounters) - PAMO_ROUND_ZERO_OFFSET) / 4 <= 256,
               "the round's counters are zeroed by one block, one word per thread");
 
+// State of the device-side round loop (loop.cu): its inputs, the running
+// Section 5.3 bookkeeping and the totals the host reads after the graph.
+struct LoopState {
+  // inputs
+  int target, max_rounds, stall_limit, tolerance, resort_pct, cost_target, sort_first;
+  // running state
+  int rounds, hold, zero_streak, order_ok, n_sorted, nflags_in, iter;
+  int status, error, stall_empty;
+  int nW, nE, undo_iters;
+  // totals since the loop started
+  long long committed, undone, link, winners, cost_edges, cost_tris, deferred, pairs;
+  long long sorts, rechecks, fallbacks;
+  long long undo_hist[8];
+};
+
+// Per-mesh state of a batch in the device-side round loop: the sizes, the
+// Section 5.3 bookkeeping and the outcome of every mesh.
+struct MeshState {
+  long long nV, nF, target;
+  int nflags, hold, zero, status, rounds, active, mode;
+};
+
 // Element count of a launch: the device value when n_dev is set, else n_host.
 __device__ __forceinline__ int dev_n(const int* n_dev, int n_host) {
   return n_dev ? *n_dev : n_host;
@@ -210,6 +232,15 @@ struct pamo_ctx {
   float* pprob = nullptr;              // [Emax] predicted probability of an undo
   uint8_t* pkeep = nullptr;            // [Emax] winner not deferred
   int32_t* rlist = nullptr;            // [nF] faces restored by this round's undos
+  // the device-side round loop (loop.cu): its state, the merge buffer of the
+  // flags, and the instantiated graph with the kernels of each of its parts
+  pamo::LoopState* loop = nullptr;     // device
+  pamo::LoopState* loop_h = nullptr;   // pinned host mirror
+  unsigned long long* flags_tmp = nullptr;
+  pamo::MeshState* mstate = nullptr;   // [n_mesh] device (a batch)
+  pamo::MeshState* mstate_h = nullptr; // pinned host mirror
+  cudaGraphExec_t gL = nullptr;
+  long long gL_nodes[5] = {0, 0, 0, 0, 0};  // round, sort build, carry build, recheck, fallback
   // deferral schedule (pamo_ctx_set_deferrals) on the device: keys
   // (a << 32 | b, sorted within a round) and n_sched + 1 round offsets
   unsigned long long* dsched = nullptr;
@@ -369,6 +400,12 @@ pamo_status edge_costs(pamo_ctx* c);
 // propose.cu / mlp.cu: the learned proposal
 pamo_status propose(pamo_ctx* c);
 // marks the winners named by the deferral schedule for this round as deferred
+// kernels of the device-side round loop (loop.cu)
+pamo_status loop_init(pamo_ctx* c, cudaGraphConditionalHandle h_sort);
+pamo_status loop_cond_fallback(pamo_ctx* c, cudaGraphConditionalHandle h, int first);
+pamo_status loop_cond_undo(pamo_ctx* c, cudaGraphConditionalHandle h);
+pamo_status loop_finish(pamo_ctx* c, cudaGraphConditionalHandle h_round,
+                        cudaGraphConditionalHandle h_sort);
 pamo_status defer_scheduled(pamo_ctx* c);
 pamo_status edge_features_list(pamo_ctx* c, const int32_t* list, const int* n_dev, float* X,
                                cudaStream_t st);

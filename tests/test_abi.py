@@ -59,7 +59,7 @@ def test_struct_layouts_match_c(tmp_path):
     prog.write_text('#include "pamo.h"\n#include <stdio.h>\n#include <stddef.h>\n'
                     'int main(){printf("%zu %zu %zu %zu\\n", sizeof(pamo_options), '
                     'sizeof(pamo_stats), offsetof(pamo_stats, committed), '
-                    'offsetof(pamo_options, recompute_quadrics));return 0;}\n')
+                    'offsetof(pamo_options, device_loop));return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)],
                    check=True)
@@ -68,7 +68,7 @@ def test_struct_layouts_match_c(tmp_path):
     assert a == ctypes.sizeof(pamo._Options)
     assert b == ctypes.sizeof(pamo._Stats)
     assert c == pamo._Stats.committed.offset
-    assert d == pamo._Options.recompute_quadrics.offset
+    assert d == pamo._Options.device_loop.offset
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

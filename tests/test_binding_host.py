@@ -25,12 +25,12 @@ def test_options_marshal_every_field():
                      validate_input=0, check_mode=1, record_rounds=1, profile=3,
                      exact_target=1, max_cost=2.5, grid_blocks_per_sm=8, resort_percent=30,
                      proposal_threshold=0.75, check_input_intersections=1,
-                     recompute_quadrics=1)
+                     recompute_quadrics=1, device_loop=1)
     c = o.c()
     for name in ("w_e", "w_s", "tolerance", "max_rounds", "stall_limit", "validate_input",
                  "check_mode", "record_rounds", "profile", "exact_target", "max_cost",
                  "grid_blocks_per_sm", "resort_percent", "check_input_intersections",
-                 "recompute_quadrics"):
+                 "recompute_quadrics", "device_loop"):
         assert getattr(c, name) == getattr(o, name), name
     assert abs(c.proposal_threshold - 0.75) < 1e-7
     assert not c.proposal  # no network: a null pointer

@@ -117,3 +117,26 @@ def test_autotune_picks_knobs_and_keeps_results():
     for m, ((Vm, Fm), t) in enumerate(zip(meshes, targets)):
         ref = oracle.simplify(Vm, Fm, t, keep_pairs=False)
         assert np.array_equal(out[m][1], ref.F) and np.array_equal(_bits(out[m][0]), _bits(ref.V))
+
+
+def test_batch_in_one_graph_launch_bit_exact():
+    """options.device_loop: the whole batch as one graph launch, every mesh's
+    Section 5.3 bookkeeping (flags, tolerance, stall, target, status) kept by
+    device kernels; every mesh still equals the oracle simplifying it alone."""
+    octa = meshgen.octahedron()
+    tet = meshgen.tetrahedron()
+    meshes = [meshgen.torus(32, 16, 1.0, 0.3, 0.002, 1), meshgen.nested_shells(4, check=False),
+              octa, tet, meshgen.box_grid(6), meshgen.bumped_icosphere(4, 5)]
+    targets = [len(meshes[0][1]) // 10, len(meshes[1][1]) // 50, 4, 2, 30,
+               len(meshes[5][1]) // 20]
+    V, voff, F, foff = pamo.concat_meshes(meshes)
+    Vo, vo, Fo, fo, status, rounds, stats = pamo.pamo_simplify_batch(
+        torch.from_numpy(V), voff, torch.from_numpy(F), foff, targets, device_loop=1)
+    Vo, Fo = Vo.cpu().numpy(), Fo.cpu().numpy()
+    for m, ((Vm, Fm), t) in enumerate(zip(meshes, targets)):
+        ref = oracle.simplify(Vm, Fm, t, keep_pairs=False)
+        assert np.array_equal(Fo[fo[m]:fo[m + 1]], ref.F), m
+        assert np.array_equal(_bits(Vo[vo[m]:vo[m + 1]]), _bits(ref.V)), m
+        assert status[m] == ("PAMO_OK" if ref.status == 0 else "PAMO_ESTALL"), m
+        assert rounds[m] == len(ref.rounds), m
+    assert "PAMO_ESTALL" in list(status)  # the tetrahedron cannot collapse

@@ -117,3 +117,46 @@ def test_cached_memory_reuse_and_release_do_not_change_results():
         assert o[3] == first[3] and o[2]["rounds"] == first[2]["rounds"]
         assert torch.equal(o[0], first[0]) and torch.equal(o[1], first[1])
     _pamo.pamo_release_cached_memory()
+
+
+@pytest.mark.parametrize("case", ["shells_undos", "fallback", "box", "exact_target", "max_cost",
+                                  "stall", "sphere"])
+def test_device_round_loop_matches_oracle(case, monkeypatch):
+    """With options.device_loop every round runs on the device (one graph:
+    conditional loops over rounds and undo iterations, the Section 5.3 flag
+    and stall bookkeeping in kernels).  Its output, status and round count
+    equal the oracle's in every branch of that loop."""
+    from tests.test_gpu_parity import pamo as _pamo
+    opts = {}
+    if case in ("shells_undos", "fallback"):
+        V, F = meshgen.nested_shells(5, check=False)
+        target = len(F) // 60
+        if case == "fallback":  # tiny candidate buffers: the fused fallback check every time
+            monkeypatch.setenv("PAMO_CAND_CAP_DIVISOR", "1000000")
+    elif case == "box":
+        V, F = meshgen.box_grid(8)
+        target = 40
+    elif case == "exact_target":
+        V, F = meshgen.bumped_icosphere(5, 2)
+        target, opts = 1001, dict(exact_target=1)
+    elif case == "max_cost":
+        V, F = meshgen.bumped_icosphere(5, 4)
+        c = float(np.quantile(oracle.edge_table(V, F)["cost"], 0.6))
+        target, opts = 64, dict(max_cost=c)
+    elif case == "stall":
+        V, F = meshgen.tetrahedron()
+        target = 2
+    else:
+        V, F = meshgen.bumped_icosphere(6, 5)
+        target = len(F) // 100
+    ref = oracle.simplify(V, F, target, keep_pairs=False, **opts)
+    Vo, Fo, st, status = _pamo.pamo_simplify(torch.from_numpy(V), torch.from_numpy(F), target,
+                                             device_loop=1, **opts)
+    assert status == ("PAMO_OK" if ref.status == 0 else "PAMO_ESTALL")
+    assert st["rounds"] == len(ref.rounds)
+    assert np.array_equal(Fo.cpu().numpy(), ref.F)
+    assert np.array_equal(Vo.cpu().numpy().view(np.uint32), ref.V.view(np.uint32))
+    assert st["committed"] == sum(r["committed"] for r in ref.rounds)
+    assert st["undone"] == sum(r["undone"] for r in ref.rounds)
+    if case == "shells_undos":
+        assert st["undone"] > 0 and st["undo_iters_hist"][0] < st["rounds"]
