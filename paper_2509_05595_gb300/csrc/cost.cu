@@ -269,8 +269,13 @@ __global__ void __launch_bounds__(kItemBlock) k_edge_cost(
     a0 = off[a]; a1 = off[a + 1]; b0 = off[b]; b1 = off[b + 1];
     // ---- link condition: exactly two common neighbours (the apexes of the
     // two faces on ab) and not both faces (a,c,d), (b,c,d) present
+    // common = the (x, y) pairs with x = next_of(face around a, a) equal to
+    // y = next_of(face around b, b); a 64-bit mask of the y (bit y & 63) skips
+    // the scan of b's faces for every x that cannot match
     int common = 0;
     int apex[2] = {-1, -1}, na = 0;
+    unsigned long long ymask = 0ull;
+    for (int j = b0; j < b1; j++) ymask |= 1ull << (next_of(F[idx[j]], b) & 63);
     for (int i = a0; i < a1; i++) {
       const int4 fa = F[idx[i]];
       const int x = next_of(fa, a);
@@ -279,7 +284,8 @@ __global__ void __launch_bounds__(kItemBlock) k_edge_cost(
         if (na < 2) apex[na] = t;
         na++;
       }
-      for (int j = b0; j < b1; j++) common += next_of(F[idx[j]], b) == x;
+      if ((ymask >> (x & 63)) & 1ull)
+        for (int j = b0; j < b1; j++) common += next_of(F[idx[j]], b) == x;
     }
     // the collapse produces every face around a or b but the na on ab
     nt = (a1 - a0) + (b1 - b0) - 2 * na;
