@@ -156,6 +156,8 @@ typedef struct {
   double class_flops[8];
   int64_t deferred;            /* edges deferred by the learned proposal */
   int64_t cost_edges;          /* edges whose Eq. 1 cost was evaluated (dirty edges) */
+  int64_t cost_f64;            /* of those, edges whose key took the float64 skinny sum
+                                  (the float-float bound did not decide the float key) */
 } pamo_stats;
 
 typedef struct pamo_ctx pamo_ctx;
@@ -420,6 +422,18 @@ pamo_status pamo_orient2d_batch(const float* d_P, int64_t n, int8_t* d_out,
  * divisions per second and square roots per second over the whole GPU
  * (divisions and roots timed beyond an identical loop without them). */
 pamo_status pamo_measure_fp64(void* stream, double* h_rates);
+
+/* Verification support for the skinny term of Eq. 1 (Sec. 5.1): the edge-cost
+ * kernel evaluates each produced triangle's 1 - C_ijk in float-float
+ * arithmetic and keeps a key only when an error bound proves it equal to the
+ * float64 evaluation's.  For n triangles, d_tri (device, n x 9 float32:
+ * corners P0 P1 P2, P0 the placement) gives d_t64 (device, n float64) = 1 -
+ * C_ijk as the kernel evaluates it in float64 (corners in the given order)
+ * and d_tff (device, n x 2 float32) = the float-float pair (high, low), NaN
+ * high part outside the certified range.  Asynchronous on `stream`.
+ * PAMO_EINVAL for n < 0 or a null array with n > 0. */
+pamo_status pamo_skinny_terms(const float* d_tri, int64_t n, double* d_t64, float* d_tff,
+                              void* stream);
 
 /* Thread-local message of the last failing call ("" if none). */
 const char* pamo_last_error(void);

@@ -59,7 +59,7 @@ class _Stats(ctypes.Structure):
                 ("launches", ctypes.c_int64), ("class_ms", ctypes.c_double * 8),
                 ("class_launches", ctypes.c_int64 * 8), ("class_bytes", ctypes.c_double * 8),
                 ("class_flops", ctypes.c_double * 8), ("deferred", ctypes.c_int64),
-                ("cost_edges", ctypes.c_int64)]
+                ("cost_edges", ctypes.c_int64), ("cost_f64", ctypes.c_int64)]
 
 
 @dataclass
@@ -232,6 +232,7 @@ def lib():
             "pamo_last_error": (ctypes.c_char_p, []),
             "pamo_release_cached_memory": (ctypes.c_int, []),
             "pamo_measure_fp64": (ctypes.c_int, [P, P]),
+            "pamo_skinny_terms": (ctypes.c_int, [P, i64, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -273,7 +274,7 @@ def _stats_dict(s: _Stats):
                 ms_total=s.ms_total, bytes_model=s.bytes_model, launches=s.launches,
                 class_ms=list(s.class_ms), class_launches=list(s.class_launches),
                 class_bytes=list(s.class_bytes), class_flops=list(s.class_flops),
-                deferred=s.deferred, cost_edges=s.cost_edges)
+                deferred=s.deferred, cost_edges=s.cost_edges, cost_f64=s.cost_f64)
 
 
 def pamo_simplify(V, F, target_faces, options: Options | None = None, **kw):
@@ -589,6 +590,20 @@ def pamo_orient2d_batch(P):
     _check(lib().pamo_orient2d_batch(_ptr(P), P.shape[0], _ptr(out), _stream()),
            "pamo_orient2d_batch")
     return out
+
+
+def pamo_skinny_terms(T):
+    """Both evaluations of the skinny term 1 - C_ijk (Eq. 1) of triangles T
+    ([n, 9] float32: placement, then the other two corners): the float64 value
+    the edge-cost kernel computes, and the float-float pair ([n, 2] float32)
+    it certifies keys with (NaN outside the certified range)."""
+    import torch
+    T = _dev(T, torch.float32, 9)
+    t64 = torch.empty(T.shape[0], dtype=torch.float64, device="cuda")
+    tff = torch.empty((T.shape[0], 2), dtype=torch.float32, device="cuda")
+    _check(lib().pamo_skinny_terms(_ptr(T), T.shape[0], _ptr(t64), _ptr(tff), _stream()),
+           "pamo_skinny_terms")
+    return t64, tff
 
 
 def pamo_last_error():

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpamo.so")
 SOURCES = ["api.cu", "scan.cu", "mesh.cu", "cost.cu", "select.cu", "bvh.cu", "noalloc.cu", "mlp.cu", "propose.cu", "probe.cu", "loop.cu"]
-HEADERS = ["common.cuh", "exact.cuh"]
+HEADERS = ["common.cuh", "exact.cuh", "skinny_ff.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--fmad=false", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-O2", "--expt-relaxed-constexpr"]

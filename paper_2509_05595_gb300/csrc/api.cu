@@ -992,6 +992,7 @@ pamo_status finish_round(pamo_ctx* c) {
   c->class_flops[PAMO_KC_COST] += kCostFlopsEdge * h.n_dirty + kCostFlopsTri * (double)h.cost_tris;
   c->deferred_total += h.deferred;
   c->cost_edges_total += h.n_dirty;
+  c->cost_f64_total += h.cost_f64;
   c->committed_total += committed;
   c->undone_total += nund;
   c->link_total += info[3];
@@ -1101,6 +1102,7 @@ pamo_status finish_round_batch(pamo_ctx* c) {
   // totals over the batch
   c->class_flops[PAMO_KC_COST] += kCostFlopsEdge * h.n_dirty + kCostFlopsTri * (double)h.cost_tris;
   c->cost_edges_total += h.n_dirty;
+  c->cost_f64_total += h.cost_f64;
   c->committed_total += h.committed;
   c->undone_total += h.nund;
   c->link_total += (int64_t)h.link_rejects;
@@ -1535,6 +1537,7 @@ pamo_status run_rounds_device(pamo_ctx* c, int64_t target) {
   c->win_total += L.winners;
   c->deferred_total += L.deferred;
   c->cost_edges_total += L.cost_edges;
+  c->cost_f64_total += L.cost_f64;
   c->class_flops[PAMO_KC_COST] += kCostFlopsEdge * (double)L.cost_edges +
                                   kCostFlopsTri * (double)L.cost_tris;
   for (int i = 0; i < 8; i++) c->undo_hist[i] += (int32_t)L.undo_hist[i];
@@ -1597,6 +1600,7 @@ void fill_stats(const pamo_ctx* c, pamo_stats* s, double ms) {
   s->bytes_model = c->bytes_model;
   s->deferred = c->deferred_total;
   s->cost_edges = c->cost_edges_total;
+  s->cost_f64 = c->cost_f64_total;
   for (int i = 0; i < 8; i++) {
     s->class_ms[i] = c->class_ms[i];
     s->class_launches[i] = c->class_launches[i];

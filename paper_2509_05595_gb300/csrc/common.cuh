@@ -102,7 +102,7 @@ struct RoundCounters {
   int go;                   // commit gate: 1 when the last check was clean
   int goV, goF, goW;        // gated sizes for the commit (0 when not committing)
   int goVn, goFn;           // gated sizes of the committed mesh
-  int sort_len;             // spare
+  int cost_f64;             // edges whose key came from the float64 skinny sum
   int deferred;             // edges deferred by the learned proposal
   int n_listed;             // eligible edges listed for the proposal
   // faces restored by undos this round (rlist): [rest_lo, rest_mid) are the
@@ -125,7 +125,7 @@ struct LoopState {
   int status, error, stall_empty;
   int nW, nE, undo_iters;
   // totals since the loop started
-  long long committed, undone, link, winners, cost_edges, cost_tris, deferred, pairs;
+  long long committed, undone, link, winners, cost_edges, cost_tris, cost_f64, deferred, pairs;
   long long sorts, rechecks, fallbacks;
   long long undo_hist[8];
 };
@@ -251,6 +251,7 @@ struct pamo_ctx {
   cudaEvent_t round_ev[2] = {nullptr, nullptr};  // device time of a round (records)
   int64_t last_round_us = 0;
   int64_t cost_edges_total = 0;        // dirty edges evaluated by k_edge_cost
+  int64_t cost_f64_total = 0;          // of those, keys from the float64 skinny sum
   int32_t* dlist = nullptr;            // [Emax] edges whose cost is recomputed
   bool have_prev = false;
   unsigned long long* key = nullptr;   // [Emax]

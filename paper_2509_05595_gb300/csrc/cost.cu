@@ -11,6 +11,7 @@
 // (the library is compiled with --fmad=false, so only the explicit __fma_rn
 // calls fuse), so the keys are reproducible bit for bit.
 #include "common.cuh"
+#include "skinny_ff.cuh"
 
 namespace pamo {
 
@@ -205,12 +206,36 @@ __global__ void __launch_bounds__(kBlock) k_edge_reuse(
 // ascending order -- the same roundings as the per-lane loop.
 constexpr int kFlatCap = 320;  // produced triangles per warp; more: per-lane loop
 struct FlatTris {
-  double t[kFlatCap];               // 1 - C_ijk of each produced triangle
-  double vx[32], vy[32], vz[32];    // the owner edge's placement
+  union {
+    double t[kFlatCap];             // 1 - C_ijk in float64 (edges evaluated in float64)
+    float2 tf[kFlatCap];            // 1 - C_ijk as a float pair (certified edges)
+  };
+  float vx[32], vy[32], vz[32];     // the owner edge's placement
   int face[kFlatCap];
   int a[32], b[32];
+  short slot[kFlatCap];             // triangles of the edges evaluated in float64
   unsigned char own[kFlatCap];      // lane of the owner edge
 };
+
+// Key bits of a cost: float(cost) clamped at 0, ~0 when not finite.  On finite
+// floats the map is monotone, which the certification below relies on.
+__device__ __forceinline__ uint32_t key_bits(double cost) {
+  float cf = __double2float_rn(cost);
+  if (isnan(cost) || isinf(cf)) return 0xffffffffu;
+  if (!(cf > 0.0f)) cf = 0.0f;
+  return __float_as_uint(cf);
+}
+
+// 1 - C_ijk of face t with corners a and b moved to (vx, vy, vz), float-float
+__device__ __forceinline__ float2 skinny_term_ff(const int4& t, int a, int b, float vx, float vy,
+                                                 float vz, const float4* __restrict__ pos) {
+  // the placement is the one corner that is a or b; C_ijk is symmetric
+  int p = t.x, q = t.y;
+  if (t.x == a || t.x == b) { p = t.y; q = t.z; }
+  else if (t.y == a || t.y == b) { p = t.z; q = t.x; }
+  const float4 P = pos[p], R = pos[q];
+  return ff::skinny_term_ff(vx, vy, vz, P.x, P.y, P.z, R.x, R.y, R.z);
+}
 
 // 1 - C_ijk of face t with corners a and b moved to (vx, vy, vz)
 __device__ __forceinline__ double skinny_term(const int4& t, int a, int b, double vx, double vy,
@@ -244,7 +269,7 @@ __global__ void __launch_bounds__(kItemBlock) k_edge_cost(
   const int ndirty = dc->n_dirty;
   const int nflags = dc->nflags;
   const unsigned max_bits = dc->max_bits;
-  int link_bad = 0, flagged = 0, eligible = 0, ntri = 0;
+  int link_bad = 0, flagged = 0, eligible = 0, ntri = 0, nf64 = 0;
   // block-uniform iterations: the triangle stage and the per-mesh count are
   // warp-wide operations
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < ndirty;
@@ -361,14 +386,17 @@ __global__ void __launch_bounds__(kItemBlock) k_edge_cost(
   const int T = __shfl_sync(0xffffffffu, incl, 31);
   const int o = incl - nt;
   const double vxd = f2d(vx), vyd = f2d(vy), vzd = f2d(vz);
-  double Cs = 0.0;
+  const double Tq = __fma_rn(wes, l, s2 * Q);  // the cost without its skinny term
+  double Cs = 0.0;                             // the skinny sum in float64
+  uint32_t cb = 0xffffffffu;                   // key bits (non-finite: never eligible)
+  bool f64 = true;                             // the key comes from Cs
   if (T <= kFlatCap) {  // warp-uniform
     if (live) {
       S.a[lane] = a;
       S.b[lane] = b;
-      S.vx[lane] = vxd;
-      S.vy[lane] = vyd;
-      S.vz[lane] = vzd;
+      S.vx[lane] = vx;
+      S.vy[lane] = vy;
+      S.vz[lane] = vz;
       int i = a0, j = b0, k = o;
       while (i < a1 || j < b1) {
         const int fi = i < a1 ? idx[i] : 0x7fffffff;
@@ -388,10 +416,60 @@ __global__ void __launch_bounds__(kItemBlock) k_edge_cost(
     __syncwarp();
     for (int s = lane; s < T; s += 32) {
       const int L = S.own[s];
-      S.t[s] = skinny_term(F[S.face[s]], S.a[L], S.b[L], S.vx[L], S.vy[L], S.vz[L], pos);
+      S.tf[s] = skinny_term_ff(F[S.face[s]], S.a[L], S.b[L], S.vx[L], S.vy[L], S.vz[L], pos);
     }
     __syncwarp();
-    for (int k = 0; k < nt; k++) Cs = Cs + S.t[o + k];
+    if (live) {
+      // The lane's sum in float-float.  Its distance from the float64 sum Cs
+      // (terms within kTriBound each; both sums' roundings, at most
+      // 3.02 u^2 and 2^-53 of the running magnitude per addition) is below
+      // B = nt (kTriBound + 3.2 u^2 sum|t|), all rounded upwards.
+      ff::FF cs = {0.f, 0.f};
+      float A = 0.f;
+      for (int k = 0; k < nt; k++) {
+        const float2 t = S.tf[o + k];
+        cs = ff::add(cs, {t.x, t.y});
+        A = __fadd_ru(A, fabsf(t.x));
+      }
+      A = __fmul_ru(A, 1.0f + 0x1p-22f);
+      const float B = __fmul_ru((float)nt, __fmaf_ru(0x1.99999ap-47f, A, ff::kTriBound));
+      // Cs lies in [lo, hi]; x -> fl(w_s x + Tq) and key_bits are monotone, so
+      // equal keys at both ends are the key of the float64 evaluation
+      const double h = f2d(cs.h), hl = f2d(cs.l), Bd = f2d(B);
+      const double lo = __dsub_rd(__dadd_rd(h, hl), Bd);
+      const double hi = __dadd_ru(__dadd_ru(h, hl), Bd);
+      const uint32_t k0 = key_bits(__fma_rn(ws, ws >= 0.0 ? lo : hi, Tq));
+      const uint32_t k1 = key_bits(__fma_rn(ws, ws >= 0.0 ? hi : lo, Tq));
+      if (k0 == k1 && k0 != 0xffffffffu) {
+        cb = k0;
+        f64 = false;
+      }
+    }
+    // edges the bound leaves open: their triangles in float64, compacted over
+    // the warp, each lane's terms then summed in order as before
+    const bool redo = live && f64;
+    if (__ballot_sync(0xffffffffu, redo)) {
+      const int rn = redo ? nt : 0;
+      int rinc = rn;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, rinc, d);
+        if (lane >= d) rinc += y;
+      }
+      const int RT = __shfl_sync(0xffffffffu, rinc, 31);
+      const int ro = rinc - rn;
+      for (int k = 0; k < rn; k++) S.slot[ro + k] = (short)(o + k);
+      __syncwarp();
+      for (int s = lane; s < RT; s += 32) {
+        const int sl = S.slot[s];
+        const int L = S.own[sl];
+        S.t[sl] = skinny_term(F[S.face[sl]], S.a[L], S.b[L], f2d(S.vx[L]), f2d(S.vy[L]),
+                              f2d(S.vz[L]), pos);
+      }
+      __syncwarp();
+      if (redo)
+        for (int k = 0; k < nt; k++) Cs = Cs + S.t[o + k];
+    }
     __syncwarp();  // the next iteration overwrites the warp's slots
   } else if (live) {
     int i = a0, j = b0;
@@ -411,12 +489,9 @@ __global__ void __launch_bounds__(kItemBlock) k_edge_cost(
   }
   if (live) {
     ntri += nt;
-    const double cost = __fma_rn(ws, Cs, __fma_rn(wes, l, s2 * Q));
-    float cf = __double2float_rn(cost);
-    uint32_t cb = 0xffffffffu;  // non-finite: never eligible
-    if (!isnan(cost) && !isinf(cf)) {
-      if (!(cf > 0.0f)) cf = 0.0f;
-      cb = __float_as_uint(cf);
+    if (f64) {
+      cb = key_bits(__fma_rn(ws, Cs, Tq));
+      nf64++;
     }
     unsigned long long k = ~0ull;
     if (cb != 0xffffffffu && cb <= max_bits && link_ok && !flag && (!vmesh || mactive[m])) {
@@ -438,11 +513,25 @@ __global__ void __launch_bounds__(kItemBlock) k_edge_cost(
   flagged = __reduce_add_sync(0xffffffffu, flagged);
   eligible = __reduce_add_sync(0xffffffffu, eligible);
   ntri = __reduce_add_sync(0xffffffffu, ntri);
+  nf64 = __reduce_add_sync(0xffffffffu, nf64);
   if ((threadIdx.x & 31) == 0) {
     if (ntri) atomicAdd(&dc->cost_tris, (unsigned long long)ntri);
+    if (nf64) atomicAdd(&dc->cost_f64, nf64);
     if (link_bad) atomicAdd(&dc->link_rejects, (unsigned long long)link_bad);
     if (flagged) atomicAdd(&dc->flagged, (unsigned long long)flagged);
     if (eligible) atomicAdd(&dc->eligible, (unsigned long long)eligible);
+  }
+}
+
+// Verification support: both evaluations of 1 - C_ijk for given triangles
+__global__ void k_skinny_terms(const float* __restrict__ tri, int64_t n, double* __restrict__ t64,
+                               float2* __restrict__ tff) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float* p = tri + 9 * i;
+    t64[i] = 1.0 - quality(f2d(p[0]), f2d(p[1]), f2d(p[2]), f2d(p[3]), f2d(p[4]), f2d(p[5]),
+                           f2d(p[6]), f2d(p[7]), f2d(p[8]));
+    tff[i] = ff::skinny_term_ff(p[0], p[1], p[2], p[3], p[4], p[5], p[6], p[7], p[8]);
   }
 }
 
@@ -467,3 +556,19 @@ pamo_status edge_costs(pamo_ctx* c) {
 }
 
 }  // namespace pamo
+
+extern "C" pamo_status pamo_skinny_terms(const float* d_tri, int64_t n, double* d_t64,
+                                         float* d_tff, void* stream) {
+  if (n < 0 || (n > 0 && (!d_tri || !d_t64 || !d_tff))) {
+    pamo::set_error("pamo_skinny_terms: n >= 0 and three device arrays required");
+    return PAMO_EINVAL;
+  }
+  if (n == 0) return PAMO_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t blocks = (n + pamo::kBlock - 1) / pamo::kBlock;
+  pamo::k_skinny_terms<<<(int)(blocks < 4096 ? blocks : 4096), pamo::kBlock, 0, st>>>(
+      d_tri, n, d_t64, reinterpret_cast<float2*>(d_tff));
+  pamo::note_launch();
+  PAMO_CUDA(cudaGetLastError());
+  return PAMO_OK;
+}

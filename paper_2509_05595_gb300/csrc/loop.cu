@@ -108,6 +108,7 @@ __global__ void k_round_finish(RoundCounters* __restrict__ dc, LoopState* __rest
   ls->winners += dc->nW;
   ls->cost_edges += dc->n_dirty;
   ls->cost_tris += (long long)dc->cost_tris;
+  ls->cost_f64 += dc->cost_f64;
   ls->deferred += dc->deferred;
   ls->pairs = dc->pairs_total;
   ls->undo_hist[dc->undo_iters < 7 ? dc->undo_iters : 7]++;
@@ -238,6 +239,7 @@ __global__ void __launch_bounds__(256) k_batch_finish(
   ls->winners += dc->nW;
   ls->cost_edges += dc->n_dirty;
   ls->cost_tris += (long long)dc->cost_tris;
+  ls->cost_f64 += dc->cost_f64;
   ls->pairs = dc->pairs_total;
   ls->undo_hist[dc->undo_iters < 7 ? dc->undo_iters : 7]++;
   ls->undo_iters = dc->undo_iters;
