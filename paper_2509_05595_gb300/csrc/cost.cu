@@ -254,7 +254,10 @@ __device__ __forceinline__ double skinny_term(const int4& t, int a, int b, doubl
   return 1.0 - quality(q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7], q[8]);
 }
 
-__global__ void __launch_bounds__(kItemBlock) k_edge_cost(
+// 14 blocks of 64 per SM (72 registers): the kernel waits on dependent
+// gathers (incidence lists, faces, positions), so more resident warps pay
+// more than the few spilled registers cost
+__global__ void __launch_bounds__(kItemBlock, 14) k_edge_cost(
     const int32_t* __restrict__ dlist, const int2* __restrict__ E, const float4* __restrict__ pos,
     const double* __restrict__ Kv, const int4* __restrict__ F, const int32_t* __restrict__ off,
     const int32_t* __restrict__ idx, const unsigned long long* __restrict__ flags,
