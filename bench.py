@@ -10,8 +10,9 @@ paper's scale for its Thingi10K meshes.  One step = one full simplification
           each step one plain pamo_simplify call (one graph replay per round)
   e2e     the same call with host buffers (pamo_simplify_host): host->device
           copy of the input and device->host copy of the output inside timing
-  roofline  dominant kernel class: algorithmic work / its CUDA-event time per
-          launch, from as many profiled steps right after the timed ones
+  roofline  the class of the dominant kernel (k_edge_cost): algorithmic work /
+          its CUDA-event time per launch, from as many profiled steps right
+          after the timed ones; class_share gives every class's share
   cpu_baseline  the CPU oracle (test infrastructure) on a bounded sample
 
 Multi-GPU: a single mesh does not shard (every round needs global 2-hop
@@ -47,9 +48,13 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # length and the cost (additions, multiplies, FMAs, min/max and compares: 85,
 # plus 3 divisions and 1 square root); per produced triangle, the quality term
 # (edge differences, cross product, squared lengths, sums: 32, plus 1 division
-# and 1 square root)
+# and 1 square root).  The kernel runs the triangle terms as certified
+# float-float arithmetic on the float32 pipe; only the edges whose key the
+# bound leaves open take them in float64.  Certifying a key costs 8 float64
+# operations per edge (4 directed additions, 2 FMAs, 2 conversions).
 COST_OPS_EDGE, COST_DIV_EDGE, COST_SQRT_EDGE = 85, 3, 1
 COST_OPS_TRI, COST_DIV_TRI, COST_SQRT_TRI = 32, 1, 1
+COST_OPS_CERT = 8
 # algorithmic flops (FMA = 2, division and root = 1) per dirty edge and per
 # produced triangle; the library's class_flops use the same counts
 COST_FLOPS_EDGE, COST_FLOPS_TRI = 114.0, 45.0
@@ -58,8 +63,12 @@ COST_FLOPS_EDGE, COST_FLOPS_TRI = 114.0, 45.0
 # round 0 of the level-7 sphere (491,520 edges, all evaluated); the traffic of a launch grows
 # with the edges it evaluates, so a launch's traffic is this times its edge count.  None
 # (traffic reported as null) while no capture of the current kernel exists.
-COST_DRAM_BYTES_PER_EDGE = 31.82e6 / 491520
-COST_FP64_PIPE_BUSY = 0.799  # same capture
+COST_DRAM_BYTES_PER_EDGE = 31.79e6 / 491520
+COST_FP64_PIPE_BUSY = 0.442  # same capture
+# the kernel the roofline describes: k_edge_cost has the largest share of the
+# ncu launch list of the level-8 run (23 %, then k_traverse 21 %); its class
+# (k_edge_reuse + k_edge_cost) is timed with CUDA events
+ROOFLINE_CLASS = "cost"
 
 
 def max_over_ranks(x, device=None):
@@ -702,10 +711,10 @@ def main():
                    "tail_rounds_below_100k_faces": len(tail),
                    "tail_ms": sum(r["us"] for r in tail) / 1e3,
                    "tail_share": sum(r["us"] for r in tail) / max(sum(round_us), 1)}
-    # which class dominates: one profiled warm-up run with every class timed
+    # every class's share: one profiled warm-up run with every class timed
     opts = pamo.Options(validate_input=0, profile=0xFF)
     _, _, st_prof, _ = pamo.pamo_simplify(Vd, Fd, target, options=opts)
-    dom = int(np.argmax(st_prof["class_ms"]))
+    dom = CLASS_NAMES.index(ROOFLINE_CLASS)
     prof_opts = pamo.Options(validate_input=0, profile=1 << dom)
     # the timed steps: plain calls, without the class events
     plain_opts = pamo.Options(validate_input=0)
@@ -735,9 +744,10 @@ def main():
         out = (Vo, Fo, st, status)
     torch.cuda.synchronize()
     barrier()
-    # the dominant kernel class per launch: the same number of steps right after,
+    # the roofline class per launch: the same number of steps right after,
     # with CUDA events around the class
     dom_ms, dom_launch, dom_bytes, dom_flops, bytes_alg, cost_edges = 0.0, 0, 0.0, 0.0, 0.0, 0
+    cost_f64 = 0
     for _ in range(args.steps):
         flush.fill_(1)
         _, _, stp, _ = pamo.pamo_simplify(Vd, Fd, target, options=prof_opts)
@@ -747,6 +757,7 @@ def main():
         dom_flops += stp["class_flops"][dom]
         bytes_alg += stp["bytes_model"]
         cost_edges += stp["cost_edges"]
+        cost_f64 += stp["cost_f64"]
     torch.cuda.synchronize()
     clk = clocks.stop()
     total_ms = max_over_ranks(sum(times), device="cuda")
@@ -761,15 +772,20 @@ def main():
     share = {CLASS_NAMES[i]: round(st_prof["class_ms"][i] / max(sum(st_prof["class_ms"]), 1e-9), 4)
              for i in range(7)}
     if CLASS_NAMES[dom] == "cost":
-        # float64-ALU bound: algorithmic flops of the evaluated edges per launch
+        # ALU bound: the algorithmic float64 operations of Eq. 1 for the
+        # evaluated edges per launch (the method's count; the kernel certifies
+        # the triangle terms in float-float on the float32 pipe and needs the
+        # float64 pipe only for the rest, see pipe_model)
         flops_per_launch = dom_flops / max(dom_launch, 1)
         achieved = flops_per_launch / (avg_launch_ms * 1e-3) / 1e12 if avg_launch_ms > 0 else 0.0
         # two launches per round in this class (reuse + cost): edges per k_edge_cost launch
         edges_per_launch = cost_edges / max(dom_launch / 2, 1)
+        f64_edges_per_launch = cost_f64 / max(dom_launch / 2, 1)
         # produced triangles per launch, from the flop model
         flops_cost = flops_per_launch * 2  # the reuse launch has no flops
         tris_per_launch = (max(flops_cost - COST_FLOPS_EDGE * edges_per_launch, 0.0)
                            / COST_FLOPS_TRI)
+        f64_tris_per_launch = tris_per_launch * f64_edges_per_launch / max(edges_per_launch, 1e-9)
         # peak: the float64 FMA rate measured on this GPU just before the timed
         # region (independent FMA chains over one full wave); the nominal
         # figure from the unit count and clock when no measurement exists
@@ -778,8 +794,10 @@ def main():
             peak_source = "measured live: pamo_measure_fp64, independent float64 FMA chains"
         else:
             peak, peak_source = FP64_PEAK_TFLOPS, "derived: float64 FMA units x clock"
-        roof = {"bound": "alu", "kernel_class": "cost", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+        roof = {"bound": "alu", "kernel_class": "cost", "kernel": "k_edge_cost",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "achieved_note": ("Eq. 1 float64 operations per second; the triangle terms run "
+                                  "as certified float-float on the float32 pipe"),
                 "traffic": (COST_DRAM_BYTES_PER_EDGE * edges_per_launch
                             if COST_DRAM_BYTES_PER_EDGE else None),
                 "traffic_note": "ncu DRAM bytes per edge (L7 round-0 capture) x edges per launch",
@@ -787,20 +805,22 @@ def main():
                 "peak_source": peak_source, "peak_nominal": FP64_PEAK_TFLOPS,
                 "launch_ms": avg_launch_ms, "class_share": share}
         if fp64 is not None:
-            # the float64 pipe time the source's operations need at the measured
-            # rates, against the event-timed class time of a round (k_edge_reuse +
-            # k_edge_cost: two launches)
-            t_model = ((COST_OPS_EDGE * edges_per_launch + COST_OPS_TRI * tris_per_launch)
-                       / fp64["fma_per_s"]
-                       + (COST_DIV_EDGE * edges_per_launch + COST_DIV_TRI * tris_per_launch)
+            # the float64 pipe time of the float64 operations the kernel still
+            # runs (per edge, the certification, and the triangles of the edges
+            # the bound left open) at the measured rates, against the event-timed
+            # class time of a round (k_edge_reuse + k_edge_cost: two launches)
+            t_model = (((COST_OPS_EDGE + COST_OPS_CERT) * edges_per_launch
+                        + COST_OPS_TRI * f64_tris_per_launch) / fp64["fma_per_s"]
+                       + (COST_DIV_EDGE * edges_per_launch + COST_DIV_TRI * f64_tris_per_launch)
                        / max(fp64["div_per_s"], 1.0)
-                       + (COST_SQRT_EDGE * edges_per_launch + COST_SQRT_TRI * tris_per_launch)
+                       + (COST_SQRT_EDGE * edges_per_launch + COST_SQRT_TRI * f64_tris_per_launch)
                        / max(fp64["sqrt_per_s"], 1.0))
             roof["fp64_measured"] = {"fma_tflops": 2 * fp64["fma_per_s"] / 1e12,
                                      "div_per_s": fp64["div_per_s"],
                                      "sqrt_per_s": fp64["sqrt_per_s"]}
             roof["pipe_model"] = {"edges_per_launch": edges_per_launch,
                                   "tris_per_launch": tris_per_launch,
+                                  "f64_fallback_edges_per_launch": f64_edges_per_launch,
                                   "model_ms": t_model * 1e3,
                                   "frac": (t_model * 1e3 / (2 * avg_launch_ms)
                                            if avg_launch_ms else 0.0)}

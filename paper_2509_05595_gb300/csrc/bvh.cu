@@ -537,47 +537,55 @@ __device__ __forceinline__ void append_candidate(int f, const int4& tv, int g,
   if (slot < cb.cap[r]) cb.c[r][slot] = make_int2(f, g);
 }
 
-// Depth-first traversal of the subtree at `node` for query f (one thread).
+// Depth-first traversal of the subtree at `node` for query f (one thread),
+// two nodes per step: the two deepest pending nodes are loaded together, so a
+// lane has two node loads in flight instead of one chain.  Children are pushed
+// shallower node first, so the stack stays sorted by depth and holds at most
+// two nodes per level (a visited pair leaves at most two of its up to four
+// children behind): 2 x 62 levels fit in kStackPair entries.
 // Returns false after a stack or visit-cap overflow (flagged in dc).
+constexpr int kStackPair = 128;
 __device__ __forceinline__ bool dfs_query(const float* __restrict__ nodes, int node, int n, int f,
                                           const int4& tv, const float3& lo, const float3& hi,
                                           const int32_t* __restrict__ ftag, int query_all,
                                           const int4* __restrict__ F, CandBufs& cb,
                                           int* __restrict__ ncand, RoundCounters* __restrict__ dc) {
-  int stack[kStack];
+  int stack[kStackPair];
   int sp = 0;
-  for (int visits = 0;; visits++) {
+  int a = node, b = -1;  // the pair visited next (b < 0: a alone)
+  for (int visits = 0;; visits += 2) {
     if (visits >= 2 * n) {
       atomicOr(&dc->overflow, 4);
       return false;
     }
-    const NodeHits h = visit(nodes, node, lo, hi);
-    int next = -1;
+    const NodeHits ha = visit(nodes, a, lo, hi);
+    NodeHits hb = visit(nodes, b >= 0 ? b : a, lo, hi);
+    if (b < 0) hb.l = hb.r = false;
 #pragma unroll
-    for (int k = 0; k < 2; k++) {
-      if (!(k ? h.r : h.l)) continue;
-      const int cn = k ? h.R : h.L;
+    for (int k = 0; k < 4; k++) {
+      const NodeHits& h = k < 2 ? ha : hb;
+      if (!((k & 1) ? h.r : h.l)) continue;
+      const int cn = (k & 1) ? h.R : h.L;
       if (cn < 0) {
         const int g = ~cn;
         if (g == f) continue;
         const int tg = ftag ? ftag[g] : -1;
         if (query_all ? (g < f) : (tg >= 0 && g < f)) continue;
         append_candidate(f, tv, g, F, cb, ncand);
-      } else if (next < 0) {
-        next = cn;
       } else {
-        if (sp >= kStack) {
+        if (sp >= kStackPair) {
           atomicOr(&dc->overflow, 1);
           return false;
         }
         stack[sp++] = cn;
       }
     }
-    if (next >= 0) {
-      node = next;
-    } else {
-      if (sp == 0) return true;
-      node = stack[--sp];
+    if (sp == 0) return true;
+    b = stack[--sp];
+    a = sp > 0 ? stack[--sp] : -1;
+    if (a < 0) {
+      a = b;
+      b = -1;
     }
   }
 }
