@@ -63,8 +63,8 @@ COST_FLOPS_EDGE, COST_FLOPS_TRI = 114.0, 45.0
 # round 0 of the level-7 sphere (491,520 edges, all evaluated); the traffic of a launch grows
 # with the edges it evaluates, so a launch's traffic is this times its edge count.  None
 # (traffic reported as null) while no capture of the current kernel exists.
-COST_DRAM_BYTES_PER_EDGE = 31.79e6 / 491520
-COST_FP64_PIPE_BUSY = 0.442  # same capture
+COST_DRAM_BYTES_PER_EDGE = 32.44e6 / 491520
+COST_FP64_PIPE_BUSY = 0.481  # same capture
 # the kernel the roofline describes: k_edge_cost has the largest share of the
 # ncu launch list of the level-8 run (23 %, then k_traverse 21 %); its class
 # (k_edge_reuse + k_edge_cost) is timed with CUDA events
