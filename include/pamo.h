@@ -382,7 +382,7 @@ pamo_status pamo_check_self_intersections(const float* d_V, int64_t nV,
  * those of pamo_check_self_intersections (d_V/d_F device mesh, *n_pairs host,
  * d_pairs device [cap][2], caller-owned).
  *   - All scratch lives in one fixed device array inside the library (about
- *     4.1 MiB); every GPU that loads the library holds it until the process
+ *     4.9 MiB); every GPU that loads the library holds it until the process
  *     exits.  Limit: nF <= 32768 and nV <= 32768; larger meshes return
  *     PAMO_EINVAL with a message.
  *   - Face indices outside [0, nV) return PAMO_EINVAL before the mesh is

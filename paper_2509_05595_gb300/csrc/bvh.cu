@@ -204,6 +204,7 @@ __device__ __forceinline__ int delta(const unsigned* __restrict__ k,
 //   floats 0-5:  left child box  (lo.xyz, hi.xyz)
 //   floats 6-11: right child box (lo.xyz, hi.xyz)
 //   ints 12, 13: left, right child (internal index >= 0, or ~face for a leaf)
+//   ints 14, 15: the node's leaf range [first, last] (read by the refit)
 // parent[x] = (parent node << 1) | side for internal x in [0, n-1) and leaf
 // positions x = n-1+j; the root has -1.
 // With high words (a batch), the node whose range is exactly one mesh's
@@ -242,6 +243,8 @@ __global__ void k_karras(const unsigned* __restrict__ k, const unsigned* __restr
   int* links = reinterpret_cast<int*>(nodes + 16 * (size_t)i + 12);
   links[0] = left;
   links[1] = right;
+  links[2] = min(i, j);
+  links[3] = max(i, j);
   parent[lleaf ? n - 1 + g : g] = (i << 1) | 0;
   parent[rleaf ? n - 1 + g + 1 : g + 1] = (i << 1) | 1;
   if (i == 0) parent[0] = -1;
@@ -283,11 +286,6 @@ __device__ __forceinline__ void store_box(float* __restrict__ nodes, int p, int 
   dst[2] = make_float2(hi.y, hi.z);
 }
 
-// leaf boxes go into their parent's slot; then bottom-up unions: the second
-// child to arrive at a parent computes the parent's box and stores it in the
-// grandparent (no waiting; every thread stops at a first arrival or the root).
-// Each leaf also writes its face's predicate info (dominant normal axis and
-// orientation, read by the exact pair test) from the corners it loaded.
 // atomic add with acquire-release semantics at device scope
 __device__ __forceinline__ int add_acq_rel(int* p, int v) {
   int old;
@@ -298,66 +296,106 @@ __device__ __forceinline__ int add_acq_rel(int* p, int v) {
   return old;
 }
 
-__global__ void k_refit(const float4* __restrict__ pos, const int4* __restrict__ F,
-                        const uint8_t* __restrict__ fdead, const int32_t* __restrict__ vals,
-                        const int* n_dev, int n_host, float* __restrict__ nodes,
-                        const int32_t* __restrict__ parent, int32_t* __restrict__ flags,
-                        int* __restrict__ overflow, uint8_t* __restrict__ info) {
+// Leaf boxes in leaf order (lo.xyz, hi.xyz as two float4; a dead face's box
+// is empty), and each face's predicate info (dominant normal axis and
+// orientation, read by the exact pair test) from the corners loaded for it.
+__global__ void k_leaf_boxes(const float4* __restrict__ pos, const int4* __restrict__ F,
+                             const uint8_t* __restrict__ fdead, const int32_t* __restrict__ vals,
+                             const int* n_dev, int n_host, float4* __restrict__ lbox,
+                             uint8_t* __restrict__ info) {
   const int n = dev_n(n_dev, n_host);
-  if (n == 1) {  // no internal node; the face's info only
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      const int f = vals[0];
-      if (fdead && fdead[f]) {
-        info[f] = pack_info(exact::FaceInfo{0, 0});
-      } else {
-        const int4 t = F[f];
-        const float4 a = pos[t.x], b = pos[t.y], c = pos[t.z];
-        info[f] = pack_info(exact::face_info(make_float3(a.x, a.y, a.z),
-                                             make_float3(b.x, b.y, b.z),
-                                             make_float3(c.x, c.y, c.z)));
-      }
-    }
-    return;
-  }
-  if (n < 2) return;
   GRID_STRIDE(j, n) {
-  const int f = vals[j];
-  float3 lo, hi;
-  if (fdead && fdead[f]) {
-    lo = make_float3(INFINITY, INFINITY, INFINITY);
-    hi = make_float3(-INFINITY, -INFINITY, -INFINITY);
-    info[f] = pack_info(exact::FaceInfo{0, 0});
-  } else {
-    const int4 t = F[f];
-    const float4 a = pos[t.x], b = pos[t.y], c = pos[t.z];
-    lo = make_float3(fminf(fminf(a.x, b.x), c.x), fminf(fminf(a.y, b.y), c.y),
-                     fminf(fminf(a.z, b.z), c.z));
-    hi = make_float3(fmaxf(fmaxf(a.x, b.x), c.x), fmaxf(fmaxf(a.y, b.y), c.y),
-                     fmaxf(fmaxf(a.z, b.z), c.z));
-    info[f] = pack_info(exact::face_info(make_float3(a.x, a.y, a.z), make_float3(b.x, b.y, b.z),
-                                         make_float3(c.x, c.y, c.z)));
-  }
-  int ps = parent[n - 1 + j];
-  store_box(nodes, ps >> 1, ps & 1, lo, hi);
-  // a radix tree over n leaves is at most n - 1 levels deep; the cap only
-  // guards against a malformed tree
-  for (int steps = 0;; steps++) {
-    const int p = ps >> 1;
-    if (steps >= n) {
-      atomicOr(overflow, 2);
-      break;
+    const int f = vals[j];
+    float3 lo, hi;
+    if (fdead && fdead[f]) {
+      lo = make_float3(INFINITY, INFINITY, INFINITY);
+      hi = make_float3(-INFINITY, -INFINITY, -INFINITY);
+      info[f] = pack_info(exact::FaceInfo{0, 0});
+    } else {
+      const int4 t = F[f];
+      const float4 a = pos[t.x], b = pos[t.y], c = pos[t.z];
+      lo = make_float3(fminf(fminf(a.x, b.x), c.x), fminf(fminf(a.y, b.y), c.y),
+                       fminf(fminf(a.z, b.z), c.z));
+      hi = make_float3(fmaxf(fmaxf(a.x, b.x), c.x), fmaxf(fmaxf(a.y, b.y), c.y),
+                       fmaxf(fmaxf(a.z, b.z), c.z));
+      info[f] = pack_info(exact::face_info(make_float3(a.x, a.y, a.z), make_float3(b.x, b.y, b.z),
+                                           make_float3(c.x, c.y, c.z)));
     }
-    // arrival count with release (our box store is visible before the count)
-    // and acquire (the sibling's box is visible to the second arrival)
-    if (add_acq_rel(&flags[p], 1) == 0) break;  // sibling not ready: it finishes
-    const float4* q = reinterpret_cast<const float4*>(nodes + 16 * (size_t)p);
-    const float4 a = __ldcg(q), b = __ldcg(q + 1), c = __ldcg(q + 2);
-    ps = parent[p];
-    if (ps < 0) break;  // root: its box is never needed
-    lo = make_float3(fminf(a.x, b.z), fminf(a.y, b.w), fminf(a.z, c.x));
-    hi = make_float3(fmaxf(a.w, c.y), fmaxf(b.x, c.z), fmaxf(b.y, c.w));
-    store_box(nodes, ps >> 1, ps & 1, lo, hi);
+    lbox[2 * (size_t)j] = make_float4(lo.x, lo.y, lo.z, 0.f);
+    lbox[2 * (size_t)j + 1] = make_float4(hi.x, hi.y, hi.z, 0.f);
   }
+}
+
+// union of the leaf boxes [a, b]
+__device__ __forceinline__ void range_box(const float4* __restrict__ lbox, int a, int b,
+                                          float3& lo, float3& hi) {
+  float4 l = lbox[2 * (size_t)a], h = lbox[2 * (size_t)a + 1];
+  for (int j = a + 1; j <= b; j++) {
+    const float4 l2 = lbox[2 * (size_t)j], h2 = lbox[2 * (size_t)j + 1];
+    l.x = fminf(l.x, l2.x); l.y = fminf(l.y, l2.y); l.z = fminf(l.z, l2.z);
+    h.x = fmaxf(h.x, h2.x); h.y = fmaxf(h.y, h2.y); h.z = fmaxf(h.z, h2.z);
+  }
+  lo = make_float3(l.x, l.y, l.z);
+  hi = make_float3(h.x, h.y, h.z);
+}
+
+// Internal-node boxes, one thread per node (6 blocks of 256 per SM).  A child
+// covering at most kRefitLeaves leaves (or one leaf) gets its box straight from
+// the leaf boxes, with no ordering against other threads; most nodes lie in
+// the bottom levels, so most boxes come this way.  Only nodes covering more leaves than that wait
+// for their children: each such node counts two arrivals, one per child (its
+// own thread arrives for a child it filled itself, a child's climb for a
+// larger child), with a release-acquire counter, and the second arrival
+// computes the node's box, stores it in the parent and climbs on.  Box values
+// are min/max of the same leaf boxes as any bottom-up order, so they are
+// identical to a leaf-by-leaf climb.
+constexpr int kRefitLeaves = 16;
+__global__ void __launch_bounds__(kBlock, 6)
+    k_refit_nodes(const float4* __restrict__ lbox, const int* n_dev, int n_host,
+                  float* __restrict__ nodes, const int32_t* __restrict__ parent,
+                  int32_t* __restrict__ flags, int* __restrict__ overflow) {
+  const int n = dev_n(n_dev, n_host);
+  if (n < 2) return;
+  GRID_STRIDE(i, n - 1) {
+    const int4 t = *reinterpret_cast<const int4*>(nodes + 16 * (size_t)i + 12);
+    const int first = t.z, last = t.w;
+    const int g = t.x >= 0 ? t.x : first;  // the left child covers [first, g]
+    const bool lsmall = g - first + 1 <= kRefitLeaves, rsmall = last - g <= kRefitLeaves;
+    float3 lo, hi;
+    if (lsmall) {
+      range_box(lbox, first, g, lo, hi);
+      store_box(nodes, i, 0, lo, hi);
+    }
+    if (rsmall) {
+      range_box(lbox, g + 1, last, lo, hi);
+      store_box(nodes, i, 1, lo, hi);
+    }
+    // a node this small is read by its parent from the leaves directly
+    if (last - first + 1 <= kRefitLeaves) continue;
+    const int own = (int)lsmall + (int)rsmall;
+    if (own == 0) continue;  // both children larger: their climbs complete this node
+    // one side filled here: arrive for it (release); the second arrival goes on
+    if (own == 1 && add_acq_rel(&flags[i], 1) == 0) continue;
+    int p = i;
+    // a radix tree over n leaves is at most n - 1 levels deep; the cap only
+    // guards against a malformed tree
+    for (int steps = 0;; steps++) {
+      if (steps >= n) {
+        atomicOr(overflow, 2);
+        break;
+      }
+      const int ps = parent[p];
+      if (ps < 0) break;  // root: its box is never needed
+      const float4* q = reinterpret_cast<const float4*>(nodes + 16 * (size_t)p);
+      const float4 a = __ldcg(q), b = __ldcg(q + 1), c = __ldcg(q + 2);
+      lo = make_float3(fminf(a.x, b.z), fminf(a.y, b.w), fminf(a.z, c.x));
+      hi = make_float3(fmaxf(a.w, c.y), fmaxf(b.x, c.z), fmaxf(b.y, c.w));
+      store_box(nodes, ps >> 1, ps & 1, lo, hi);
+      p = ps >> 1;
+      // arrival count with release (our box store is visible before the count)
+      // and acquire (the sibling's box is visible to the second arrival)
+      if (add_acq_rel(&flags[p], 1) == 0) break;  // sibling not ready: it finishes
+    }
   }
 }
 
@@ -894,7 +932,8 @@ pamo_status bvh_alloc(Bvh& b, int n_max, cudaStream_t st) {
 void bvh_bytes(int n, size_t* nodes, size_t* parent, size_t* flags, size_t* kv, size_t* hist,
                size_t* aux, int64_t* hist_words) {
   const int tiles = n > 0 ? (n + kSortTile - 1) / kSortTile : 1;
-  *nodes = sizeof(float) * 16 * (size_t)(n > 1 ? n : 1);
+  // 64-byte internal nodes, then 32-byte leaf boxes (read by the refit)
+  *nodes = sizeof(float) * (16 * (size_t)(n > 1 ? n : 1) + 8 * (size_t)(n > 1 ? n : 1));
   *parent = sizeof(int32_t) * (size_t)(2 * n + 1);
   *flags = sizeof(int32_t) * (size_t)(n + 2);
   *kv = sizeof(uint32_t) * (size_t)(n > 1 ? n : 1);
@@ -963,10 +1002,13 @@ pamo_status bvh_refit(Bvh& b, const float4* pos, const int4* F, const uint8_t* f
                       const int* n_dev, int n_host, int grid, cudaStream_t st) {
   int32_t* fl = (int32_t*)b.flags.p;
   PAMO_CUDA(cudaMemsetAsync(fl, 0, sizeof(int32_t) * (size_t)(b.n_max + 2), st));
-  static const int g_refit = occ_grid(k_refit);
-  k_refit<<<g_refit, kBlock, 0, st>>>(pos, F, fdead, (const int32_t*)b.vals.p, n_dev, n_host,
-                                   (float*)b.nodes.p, (const int32_t*)b.parent.p, fl,
-                                   fl + b.n_max + 1, (uint8_t*)b.face_aux.p); note_launch();
+  float4* lbox = reinterpret_cast<float4*>((float*)b.nodes.p + 16 * (size_t)(b.n_max > 1 ? b.n_max : 1));
+  static const int g_leaf = occ_grid(k_leaf_boxes);
+  k_leaf_boxes<<<g_leaf, kBlock, 0, st>>>(pos, F, fdead, (const int32_t*)b.vals.p, n_dev, n_host,
+                                          lbox, (uint8_t*)b.face_aux.p); note_launch();
+  static const int g_refit = occ_grid(k_refit_nodes);
+  k_refit_nodes<<<g_refit, kBlock, 0, st>>>(lbox, n_dev, n_host, (float*)b.nodes.p,
+                                            (const int32_t*)b.parent.p, fl, fl + b.n_max + 1); note_launch();
   PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;
 }

@@ -36,7 +36,7 @@ constexpr size_t kTiles = (kMaxFaces + kSortTile - 1) / kSortTile;  // radix-sor
 
 constexpr Layout make_layout() {
   Layout L{};
-  L.nodes_b = sizeof(float) * 4 * 2 * (size_t)(2 * kMaxFaces);
+  L.nodes_b = sizeof(float) * 24 * (size_t)kMaxFaces;  // nodes, then leaf boxes
   L.parent_b = sizeof(int32_t) * (size_t)(2 * kMaxFaces + 1);
   L.flags_b = sizeof(int32_t) * (size_t)(kMaxFaces + 2);
   L.kv_b = sizeof(uint32_t) * (size_t)kMaxFaces;
@@ -67,7 +67,7 @@ constexpr Layout make_layout() {
 
 constexpr Layout kL = make_layout();
 
-// The scratch (about 4.1 MiB).  In host code this name is only a host-side
+// The scratch (about 4.9 MiB).  In host code this name is only a host-side
 // stand-in: kernels get the device address from cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_scratch[kL.total];
 
