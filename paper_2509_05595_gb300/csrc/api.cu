@@ -227,7 +227,7 @@ void free_ctx_buffers(pamo_ctx* c) {
   release(c->pos, st); release(c->pos_s, st);
   release(c->K, st); release(c->K_s, st);
   release(c->F, st); release(c->F_s, st);
-  release(c->vf_off, st); release(c->vf_idx, st); release(c->vcount, st);
+  release(c->vf_off, st); release(c->vf_idx, st); release(c->vf_nbr, st); release(c->vcount, st);
   release(c->E, st); release(c->e_off, st); release(c->key, st); release(c->vbar, st);
   release(c->vkey, st); release(c->win, st); release(c->wscan, st); release(c->wlist, st);
   release(c->standing, st); release(c->undo, st); release(c->ftag, st); release(c->qlist, st);
@@ -375,7 +375,7 @@ pamo_status alloc_state(pamo_ctx* c, int64_t nV, int64_t nF) {
   pamo_status s = PAMO_OK;
 #define A(ptr, n) if (s == PAMO_OK) s = alloc(&c->ptr, (size_t)(n), st)
   A(pos, nV); A(pos_s, nV); A(K, 10 * nV); A(K_s, 10 * nV); A(F, nF); A(F_s, nF);
-  A(vf_off, nV + 1); A(vf_idx, 3 * nF); A(vcount, nV + 1);
+  A(vf_off, nV + 1); A(vf_idx, 3 * nF); A(vf_nbr, 3 * nF); A(vcount, nV + 1);
   A(E, c->Emax); A(e_off, nV + 1); A(key, c->Emax); A(vbar, c->Emax); A(vkey, nV);
   A(win, c->Emax); A(wscan, c->Emax + 1); A(wlist, c->Emax); A(standing, c->Emax);
   A(undo, c->Emax); A(ftag, nF); A(qlist, nF); A(rlist, nF);
@@ -710,7 +710,7 @@ pamo_status phase_begin(pamo_ctx* c) {
   // the round's counters start at zero; last round's edges and their costs
   // become the reuse source
   PAMO_TRY(save_prev(c));
-  PAMO_TRY(build_vertex_faces(c));
+  PAMO_TRY(build_vertex_faces(c, true));
   PAMO_TRY(build_edges(c));
   if (c->opt.recompute_quadrics) PAMO_TRY(recompute_quadrics(c));
   const double nV = (double)c->nV, nF = (double)c->nF, nE = 1.5 * nF;

@@ -207,6 +207,7 @@ struct pamo_ctx {
   // --- adjacency of M_1: faces around each vertex, ascending face id
   int32_t* vf_off = nullptr;  // [nV0+1]
   int32_t* vf_idx = nullptr;  // [3 nF0]
+  int32_t* vf_nbr = nullptr;  // [3 nF0] per vertex segment: its higher neighbours, ascending
   int32_t* vcount = nullptr;  // [nV0+1] scratch counts / cursors
   // --- edges of M_1 (sorted unique (a<b) pairs) and their keys
   int2* E = nullptr;          // [Emax]
@@ -369,7 +370,7 @@ pamo_status mesh_bbox(const float4* pos, int64_t nV, float lo[3], float hi[3],
 pamo_status mesh_bbox_into(const float4* pos, int64_t nV, unsigned* d_tmp, float lo[3],
                            float hi[3], cudaStream_t st);
 pamo_status validate_mesh(pamo_ctx* c);
-pamo_status build_vertex_faces(pamo_ctx* c);
+pamo_status build_vertex_faces(pamo_ctx* c, bool neighbours = false);
 pamo_status build_edges(pamo_ctx* c);
 pamo_status save_prev(pamo_ctx* c);
 pamo_status init_quadrics(pamo_ctx* c);

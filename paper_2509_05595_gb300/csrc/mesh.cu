@@ -297,6 +297,10 @@ __global__ void k_fill_corners(const int4* __restrict__ F, const int* nF_dev, in
   }
 }
 
+__device__ __forceinline__ int next_after(const int4& f, int v) {
+  return f.x == v ? f.y : (f.y == v ? f.z : f.x);
+}
+
 // insertion sort of each vertex's incident faces (typically 4..10 entries)
 __global__ void k_sort_segments(const int32_t* __restrict__ off, const int* nV_dev, int nV_host,
                                 int32_t* __restrict__ idx) {
@@ -330,21 +334,69 @@ __global__ void k_sort_segments(const int32_t* __restrict__ off, const int* nV_d
   }
 }
 
-// ---- edges ----------------------------------------------------------------
-__device__ __forceinline__ int next_after(const int4& f, int v) {
-  return f.x == v ? f.y : (f.y == v ? f.z : f.x);
-}
-
-__global__ void k_count_edges(const int4* __restrict__ F, const int32_t* __restrict__ off,
-                              const int32_t* __restrict__ idx, const int* nV_dev,
-                              int32_t* __restrict__ cnt) {
+// The same sort, and each vertex's edges to higher-numbered neighbours: the
+// corner after v in each incident face, those above v in ascending order,
+// go to the start of v's segment of nbr and their count to cnt[v] (on a
+// closed manifold mesh these corners are v's distinct neighbours).
+__global__ void k_sort_segments_nbr(const int4* __restrict__ F, const int32_t* __restrict__ off,
+                                    const int* nV_dev, int32_t* __restrict__ idx,
+                                    int32_t* __restrict__ nbr, int32_t* __restrict__ cnt) {
   const int nV = *nV_dev;
   GRID_STRIDE(v, nV) {
-    int c = 0;
-    for (int s = off[v]; s < off[v + 1]; s++) c += next_after(F[idx[s]], (int)v) > v;
-    cnt[v] = c;
+    const int b = off[v], e = off[v + 1];
+    int m = 0;
+    if (e - b <= 16) {
+      int a[16], x[16];
+      const int n = e - b;
+      for (int i = 0; i < n; i++) {
+        const int y = idx[b + i];
+        int j = i;
+        while (j > 0 && a[j - 1] > y) {
+          a[j] = a[j - 1];
+          j--;
+        }
+        a[j] = y;
+      }
+      for (int i = 0; i < n; i++) {
+        idx[b + i] = a[i];
+        const int y = next_after(F[a[i]], (int)v);
+        if (y <= v) continue;
+        int j = m;
+        while (j > 0 && x[j - 1] > y) {
+          x[j] = x[j - 1];
+          j--;
+        }
+        x[j] = y;
+        m++;
+      }
+      for (int i = 0; i < m; i++) nbr[b + i] = x[i];
+    } else {
+      for (int i = b + 1; i < e; i++) {
+        const int y = idx[i];
+        int j = i;
+        while (j > b && idx[j - 1] > y) {
+          idx[j] = idx[j - 1];
+          j--;
+        }
+        idx[j] = y;
+      }
+      for (int i = b; i < e; i++) {
+        const int y = next_after(F[idx[i]], (int)v);
+        if (y <= v) continue;
+        int j = b + m;
+        while (j > b && nbr[j - 1] > y) {
+          nbr[j] = nbr[j - 1];
+          j--;
+        }
+        nbr[j] = y;
+        m++;
+      }
+    }
+    cnt[v] = m;
   }
 }
+
+// ---- edges ----------------------------------------------------------------
 
 // the edge count; a closed triangle mesh has exactly 3F/2 edges, anything
 // else means a non-manifold mesh (the host reports it at the next sync)
@@ -358,33 +410,21 @@ __device__ __forceinline__ void edge_total(const int32_t* __restrict__ eoff,
   dc->nE = ne <= cap ? ne : (int)cap;
 }
 
-// Each vertex writes its edges to higher-numbered neighbours, sorted, at its
-// offset; the per-vertex counts are zeroed for the next corner count (the
-// next round's vertices are a prefix of these), and one thread sets the
-// edge total (only the counters read it before the next kernel).
-__global__ void k_write_edges(const int4* __restrict__ F, const int32_t* __restrict__ off,
-                              const int32_t* __restrict__ idx, RoundCounters* __restrict__ dc,
-                              const int32_t* __restrict__ eoff, int64_t cap, int2* __restrict__ E,
-                              int32_t* __restrict__ cnt) {
+// Each vertex copies its sorted edges to higher-numbered neighbours (from
+// k_sort_segments_nbr) to its offset; the per-vertex counts are zeroed for the
+// next corner count (the next round's vertices are a prefix of these), and
+// one thread sets the edge total (only the counters read it before the next
+// kernel).
+__global__ void k_write_edges(const int32_t* __restrict__ off, const int32_t* __restrict__ nbr,
+                              RoundCounters* __restrict__ dc, const int32_t* __restrict__ eoff,
+                              int64_t cap, int2* __restrict__ E, int32_t* __restrict__ cnt) {
   const int nV = dc->nV;
   if (blockIdx.x == 0 && threadIdx.x == 0) edge_total(eoff, dc, cap);
   GRID_STRIDE(v, nV) {
+    const int m = cnt[v];
     cnt[v] = 0;
-    const int base = eoff[v];
-    int n = 0;
-    for (int s = off[v]; s < off[v + 1]; s++) {
-      const int x = next_after(F[idx[s]], (int)v);
-      if (x <= v) continue;
-      // insertion into the sorted run E[base .. base+n), never past capacity
-      if (base + n >= cap) break;
-      int j = n;
-      while (j > 0 && E[base + j - 1].y > x) {
-        E[base + j] = E[base + j - 1];
-        j--;
-      }
-      E[base + j] = make_int2((int)v, x);
-      n++;
-    }
+    const int base = eoff[v], b = off[v];
+    for (int k = 0; k < m && base + k < cap; k++) E[base + k] = make_int2((int)v, nbr[b + k]);
   }
 }
 
@@ -712,19 +752,28 @@ pamo_status mesh_bbox(const float4* pos, int64_t nV, float lo[3], float hi[3], B
   return mesh_bbox_into(pos, nV, (unsigned*)tmp.p, lo, hi, st);
 }
 
-// vertex -> incident faces of the current mesh (device sizes)
-pamo_status build_vertex_faces(pamo_ctx* c) {
+// vertex -> incident faces of the current mesh (device sizes); with
+// neighbours, also each vertex's sorted higher-numbered neighbours and their
+// counts in vcount, which build_edges must consume next
+pamo_status build_vertex_faces(pamo_ctx* c, bool neighbours) {
   cudaStream_t st = c->st;
   RoundCounters* dc = c->dc;
   const int G = c->grid;
   // vcount is zero here: zeroed at allocation, after each use as fill
-  // cursors below, and by k_write_edges after its use as edge counts
+  // cursors below, and by k_write_edges after its use as edge counts (the
+  // neighbour sort writes those counts only when build_edges follows)
   k_count_corners<<<G, kBlock, 0, st>>>(c->F, &dc->nF, 0, c->vcount); note_launch();
   PAMO_TRY(scan_dev_i32(c->vcount, &dc->nV, c->vf_off, c->scan_sums, G, st));
   static const int g_fill = occ_grid(k_fill_corners);
   static const int g_sort = occ_grid(k_sort_segments);
+  static const int g_nbr = occ_grid(k_sort_segments_nbr);
   k_fill_corners<<<g_fill, kBlock, 0, st>>>(c->F, &dc->nF, 0, c->vf_off, c->vcount, c->vf_idx); note_launch();
-  k_sort_segments<<<g_sort, kBlock, 0, st>>>(c->vf_off, &dc->nV, 0, c->vf_idx); note_launch();
+  if (neighbours) {
+    k_sort_segments_nbr<<<g_nbr, kBlock, 0, st>>>(c->F, c->vf_off, &dc->nV, c->vf_idx, c->vf_nbr,
+                                                  c->vcount); note_launch();
+  } else {
+    k_sort_segments<<<g_sort, kBlock, 0, st>>>(c->vf_off, &dc->nV, 0, c->vf_idx); note_launch();
+  }
   PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;
 }
@@ -742,7 +791,7 @@ pamo_status validate_mesh(pamo_ctx* c) {
   if (hb & 1) { set_error("face index out of range"); return PAMO_EINVAL; }
   if (hb & 2) { set_error("face with a repeated corner"); return PAMO_ENOTMANIFOLD; }
   if (hb & 4) { set_error("non-finite vertex coordinate"); return PAMO_EINVAL; }
-  PAMO_TRY(build_vertex_faces(c));
+  PAMO_TRY(build_vertex_faces(c, false));
   k_check_vertices<<<grid_for(c->nV), kBlock, 0, st>>>(c->F, c->vf_off, c->vf_idx, c->nV, bad); note_launch();
   PAMO_CUDA(cudaGetLastError());
   PAMO_CUDA(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -763,17 +812,16 @@ pamo_status save_prev(pamo_ctx* c) {
   return PAMO_OK;
 }
 
-// canonical edge list of the current mesh (device sizes); sets dc->nE
+// canonical edge list of the current mesh (device sizes); sets dc->nE.
+// Follows build_vertex_faces(c, true), whose neighbour lists it copies.
 pamo_status build_edges(pamo_ctx* c) {
   cudaStream_t st = c->st;
   RoundCounters* dc = c->dc;
   const int G = c->grid;
-  static const int g_count = occ_grid(k_count_edges);
   static const int g_write = occ_grid(k_write_edges);
-  k_count_edges<<<g_count, kBlock, 0, st>>>(c->F, c->vf_off, c->vf_idx, &dc->nV, c->vcount); note_launch();
   PAMO_TRY(scan_dev_i32(c->vcount, &dc->nV, c->e_off, c->scan_sums, G, st));
-  k_write_edges<<<g_write, kBlock, 0, st>>>(c->F, c->vf_off, c->vf_idx, dc, c->e_off, c->Emax,
-                                            c->E, c->vcount); note_launch();
+  k_write_edges<<<g_write, kBlock, 0, st>>>(c->vf_off, c->vf_nbr, dc, c->e_off, c->Emax, c->E,
+                                            c->vcount); note_launch();
   PAMO_CUDA(cudaGetLastError());
   return PAMO_OK;
 }
