@@ -89,9 +89,6 @@ __device__ __forceinline__ void count_by_mesh(int m, int32_t* __restrict__ melig
   if (m >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&melig[m], __popc(peers));
 }
 
-__device__ __forceinline__ int next_of(const int4& f, int v) {
-  return f.x == v ? f.y : (f.y == v ? f.z : f.x);
-}
 __device__ __forceinline__ bool has(const int4& f, int v) {
   return f.x == v || f.y == v || f.z == v;
 }
@@ -260,7 +257,8 @@ __device__ __forceinline__ double skinny_term(const int4& t, int a, int b, doubl
 __global__ void __launch_bounds__(kItemBlock, 14) k_edge_cost(
     const int32_t* __restrict__ dlist, const int2* __restrict__ E, const float4* __restrict__ pos,
     const double* __restrict__ Kv, const int4* __restrict__ F, const int32_t* __restrict__ off,
-    const int32_t* __restrict__ idx, const unsigned long long* __restrict__ flags,
+    const int32_t* __restrict__ idx, const int32_t* __restrict__ nbr,
+    const unsigned long long* __restrict__ flags,
     double s2_in, double wes_in, double ws, unsigned long long* __restrict__ key,
     float4* __restrict__ vbar, uint32_t* __restrict__ cbits, uint8_t* __restrict__ link,
     RoundCounters* __restrict__ dc, const int32_t* __restrict__ vmesh,
@@ -296,30 +294,42 @@ __global__ void __launch_bounds__(kItemBlock, 14) k_edge_cost(
     wes = vmesh ? mcost[2 * m + 1] : wes_in;
     a0 = off[a]; a1 = off[a + 1]; b0 = off[b]; b1 = off[b + 1];
     // ---- link condition: exactly two common neighbours (the apexes of the
-    // two faces on ab) and not both faces (a,c,d), (b,c,d) present
-    // common = the (x, y) pairs with x = next_of(face around a, a) equal to
-    // y = next_of(face around b, b); a 64-bit mask of the y (bit y & 63) skips
-    // the scan of b's faces for every x that cannot match
+    // two faces on ab) and not both faces (a,c,d), (b,c,d) present.
+    // common = the pairs of equal entries of the neighbour multisets of a and
+    // b (the corner after a, resp. b, in each incident face; sorted, at the
+    // incidence lists' offsets); the faces on ab are the face ids both sorted
+    // incidence lists hold, in ascending order
     int common = 0;
-    int apex[2] = {-1, -1}, na = 0;
-    unsigned long long ymask = 0ull;
-    for (int j = b0; j < b1; j++) ymask |= 1ull << (next_of(F[idx[j]], b) & 63);
-    for (int i = a0; i < a1; i++) {
-      const int4 fa = F[idx[i]];
-      const int x = next_of(fa, a);
-      if (has(fa, b)) {
-        const int t = fa.x != a && fa.x != b ? fa.x : (fa.y != a && fa.y != b ? fa.y : fa.z);
-        if (na < 2) apex[na] = t;
+    for (int i = a0, j = b0; i < a1 && j < b1;) {
+      const int x = nbr[i], y = nbr[j];
+      if (x != y) {
+        i += x < y;
+        j += y < x;
+        continue;
+      }
+      int ra = 0, rb = 0;
+      for (; i < a1 && nbr[i] == x; i++) ra++;
+      for (; j < b1 && nbr[j] == x; j++) rb++;
+      common += ra * rb;
+    }
+    int fab[2] = {-1, -1}, na = 0;
+    for (int i = a0, j = b0; i < a1 && j < b1;) {
+      const int x = idx[i], y = idx[j];
+      if (x == y) {
+        if (na < 2) fab[na] = x;
         na++;
       }
-      if ((ymask >> (x & 63)) & 1ull)
-        for (int j = b0; j < b1; j++) common += next_of(F[idx[j]], b) == x;
+      i += x <= y;
+      j += y <= x;
     }
     // the collapse produces every face around a or b but the na on ab
     nt = (a1 - a0) + (b1 - b0) - 2 * na;
     link_ok = (common == 2) && (na == 2);
     if (link_ok) {
-      const int c = apex[0], d = apex[1];
+      // the apexes: third corners of the two faces on ab
+      const int4 f0 = F[fab[0]], f1 = F[fab[1]];
+      const int c = f0.x != a && f0.x != b ? f0.x : (f0.y != a && f0.y != b ? f0.y : f0.z);
+      const int d = f1.x != a && f1.x != b ? f1.x : (f1.y != a && f1.y != b ? f1.y : f1.z);
       bool acd = false, bcd = false;
       for (int i = off[c]; i < off[c + 1]; i++) {
         const int4 f = F[idx[i]];
@@ -551,7 +561,7 @@ pamo_status edge_costs(pamo_ctx* c) {
                                         batch ? c->vmesh : nullptr, c->mactive, c->mcount,
                                         c->vkey); note_launch();
   k_edge_cost<<<g_cost, kItemBlock, 0, c->st>>>(c->dlist, c->E, c->pos, c->K, c->F, c->vf_off, c->vf_idx,
-                                       c->flags, s2, wes, c->opt.w_s, c->key, c->vbar, c->cbits,
+                                       c->vf_nbr, c->flags, s2, wes, c->opt.w_s, c->key, c->vbar, c->cbits,
                                        c->link, c->dc, batch ? c->vmesh : nullptr, c->mcost,
                                        c->mactive, c->mcount); note_launch();
   PAMO_CUDA(cudaGetLastError());

@@ -334,10 +334,10 @@ __global__ void k_sort_segments(const int32_t* __restrict__ off, const int* nV_d
   }
 }
 
-// The same sort, and each vertex's edges to higher-numbered neighbours: the
-// corner after v in each incident face, those above v in ascending order,
-// go to the start of v's segment of nbr and their count to cnt[v] (on a
-// closed manifold mesh these corners are v's distinct neighbours).
+// The same sort, and each vertex's neighbour multiset: the corner after v in
+// each incident face, in ascending order, in v's segment of nbr (on a closed
+// manifold mesh these are v's distinct neighbours).  cnt[v] = how many exceed
+// v: the last cnt[v] entries are v's edges to higher-numbered neighbours.
 __global__ void k_sort_segments_nbr(const int4* __restrict__ F, const int32_t* __restrict__ off,
                                     const int* nV_dev, int32_t* __restrict__ idx,
                                     int32_t* __restrict__ nbr, int32_t* __restrict__ cnt) {
@@ -360,16 +360,15 @@ __global__ void k_sort_segments_nbr(const int4* __restrict__ F, const int32_t* _
       for (int i = 0; i < n; i++) {
         idx[b + i] = a[i];
         const int y = next_after(F[a[i]], (int)v);
-        if (y <= v) continue;
-        int j = m;
+        m += y > v;
+        int j = i;
         while (j > 0 && x[j - 1] > y) {
           x[j] = x[j - 1];
           j--;
         }
         x[j] = y;
-        m++;
       }
-      for (int i = 0; i < m; i++) nbr[b + i] = x[i];
+      for (int i = 0; i < n; i++) nbr[b + i] = x[i];
     } else {
       for (int i = b + 1; i < e; i++) {
         const int y = idx[i];
@@ -382,14 +381,13 @@ __global__ void k_sort_segments_nbr(const int4* __restrict__ F, const int32_t* _
       }
       for (int i = b; i < e; i++) {
         const int y = next_after(F[idx[i]], (int)v);
-        if (y <= v) continue;
-        int j = b + m;
+        m += y > v;
+        int j = i;
         while (j > b && nbr[j - 1] > y) {
           nbr[j] = nbr[j - 1];
           j--;
         }
         nbr[j] = y;
-        m++;
       }
     }
     cnt[v] = m;
@@ -410,8 +408,9 @@ __device__ __forceinline__ void edge_total(const int32_t* __restrict__ eoff,
   dc->nE = ne <= cap ? ne : (int)cap;
 }
 
-// Each vertex copies its sorted edges to higher-numbered neighbours (from
-// k_sort_segments_nbr) to its offset; the per-vertex counts are zeroed for the
+// Each vertex copies its sorted edges to higher-numbered neighbours (the last
+// cnt[v] entries of its neighbour segment, from k_sort_segments_nbr) to its
+// offset; the per-vertex counts are zeroed for the
 // next corner count (the next round's vertices are a prefix of these), and
 // one thread sets the edge total (only the counters read it before the next
 // kernel).
@@ -423,7 +422,7 @@ __global__ void k_write_edges(const int32_t* __restrict__ off, const int32_t* __
   GRID_STRIDE(v, nV) {
     const int m = cnt[v];
     cnt[v] = 0;
-    const int base = eoff[v], b = off[v];
+    const int base = eoff[v], b = off[v + 1] - m;
     for (int k = 0; k < m && base + k < cap; k++) E[base + k] = make_int2((int)v, nbr[b + k]);
   }
 }
