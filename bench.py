@@ -10,9 +10,10 @@ paper's scale for its Thingi10K meshes.  One step = one full simplification
           each step one plain pamo_simplify call (one graph replay per round)
   e2e     the same call with host buffers (pamo_simplify_host): host->device
           copy of the input and device->host copy of the output inside timing
-  roofline  the class of the dominant kernel (k_edge_cost): algorithmic work /
-          its CUDA-event time per launch, from as many profiled steps right
-          after the timed ones; class_share gives every class's share
+  roofline  the class of the dominant kernel (k_traverse, the check):
+          algorithmic bytes / its CUDA-event time per launch, from as many
+          profiled steps right after the timed ones; class_share gives every
+          class's share; roofline_cost the same for k_edge_cost (Eq. 1 flops)
   cpu_baseline  the CPU oracle (test infrastructure) on a bounded sample
 
 Multi-GPU: a single mesh does not shard (every round needs global 2-hop
@@ -63,12 +64,70 @@ COST_FLOPS_EDGE, COST_FLOPS_TRI = 114.0, 45.0
 # round 0 of the level-7 sphere (491,520 edges, all evaluated); the traffic of a launch grows
 # with the edges it evaluates, so a launch's traffic is this times its edge count.  None
 # (traffic reported as null) while no capture of the current kernel exists.
-COST_DRAM_BYTES_PER_EDGE = 32.44e6 / 491520
-COST_FP64_PIPE_BUSY = 0.481  # same capture
-# the kernel the roofline describes: k_edge_cost has the largest share of the
-# ncu launch list of the level-8 run (23 %, then k_traverse 21 %); its class
-# (k_edge_reuse + k_edge_cost) is timed with CUDA events
-ROOFLINE_CLASS = "cost"
+COST_DRAM_BYTES_PER_EDGE = 36.49e6 / 491520
+COST_FP64_PIPE_BUSY = 0.610  # same capture
+# the kernel the roofline describes: k_traverse has the largest share of the
+# ncu launch list of the level-8 run (22.5 %, then k_edge_cost 18 %); its class
+# (the check: k_traverse, k_pairs and the small kernels around them) is timed
+# with CUDA events.  The cost class (k_edge_reuse + k_edge_cost) is reported
+# beside it under roofline_cost.
+ROOFLINE_CLASS = "query"
+
+
+def cost_roofline(c_ms, c_launch, c_flops, cost_edges, cost_f64, fp64):
+    """ALU roofline of the cost class (k_edge_reuse + k_edge_cost): the
+    algorithmic float64 operations of Eq. 1 for the evaluated edges per launch
+    (the method's count; the kernel certifies the triangle terms in
+    float-float on the float32 pipe and needs the float64 pipe only for the
+    rest, see pipe_model) over the class's CUDA-event time."""
+    avg_launch_ms = c_ms / max(c_launch, 1)
+    flops_per_launch = c_flops / max(c_launch, 1)
+    achieved = flops_per_launch / (avg_launch_ms * 1e-3) / 1e12 if avg_launch_ms > 0 else 0.0
+    # two launches per round in this class (reuse + cost): edges per k_edge_cost launch
+    edges_per_launch = cost_edges / max(c_launch / 2, 1)
+    f64_edges_per_launch = cost_f64 / max(c_launch / 2, 1)
+    # produced triangles per launch, from the flop model
+    flops_cost = flops_per_launch * 2  # the reuse launch has no flops
+    tris_per_launch = max(flops_cost - COST_FLOPS_EDGE * edges_per_launch, 0.0) / COST_FLOPS_TRI
+    f64_tris_per_launch = tris_per_launch * f64_edges_per_launch / max(edges_per_launch, 1e-9)
+    # peak: the float64 FMA rate measured on this GPU just before the timed
+    # region (independent FMA chains over one full wave); the nominal figure
+    # from the unit count and clock when no measurement exists
+    if fp64 is not None:
+        peak = 2 * fp64["fma_per_s"] / 1e12
+        peak_source = "measured live: pamo_measure_fp64, independent float64 FMA chains"
+    else:
+        peak, peak_source = FP64_PEAK_TFLOPS, "derived: float64 FMA units x clock"
+    roof = {"bound": "alu", "kernel_class": "cost", "kernel": "k_edge_cost",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "achieved_note": ("Eq. 1 float64 operations per second; the triangle terms run "
+                              "as certified float-float on the float32 pipe"),
+            "traffic": (COST_DRAM_BYTES_PER_EDGE * edges_per_launch
+                        if COST_DRAM_BYTES_PER_EDGE else None),
+            "traffic_note": "ncu DRAM bytes per edge (L7 round-0 capture) x edges per launch",
+            "ncu_fp64_pipe_busy": COST_FP64_PIPE_BUSY,
+            "peak_source": peak_source, "peak_nominal": FP64_PEAK_TFLOPS,
+            "launch_ms": avg_launch_ms}
+    if fp64 is not None:
+        # the float64 pipe time of the float64 operations the kernel still runs
+        # (per edge, the certification, and the triangles of the edges the bound
+        # left open) at the measured rates, against the event-timed class time
+        # of a round (k_edge_reuse + k_edge_cost: two launches)
+        t_model = (((COST_OPS_EDGE + COST_OPS_CERT) * edges_per_launch
+                    + COST_OPS_TRI * f64_tris_per_launch) / fp64["fma_per_s"]
+                   + (COST_DIV_EDGE * edges_per_launch + COST_DIV_TRI * f64_tris_per_launch)
+                   / max(fp64["div_per_s"], 1.0)
+                   + (COST_SQRT_EDGE * edges_per_launch + COST_SQRT_TRI * f64_tris_per_launch)
+                   / max(fp64["sqrt_per_s"], 1.0))
+        roof["fp64_measured"] = {"fma_tflops": 2 * fp64["fma_per_s"] / 1e12,
+                                 "div_per_s": fp64["div_per_s"],
+                                 "sqrt_per_s": fp64["sqrt_per_s"]}
+        roof["pipe_model"] = {"edges_per_launch": edges_per_launch,
+                              "tris_per_launch": tris_per_launch,
+                              "f64_fallback_edges_per_launch": f64_edges_per_launch,
+                              "model_ms": t_model * 1e3,
+                              "frac": t_model * 1e3 / (2 * avg_launch_ms) if avg_launch_ms else 0.0}
+    return roof
 
 
 def max_over_ranks(x, device=None):
@@ -715,11 +774,12 @@ def main():
     opts = pamo.Options(validate_input=0, profile=0xFF)
     _, _, st_prof, _ = pamo.pamo_simplify(Vd, Fd, target, options=opts)
     dom = CLASS_NAMES.index(ROOFLINE_CLASS)
-    prof_opts = pamo.Options(validate_input=0, profile=1 << dom)
+    ic = CLASS_NAMES.index("cost")
+    prof_opts = pamo.Options(validate_input=0, profile=(1 << dom) | (1 << ic))
     # the timed steps: plain calls, without the class events
     plain_opts = pamo.Options(validate_input=0)
     # float64 rates of this GPU (before the timed region)
-    fp64 = pamo.pamo_measure_fp64() if CLASS_NAMES[dom] == "cost" else None
+    fp64 = pamo.pamo_measure_fp64()
     # the clock sampler starts before the warm-up steps: nvidia-smi's start-up
     # (NVML initialisation) then never lands in a timed step
     clocks = ClockSampler(local)
@@ -746,15 +806,17 @@ def main():
     barrier()
     # the roofline class per launch: the same number of steps right after,
     # with CUDA events around the class
-    dom_ms, dom_launch, dom_bytes, dom_flops, bytes_alg, cost_edges = 0.0, 0, 0.0, 0.0, 0.0, 0
-    cost_f64 = 0
+    dom_ms, dom_launch, dom_bytes, bytes_alg, cost_edges = 0.0, 0, 0.0, 0.0, 0
+    c_ms, c_launch, c_flops, cost_f64 = 0.0, 0, 0.0, 0
     for _ in range(args.steps):
         flush.fill_(1)
         _, _, stp, _ = pamo.pamo_simplify(Vd, Fd, target, options=prof_opts)
         dom_ms += stp["class_ms"][dom]
         dom_launch += stp["class_launches"][dom]
         dom_bytes += stp["class_bytes"][dom]
-        dom_flops += stp["class_flops"][dom]
+        c_ms += stp["class_ms"][ic]
+        c_launch += stp["class_launches"][ic]
+        c_flops += stp["class_flops"][ic]
         bytes_alg += stp["bytes_model"]
         cost_edges += stp["cost_edges"]
         cost_f64 += stp["cost_f64"]
@@ -768,69 +830,22 @@ def main():
     e2e = None
     if not args.no_e2e:
         e2e = host_leg(pamo, torch, V, F, target, args.steps, world, barrier)
-    avg_launch_ms = dom_ms / max(dom_launch, 1)
     share = {CLASS_NAMES[i]: round(st_prof["class_ms"][i] / max(sum(st_prof["class_ms"]), 1e-9), 4)
              for i in range(7)}
-    if CLASS_NAMES[dom] == "cost":
-        # ALU bound: the algorithmic float64 operations of Eq. 1 for the
-        # evaluated edges per launch (the method's count; the kernel certifies
-        # the triangle terms in float-float on the float32 pipe and needs the
-        # float64 pipe only for the rest, see pipe_model)
-        flops_per_launch = dom_flops / max(dom_launch, 1)
-        achieved = flops_per_launch / (avg_launch_ms * 1e-3) / 1e12 if avg_launch_ms > 0 else 0.0
-        # two launches per round in this class (reuse + cost): edges per k_edge_cost launch
-        edges_per_launch = cost_edges / max(dom_launch / 2, 1)
-        f64_edges_per_launch = cost_f64 / max(dom_launch / 2, 1)
-        # produced triangles per launch, from the flop model
-        flops_cost = flops_per_launch * 2  # the reuse launch has no flops
-        tris_per_launch = (max(flops_cost - COST_FLOPS_EDGE * edges_per_launch, 0.0)
-                           / COST_FLOPS_TRI)
-        f64_tris_per_launch = tris_per_launch * f64_edges_per_launch / max(edges_per_launch, 1e-9)
-        # peak: the float64 FMA rate measured on this GPU just before the timed
-        # region (independent FMA chains over one full wave); the nominal
-        # figure from the unit count and clock when no measurement exists
-        if fp64 is not None:
-            peak = 2 * fp64["fma_per_s"] / 1e12
-            peak_source = "measured live: pamo_measure_fp64, independent float64 FMA chains"
-        else:
-            peak, peak_source = FP64_PEAK_TFLOPS, "derived: float64 FMA units x clock"
-        roof = {"bound": "alu", "kernel_class": "cost", "kernel": "k_edge_cost",
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "achieved_note": ("Eq. 1 float64 operations per second; the triangle terms run "
-                                  "as certified float-float on the float32 pipe"),
-                "traffic": (COST_DRAM_BYTES_PER_EDGE * edges_per_launch
-                            if COST_DRAM_BYTES_PER_EDGE else None),
-                "traffic_note": "ncu DRAM bytes per edge (L7 round-0 capture) x edges per launch",
-                "ncu_fp64_pipe_busy": COST_FP64_PIPE_BUSY,
-                "peak_source": peak_source, "peak_nominal": FP64_PEAK_TFLOPS,
-                "launch_ms": avg_launch_ms, "class_share": share}
-        if fp64 is not None:
-            # the float64 pipe time of the float64 operations the kernel still
-            # runs (per edge, the certification, and the triangles of the edges
-            # the bound left open) at the measured rates, against the event-timed
-            # class time of a round (k_edge_reuse + k_edge_cost: two launches)
-            t_model = (((COST_OPS_EDGE + COST_OPS_CERT) * edges_per_launch
-                        + COST_OPS_TRI * f64_tris_per_launch) / fp64["fma_per_s"]
-                       + (COST_DIV_EDGE * edges_per_launch + COST_DIV_TRI * f64_tris_per_launch)
-                       / max(fp64["div_per_s"], 1.0)
-                       + (COST_SQRT_EDGE * edges_per_launch + COST_SQRT_TRI * f64_tris_per_launch)
-                       / max(fp64["sqrt_per_s"], 1.0))
-            roof["fp64_measured"] = {"fma_tflops": 2 * fp64["fma_per_s"] / 1e12,
-                                     "div_per_s": fp64["div_per_s"],
-                                     "sqrt_per_s": fp64["sqrt_per_s"]}
-            roof["pipe_model"] = {"edges_per_launch": edges_per_launch,
-                                  "tris_per_launch": tris_per_launch,
-                                  "f64_fallback_edges_per_launch": f64_edges_per_launch,
-                                  "model_ms": t_model * 1e3,
-                                  "frac": (t_model * 1e3 / (2 * avg_launch_ms)
-                                           if avg_launch_ms else 0.0)}
-    else:
-        peak, peak_kind = peaks()
-        bytes_per_launch = dom_bytes / max(dom_launch, 1)
-        achieved = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9 if avg_launch_ms > 0 else 0.0
-        roof = {"bound": "hbm", "kernel_class": CLASS_NAMES[dom], "achieved": achieved,
-                "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": peak_kind, "launch_ms": avg_launch_ms, "class_share": share}
+    # the dominant kernel's class: latency-bound node and pair gathers, set
+    # against HBM by its algorithmic bytes (the check's reads and writes per
+    # launch, pamo_stats.class_bytes) over its CUDA-event time
+    peak, peak_kind = peaks()
+    avg_launch_ms = dom_ms / max(dom_launch, 1)
+    bytes_per_launch = dom_bytes / max(dom_launch, 1)
+    achieved = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9 if avg_launch_ms > 0 else 0.0
+    roof = {"bound": "hbm", "kernel_class": CLASS_NAMES[dom], "kernel": "k_traverse",
+            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None,
+            "traffic_note": ("bound by dependent node loads, not bytes (DRAM 1.7 % of peak "
+                             "under ncu); a launch's traffic is not tracked"),
+            "peak_source": peak_kind, "launch_ms": avg_launch_ms, "class_share": share}
+    roof_cost = cost_roofline(c_ms, c_launch, c_flops, cost_edges, cost_f64, fp64)
     Vo, Fo, st, status = out
     # the whole pipeline against HBM: algorithmic bytes of every round / wall
     hbm_peak, hbm_kind = peaks()
@@ -847,7 +862,7 @@ def main():
                        "round_times": rounds_info,
                        "l2": "flushed between steps (256 MiB write, outside the timed span)",
                        "parallelism": f"replicas x{world}"},
-            "roofline": roof, "pipeline_hbm": pipeline, "clocks": clk, "e2e": e2e,
+            "roofline": roof, "roofline_cost": roof_cost, "pipeline_hbm": pipeline, "clocks": clk, "e2e": e2e,
             "gpu_launches": int(launches)}
     if not args.no_batch and args.level == 8:
         # the batched path (many meshes per pass) on its own workload, beside
