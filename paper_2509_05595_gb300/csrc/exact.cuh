@@ -82,8 +82,11 @@ __device__ __noinline__ int orient3d_exact(const float3 a, const float3 b, const
   return sign_of(h, n);
 }
 
-__device__ __forceinline__ int orient3d(const float3 a, const float3 b, const float3 c,
-                                        const float3 d) {
+// Out of line, like orient2d: the pair test calls both from many places, and
+// inlined copies made the pair kernel's code large enough that instruction
+// fetch stalled it
+__device__ __noinline__ int orient3d(const float3 a, const float3 b, const float3 c,
+                                     const float3 d) {
   // float32 stage, valid when no product can underflow: every non-zero
   // difference lies in [2^-40, 2^40]
   {
@@ -151,8 +154,8 @@ __device__ __noinline__ int orient2d_exact(float au, float av, float bu, float b
   return sign_of(h, n);
 }
 
-__device__ __forceinline__ int orient2d(float au, float av, float bu, float bv, float cu,
-                                        float cv) {
+__device__ __noinline__ int orient2d(float au, float av, float bu, float bv, float cu,
+                                     float cv) {
   {
     const float x1 = __fsub_rn(bu, au), y1 = __fsub_rn(bv, av);
     const float x2 = __fsub_rn(cu, au), y2 = __fsub_rn(cv, av);
