@@ -1025,7 +1025,6 @@ pamo_status finish_round_batch(pamo_ctx* c) {
   const int M = c->n_mesh;
   const int32_t* elig = c->mcount_h;
   const int32_t* com = elig + M;
-  const int32_t* und = elig + 2 * M;
   const int64_t nflags_in = c->nflags, nund = h.nund;
   std::vector<unsigned long long> old(nflags_in), nw(nund);
   if (nflags_in)
