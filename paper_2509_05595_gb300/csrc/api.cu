@@ -1088,7 +1088,6 @@ pamo_status finish_round_batch(pamo_ctx* c) {
     c->m_nflags[m] = (int64_t)fm.size();
     next.insert(next.end(), fm.begin(), fm.end());
   }
-  (void)und;
   const int nf = (int)next.size();
   if (nf)
     PAMO_CUDA(cudaMemcpyAsync(c->flags, next.data(), sizeof(unsigned long long) * nf,
