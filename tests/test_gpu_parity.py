@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
 
-Bar (spec precision split): integer and index results bit-exact --
+Bar: integer and index results bit-exact --
 per-round winner / committed / undone collapse sets, every counter, and the
 output connectivity; positions bit-identical (float32 bits), which implies
 the required 1e-12 x bbox-diagonal bound; edge keys bit-identical (the FP64
