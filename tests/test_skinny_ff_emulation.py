@@ -10,7 +10,13 @@ the emulation's bit for bit), and these tests search its error.
     from the origin, D at both ends of the certified range, needles, exact
     collinear triangles), and within 112.4 u^2 of the exact value (120-digit
     decimal arithmetic) on the worst cases found and on samples;
-  * outside the certified range the high part is NaN.
+  * outside the certified range the high part is NaN;
+  * per edge, on the round-0 edges of real meshes: the float-float sum of the
+    edge's terms lies within B = nt (2^-40 + 3.2 u^2 sum|t|) of the oracle's
+    float64 sum, and the kernel's interval test (B rounded upwards in float32,
+    the interval's ends rounded outwards in float64, both ends through
+    fl(w_s x + Tq) to key bits), emulated exactly, certifies only keys equal to
+    the oracle's.
 """
 import decimal
 from fractions import Fraction
@@ -119,3 +125,121 @@ def test_float_float_term_within_the_analysis():
 def test_outside_the_certified_range_is_nan():
     for name, T in skinny_cases.out_of_range().items():
         assert np.isnan(ff_emulation.skinny_term_ff(T)[:, 0]).all(), name
+
+
+# ---- the per-edge certification (the edge-cost kernel's key decision) ------
+
+def _rd64(q):
+    f = float(q)
+    return f if Fraction(f) <= q else float(np.nextafter(f, -np.inf))
+
+
+def _ru64(q):
+    f = float(q)
+    return f if Fraction(f) >= q else float(np.nextafter(f, np.inf))
+
+
+def _ru32(q):
+    f = np.float32(float(q))
+    while Fraction(float(f)) < q:
+        f = np.nextafter(f, np.float32(np.inf))
+    while Fraction(float(np.nextafter(f, np.float32(-np.inf)))) >= q:
+        f = np.nextafter(f, np.float32(-np.inf))
+    return f
+
+
+def _fma64(a, b, c):
+    return float(Fraction(a) * Fraction(b) + Fraction(c))
+
+
+def _key_bits(cost):
+    with np.errstate(over="ignore"):
+        cf = np.float32(cost)
+    if np.isnan(cost) or np.isinf(cf):
+        return 0xFFFFFFFF
+    if not cf > 0:
+        cf = np.float32(0)
+    return int(np.array([cf], np.float32).view(np.uint32)[0])
+
+
+def _produced(V, F, ab, vbar):
+    """Per edge, its produced triangles [vbar, p, q] in ascending face order."""
+    around = [[] for _ in range(len(V))]
+    for f, t in enumerate(F):
+        for v in t:
+            around[v].append(f)
+    tris, owner = [], []
+    for e, (a, b) in enumerate(ab):
+        fa, fb = set(around[a]), set(around[b])
+        for f in sorted(fa ^ fb):
+            others = [v for v in F[f] if v != a and v != b]
+            tris.append(np.concatenate([vbar[e], V[others[0]], V[others[1]]]))
+            owner.append(e)
+    return np.array(tris, np.float32), np.array(owner)
+
+
+def _meshes():
+    import meshgen
+    out = {"bumped_icosphere_l4": meshgen.bumped_icosphere(level=4, seed=0)[:2],
+           "torus_48x24": meshgen.torus(48, 24)[:2],
+           "nested_shells_l3": meshgen.nested_shells(level=3)[:2]}
+    return {k: (np.asarray(V, np.float32), np.asarray(F, np.int32)) for k, (V, F) in out.items()}
+
+
+def test_edge_skinny_sum_within_its_bound_and_certified_keys_are_the_oracles():
+    """On the round-0 edges of real meshes: the float-float sum of an edge's
+    terms lies within B = nt (2^-40 + 3.2 u^2 sum|t|) of the oracle's float64
+    sum Cs, and every key the kernel's interval test certifies equals the
+    oracle's key."""
+    w_e, w_s = oracle.W_E, oracle.W_S
+    C1 = float.fromhex("0x1.99999ap-47")
+    for name, (V, F) in _meshes().items():
+        et = oracle.edge_table(V, F)
+        ab, vbar = et["ab"], et["vbar"]
+        T, owner = _produced(V, F, ab, vbar)
+        tff = ff_emulation.skinny_term_ff(T)
+        assert np.isfinite(tff).all(), name
+        # the lane's float-float sum, in the produced triangles' order
+        ne = len(ab)
+        cs = (np.zeros(ne, np.float32), np.zeros(ne, np.float32))
+        nt = np.bincount(owner, minlength=ne)
+        starts = np.concatenate([[0], np.cumsum(nt)[:-1]])
+        for k in range(nt.max()):
+            sel = np.nonzero(nt > k)[0]
+            rows = starts[sel] + k
+            s0, s1 = ff_emulation.add((cs[0][sel], cs[1][sel]), (tff[rows, 0], tff[rows, 1]))
+            cs[0][sel], cs[1][sel] = s0, s1
+        # the non-skinny part, restated from the oracle's scale and fma order
+        lo_b, hi_b = V.astype(np.float64).min(0), V.astype(np.float64).max(0)
+        ext = float(np.max(hi_b - lo_b))
+        scale = 1.0 / ext
+        s2, wes = scale * scale, w_e * scale
+        worst, certified = 0.0, 0
+        for e in range(ne):
+            Tq = _fma64(wes, et["l"][e], s2 * et["Q"][e])
+            assert _fma64(w_s, et["Cs"][e], Tq) == et["cost"][e], (name, e)  # restatement check
+            terms = tff[starts[e]:starts[e] + nt[e]]
+            A_exact = sum(abs(Fraction(float(t))) for t in terms[:, 0])
+            B_min = nt[e] * (Fraction(2) ** -40 + Fraction(C1) * A_exact)
+            Cs_ff = Fraction(float(cs[0][e])) + Fraction(float(cs[1][e]))
+            err = abs(Cs_ff - Fraction(et["Cs"][e]))
+            assert err <= B_min, (name, e, float(err / B_min))
+            worst = max(worst, float(err / B_min))
+            # the kernel's B (float32, rounded upwards) and its interval test
+            A = np.float32(0)
+            for t in terms[:, 0]:
+                A = _ru32(Fraction(float(A)) + abs(Fraction(float(t))))
+            A = _ru32(Fraction(float(A)) * (1 + Fraction(2) ** -22))
+            B = _ru32(nt[e] * Fraction(float(_ru32(Fraction(C1) * Fraction(float(A))
+                                                      + Fraction(2) ** -40))))
+            Bd = Fraction(float(B))
+            lo = _rd64(Fraction(_rd64(Cs_ff)) - Bd)
+            hi = _ru64(Fraction(_ru64(Cs_ff)) + Bd)
+            k0 = _key_bits(_fma64(w_s, lo if w_s >= 0 else hi, Tq))
+            k1 = _key_bits(_fma64(w_s, hi if w_s >= 0 else lo, Tq))
+            if k0 == k1 and k0 != 0xFFFFFFFF:
+                certified += 1
+                assert k0 == _key_bits(et["cost"][e]), (name, e)
+        print(f"{name}: {ne} edges, {certified} keys certified, "
+              f"max |Cs_ff - Cs| / B = {worst:.2e}")
+        assert certified >= 0.99 * ne, name
